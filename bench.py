@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched runtime distance check on one GB300 (or N replicas).
+
+Workload ("paper"): a seeded 6-DoF arm with 7 capsule+box link meshes (1,968
+triangles each), 96^3 FP32 Link SDF grids, a 500-waypoint cubic-spline trajectory
+and 20,000 obstacle points (2 cm voxel centres of three human-like clusters).
+One step = one call of check_trajectory (forward kinematics, transform, cull,
+trilinear lookup and min/arg-min per waypoint) with inputs resident in HBM.  The
+L2 cache is flushed (256 MiB write) before every timed step, so each step starts
+with cold caches (grids included).
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead (the
+only other implementation of this path).  Under torchrun every rank runs an
+independent replica on its own GPU (the check does not shard across GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "µs per 500-waypoint×20k-point check (p50/p99); SDF queries/s vs gather roofline"
+UNIT = "µs per check"
+# one cull test per (waypoint, link, point) pair: 3 sub, 1 mul, 2 fma, 1 compare
+CULL_OPS_PER_PAIR = 7
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="paper", choices=["paper", "tiny"])
+    ap.add_argument("--order", default="voxel", choices=["voxel", "random"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    return ap.parse_args()
+
+
+def scene_for(args):
+    import scenegen
+    if args.config == "paper":
+        return scenegen.make_scene("paper", order=args.order)
+    return scenegen.make_scene("tiny")
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) taken while the timed loop runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+
+def percentile(xs, q):
+    return float(np.percentile(np.asarray(xs), q)) if xs else None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def oracle_grids(scene):
+    import oracle
+    return oracle.build_grids_cached(scene.meshes, scene.resolution, scene.margin)
+
+
+def time_oracle(scene, vals, metas, budget_s=15.0, max_reps=5):
+    """Oracle check timed on the host cores: whole waypoint batches, repeated while
+    within the budget.  Returns (us per full check, reps, cores, sample text)."""
+    import oracle
+    cores = cpu_cores()
+    oracle.set_threads(cores)
+    W = scene.q.shape[0]
+    # first a probe on a slice of waypoints to size the sample
+    k = max(1, min(W, 25))
+    t = time.perf_counter()
+    oracle.check(scene.dh, scene.base, vals, metas, scene.q[:k], scene.points)
+    probe = time.perf_counter() - t
+    full_est = probe * W / k
+    if full_est * 1 <= budget_s:
+        wsel, scale = W, 1.0
+    else:
+        wsel = max(1, int(k * budget_s / max(probe, 1e-9) / 2))
+        wsel = min(wsel, W)
+        scale = W / wsel
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max_reps and (time.perf_counter() - t_start) < budget_s:
+        t = time.perf_counter()
+        oracle.check(scene.dh, scene.base, vals, metas, scene.q[:wsel], scene.points)
+        times.append((time.perf_counter() - t) * scale)
+    us = statistics.median(times) * 1e6
+    sample = (f"oracle_check (FP64, OpenMP over waypoints, {cores} threads) on {wsel} of {W} "
+              f"waypoints x {scene.points.shape[0]} points, median of {len(times)} runs, "
+              f"scaled to the full check")
+    return us, len(times), cores, sample
+
+
+# --------------------------------------------------------------- reference
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    scene = scene_for(args)
+    vals, metas = oracle_grids(scene)
+    import oracle
+    cores = cpu_cores()
+    oracle.set_threads(cores)
+    W, N, L = scene.q.shape[0], scene.points.shape[0], scene.n_links
+    # each step: a bounded sample of the workload (a slice of waypoints), scaled
+    k = max(1, min(W, 25))
+    t = time.perf_counter()
+    oracle.check(scene.dh, scene.base, vals, metas, scene.q[:k], scene.points)
+    probe = time.perf_counter() - t
+    per_step_budget = 120.0 / max(args.steps + args.warmup, 1)
+    wsel = int(min(W, max(1, k * per_step_budget / max(probe, 1e-9))))
+    for _ in range(args.warmup):
+        oracle.check(scene.dh, scene.base, vals, metas, scene.q[:wsel], scene.points)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.check(scene.dh, scene.base, vals, metas, scene.q[:wsel], scene.points)
+        times.append((time.perf_counter() - t) * W / wsel * 1e6)
+    value = float(np.mean(times))
+    sample = (f"oracle_check on {wsel} of {W} waypoints x {N} points per step, scaled to {W}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value / 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "p50_us": percentile(times, 50), "p99_us": percentile(times, 99),
+        "config": config_dict(scene, args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def config_dict(scene, args):
+    return {"workload": f"{args.config}: {scene.dof}-DoF arm, {scene.n_links} links x "
+                        f"{scene.meshes[0].n_tris}-triangle meshes, {scene.resolution}^3 FP32 grids, "
+                        f"W={scene.q.shape[0]} waypoints, N={scene.points.shape[0]} points "
+                        f"({args.order} order)",
+            "waypoints": int(scene.q.shape[0]), "points": int(scene.points.shape[0]),
+            "links": scene.n_links, "grid_resolution": scene.resolution,
+            "l2": "flushed before every timed step (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    import paper_2309_12543_gb300 as sdf
+    from paper_2309_12543_gb300 import build as pkg_build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg_build.build()
+
+    scene = scene_for(args)
+    W, N, L = scene.q.shape[0], scene.points.shape[0], scene.n_links
+    stream = torch.cuda.current_stream(dev)
+    ctx = sdf.Context(local, stream)
+    t = time.perf_counter()
+    grids = sdf.sdf_build_grids(ctx, scene.meshes, scene.resolution, scene.margin)
+    grid_build_s = time.perf_counter() - t
+    robot = sdf.Robot(ctx, scene.dh, grids, scene.base)
+    q = torch.tensor(scene.q, dtype=torch.float32, device=dev)
+    pts = torch.tensor(scene.points, dtype=torch.float32, device=dev)
+    dist_o = torch.empty(W, dtype=torch.float32, device=dev)
+    al = torch.empty(W, dtype=torch.int32, device=dev)
+    ap = torch.empty(W, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ctx.set_option(sdf.SDF_OPT_TIME_KERNELS, 1)
+
+    def step():
+        sdf.check_trajectory(ctx, robot, q, W, pts, N, dist_o, al, ap)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    rc = ctx.synchronize()
+    if rc != 0:
+        raise RuntimeError(f"warm-up check failed: {ctx.last_error()}")
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kernel_ms, prep_ms = [], []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        if i % 16 == 15 or i == args.steps - 1:
+            # kernel events live in the library (one pair per context): read them
+            # for the last step of each group of 16
+            kernel_ms.append(ctx.last_kernel_ms(sdf.SDF_KERNEL_CHECK))
+            prep_ms.append(ctx.last_kernel_ms(sdf.SDF_KERNEL_PREP))
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    rc = ctx.synchronize()
+    if rc != 0:
+        raise RuntimeError(f"timed checks failed: {ctx.last_error()}")
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    qh = torch.tensor(scene.q, dtype=torch.float32).pin_memory().numpy()
+    ph = torch.tensor(scene.points, dtype=torch.float32).pin_memory().numpy()
+    dh_ = torch.empty(W, dtype=torch.float32).pin_memory().numpy()
+    lh = torch.empty(W, dtype=torch.int32).pin_memory().numpy()
+    ph_ = torch.empty(W, dtype=torch.int32).pin_memory().numpy()
+    e2e = []
+    for i in range(args.e2e_steps + 5):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        rc = sdf.check_trajectory_host(ctx, robot, qh, W, ph, N, dh_, lh, ph_)
+        dt = time.perf_counter() - t
+        if rc != 0:
+            raise RuntimeError(f"host check failed: {ctx.last_error()}")
+        if i >= 5:
+            e2e.append(dt * 1e6)
+    assert np.array_equal(dh_.view(np.uint32), dist_o.cpu().numpy().view(np.uint32))
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    value = total_ms * 1e3 / (ws * args.steps)          # whole-job µs per check
+    kern_us = statistics.mean(kernel_ms) * 1e3
+    pairs = W * L * N
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak_ops = sms * FP32_LANES_PER_SM * max_mhz * 1e6         # FP32 lane-ops/s
+    achieved_ops = pairs * CULL_OPS_PER_PAIR / (kern_us * 1e-6)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(scene, args),
+        "p50_us": percentile([s * 1e3 for s in step_ms], 50),
+        "p99_us": percentile([s * 1e3 for s in step_ms], 99),
+        "queries_per_s": pairs / (value * 1e-6),
+        "grid_build_s": grid_build_s,
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved_ops / peak_ops, "traffic": None,
+                     "kernel": "check_kernel", "kernel_us": kern_us,
+                     "prep_kernel_us": statistics.mean(prep_ms) * 1e3,
+                     "algorithmic": f"{CULL_OPS_PER_PAIR} FP32 ops x {pairs} (waypoint, link, point) pairs",
+                     "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz"},
+        "e2e": {"value": statistics.median(e2e), "unit": UNIT, "p99": percentile(e2e, 99),
+                "h2d_bytes_per_step": int(qh.nbytes + ph.nbytes),
+                "d2h_bytes_per_step": int(dh_.nbytes + lh.nbytes + ph_.nbytes)},
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        vals, metas = oracle_grids(scene)
+        us, reps, cores, sample = time_oracle(scene, vals, metas)
+        out["cpu_baseline"] = {"value": us, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * sdfcheck -- batched runtime robot/obstacle distance check on one GPU (C ABI).
+ *
+ * Method: Fujii & Pham, "Real-time Batched Distance Computation for Time-Optimal
+ * Safe Path Tracking" (arXiv 2309.12543).  For every configuration (waypoint) of a
+ * trajectory the library returns the minimum signed distance between the robot's
+ * links and a set of obstacle points, with the arg-min link and point (Sec. III-A:
+ * "extracting the distances at the voxels occupied by the obstacles and taking the
+ * minimum").  Distances come from Link SDFs -- signed distance grids of each link
+ * in its own frame (Sec. III-A, "Link SDFs").  Obstacle points are mapped into
+ * every link frame (the per-point form contrasted in Sec. II-B and Fig. 2) and the
+ * link grid is interpolated trilinearly (the grid-sample interpolation of Sec.
+ * III-A).
+ *
+ * Conventions (all entry points):
+ *   - Units are metres and radians; the world frame is the robot base frame unless
+ *     a base transform is given.
+ *   - Transforms are 3x4 row-major [R | t] (world-from-frame), FP32.
+ *   - Link 0 is the static base link (frame 0); link j (1..dof) is DH frame j.
+ *     A robot with `dof` joints has L = dof + 1 links and needs L grids.
+ *   - Pointers named *_dev are CUDA device pointers, *_host host pointers.  The
+ *     caller owns every buffer it passes; the library copies host meshes and
+ *     tables during the call and owns the objects it creates (ctx, grids,
+ *     robot), freed by the matching *_destroy.
+ *   - Work is enqueued on the context's CUDA stream and the call returns without
+ *     waiting, except where a function says it synchronises.  Results are valid
+ *     after the stream has been synchronised.  Calls on one context must not be
+ *     made from several host threads at once.
+ *   - Every int-returning function returns SDF_OK (0) or a negative SDF_ERR_*
+ *     code; no C++ exception crosses this boundary.  sdf_last_error() gives a
+ *     message for the last failure on a context.  Faults that happen on the
+ *     device after a call returned surface in sdf_ctx_synchronize().
+ */
+#ifndef SDFCHECK_H
+#define SDFCHECK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define SDF_OK 0
+#define SDF_ERR_INVALID_ARG (-1)  /* bad pointer, size, layout or mismatched objects */
+#define SDF_ERR_OOM (-2)          /* device or host allocation failed                 */
+#define SDF_ERR_CUDA (-3)         /* a CUDA runtime call failed (message has details)  */
+#define SDF_ERR_TIMEOUT (-4)      /* a bounded device wait gave up                     */
+#define SDF_ERR_UNSUPPORTED (-5)  /* device or option not supported by this build      */
+#define SDF_ERR_NONFINITE (-6)    /* a NaN/Inf joint value or point was seen           */
+
+#define SDF_MAX_LINKS 16          /* L = dof + 1 <= 16                                  */
+#define SDF_MAX_POINTS 16777215   /* N < 2^24 (point index packed with waypoint/link)  */
+#define SDF_MAX_RESOLUTION 512    /* grid nodes per axis                               */
+
+typedef struct sdf_ctx sdf_ctx;       /* device, stream, scratch, options          */
+typedef struct sdf_grids sdf_grids;   /* device Link SDF grids + per-link metadata */
+typedef struct sdf_robot sdf_robot;   /* DH table + base transform + grids          */
+
+/* A link mesh in its own frame: closed, outward (counter-clockwise seen from
+ * outside) triangles.  Several closed components may form one link (a union);
+ * component c is triangles [comp_tri_offsets[c], comp_tri_offsets[c+1]).  With
+ * n_components == 1, comp_tri_offsets may be NULL. */
+typedef struct {
+    const float* verts;               /* host, n_verts x 3                          */
+    int32_t n_verts;
+    const int32_t* tris;              /* host, n_tris x 3 vertex indices            */
+    int32_t n_tris;
+    int32_t n_components;
+    const int32_t* comp_tri_offsets;  /* host, n_components + 1 entries, or NULL    */
+} sdf_mesh;
+
+/* Standard Denavit-Hartenberg row of one revolute joint: the joint transform is
+ * Rz(theta_offset + q) Tz(d) Tx(a) Rx(alpha).  q_min/q_max are informational. */
+typedef struct {
+    float a, alpha, d, theta_offset, q_min, q_max;
+} sdf_dh;
+
+/* Grid of one link: node (i,j,k) sits at origin + (i,j,k) h, value index
+ * i + n (j + n k) (x fastest).  center/radius bound the link mesh (every vertex
+ * lies within radius of center).  margin is informational. */
+typedef struct {
+    float origin[3];
+    float h;
+    int32_t n;
+    float center[3];
+    float radius;
+    float margin;
+} sdf_grid_meta;
+
+/* ------------------------------------------------------------------- context */
+
+/* Create a context on `device` that enqueues on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  Errors: INVALID_ARG (out NULL, bad device),
+ * UNSUPPORTED (device is not compute capability 10.3), CUDA, OOM. */
+int sdf_ctx_create(sdf_ctx** out, int device, void* cuda_stream);
+void sdf_ctx_destroy(sdf_ctx* ctx);
+/* Change the stream later calls enqueue on. */
+int sdf_ctx_set_stream(sdf_ctx* ctx, void* cuda_stream);
+/* Message of the last failure on ctx ("" if none).  Valid until the next call. */
+const char* sdf_last_error(const sdf_ctx* ctx);
+
+/* Options (sdf_ctx_set_option / sdf_ctx_get_option). */
+#define SDF_OPT_CULL 1            /* 1 (default): bounding-sphere culling; 0: evaluate every pair */
+#define SDF_OPT_POINT_STRIDE 2    /* floats per point: 3 (default, x y z) or 4 (x y z pad)       */
+#define SDF_OPT_WAYPOINTS_PER_BLOCK 3 /* 0 (default) = automatic, else 1, 2 or 4 (x links <= 32)    */
+#define SDF_OPT_POINT_SPLITS 4    /* 0 (default) = automatic, else tile chunks per waypoint block */
+#define SDF_OPT_TIME_KERNELS 6    /* 1: record CUDA events around the two kernels of a check      */
+int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t value);
+int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* value);
+
+/* Wait for the context's stream, then return and clear the device-side status:
+ * NONFINITE if a non-finite joint value or point was met since the last call,
+ * CUDA if the stream reported an error, else OK. */
+int sdf_ctx_synchronize(sdf_ctx* ctx);
+
+/* With SDF_OPT_TIME_KERNELS set: device time in milliseconds of one kernel of the
+ * last check_trajectory call -- SDF_KERNEL_PREP (spatial sort of the points) or
+ * SDF_KERNEL_CHECK (FK + cull + lookup + reduction).  Synchronises on that call. */
+#define SDF_KERNEL_PREP 0
+#define SDF_KERNEL_CHECK 1
+int sdf_ctx_last_kernel_ms(sdf_ctx* ctx, int32_t kernel, float* ms);
+
+/* --------------------------------------------------------------------- grids */
+
+/* Pre-processing (Sec. III-A, "Link SDFs"): build one signed distance grid per link
+ * mesh on the GPU.  For link i: box = mesh bounding box grown by `margin` on every
+ * side and made cubic (span s = max extent + 2 margin), n = `resolution` nodes per
+ * axis, h = s / (n - 1).  Node value = signed distance to the mesh: distance to
+ * the closest triangle, negative where the generalised winding number (sum of
+ * triangle solid angles / 4 pi) is >= 1/2; a multi-component mesh takes the
+ * minimum over components.  Synchronises.  Errors: INVALID_ARG (n_links outside
+ * 1..SDF_MAX_LINKS, resolution outside 2..SDF_MAX_RESOLUTION, margin < 0, empty or
+ * out-of-range mesh), OOM, CUDA. */
+int sdf_build_grids(sdf_ctx* ctx, const sdf_mesh* links, int32_t n_links, int32_t resolution,
+                    float margin, sdf_grids** out);
+
+/* Use grids computed elsewhere: host_values holds n_links grids of n^3 FP32
+ * values each (same n for all links, layout as sdf_grid_meta).  Synchronises. */
+int sdf_grids_upload(sdf_ctx* ctx, const float* host_values, const sdf_grid_meta* meta,
+                     int32_t n_links, sdf_grids** out);
+
+/* Copy grids back: host_values (n_links x n^3 floats) and/or meta (n_links
+ * entries) may be NULL.  Synchronises. */
+int sdf_grids_download(sdf_ctx* ctx, const sdf_grids* grids, float* host_values,
+                       sdf_grid_meta* meta);
+int sdf_grids_info(const sdf_grids* grids, int32_t* n_links, int32_t* resolution);
+void sdf_grids_destroy(sdf_grids* grids);
+
+/* --------------------------------------------------------------------- robot */
+
+/* A serial arm of `dof` revolute joints (standard DH rows) with world-from-base
+ * transform base_3x4 (NULL = identity) whose L = dof + 1 links use `grids`
+ * (which must hold exactly L grids and outlive the robot).  Errors: INVALID_ARG. */
+int sdf_robot_create(sdf_ctx* ctx, const sdf_dh* dh, int32_t dof, const float* base_3x4,
+                     const sdf_grids* grids, sdf_robot** out);
+void sdf_robot_destroy(sdf_robot* robot);
+
+/* Parallel forward kinematics (Sec. III-A): for each waypoint w and link l write
+ * 16 floats to out_dev[(w L + l) 16 ...]: the link-from-world transform
+ * [R^T | -R^T t] (12 floats, row-major) followed by the world position of the
+ * link's bounding-sphere centre (3 floats) and its radius.  q_dev: W x dof FP32
+ * row-major.  Asynchronous. */
+int sdf_forward_kinematics(sdf_ctx* ctx, const sdf_robot* robot, const float* q_dev, int32_t W,
+                           float* out_dev);
+
+/* ------------------------------------------------------------------- check */
+
+/* The runtime distance check (Sec. III-A, runtime): for each waypoint w,
+ *   dist[w] = min over links l and points p of g_l(T_{w,l}^{-1} p)
+ * where T_{w,l} is link l's pose from forward kinematics of q[w] and g_l is link
+ * l's grid interpolated trilinearly; a point outside the grid box gets the
+ * distance to the box plus the interpolated value at the nearest box point.
+ * argmin_link[w], argmin_point[w] attain the minimum (ties: smallest point, then
+ * smallest link; results equal to within FP32 rounding may pick either).
+ *
+ * q_dev: W x dof FP32 row-major.  points_dev: N x 3 FP32 (or N x 4 with
+ * SDF_OPT_POINT_STRIDE = 4), 16-byte aligned.  Outputs: W entries each.
+ * N = 0 gives dist = +inf and argmins = -1; W = 0 is a no-op.  Pairs whose value
+ * is NaN are ignored; non-finite inputs also raise SDF_ERR_NONFINITE in
+ * sdf_ctx_synchronize.  Asynchronous; enqueues two kernels (a spatial sort of
+ * the points into 32-point tiles, then the check) and uses context-owned scratch
+ * (about 16 bytes per point plus 8 bytes per waypoint).
+ * Errors: INVALID_ARG (NULL pointer with W, N > 0, N > SDF_MAX_POINTS, W < 0,
+ * misaligned points), OOM (growing scratch), CUDA. */
+int check_trajectory(sdf_ctx* ctx, const sdf_robot* robot, const float* q_dev, int32_t W,
+                     const float* points_dev, int32_t N, float* dist_dev,
+                     int32_t* argmin_link_dev, int32_t* argmin_point_dev);
+
+/* The same check on HOST buffers: copies q and points to context-owned device
+ * staging buffers, runs check_trajectory, copies the three outputs back and
+ * synchronises.  Host buffers may be pageable; page-locked buffers copy faster.
+ * Returns the check's status (including NONFINITE). */
+int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* robot, const float* q_host, int32_t W,
+                          const float* points_host, int32_t N, float* dist_host,
+                          int32_t* argmin_link_host, int32_t* argmin_point_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDFCHECK_H */

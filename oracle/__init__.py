@@ -235,3 +235,28 @@ def pair_values(dh, base, values, metas, q, points) -> np.ndarray:
     _load().oracle_pair_values(_p(dh), int(dh.shape[0]), _p(base), _p(flat), _p(offsets),
                                _p(metas), _p(q), int(W), _p(pts), int(N), _p(out))
     return out
+
+
+def build_grids_cached(meshes, n: int, margin: float, cache_dir: str | None = None):
+    """``build_grids`` with an on-disk cache keyed by a hash of the meshes and grid
+    parameters (the full-size brute-force build takes about a minute)."""
+    import hashlib
+    import tempfile
+    h = hashlib.sha256()
+    for m in meshes:
+        for a in (np.ascontiguousarray(m.verts, np.float64), np.ascontiguousarray(m.tris, np.int32),
+                  np.ascontiguousarray(m.comp_offsets, np.int32)):
+            h.update(a.tobytes())
+    h.update(np.array([n, margin], dtype=np.float64).tobytes())
+    h.update(open(_SRC, "rb").read())
+    d = cache_dir or os.path.join(tempfile.gettempdir(), "sdfcheck_oracle_grids")
+    os.makedirs(d, exist_ok=True)
+    path = os.path.join(d, h.hexdigest()[:32] + ".npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return list(z["values"]), z["metas"]
+    vals, metas = build_grids(meshes, n, margin)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, values=np.stack(vals), metas=metas)
+    os.replace(tmp, path)
+    return vals, metas

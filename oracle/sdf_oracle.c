@@ -341,6 +341,8 @@ static double trilinear(const double *v, int64_t n, const double *u) {
 /* Interpolated link SDF at p_loc (link frame).  Inside the grid box: trilinear.
  * Outside: |p_loc - q| + trilinear(q), q the nearest point of the box. */
 double oracle_lookup(const double *values, const double *meta, const double *p_loc) {
+    /* a NaN coordinate has no grid cell: the value is NaN (such pairs are ignored) */
+    if (isnan(p_loc[0]) || isnan(p_loc[1]) || isnan(p_loc[2])) return NAN;
     const int64_t n = (int64_t)meta[4];
     const double h = meta[3], top = (double)(n - 1);
     double u[3];

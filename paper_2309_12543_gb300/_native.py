@@ -1,0 +1,301 @@
+"""ctypes binding of libsdfcheck (the C ABI in include/sdfcheck.h).
+
+Argument marshalling only: every step of the distance check runs in the CUDA
+library.  Device buffers are passed as torch CUDA tensors (or raw integer
+addresses); host buffers as numpy arrays.  If the compiled library is missing the
+import fails with an error -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsdfcheck.so")
+
+SDF_OK = 0
+SDF_ERR_INVALID_ARG = -1
+SDF_ERR_OOM = -2
+SDF_ERR_CUDA = -3
+SDF_ERR_TIMEOUT = -4
+SDF_ERR_UNSUPPORTED = -5
+SDF_ERR_NONFINITE = -6
+SDF_MAX_LINKS = 16
+SDF_MAX_POINTS = 16777215
+
+SDF_OPT_CULL = 1
+SDF_OPT_POINT_STRIDE = 2
+SDF_OPT_WAYPOINTS_PER_BLOCK = 3
+SDF_OPT_POINT_SPLITS = 4
+SDF_OPT_TIME_KERNELS = 6
+SDF_KERNEL_PREP = 0
+SDF_KERNEL_CHECK = 1
+
+ERROR_NAMES = {0: "SDF_OK", -1: "SDF_ERR_INVALID_ARG", -2: "SDF_ERR_OOM", -3: "SDF_ERR_CUDA",
+               -4: "SDF_ERR_TIMEOUT", -5: "SDF_ERR_UNSUPPORTED", -6: "SDF_ERR_NONFINITE"}
+
+
+class SdfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sdf_mesh(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("n_verts", ctypes.c_int32),
+                ("tris", ctypes.c_void_p), ("n_tris", ctypes.c_int32),
+                ("n_components", ctypes.c_int32), ("comp_tri_offsets", ctypes.c_void_p)]
+
+
+class sdf_dh(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("a", "alpha", "d", "theta_offset", "q_min", "q_max")]
+
+
+class sdf_grid_meta(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("h", ctypes.c_float), ("n", ctypes.c_int32),
+                ("center", ctypes.c_float * 3), ("radius", ctypes.c_float), ("margin", ctypes.c_float)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2309_12543_gb300.build.build() "
+                          "(nvcc for sm_103a) -- there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sigs = {
+        "sdf_ctx_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, P]),
+        "sdf_ctx_destroy": (None, [P]),
+        "sdf_ctx_set_stream": (ctypes.c_int, [P, P]),
+        "sdf_last_error": (ctypes.c_char_p, [P]),
+        "sdf_ctx_set_option": (ctypes.c_int, [P, i32, i64]),
+        "sdf_ctx_get_option": (ctypes.c_int, [P, i32, ctypes.POINTER(i64)]),
+        "sdf_ctx_synchronize": (ctypes.c_int, [P]),
+        "sdf_ctx_last_kernel_ms": (ctypes.c_int, [P, i32, ctypes.POINTER(ctypes.c_float)]),
+        "sdf_build_grids": (ctypes.c_int, [P, P, i32, i32, ctypes.c_float, ctypes.POINTER(P)]),
+        "sdf_grids_upload": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(P)]),
+        "sdf_grids_download": (ctypes.c_int, [P, P, P, P]),
+        "sdf_grids_info": (ctypes.c_int, [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "sdf_grids_destroy": (None, [P]),
+        "sdf_robot_create": (ctypes.c_int, [P, P, i32, P, P, ctypes.POINTER(P)]),
+        "sdf_robot_destroy": (None, [P]),
+        "sdf_forward_kinematics": (ctypes.c_int, [P, P, P, i32, P]),
+        "check_trajectory": (ctypes.c_int, [P, P, P, i32, P, i32, P, P, P]),
+        "check_trajectory_host": (ctypes.c_int, [P, P, P, i32, P, i32, P, P, P]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+# the symbols include/sdfcheck.h declares (tests check the export table against it)
+EXPORTED = ("sdf_ctx_create", "sdf_ctx_destroy", "sdf_ctx_set_stream", "sdf_last_error",
+            "sdf_ctx_set_option", "sdf_ctx_get_option", "sdf_ctx_synchronize",
+            "sdf_ctx_last_kernel_ms", "sdf_build_grids", "sdf_grids_upload", "sdf_grids_download",
+            "sdf_grids_info", "sdf_grids_destroy", "sdf_robot_create", "sdf_robot_destroy",
+            "sdf_forward_kinematics", "check_trajectory", "check_trajectory_host")
+
+
+def _ptr(x) -> int:
+    """Device address of a torch tensor (or an int), host address of a numpy array."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError(type(x))
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Context:
+    """Owns an sdf_ctx: device, stream binding, scratch and options."""
+
+    def __init__(self, device: int = 0, stream=None):
+        h = ctypes.c_void_p()
+        rc = lib.sdf_ctx_create(ctypes.byref(h), int(device), _stream_handle(stream))
+        if rc != SDF_OK:
+            raise SdfError(rc, "sdf_ctx_create failed")
+        self.handle = h
+        self.device = device
+
+    def _check(self, rc: int, what: str):
+        if rc != SDF_OK:
+            raise SdfError(rc, f"{what}: {lib.sdf_last_error(self.handle).decode()}")
+
+    def set_stream(self, stream):
+        self._check(lib.sdf_ctx_set_stream(self.handle, _stream_handle(stream)), "set_stream")
+
+    def set_option(self, key: int, value: int):
+        self._check(lib.sdf_ctx_set_option(self.handle, int(key), int(value)), "set_option")
+
+    def get_option(self, key: int) -> int:
+        v = ctypes.c_int64()
+        self._check(lib.sdf_ctx_get_option(self.handle, int(key), ctypes.byref(v)), "get_option")
+        return int(v.value)
+
+    def synchronize(self) -> int:
+        """Wait for the stream; return the device status code (does not raise)."""
+        return int(lib.sdf_ctx_synchronize(self.handle))
+
+    def last_error(self) -> str:
+        return lib.sdf_last_error(self.handle).decode()
+
+    def last_kernel_ms(self, kernel: int = 1) -> float:
+        """Device ms of SDF_KERNEL_PREP (0) or SDF_KERNEL_CHECK (1) of the last check."""
+        v = ctypes.c_float()
+        self._check(lib.sdf_ctx_last_kernel_ms(self.handle, int(kernel), ctypes.byref(v)), "last_kernel_ms")
+        return float(v.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.sdf_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Grids:
+    """Owns an sdf_grids handle (device Link SDFs + metadata)."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.handle = handle
+        nl, n = ctypes.c_int32(), ctypes.c_int32()
+        lib.sdf_grids_info(handle, ctypes.byref(nl), ctypes.byref(n))
+        self.n_links, self.resolution = int(nl.value), int(n.value)
+
+    def download(self):
+        """(values float32 [L, n^3], meta list of dicts)."""
+        L, n = self.n_links, self.resolution
+        vals = np.empty((L, n ** 3), dtype=np.float32)
+        metas = (sdf_grid_meta * L)()
+        self.ctx._check(lib.sdf_grids_download(self.ctx.handle, self.handle, _ptr(vals),
+                                               ctypes.addressof(metas)), "sdf_grids_download")
+        return vals, [meta_to_dict(m) for m in metas]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.sdf_grids_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def meta_to_dict(m: sdf_grid_meta) -> dict:
+    return dict(origin=np.array(m.origin[:], dtype=np.float32), h=float(m.h), n=int(m.n),
+                center=np.array(m.center[:], dtype=np.float32), radius=float(m.radius),
+                margin=float(m.margin))
+
+
+def sdf_build_grids(ctx: Context, meshes, resolution: int, margin: float) -> Grids:
+    """meshes: objects with verts (V x 3), tris (T x 3) and comp_offsets (C + 1)."""
+    keep = []
+    arr = (sdf_mesh * len(meshes))()
+    for i, m in enumerate(meshes):
+        v = np.ascontiguousarray(m.verts, dtype=np.float32)
+        t = np.ascontiguousarray(m.tris, dtype=np.int32)
+        off = np.ascontiguousarray(m.comp_offsets, dtype=np.int32)
+        keep += [v, t, off]
+        arr[i] = sdf_mesh(_ptr(v), v.shape[0], _ptr(t), t.shape[0], off.shape[0] - 1, _ptr(off))
+    h = ctypes.c_void_p()
+    ctx._check(lib.sdf_build_grids(ctx.handle, ctypes.addressof(arr), len(meshes), int(resolution),
+                                   float(margin), ctypes.byref(h)), "sdf_build_grids")
+    return Grids(ctx, h)
+
+
+def sdf_grids_upload(ctx: Context, values, metas) -> Grids:
+    """values: [L, n^3] (any float dtype, rounded to FP32); metas: rows of the
+    oracle layout (origin[3], h, n, centre[3], radius, margin) or dicts."""
+    vals = np.ascontiguousarray(np.asarray(values, dtype=np.float32).reshape(len(metas), -1))
+    arr = (sdf_grid_meta * len(metas))()
+    for i, m in enumerate(metas):
+        if isinstance(m, dict):
+            o, h, n, c, r, mg = m["origin"], m["h"], m["n"], m["center"], m["radius"], m["margin"]
+        else:
+            o, h, n, c, r, mg = m[0:3], m[3], m[4], m[5:8], m[8], m[9]
+        arr[i].origin[:] = [float(x) for x in o]
+        arr[i].h = float(h)
+        arr[i].n = int(n)
+        arr[i].center[:] = [float(x) for x in c]
+        # round the radius up so the FP32 sphere holds every vertex
+        arr[i].radius = float(np.nextafter(np.float32(r), np.float32(np.inf)))
+        arr[i].margin = float(mg)
+    h = ctypes.c_void_p()
+    ctx._check(lib.sdf_grids_upload(ctx.handle, _ptr(vals), ctypes.addressof(arr), len(metas),
+                                    ctypes.byref(h)), "sdf_grids_upload")
+    return Grids(ctx, h)
+
+
+class Robot:
+    """Owns an sdf_robot (DH table + base + grids)."""
+
+    def __init__(self, ctx: Context, dh, grids: Grids, base=None):
+        dh = np.asarray(dh, dtype=np.float64).reshape(-1, 6)
+        rows = (sdf_dh * max(len(dh), 1))()
+        for j, r in enumerate(dh):
+            rows[j] = sdf_dh(*[float(x) for x in r])
+        b = None if base is None else np.ascontiguousarray(np.asarray(base, np.float32).reshape(12))
+        h = ctypes.c_void_p()
+        ctx._check(lib.sdf_robot_create(ctx.handle, ctypes.addressof(rows), len(dh), _ptr(b),
+                                        grids.handle, ctypes.byref(h)), "sdf_robot_create")
+        self.ctx, self.grids, self.handle, self.dof = ctx, grids, h, len(dh)
+        self.n_links = self.dof + 1
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.sdf_robot_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sdf_forward_kinematics(ctx: Context, robot: Robot, q_dev, W: int, out_dev) -> None:
+    ctx._check(lib.sdf_forward_kinematics(ctx.handle, robot.handle, _ptr(q_dev), int(W),
+                                          _ptr(out_dev)), "sdf_forward_kinematics")
+
+
+def check_trajectory(ctx: Context, robot: Robot, q_dev, W: int, points_dev, N: int, dist_dev,
+                     argmin_link_dev, argmin_point_dev) -> None:
+    """Enqueue the check on the context's stream (device buffers)."""
+    ctx._check(lib.check_trajectory(ctx.handle, robot.handle, _ptr(q_dev), int(W), _ptr(points_dev),
+                                    int(N), _ptr(dist_dev), _ptr(argmin_link_dev),
+                                    _ptr(argmin_point_dev)), "check_trajectory")
+
+
+def check_trajectory_host(ctx: Context, robot: Robot, q_host, W: int, points_host, N: int, dist_host,
+                          argmin_link_host, argmin_point_host) -> int:
+    """Host-buffer check (copies inside, synchronises); returns the status code
+    (SDF_ERR_NONFINITE is returned, other errors raise)."""
+    rc = lib.check_trajectory_host(ctx.handle, robot.handle, _ptr(q_host), int(W), _ptr(points_host),
+                                   int(N), _ptr(dist_host), _ptr(argmin_link_host),
+                                   _ptr(argmin_point_host))
+    if rc not in (SDF_OK, SDF_ERR_NONFINITE):
+        ctx._check(rc, "check_trajectory_host")
+    return int(rc)

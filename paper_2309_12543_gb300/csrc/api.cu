@@ -1,0 +1,565 @@
+// C ABI of the sdfcheck library: argument checks, object lifetimes, scratch
+// management and launch configuration.  All device work is in check.cu and
+// grid_build.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+int fail(sdf_ctx* ctx, int code, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(sdf_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? SDF_ERR_OOM : SDF_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define SDF_CUDA(ctx, call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// Make ctx->device current for the duration of a call and restore the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+int grow(sdf_ctx* ctx, T** buf, size_t* cap, size_t need, bool fill_ff) {
+    if (need <= *cap) return SDF_OK;
+    size_t n = std::max(need, *cap * 2);
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc((void**)buf, n * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(scratch)");
+    e = cudaMemsetAsync(*buf, fill_ff ? 0xff : 0, n * sizeof(T), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(scratch)");
+    *cap = n;
+    return SDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+// ------------------------------------------------------------------ context
+
+int sdf_ctx_create(sdf_ctx** out, int device, void* cuda_stream) {
+    if (!out) return SDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+        return SDF_ERR_INVALID_ARG;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return SDF_ERR_CUDA;
+    if (prop.major != 10 || prop.minor != 3) return SDF_ERR_UNSUPPORTED;
+    sdf_ctx* ctx = new (std::nothrow) sdf_ctx();
+    if (!ctx) return SDF_ERR_OOM;
+    ctx->device = device;
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    DeviceGuard g(device);
+    if (cudaMalloc((void**)&ctx->status, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->n_valid, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev2) != cudaSuccess) {
+        sdf_ctx_destroy(ctx);
+        return SDF_ERR_OOM;
+    }
+    if (sdf::configure_kernels() != cudaSuccess) {
+        sdf_ctx_destroy(ctx);
+        return SDF_ERR_CUDA;
+    }
+    *out = ctx;
+    return SDF_OK;
+}
+
+void sdf_ctx_destroy(sdf_ctx* ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->sorted);
+    cudaFree(ctx->tiles);
+    cudaFree(ctx->n_valid);
+    cudaFree(ctx->keys);
+    cudaFree(ctx->tickets);
+    cudaFree(ctx->status);
+    cudaFree(ctx->st_q);
+    cudaFree(ctx->st_pts);
+    cudaFree(ctx->st_dist);
+    cudaFree(ctx->st_link);
+    cudaFree(ctx->st_point);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->ev2) cudaEventDestroy(ctx->ev2);
+    delete ctx;
+}
+
+int sdf_ctx_set_stream(sdf_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return SDF_ERR_INVALID_ARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return SDF_OK;
+}
+
+const char* sdf_last_error(const sdf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t v) {
+    if (!ctx) return SDF_ERR_INVALID_ARG;
+    switch (key) {
+        case SDF_OPT_CULL: ctx->cull = v ? 1 : 0; return SDF_OK;
+        case SDF_OPT_POINT_STRIDE:
+            if (v != 3 && v != 4) return fail(ctx, SDF_ERR_INVALID_ARG, "point stride must be 3 or 4");
+            ctx->point_stride = (int)v;
+            return SDF_OK;
+        case SDF_OPT_WAYPOINTS_PER_BLOCK:
+            if (v != 0 && v != 1 && v != 2 && v != 4)
+                return fail(ctx, SDF_ERR_INVALID_ARG, "waypoints per block must be 0, 1, 2 or 4");
+            ctx->tw = (int)v;
+            return SDF_OK;
+        case SDF_OPT_POINT_SPLITS:
+            if (v < 0 || v > 65535) return fail(ctx, SDF_ERR_INVALID_ARG, "point splits out of range");
+            ctx->splits = (int)v;
+            return SDF_OK;
+        case SDF_OPT_TIME_KERNELS: ctx->time_kernels = v ? 1 : 0; return SDF_OK;
+        default: return fail(ctx, SDF_ERR_INVALID_ARG, "unknown option %d", (int)key);
+    }
+}
+
+int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* v) {
+    if (!ctx || !v) return SDF_ERR_INVALID_ARG;
+    switch (key) {
+        case SDF_OPT_CULL: *v = ctx->cull; return SDF_OK;
+        case SDF_OPT_POINT_STRIDE: *v = ctx->point_stride; return SDF_OK;
+        case SDF_OPT_WAYPOINTS_PER_BLOCK: *v = ctx->tw; return SDF_OK;
+        case SDF_OPT_POINT_SPLITS: *v = ctx->splits; return SDF_OK;
+        case SDF_OPT_TIME_KERNELS: *v = ctx->time_kernels; return SDF_OK;
+        default: return SDF_ERR_INVALID_ARG;
+    }
+}
+
+int sdf_ctx_synchronize(sdf_ctx* ctx) {
+    if (!ctx) return SDF_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    SDF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int st = 0;
+    SDF_CUDA(ctx, cudaMemcpy(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+        SDF_CUDA(ctx, cudaMemset(ctx->status, 0, sizeof(int)));
+        if (st & sdf::kStatusTimeout)
+            return fail(ctx, SDF_ERR_TIMEOUT, "a bounded device wait gave up; results of that call are invalid");
+        if (st & sdf::kStatusNonFinite)
+            return fail(ctx, SDF_ERR_NONFINITE, "non-finite joint value or point in a check");
+    }
+    return SDF_OK;
+}
+
+int sdf_ctx_last_kernel_ms(sdf_ctx* ctx, int32_t kernel, float* ms) {
+    if (!ctx || !ms || (kernel != SDF_KERNEL_PREP && kernel != SDF_KERNEL_CHECK)) return SDF_ERR_INVALID_ARG;
+    if (!ctx->timed_valid) return fail(ctx, SDF_ERR_INVALID_ARG, "no timed check recorded");
+    DeviceGuard g(ctx->device);
+    SDF_CUDA(ctx, cudaEventSynchronize(ctx->ev2));
+    if (kernel == SDF_KERNEL_PREP)
+        SDF_CUDA(ctx, cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1));
+    else
+        SDF_CUDA(ctx, cudaEventElapsedTime(ms, ctx->ev1, ctx->ev2));
+    return SDF_OK;
+}
+
+// -------------------------------------------------------------------- grids
+
+static bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+int sdf_build_grids(sdf_ctx* ctx, const sdf_mesh* links, int32_t n_links, int32_t resolution,
+                    float margin, sdf_grids** out) {
+    if (!ctx || !out) return SDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!links || n_links < 1 || n_links > SDF_MAX_LINKS)
+        return fail(ctx, SDF_ERR_INVALID_ARG, "n_links must be 1..%d", SDF_MAX_LINKS);
+    if (resolution < 2 || resolution > SDF_MAX_RESOLUTION)
+        return fail(ctx, SDF_ERR_INVALID_ARG, "resolution must be 2..%d", SDF_MAX_RESOLUTION);
+    if (!(margin >= 0.f) || !std::isfinite(margin)) return fail(ctx, SDF_ERR_INVALID_ARG, "bad margin");
+    for (int l = 0; l < n_links; ++l) {
+        const sdf_mesh& m = links[l];
+        if (!m.verts || !m.tris || m.n_verts < 3 || m.n_tris < 1 || m.n_components < 1)
+            return fail(ctx, SDF_ERR_INVALID_ARG, "link %d: empty mesh", l);
+        if (m.n_components > 1 && !m.comp_tri_offsets)
+            return fail(ctx, SDF_ERR_INVALID_ARG, "link %d: component offsets missing", l);
+        for (int v = 0; v < m.n_verts; ++v)
+            if (!finite3(m.verts + 3 * v)) return fail(ctx, SDF_ERR_INVALID_ARG, "link %d: non-finite vertex", l);
+        for (int t = 0; t < 3 * m.n_tris; ++t)
+            if (m.tris[t] < 0 || m.tris[t] >= m.n_verts)
+                return fail(ctx, SDF_ERR_INVALID_ARG, "link %d: triangle index out of range", l);
+        if (m.comp_tri_offsets) {
+            if (m.comp_tri_offsets[0] != 0 || m.comp_tri_offsets[m.n_components] != m.n_tris)
+                return fail(ctx, SDF_ERR_INVALID_ARG, "link %d: component offsets must span 0..n_tris", l);
+            for (int c = 0; c < m.n_components; ++c)
+                if (m.comp_tri_offsets[c + 1] <= m.comp_tri_offsets[c])
+                    return fail(ctx, SDF_ERR_INVALID_ARG, "link %d: empty or unordered component", l);
+        }
+    }
+    DeviceGuard g(ctx->device);
+    const int n = resolution;
+    const size_t per = (size_t)n * n * n;
+    sdf_grids* G = new (std::nothrow) sdf_grids();
+    if (!G) return fail(ctx, SDF_ERR_OOM, "host allocation");
+    G->device = ctx->device;
+    G->n_links = n_links;
+    G->n = n;
+    cudaError_t e = cudaMalloc((void**)&G->values, per * n_links * sizeof(float));
+    if (e != cudaSuccess) {
+        delete G;
+        return cuda_fail(ctx, e, "cudaMalloc(grids)");
+    }
+    float* d_tris = nullptr;
+    int* d_off = nullptr;
+    int rc = SDF_OK;
+    for (int l = 0; l < n_links && rc == SDF_OK; ++l) {
+        const sdf_mesh& m = links[l];
+        // box and bounding sphere in double from the FP32 vertices
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int v = 0; v < m.n_verts; ++v)
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = std::min(lo[k], (double)m.verts[3 * v + k]);
+                hi[k] = std::max(hi[k], (double)m.verts[3 * v + k]);
+            }
+        double mid[3], span = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            mid[k] = 0.5 * (lo[k] + hi[k]);
+            span = std::max(span, hi[k] - lo[k]);
+        }
+        span += 2.0 * (double)margin;
+        const double h = span / (double)(n - 1);
+        double r2 = 0.0;
+        for (int v = 0; v < m.n_verts; ++v) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += ((double)m.verts[3 * v + k] - mid[k]) * ((double)m.verts[3 * v + k] - mid[k]);
+            r2 = std::max(r2, s);
+        }
+        sdf_grid_meta& md = G->meta[l];
+        for (int k = 0; k < 3; ++k) {
+            md.origin[k] = (float)(mid[k] - 0.5 * span);
+            md.center[k] = (float)mid[k];
+        }
+        md.h = (float)h;
+        md.n = n;
+        // round the radius up so the FP32 sphere still holds every vertex
+        md.radius = nextafterf((float)std::sqrt(r2), INFINITY) * (1.f + 1e-6f);
+        md.margin = margin;
+        // triangles as 9 floats each, components as offsets
+        std::vector<float> tri9((size_t)m.n_tris * 9);
+        for (int t = 0; t < m.n_tris; ++t)
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 3; ++k) tri9[(size_t)t * 9 + 3 * c + k] = m.verts[3 * m.tris[3 * t + c] + k];
+        std::vector<int> off(m.n_components + 1);
+        if (m.comp_tri_offsets) {
+            for (int c = 0; c <= m.n_components; ++c) off[c] = m.comp_tri_offsets[c];
+        } else {
+            off[0] = 0;
+            off[1] = m.n_tris;
+        }
+        e = cudaMalloc((void**)&d_tris, tri9.size() * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&d_off, off.size() * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_tris, tri9.data(), tri9.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = sdf::launch_grid_build(d_tris, d_off, m.n_components, m.n_tris, md.origin[0], md.origin[1],
+                                       md.origin[2], md.h, n, G->values + per * l, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "grid build");
+        cudaFree(d_tris);
+        cudaFree(d_off);
+        d_tris = nullptr;
+        d_off = nullptr;
+    }
+    if (rc != SDF_OK) {
+        sdf_grids_destroy(G);
+        return rc;
+    }
+    *out = G;
+    return SDF_OK;
+}
+
+int sdf_grids_upload(sdf_ctx* ctx, const float* host_values, const sdf_grid_meta* meta, int32_t n_links,
+                     sdf_grids** out) {
+    if (!ctx || !out) return SDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!host_values || !meta || n_links < 1 || n_links > SDF_MAX_LINKS)
+        return fail(ctx, SDF_ERR_INVALID_ARG, "bad grids");
+    const int n = meta[0].n;
+    if (n < 2 || n > SDF_MAX_RESOLUTION) return fail(ctx, SDF_ERR_INVALID_ARG, "bad resolution");
+    for (int l = 0; l < n_links; ++l) {
+        if (meta[l].n != n) return fail(ctx, SDF_ERR_INVALID_ARG, "all grids need the same resolution");
+        if (!(meta[l].h > 0.f) || !std::isfinite(meta[l].h) || !(meta[l].radius >= 0.f) ||
+            !finite3(meta[l].origin) || !finite3(meta[l].center))
+            return fail(ctx, SDF_ERR_INVALID_ARG, "link %d: bad grid metadata", l);
+    }
+    DeviceGuard g(ctx->device);
+    sdf_grids* G = new (std::nothrow) sdf_grids();
+    if (!G) return fail(ctx, SDF_ERR_OOM, "host allocation");
+    G->device = ctx->device;
+    G->n_links = n_links;
+    G->n = n;
+    for (int l = 0; l < n_links; ++l) G->meta[l] = meta[l];
+    const size_t bytes = (size_t)n * n * n * n_links * sizeof(float);
+    cudaError_t e = cudaMalloc((void**)&G->values, bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(G->values, host_values, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        sdf_grids_destroy(G);
+        return cuda_fail(ctx, e, "grid upload");
+    }
+    *out = G;
+    return SDF_OK;
+}
+
+int sdf_grids_download(sdf_ctx* ctx, const sdf_grids* G, float* host_values, sdf_grid_meta* meta) {
+    if (!ctx || !G) return SDF_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (meta)
+        for (int l = 0; l < G->n_links; ++l) meta[l] = G->meta[l];
+    if (host_values) {
+        const size_t bytes = (size_t)G->n * G->n * G->n * G->n_links * sizeof(float);
+        SDF_CUDA(ctx, cudaMemcpyAsync(host_values, G->values, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        SDF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return SDF_OK;
+}
+
+int sdf_grids_info(const sdf_grids* G, int32_t* n_links, int32_t* resolution) {
+    if (!G) return SDF_ERR_INVALID_ARG;
+    if (n_links) *n_links = G->n_links;
+    if (resolution) *resolution = G->n;
+    return SDF_OK;
+}
+
+void sdf_grids_destroy(sdf_grids* G) {
+    if (!G) return;
+    DeviceGuard g(G->device);
+    cudaFree(G->values);
+    delete G;
+}
+
+// -------------------------------------------------------------------- robot
+
+int sdf_robot_create(sdf_ctx* ctx, const sdf_dh* dh, int32_t dof, const float* base_3x4,
+                     const sdf_grids* grids, sdf_robot** out) {
+    if (!ctx || !out) return SDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!grids || dof < 0 || dof + 1 > SDF_MAX_LINKS || (dof > 0 && !dh))
+        return fail(ctx, SDF_ERR_INVALID_ARG, "dof must be 0..%d with a DH table", SDF_MAX_LINKS - 1);
+    if (grids->n_links != dof + 1)
+        return fail(ctx, SDF_ERR_INVALID_ARG, "robot with %d joints needs %d grids, got %d", dof, dof + 1,
+                    grids->n_links);
+    for (int j = 0; j < dof; ++j)
+        if (!std::isfinite(dh[j].a) || !std::isfinite(dh[j].alpha) || !std::isfinite(dh[j].d) ||
+            !std::isfinite(dh[j].theta_offset))
+            return fail(ctx, SDF_ERR_INVALID_ARG, "joint %d: non-finite DH row", j);
+    if (base_3x4)
+        for (int k = 0; k < 12; ++k)
+            if (!std::isfinite(base_3x4[k])) return fail(ctx, SDF_ERR_INVALID_ARG, "non-finite base transform");
+    sdf_robot* R = new (std::nothrow) sdf_robot();
+    if (!R) return fail(ctx, SDF_ERR_OOM, "host allocation");
+    R->device = ctx->device;
+    R->dof = dof;
+    R->grids = grids;
+    sdf::LinkTable& T = R->table;
+    memset(&T, 0, sizeof T);
+    T.L = dof + 1;
+    T.dof = dof;
+    T.n = grids->n;
+    static const float kId[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    memcpy(T.base, base_3x4 ? base_3x4 : kId, sizeof T.base);
+    for (int j = 0; j < dof; ++j) {
+        T.dh_a[j] = dh[j].a;
+        T.dh_d[j] = dh[j].d;
+        T.dh_ca[j] = (float)std::cos((double)dh[j].alpha);
+        T.dh_sa[j] = (float)std::sin((double)dh[j].alpha);
+        T.dh_th[j] = dh[j].theta_offset;
+    }
+    for (int l = 0; l < T.L; ++l) {
+        const sdf_grid_meta& m = grids->meta[l];
+        T.sph_local[l] = make_float4(m.center[0], m.center[1], m.center[2], m.radius);
+        T.grid_o[l] = make_float4(m.origin[0], m.origin[1], m.origin[2], (float)(1.0 / (double)m.h));
+        T.grid_h[l] = m.h;
+    }
+    T.values = grids->values;
+    *out = R;
+    return SDF_OK;
+}
+
+void sdf_robot_destroy(sdf_robot* R) { delete R; }
+
+int sdf_forward_kinematics(sdf_ctx* ctx, const sdf_robot* R, const float* q_dev, int32_t W, float* out_dev) {
+    if (!ctx || !R || W < 0) return SDF_ERR_INVALID_ARG;
+    if (W == 0) return SDF_OK;
+    if ((R->dof > 0 && !q_dev) || !out_dev) return fail(ctx, SDF_ERR_INVALID_ARG, "null buffer");
+    if ((reinterpret_cast<uintptr_t>(out_dev) & 15u) != 0)
+        return fail(ctx, SDF_ERR_INVALID_ARG, "output must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    SDF_CUDA(ctx, sdf::launch_fk(R->table, q_dev, W, out_dev, ctx->status, ctx->stream));
+    return SDF_OK;
+}
+
+// -------------------------------------------------------------------- check
+
+// Waypoints per block: the most that keeps one (waypoint, link) pair per lane.
+// Tile chunks per waypoint tile: enough blocks for about two per SM.
+static void choose_tiles(const sdf_ctx* ctx, int W, int N, int L, int* tw, int* splits, int* tiles_per_split) {
+    int t = ctx->tw;
+    if (t == 0) t = (4 * L <= 32) ? 4 : (2 * L <= 32 ? 2 : 1);
+    const int wt = (W + t - 1) / t;
+    const int n_tiles = std::max(1, (N + 31) / 32);
+    int s = ctx->splits;
+    if (s == 0) s = std::max(1, (2 * ctx->num_sms + wt - 1) / wt);
+    s = std::min(s, n_tiles);
+    const int per = (n_tiles + s - 1) / s;
+    *tw = t;
+    *splits = (n_tiles + per - 1) / per;
+    *tiles_per_split = per;
+}
+
+int check_trajectory(sdf_ctx* ctx, const sdf_robot* R, const float* q_dev, int32_t W, const float* points_dev,
+                     int32_t N, float* dist_dev, int32_t* argmin_link_dev, int32_t* argmin_point_dev) {
+    if (!ctx || !R) return SDF_ERR_INVALID_ARG;
+    if (W < 0 || N < 0) return fail(ctx, SDF_ERR_INVALID_ARG, "negative size");
+    if (N > SDF_MAX_POINTS) return fail(ctx, SDF_ERR_INVALID_ARG, "N > %d", SDF_MAX_POINTS);
+    if (W == 0) return SDF_OK;
+    if (!dist_dev || !argmin_link_dev || !argmin_point_dev || (R->dof > 0 && !q_dev) || (N > 0 && !points_dev))
+        return fail(ctx, SDF_ERR_INVALID_ARG, "null buffer");
+    if (ctx->point_stride == 4 && (reinterpret_cast<uintptr_t>(points_dev) & 15u) != 0)
+        return fail(ctx, SDF_ERR_INVALID_ARG, "points must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(points_dev) & 3u) != 0)
+        return fail(ctx, SDF_ERR_INVALID_ARG, "points must be 4-byte aligned");
+    const int L = R->table.L;
+    int tw, splits, per;
+    choose_tiles(ctx, W, N, L, &tw, &splits, &per);
+    if (tw * L > 32)
+        return fail(ctx, SDF_ERR_INVALID_ARG, "%d waypoints per block x %d links exceeds 32 pairs", tw, L);
+    DeviceGuard g(ctx->device);
+    const size_t n_tiles = (size_t)std::max(1, (N + 31) / 32);
+    int rc = grow(ctx, &ctx->sorted, &ctx->sorted_cap, (size_t)std::max(N, 1), false);
+    if (rc == SDF_OK) rc = grow(ctx, &ctx->tiles, &ctx->tiles_cap, n_tiles, false);
+    if (rc == SDF_OK && splits > 1) {
+        rc = grow(ctx, &ctx->keys, &ctx->keys_cap, (size_t)W, true);
+        if (rc == SDF_OK) rc = grow(ctx, &ctx->tickets, &ctx->tickets_cap, (size_t)((W + tw - 1) / tw), false);
+    }
+    if (rc != SDF_OK) return rc;
+
+    sdf::PrepParams pp;
+    pp.points = points_dev;
+    pp.N = N;
+    pp.stride = ctx->point_stride;
+    pp.sorted = ctx->sorted;
+    pp.tiles = ctx->tiles;
+    pp.n_valid = ctx->n_valid;
+    pp.status = ctx->status;
+
+    sdf::CheckParams p;
+    p.T = R->table;
+    p.q = q_dev;
+    p.W = W;
+    p.sorted = ctx->sorted;
+    p.tiles = ctx->tiles;
+    p.n_valid = ctx->n_valid;
+    p.splits = splits;
+    p.tiles_per_split = per;
+    p.max_tiles = (int)n_tiles;
+    p.stage_tiles = n_tiles <= (size_t)sdf::kMaxStagedTiles ? 1 : 0;
+    p.cull = ctx->cull;
+    p.dist = dist_dev;
+    p.arg_link = argmin_link_dev;
+    p.arg_point = argmin_point_dev;
+    p.keys = splits > 1 ? ctx->keys : nullptr;
+    p.tickets = splits > 1 ? ctx->tickets : nullptr;
+    p.status = ctx->status;
+
+    if (ctx->time_kernels) SDF_CUDA(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+    SDF_CUDA(ctx, sdf::launch_prep(pp, ctx->stream));
+    if (ctx->time_kernels) SDF_CUDA(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
+    SDF_CUDA(ctx, sdf::launch_check(p, tw, ctx->stream));
+    if (ctx->time_kernels) {
+        SDF_CUDA(ctx, cudaEventRecord(ctx->ev2, ctx->stream));
+        ctx->timed_valid = true;
+    }
+    return SDF_OK;
+}
+
+int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* R, const float* q_host, int32_t W,
+                          const float* points_host, int32_t N, float* dist_host, int32_t* argmin_link_host,
+                          int32_t* argmin_point_host) {
+    if (!ctx || !R) return SDF_ERR_INVALID_ARG;
+    if (W < 0 || N < 0) return fail(ctx, SDF_ERR_INVALID_ARG, "negative size");
+    if (W == 0) return SDF_OK;
+    if (!dist_host || !argmin_link_host || !argmin_point_host || (R->dof > 0 && !q_host) ||
+        (N > 0 && !points_host))
+        return fail(ctx, SDF_ERR_INVALID_ARG, "null buffer");
+    DeviceGuard g(ctx->device);
+    const size_t nq = (size_t)W * std::max(R->dof, 1);
+    const size_t np = (size_t)std::max(N, 1) * ctx->point_stride;
+    int rc = grow(ctx, &ctx->st_q, &ctx->st_q_cap, nq, false);
+    if (rc == SDF_OK) rc = grow(ctx, &ctx->st_pts, &ctx->st_pts_cap, np, false);
+    if (rc == SDF_OK && (size_t)W > ctx->st_out_cap) {
+        cudaFree(ctx->st_dist);
+        cudaFree(ctx->st_link);
+        cudaFree(ctx->st_point);
+        ctx->st_dist = nullptr;
+        ctx->st_link = ctx->st_point = nullptr;
+        ctx->st_out_cap = 0;
+        const size_t cap = std::max((size_t)W, (size_t)1024);
+        if (cudaMalloc((void**)&ctx->st_dist, cap * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&ctx->st_link, cap * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc((void**)&ctx->st_point, cap * sizeof(int32_t)) != cudaSuccess)
+            rc = fail(ctx, SDF_ERR_OOM, "staging allocation");
+        else
+            ctx->st_out_cap = cap;
+    }
+    if (rc != SDF_OK) return rc;
+    if (R->dof > 0)
+        SDF_CUDA(ctx, cudaMemcpyAsync(ctx->st_q, q_host, (size_t)W * R->dof * sizeof(float), cudaMemcpyHostToDevice,
+                                      ctx->stream));
+    if (N > 0)
+        SDF_CUDA(ctx, cudaMemcpyAsync(ctx->st_pts, points_host, (size_t)N * ctx->point_stride * sizeof(float),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    rc = check_trajectory(ctx, R, ctx->st_q, W, ctx->st_pts, N, ctx->st_dist, ctx->st_link, ctx->st_point);
+    if (rc != SDF_OK) return rc;
+    SDF_CUDA(ctx, cudaMemcpyAsync(dist_host, ctx->st_dist, (size_t)W * sizeof(float), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    SDF_CUDA(ctx, cudaMemcpyAsync(argmin_link_host, ctx->st_link, (size_t)W * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    SDF_CUDA(ctx, cudaMemcpyAsync(argmin_point_host, ctx->st_point, (size_t)W * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    return sdf_ctx_synchronize(ctx);
+}
+
+}  // extern "C"
