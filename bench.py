@@ -124,6 +124,19 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float) -> float:
+    """Largest `value` over all ranks of the default process group (identity
+    without one).  The tensor lives where the backend can reduce it."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -282,11 +295,7 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if ws > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(float(sum(step_ms)))
     rc = ctx.synchronize()
     if rc != 0:
         raise RuntimeError(f"timed checks failed: {ctx.last_error()}")
