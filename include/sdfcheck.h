@@ -195,6 +195,43 @@ int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* robot, const float* q_h
                           const float* points_host, int32_t N, float* dist_host,
                           int32_t* argmin_link_host, int32_t* argmin_point_host);
 
+/* ----------------------------------------------------------- allocation-free check */
+
+/* The paper has no counterpart to this entry point; it serves deployment.
+ *
+ * check_trajectory_noalloc: the same check as check_trajectory, for callers that
+ * must not allocate GPU memory while checking -- typically a fixed-period
+ * control loop, where an allocation's unpredictable latency (and the device
+ * synchronisation cudaMalloc/cudaFree can imply) would miss the cycle deadline,
+ * or a process whose memory budget is fixed at start-up.  It needs no context:
+ * it calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch is
+ * one file-scope device array of about 1.1 MiB that every GPU loading this
+ * library holds until the process exits.
+ *
+ * Limits: W <= SDF_NOALLOC_MAX_WAYPOINTS and N <= SDF_NOALLOC_MAX_POINTS, else
+ * SDF_ERR_INVALID_ARG (nothing is enqueued).  Points are N x 3 FP32; culling and
+ * tile shapes are the automatic defaults.
+ *
+ * robot: as for check_trajectory (its device is made current for the call).
+ * cuda_stream: the cudaStream_t to enqueue on (NULL = legacy default stream).
+ * status_dev: optional device int that the call clears and the kernels OR their
+ *   status bits into (bit 0: a non-finite input was seen, bit 1: a bounded wait
+ *   gave up and the results are invalid); NULL = not reported.
+ * Returns SDF_OK after enqueueing (asynchronous), SDF_ERR_INVALID_ARG or
+ * SDF_ERR_CUDA (launch or set-up failure).
+ *
+ * The first call on each device looks up the array's device address and sets the
+ * kernels' shared-memory limit; make that first call before any stream capture.
+ * Every call shares the one array and it keeps the previous call's contents (the
+ * call resets what must start cleared), so calls whose work overlaps on the GPU --
+ * on different streams, or from different host threads -- race and must be
+ * serialised by the caller. */
+#define SDF_NOALLOC_MAX_POINTS 65536
+#define SDF_NOALLOC_MAX_WAYPOINTS 4096
+int check_trajectory_noalloc(const sdf_robot* robot, void* cuda_stream, const float* q_dev, int32_t W,
+                             const float* points_dev, int32_t N, float* dist_dev,
+                             int32_t* argmin_link_dev, int32_t* argmin_point_dev, int32_t* status_dev);
+
 #ifdef __cplusplus
 }
 #endif

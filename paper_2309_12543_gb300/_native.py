@@ -24,6 +24,8 @@ SDF_ERR_UNSUPPORTED = -5
 SDF_ERR_NONFINITE = -6
 SDF_MAX_LINKS = 16
 SDF_MAX_POINTS = 16777215
+SDF_NOALLOC_MAX_POINTS = 65536
+SDF_NOALLOC_MAX_WAYPOINTS = 4096
 
 SDF_OPT_CULL = 1
 SDF_OPT_POINT_STRIDE = 2
@@ -83,6 +85,7 @@ def _load():
         "sdf_forward_kinematics": (ctypes.c_int, [P, P, P, i32, P]),
         "check_trajectory": (ctypes.c_int, [P, P, P, i32, P, i32, P, P, P]),
         "check_trajectory_host": (ctypes.c_int, [P, P, P, i32, P, i32, P, P, P]),
+        "check_trajectory_noalloc": (ctypes.c_int, [P, P, P, i32, P, i32, P, P, P, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -98,7 +101,8 @@ EXPORTED = ("sdf_ctx_create", "sdf_ctx_destroy", "sdf_ctx_set_stream", "sdf_last
             "sdf_ctx_set_option", "sdf_ctx_get_option", "sdf_ctx_synchronize",
             "sdf_ctx_last_kernel_ms", "sdf_build_grids", "sdf_grids_upload", "sdf_grids_download",
             "sdf_grids_info", "sdf_grids_destroy", "sdf_robot_create", "sdf_robot_destroy",
-            "sdf_forward_kinematics", "check_trajectory", "check_trajectory_host")
+            "sdf_forward_kinematics", "check_trajectory", "check_trajectory_host",
+            "check_trajectory_noalloc")
 
 
 def _ptr(x) -> int:
@@ -299,3 +303,12 @@ def check_trajectory_host(ctx: Context, robot: Robot, q_host, W: int, points_hos
     if rc not in (SDF_OK, SDF_ERR_NONFINITE):
         ctx._check(rc, "check_trajectory_host")
     return int(rc)
+
+
+def check_trajectory_noalloc(robot: Robot, stream, q_dev, W: int, points_dev, N: int, dist_dev,
+                             argmin_link_dev, argmin_point_dev, status_dev=None) -> int:
+    """The allocation-free check (no context, fixed-size device scratch); returns
+    the status code of enqueueing (SDF_OK, SDF_ERR_INVALID_ARG or SDF_ERR_CUDA)."""
+    return int(lib.check_trajectory_noalloc(robot.handle, _stream_handle(stream), _ptr(q_dev), int(W),
+                                            _ptr(points_dev), int(N), _ptr(dist_dev), _ptr(argmin_link_dev),
+                                            _ptr(argmin_point_dev), _ptr(status_dev)))
