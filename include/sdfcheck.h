@@ -103,8 +103,7 @@ const char* sdf_last_error(const sdf_ctx* ctx);
 /* Options (sdf_ctx_set_option / sdf_ctx_get_option). */
 #define SDF_OPT_CULL 1            /* 1 (default): bounding-sphere culling; 0: evaluate every pair */
 #define SDF_OPT_POINT_STRIDE 2    /* floats per point: 3 (default, x y z) or 4 (x y z pad)       */
-#define SDF_OPT_WAYPOINTS_PER_BLOCK 3 /* 0 (default) = automatic, else 1, 2 or 4 (x links <= 32)    */
-#define SDF_OPT_POINT_SPLITS 4    /* 0 (default) = automatic, else tile chunks per waypoint block */
+#define SDF_OPT_WAYPOINTS_PER_BLOCK 3 /* 0 (default) = automatic, else 1..32 with value x links <= 32 */
 #define SDF_OPT_TIME_KERNELS 6    /* 1: record CUDA events around the two kernels of a check      */
 int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t value);
 int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* value);
@@ -180,7 +179,7 @@ int sdf_forward_kinematics(sdf_ctx* ctx, const sdf_robot* robot, const float* q_
  * is NaN are ignored; non-finite inputs also raise SDF_ERR_NONFINITE in
  * sdf_ctx_synchronize.  Asynchronous; enqueues two kernels (a spatial sort of
  * the points into 32-point tiles, then the check) and uses context-owned scratch
- * (about 16 bytes per point plus 8 bytes per waypoint).
+ * (about 17 bytes per point).
  * Errors: INVALID_ARG (NULL pointer with W, N > 0, N > SDF_MAX_POINTS, W < 0,
  * misaligned points), OOM (growing scratch), CUDA. */
 int check_trajectory(sdf_ctx* ctx, const sdf_robot* robot, const float* q_dev, int32_t W,
@@ -210,7 +209,7 @@ int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* robot, const float* q_h
  *
  * Limits: W <= SDF_NOALLOC_MAX_WAYPOINTS and N <= SDF_NOALLOC_MAX_POINTS, else
  * SDF_ERR_INVALID_ARG (nothing is enqueued).  Points are N x 3 FP32; culling and
- * tile shapes are the automatic defaults.
+ * the block shape are the automatic defaults.
  *
  * robot: as for check_trajectory (its device is made current for the call).
  * cuda_stream: the cudaStream_t to enqueue on (NULL = legacy default stream).

@@ -30,7 +30,6 @@ SDF_NOALLOC_MAX_WAYPOINTS = 4096
 SDF_OPT_CULL = 1
 SDF_OPT_POINT_STRIDE = 2
 SDF_OPT_WAYPOINTS_PER_BLOCK = 3
-SDF_OPT_POINT_SPLITS = 4
 SDF_OPT_TIME_KERNELS = 6
 SDF_KERNEL_PREP = 0
 SDF_KERNEL_CHECK = 1

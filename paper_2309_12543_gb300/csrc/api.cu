@@ -109,9 +109,8 @@ void sdf_ctx_destroy(sdf_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->sorted);
     cudaFree(ctx->tiles);
+    cudaFree(ctx->supers);
     cudaFree(ctx->n_valid);
-    cudaFree(ctx->keys);
-    cudaFree(ctx->tickets);
     cudaFree(ctx->status);
     cudaFree(ctx->st_q);
     cudaFree(ctx->st_pts);
@@ -141,13 +140,8 @@ int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t v) {
             ctx->point_stride = (int)v;
             return SDF_OK;
         case SDF_OPT_WAYPOINTS_PER_BLOCK:
-            if (v != 0 && v != 1 && v != 2 && v != 4)
-                return fail(ctx, SDF_ERR_INVALID_ARG, "waypoints per block must be 0, 1, 2 or 4");
+            if (v < 0 || v > 32) return fail(ctx, SDF_ERR_INVALID_ARG, "waypoints per block must be 0..32");
             ctx->tw = (int)v;
-            return SDF_OK;
-        case SDF_OPT_POINT_SPLITS:
-            if (v < 0 || v > 65535) return fail(ctx, SDF_ERR_INVALID_ARG, "point splits out of range");
-            ctx->splits = (int)v;
             return SDF_OK;
         case SDF_OPT_TIME_KERNELS: ctx->time_kernels = v ? 1 : 0; return SDF_OK;
         default: return fail(ctx, SDF_ERR_INVALID_ARG, "unknown option %d", (int)key);
@@ -160,7 +154,6 @@ int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* v) {
         case SDF_OPT_CULL: *v = ctx->cull; return SDF_OK;
         case SDF_OPT_POINT_STRIDE: *v = ctx->point_stride; return SDF_OK;
         case SDF_OPT_WAYPOINTS_PER_BLOCK: *v = ctx->tw; return SDF_OK;
-        case SDF_OPT_POINT_SPLITS: *v = ctx->splits; return SDF_OK;
         case SDF_OPT_TIME_KERNELS: *v = ctx->time_kernels; return SDF_OK;
         default: return SDF_ERR_INVALID_ARG;
     }
@@ -433,20 +426,10 @@ int sdf_forward_kinematics(sdf_ctx* ctx, const sdf_robot* R, const float* q_dev,
 
 // -------------------------------------------------------------------- check
 
-// Waypoints per block: the most that keeps one (waypoint, link) pair per lane.
-// Tile chunks per waypoint tile: enough blocks for about two per SM.
-static void choose_tiles(const sdf_ctx* ctx, int W, int N, int L, int* tw, int* splits, int* tiles_per_split) {
-    int t = ctx->tw;
-    if (t == 0) t = (4 * L <= 32) ? 4 : (2 * L <= 32 ? 2 : 1);
-    const int wt = (W + t - 1) / t;
-    const int n_tiles = std::max(1, (N + 31) / 32);
-    int s = ctx->splits;
-    if (s == 0) s = std::max(1, (2 * ctx->num_sms + wt - 1) / wt);
-    s = std::min(s, n_tiles);
-    const int per = (n_tiles + s - 1) / s;
-    *tw = t;
-    *splits = (n_tiles + per - 1) / per;
-    *tiles_per_split = per;
+// Waypoints per block (one warp per waypoint and link, so TW * L <= 32).
+static int choose_tw(const sdf_ctx* ctx, int L) {
+    if (ctx->tw > 0) return ctx->tw;
+    return 32 / L >= 2 ? 2 : 1;
 }
 
 int check_trajectory(sdf_ctx* ctx, const sdf_robot* R, const float* q_dev, int32_t W, const float* points_dev,
@@ -462,18 +445,15 @@ int check_trajectory(sdf_ctx* ctx, const sdf_robot* R, const float* q_dev, int32
     if ((reinterpret_cast<uintptr_t>(points_dev) & 3u) != 0)
         return fail(ctx, SDF_ERR_INVALID_ARG, "points must be 4-byte aligned");
     const int L = R->table.L;
-    int tw, splits, per;
-    choose_tiles(ctx, W, N, L, &tw, &splits, &per);
+    const int tw = choose_tw(ctx, L);
     if (tw * L > 32)
-        return fail(ctx, SDF_ERR_INVALID_ARG, "%d waypoints per block x %d links exceeds 32 pairs", tw, L);
+        return fail(ctx, SDF_ERR_INVALID_ARG, "%d waypoints per block x %d links exceeds 32 warps", tw, L);
     DeviceGuard g(ctx->device);
     const size_t n_tiles = (size_t)std::max(1, (N + 31) / 32);
+    const size_t n_super = (n_tiles + 31) / 32;
     int rc = grow(ctx, &ctx->sorted, &ctx->sorted_cap, (size_t)std::max(N, 1), false);
     if (rc == SDF_OK) rc = grow(ctx, &ctx->tiles, &ctx->tiles_cap, n_tiles, false);
-    if (rc == SDF_OK && splits > 1) {
-        rc = grow(ctx, &ctx->keys, &ctx->keys_cap, (size_t)W, true);
-        if (rc == SDF_OK) rc = grow(ctx, &ctx->tickets, &ctx->tickets_cap, (size_t)((W + tw - 1) / tw), false);
-    }
+    if (rc == SDF_OK) rc = grow(ctx, &ctx->supers, &ctx->supers_cap, n_super, false);
     if (rc != SDF_OK) return rc;
 
     sdf::PrepParams pp;
@@ -482,6 +462,7 @@ int check_trajectory(sdf_ctx* ctx, const sdf_robot* R, const float* q_dev, int32
     pp.stride = ctx->point_stride;
     pp.sorted = ctx->sorted;
     pp.tiles = ctx->tiles;
+    pp.supers = ctx->supers;
     pp.n_valid = ctx->n_valid;
     pp.status = ctx->status;
 
@@ -489,25 +470,23 @@ int check_trajectory(sdf_ctx* ctx, const sdf_robot* R, const float* q_dev, int32
     p.T = R->table;
     p.q = q_dev;
     p.W = W;
+    p.tw = tw;
     p.sorted = ctx->sorted;
     p.tiles = ctx->tiles;
+    p.supers = ctx->supers;
     p.n_valid = ctx->n_valid;
-    p.splits = splits;
-    p.tiles_per_split = per;
     p.max_tiles = (int)n_tiles;
-    p.stage_tiles = n_tiles <= (size_t)sdf::kMaxStagedTiles ? 1 : 0;
+    p.stage = n_tiles <= (size_t)sdf::kMaxStagedTiles ? 1 : 0;
     p.cull = ctx->cull;
     p.dist = dist_dev;
     p.arg_link = argmin_link_dev;
     p.arg_point = argmin_point_dev;
-    p.keys = splits > 1 ? ctx->keys : nullptr;
-    p.tickets = splits > 1 ? ctx->tickets : nullptr;
     p.status = ctx->status;
 
     if (ctx->time_kernels) SDF_CUDA(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
     SDF_CUDA(ctx, sdf::launch_prep(pp, ctx->stream));
     if (ctx->time_kernels) SDF_CUDA(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
-    SDF_CUDA(ctx, sdf::launch_check(p, tw, ctx->stream));
+    SDF_CUDA(ctx, sdf::launch_check(p, ctx->stream));
     if (ctx->time_kernels) {
         SDF_CUDA(ctx, cudaEventRecord(ctx->ev2, ctx->stream));
         ctx->timed_valid = true;

@@ -1,34 +1,36 @@
-// Fused runtime distance check for sm_103a.
+// Runtime distance check for sm_103a: a spatial sort of the obstacle cloud, then
+// one fused kernel for forward kinematics, culling, transform, lookup and the
+// per-waypoint min.
 //
-// Two kernels per call.
+// cloud_prep_kernel (one cluster of 8 CTAs x 1024 threads) orders the points in
+// space: bounding box, 32^3-cell Morton key per point, counting sort of the keys
+// in distributed shared memory, scatter into a float4 array (x, y, z, original
+// index), then a bounding sphere per tile of 32 consecutive sorted points and per
+// super-tile of 32 consecutive tiles.  Non-finite points are dropped from the
+// sorted cloud (and flagged), so they can never be a minimum.
 //
-// cloud_prep_kernel (one cluster of 8 CTAs x 1024 threads) orders the obstacle
-// points in space: bounding box, 32^3-cell Morton key per point, counting sort of
-// the keys in distributed shared memory, scatter into a float4 array (x, y, z,
-// original index), and a bounding sphere per tile of 32 consecutive sorted points.  Non-finite points are
-// dropped from the sorted cloud (and flagged), so they can never be a minimum.
-//
-// check_kernel: one block owns TW consecutive waypoints and one chunk of tiles.
-//   1. forward kinematics, one warp per waypoint (Sec. III-A "parallel forward
-//      kinematics"): each lane builds one DH joint transform, a warp scan composes
-//      them, the link-from-world transforms land in shared memory;
-//   2. seed: for every (waypoint, link) pair the tile whose farthest point is
-//      nearest to the link's bounding-sphere centre is evaluated in full, so the
-//      per-waypoint best starts as a tight upper bound;
-//   3. sweep: each warp walks tiles; the lanes test the tile's sphere against all
-//      (waypoint, link) spheres at once (||c_t - c_l|| - r_t - R_l > best + slack
-//      => skip, the analogue of the paper's "grids in sphere", Sec. III-B), then for
-//      each surviving pair the 32 lanes test the tile's points.  Surviving (point,
-//      pair) entries are compacted into a per-warp queue and evaluated 32 at a time:
-//      transform into the link frame (the per-point form of Sec. II-B / Fig. 2),
-//      trilinear lookup in the FP32 link grid (the grid-sample interpolation of
-//      Sec. III-A), distance-to-box outside the grid;
+// check_kernel: one warp per (waypoint, link) pair; a block holds the pairs of TW
+// waypoints.  Each warp, with no block-wide barrier after set-up:
+//   1. forward kinematics (Sec. III-A "parallel forward kinematics"): lanes build
+//      one DH joint transform each and a warp scan composes them; the warp keeps
+//      its link's link-from-world transform and world bounding-sphere centre in
+//      registers;
+//   2. seed: evaluates the tile whose farthest point is nearest to its link's
+//      sphere centre, which makes the waypoint's best value (shared by the
+//      waypoint's warps through a shared-memory atomic) a tight upper bound;
+//   3. walks super-tiles -> tiles -> points, lanes over the children, skipping
+//      every sphere with ||c - c_link|| - r - R_link > best + slack (the analogue
+//      of the paper's "grids in sphere", Sec. III-B).  Surviving points are
+//      compacted into a per-warp queue and evaluated 32 at a time: transform into
+//      the link frame (the per-point form of Sec. II-B / Fig. 2), trilinear lookup
+//      in the FP32 link grid (the grid-sample interpolation of Sec. III-A),
+//      distance to the grid box outside it;
 //   4. reduction with min per waypoint (Sec. III-A): each value is packed with its
 //      original point index and link into one 64-bit key whose unsigned order is
-//      (distance, point, link), so atomicMin yields a deterministic arg-min.
-// With several tile chunks per waypoint tile the blocks combine their keys with a
-// global atomicMin; the last block of a waypoint tile (ticket counter) decodes the
-// keys and returns the scratch to its idle state.
+//      (distance, point, link); warp shuffles, a shared-memory atomicMin, and the
+//      waypoint's last warp writes the decoded result.
+// The tile and super-tile spheres reach shared memory by one TMA bulk copy that
+// completes on an mbarrier (with a bounded wait).
 //
 // The culls are exact: a skipped pair's interpolated distance exceeds the best
 // value already found by more than the FP32 rounding of the bound, so culled and
@@ -49,6 +51,7 @@ constexpr unsigned kOrderedInf = 0xff800000u;   // ordered_bits(+inf): "no value
 constexpr int kPrepThreads = 1024;
 constexpr int kPrepCtas = 8;                        // one portable-size cluster
 constexpr int kBinsPerCta = kCells / kPrepCtas;
+constexpr int kPrepCached = 4;                      // points per thread kept in registers
 
 __device__ __forceinline__ unsigned ordered_bits(float f) {
     unsigned u = __float_as_uint(f + 0.0f);  // -0 -> +0
@@ -180,6 +183,26 @@ __device__ __forceinline__ void write_result(const CheckParams& P, int w, unsign
     }
 }
 
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(kFull, k, o);
+        k = other < k ? other : k;
+    }
+    return k;
+}
+
+// (score, index) arg-min across the warp; ties go to the smaller index.
+__device__ __forceinline__ int warp_argmin(float s, int idx) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(kFull, s, o);
+        const int io = __shfl_xor_sync(kFull, idx, o);
+        if (so < s || (so == s && io < idx)) { s = so; idx = io; }
+    }
+    return idx;
+}
+
 // 5-bit spread for a 15-bit Morton key.
 __device__ __forceinline__ unsigned spread5(unsigned v) {
     v &= 31u;
@@ -215,7 +238,8 @@ struct FMax { __device__ float operator()(float a, float b) const { return fmaxf
 
 // Spatial sort of the cloud by one thread-block cluster: the 32^3 cell counters
 // are spread over the CTAs' shared memory (distributed shared memory), so every
-// phase is one pass over the points with cluster barriers in between.
+// phase is one pass over the points with cluster barriers in between.  Up to
+// kPrepCached points per thread stay in registers between the passes.
 __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads, 1)
     cloud_prep_kernel(const __grid_constant__ PrepParams P) {
     cg::cluster_group cluster = cg::this_cluster();
@@ -229,19 +253,39 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     const int gtid = (int)rank * kPrepThreads + tid;
     constexpr int kStride = kPrepCtas * kPrepThreads;
     const float kInf = __int_as_float(0x7f800000);
+    const bool cached = P.N <= kStride * kPrepCached;
+
+    float3 pc[kPrepCached];
+#pragma unroll
+    for (int k = 0; k < kPrepCached; ++k) {
+        const int i = gtid + k * kStride;
+        pc[k] = (cached && i < P.N) ? load_point(P.points, P.stride, i) : make_float3(0.f, 0.f, 0.f);
+    }
+    auto point_at = [&](int k, int i) -> float3 { return cached ? pc[k] : load_point(P.points, P.stride, i); };
+    // visits every point index of this thread: f(point, index)
+    auto for_each_point = [&](auto&& f) {
+        if (cached) {
+#pragma unroll
+            for (int k = 0; k < kPrepCached; ++k) {
+                const int i = gtid + k * kStride;
+                if (i < P.N) f(point_at(k, i), i);
+            }
+        } else {
+            for (int i = gtid; i < P.N; i += kStride) f(load_point(P.points, P.stride, i), i);
+        }
+    };
 
     // 1. bounding box of the finite points (per CTA, then across the cluster)
     float lo[3] = {kInf, kInf, kInf}, hi[3] = {-kInf, -kInf, -kInf};
     bool bad = false;
-    for (int i = gtid; i < P.N; i += kStride) {
-        const float3 p = load_point(P.points, P.stride, i);
+    for_each_point([&](float3 p, int) {
         if (finite3(p)) {
             lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
             hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
         } else {
             bad = true;
         }
-    }
+    });
     if (__syncthreads_or(bad) && tid == 0) atomicOr(P.status, kStatusNonFinite);
     const float r0 = block_reduce(lo[0], s_tmp, FMin()), r1 = block_reduce(lo[1], s_tmp, FMin());
     const float r2 = block_reduce(lo[2], s_tmp, FMin()), r3 = block_reduce(hi[0], s_tmp, FMax());
@@ -262,13 +306,12 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
                                    32.f / fmaxf(bhi.z - blo.z, 1e-6f));
 
     // 2. histogram: cell c is counted in CTA c / kBinsPerCta
-    for (int i = gtid; i < P.N; i += kStride) {
-        const float3 p = load_point(P.points, P.stride, i);
+    for_each_point([&](float3 p, int) {
         if (finite3(p)) {
             const unsigned c = cell_key(p, blo, inv);
             atomicAdd(cluster.map_shared_rank(&s_bins[c % kBinsPerCta], (int)(c / kBinsPerCta)), 1u);
         }
-    }
+    });
     cluster.sync();
 
     // 3. exclusive scan of this CTA's cells (warp w owns a contiguous run), then
@@ -314,20 +357,20 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     cluster.sync();
 
     // 4. scatter (order inside a cell is arbitrary; keys carry the original index)
-    for (int i = gtid; i < P.N; i += kStride) {
-        const float3 p = load_point(P.points, P.stride, i);
+    for_each_point([&](float3 p, int i) {
         if (finite3(p)) {
             const unsigned c = cell_key(p, blo, inv);
             const unsigned pos = atomicAdd(cluster.map_shared_rank(&s_bins[c % kBinsPerCta], (int)(c / kBinsPerCta)), 1u);
             P.sorted[pos] = make_float4(p.x, p.y, p.z, __int_as_float(i));
         }
-    }
-    __threadfence();
-    cluster.sync();   // every CTA's writes of `sorted` are visible; no remote smem use after this
+    });
+    // the cluster barrier orders these writes before the reads below (cluster scope)
+    cluster.sync();
 
     // 5. tile spheres: centre of the tile's box, radius to its farthest point
     const int n_tiles = (n_valid + 31) >> 5;
-    for (int t = (int)rank * (kPrepThreads / 32) + warp; t < n_tiles; t += kPrepCtas * (kPrepThreads / 32)) {
+    constexpr int kClusterWarps = kPrepCtas * (kPrepThreads / 32);
+    for (int t = (int)rank * (kPrepThreads / 32) + warp; t < n_tiles; t += kClusterWarps) {
         const int i = t * 32 + lane;
         const bool v = i < n_valid;
         const float4 p = v ? __ldcg(&P.sorted[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -345,6 +388,30 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(kFull, r2, o));
         if (lane == 0) P.tiles[t] = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-6f) + 1e-7f);
+    }
+    cluster.sync();
+
+    // 6. super-tile spheres over 32 consecutive tiles: box of the tile spheres,
+    //    radius to the farthest tile sphere
+    const int n_super = (n_tiles + 31) >> 5;
+    for (int s = (int)rank * (kPrepThreads / 32) + warp; s < n_super; s += kClusterWarps) {
+        const int t = s * 32 + lane;
+        const bool v = t < n_tiles;
+        const float4 c = v ? __ldcg(&P.tiles[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float mn[3] = {v ? c.x - c.w : kInf, v ? c.y - c.w : kInf, v ? c.z - c.w : kInf};
+        float mx[3] = {v ? c.x + c.w : -kInf, v ? c.y + c.w : -kInf, v ? c.z + c.w : -kInf};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                mn[a] = fminf(mn[a], __shfl_xor_sync(kFull, mn[a], o));
+                mx[a] = fmaxf(mx[a], __shfl_xor_sync(kFull, mx[a], o));
+            }
+        const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]), cz = 0.5f * (mn[2] + mx[2]);
+        float r = v ? sqrtf((c.x - cx) * (c.x - cx) + (c.y - cy) * (c.y - cy) + (c.z - cz) * (c.z - cz)) + c.w : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(kFull, r, o));
+        if (lane == 0) P.supers[s] = make_float4(cx, cy, cz, r * (1.f + 1e-6f) + 1e-7f);
     }
     if (rank == 0 && tid == 0) *P.n_valid = n_valid;
 }
@@ -385,225 +452,199 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
-template <int TW>
-__global__ void __launch_bounds__(kBlock, 2) check_kernel(const __grid_constant__ CheckParams P) {
-    extern __shared__ float4 s_tiles[];        // tile spheres, staged by one bulk copy
-    __shared__ float4 s_xf[TW][kMaxLinks][3];
-    __shared__ float4 s_sph[TW][kMaxLinks];
-    __shared__ unsigned s_best[TW];
-    __shared__ unsigned long long s_key[TW];
-    __shared__ float s_seed_s[kWarps][32];
-    __shared__ int s_seed_t[kWarps][32];
-    __shared__ unsigned s_queue[kWarps][64];
+// The link-from-world rows and world sphere of link l for waypoint w, computed by
+// the whole warp (every lane ends with the same values).
+__device__ __forceinline__ void warp_link_pose(const LinkTable& T, const float* qw, int lane, int l,
+                                               float4* rows, float4* sph) {
+    float M[12];
+    fk_warp(T, qw, lane, M);
+    const int src = l > 0 ? l - 1 : 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const float v = __shfl_sync(kFull, M[k], src);
+        M[k] = l > 0 ? v : T.base[k];
+    }
+    store_link(M, T.sph_local[l], rows, sph);
+}
+
+// One warp per (waypoint, link) pair; blockDim.x = 32 * TW * L.
+__global__ void __launch_bounds__(1024, 1) check_kernel(const __grid_constant__ CheckParams P) {
+    extern __shared__ float4 s_spheres[];        // tiles, then super-tiles (one bulk copy)
+    __shared__ unsigned s_best[kMaxWaypointsPerBlock];
+    __shared__ unsigned long long s_key[kMaxWaypointsPerBlock];
+    __shared__ unsigned s_done[kMaxWaypointsPerBlock];
+    __shared__ unsigned s_queue[32][64];
     __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ bool s_last;
 
     const LinkTable& T = P.T;
     const int L = T.L;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int w0 = blockIdx.x * TW;
-    const int nw = min(TW, P.W - w0);
-    const int pairs = nw * L;                  // <= 32 by construction of TW
+    const int tw = P.tw;
+    const int wl = warp / L, l = warp - wl * L;
+    const int w = blockIdx.x * tw + wl;
+    const int nw = min(tw, P.W - (int)blockIdx.x * tw);
     const int n_valid = *P.n_valid;
     const int n_tiles = (n_valid + 31) >> 5;
-    const int t_begin = min(n_tiles, (int)blockIdx.y * P.tiles_per_split);
-    const int t_end = min(n_tiles, t_begin + P.tiles_per_split);
-    const bool staged = P.stage_tiles && n_tiles > 0;
+    const int n_super = (n_tiles + 31) >> 5;
+    const bool staged = P.stage && n_tiles > 0;
 
-    // 0. start the copy of all tile spheres into shared memory
+    // 0. one thread starts the copy of all tile and super-tile spheres
     if (staged && threadIdx.x == 0) {
         mbar_init(&s_mbar, 1);
-        const unsigned bytes = (unsigned)n_tiles * (unsigned)sizeof(float4);
-        mbar_expect_tx(&s_mbar, bytes);
-        bulk_copy_g2s(s_tiles, P.tiles, bytes, &s_mbar);
+        const unsigned tb = (unsigned)n_tiles * (unsigned)sizeof(float4);
+        const unsigned sb = (unsigned)n_super * (unsigned)sizeof(float4);
+        mbar_expect_tx(&s_mbar, tb + sb);
+        bulk_copy_g2s(s_spheres, P.tiles, tb, &s_mbar);
+        bulk_copy_g2s(s_spheres + P.max_tiles, P.supers, sb, &s_mbar);
     }
-
-    // 1. forward kinematics, one warp per waypoint (overlaps the copy)
-    if (warp < nw) {
-        const float* qw = P.q + (size_t)(w0 + warp) * T.dof;
-        if (lane < T.dof && !isfinite(qw[lane])) atomicOr(P.status, kStatusNonFinite);
-        fk_links(T, qw, lane, s_xf[warp], s_sph[warp]);
-    }
-    if (threadIdx.x < TW) {
+    if (threadIdx.x < kMaxWaypointsPerBlock) {
         s_best[threadIdx.x] = kOrderedInf;
         s_key[threadIdx.x] = ~0ull;
+        s_done[threadIdx.x] = 0u;
     }
-    __syncthreads();
-    if (staged) {
-        const bool ok = mbar_wait_bounded(&s_mbar, 0);
-        if (!__syncthreads_and(ok)) {
-            // the copy did not complete: report it, give it one more bounded wait so
-            // no transfer into this block's shared memory is left in flight, leave
-            if (threadIdx.x == 0) {
-                atomicOr(P.status, kStatusTimeout);
-                mbar_wait_bounded(&s_mbar, 0);
-            }
-            return;
-        }
+    __syncthreads();   // the only block-wide barrier
+    if (wl >= nw) return;
+
+    // 1. forward kinematics; this warp keeps link l's pose in registers
+    const float* qw = P.q + (size_t)w * T.dof;
+    if (l == 0 && lane < T.dof && !isfinite(qw[lane])) atomicOr(P.status, kStatusNonFinite);
+    float4 rows[3], sph;
+    warp_link_pose(T, qw, lane, l, rows, &sph);
+    const float* G = T.values + (size_t)l * T.n * T.n * T.n;
+    const float4 g_o = T.grid_o[l];
+    const float g_h = T.grid_h[l];
+
+    if (staged && !mbar_wait_bounded(&s_mbar, 0)) {
+        // the copy did not complete in time: report, then leave this warp (the block
+        // stays resident until every warp has waited the same bounded time)
+        if (lane == 0) atomicOr(P.status, kStatusTimeout);
+        return;
     }
-    const float4* tiles = staged ? s_tiles : P.tiles;
+    const float4* tiles = staged ? s_spheres : P.tiles;
+    const float4* supers = staged ? s_spheres + P.max_tiles : P.supers;
 
-    unsigned long long lk[TW];
-#pragma unroll
-    for (int i = 0; i < TW; ++i) lk[i] = ~0ull;
-
-    auto evaluate = [&](int pos, int wl, int l) {
+    unsigned long long lk = ~0ull;
+    auto evaluate = [&](int pos) {
         const float4 p = __ldg(&P.sorted[pos]);
-        const float4 r0 = s_xf[wl][l][0], r1 = s_xf[wl][l][1], r2 = s_xf[wl][l][2];
-        const float lx = fmaf(r0.x, p.x, fmaf(r0.y, p.y, fmaf(r0.z, p.z, r0.w)));
-        const float ly = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
-        const float lz = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
-        const float g = grid_lookup(T.values + (size_t)l * T.n * T.n * T.n, T.n, T.grid_o[l],
-                                    T.grid_h[l], lx, ly, lz);
+        const float lx = fmaf(rows[0].x, p.x, fmaf(rows[0].y, p.y, fmaf(rows[0].z, p.z, rows[0].w)));
+        const float ly = fmaf(rows[1].x, p.x, fmaf(rows[1].y, p.y, fmaf(rows[1].z, p.z, rows[1].w)));
+        const float lz = fmaf(rows[2].x, p.x, fmaf(rows[2].y, p.y, fmaf(rows[2].z, p.z, rows[2].w)));
+        const float g = grid_lookup(G, T.n, g_o, g_h, lx, ly, lz);
         const unsigned long long key = pack_key(g, __float_as_int(p.w), l);
+        if (key < lk) lk = key;
         const unsigned ob = (unsigned)(key >> 32);
-#pragma unroll
-        for (int i = 0; i < TW; ++i)
-            if (i == wl && key < lk[i]) lk[i] = key;
         if (ob < s_best[wl]) atomicMin(&s_best[wl], ob);
     };
+    const float kInf = __int_as_float(0x7f800000);
+    auto threshold = [&]() -> float {   // best + R + slack: a distance from the sphere centre
+        if (!P.cull) return kInf;
+        const float t = from_ordered(s_best[wl]) + sph.w + kCullSlack;
+        return (t == t) ? t : kInf;
+    };
+    auto reach = [&](float4 c, float thr) -> bool {   // sphere c may hold a pair below the bound
+        const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
+        const float base = thr + c.w;
+        return base >= 0.f && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= base * base;
+    };
 
-    // this lane's (waypoint, link) pair for the lane-parallel tile tests
-    const bool has_pair = lane < pairs;
-    const int my_wl = has_pair ? lane / L : 0;
-    const int my_l = has_pair ? lane - my_wl * L : 0;
-    const float4 my_sph = s_sph[my_wl][my_l];
-
-    // 2. seed: per pair, the tile (over the whole cloud) whose farthest point is
-    //    nearest to the link's sphere centre is evaluated in full
-    if (P.cull) {
-        float best_s = __int_as_float(0x7f800000);
-        int best_t = -1;
-        for (int t = warp; t < n_tiles; t += kWarps) {
-            const float4 tc = tiles[t];
-            const float dx = tc.x - my_sph.x, dy = tc.y - my_sph.y, dz = tc.z - my_sph.z;
-            const float s = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + tc.w;
-            if (s < best_s) { best_s = s; best_t = t; }
+    // 2. seed: nearest super-tile, nearest tile in it, all its points
+    if (P.cull && n_tiles > 0) {
+        float bs = kInf;
+        int bi = 0x7fffffff;
+        for (int s0 = 0; s0 < n_super; s0 += 32) {
+            const int s = s0 + lane;
+            if (s < n_super) {
+                const float4 c = supers[s];
+                const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
+                const float sc = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + c.w;
+                if (sc < bs) { bs = sc; bi = s; }
+            }
         }
-        s_seed_s[warp][lane] = best_s;
-        s_seed_t[warp][lane] = best_t;
-        __syncthreads();
-        if (threadIdx.x < pairs) {
-            float bs = s_seed_s[0][threadIdx.x];
-            int bt = s_seed_t[0][threadIdx.x];
-            for (int k = 1; k < kWarps; ++k)
-                if (s_seed_s[k][threadIdx.x] < bs) { bs = s_seed_s[k][threadIdx.x]; bt = s_seed_t[k][threadIdx.x]; }
-            s_seed_t[0][threadIdx.x] = bt;
+        const int s_seed = warp_argmin(bs, bi);   // n_super..INT_MAX when every score is NaN
+        if (s_seed < n_super) {
+            const int t = s_seed * 32 + lane;
+            float ts = kInf;
+            if (t < n_tiles) {
+                const float4 c = tiles[t];
+                const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
+                ts = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + c.w;
+            }
+            const int t_seed = warp_argmin(ts, t < n_tiles ? t : 0x7fffffff);
+            if (t_seed < n_tiles && t_seed * 32 + lane < n_valid) evaluate(t_seed * 32 + lane);
         }
-        __syncthreads();
-        for (int e = warp; e < pairs; e += kWarps) {
-            const int t = s_seed_t[0][e];
-            if (t >= 0 && t * 32 + lane < n_valid) evaluate(t * 32 + lane, e / L, e % L);
-        }
-        __syncthreads();
     }
 
-    // 3. sweep, kTileBatch consecutive tiles per warp step: tile tests across pairs
-    //    (lanes), point loads for all surviving tiles together, then point tests
-    //    across lanes with survivor compaction
+    // 3. hierarchical sweep with survivor compaction
     unsigned* q = s_queue[warp];
     int qn = 0;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const float kInf = __int_as_float(0x7f800000);
-    for (int t0 = t_begin + warp * kTileBatch; t0 < t_end; t0 += kWarps * kTileBatch) {
-        // this lane's pair threshold: best + R + slack (a distance from the centre)
-        float thr = kInf;
-        if (P.cull && has_pair) {
-            unsigned ob = s_best[my_wl];
-            if (P.splits > 1) {
-                const unsigned long long gk = *reinterpret_cast<volatile unsigned long long*>(&P.keys[w0 + my_wl]);
-                ob = min(ob, (unsigned)(gk >> 32));
+    auto push_points = [&](const float4 (&pk)[kTileBatch], const int (&tk)[kTileBatch], int cnt, float thr) {
+#pragma unroll
+        for (int k = 0; k < kTileBatch; ++k) {
+            if (k >= cnt) break;
+            const int pos = tk[k] * 32 + lane;
+            const float dx = pk[k].x - sph.x, dy = pk[k].y - sph.y, dz = pk[k].z - sph.z;
+            const bool surv = pos < n_valid && thr >= 0.f && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= thr * thr;
+            const unsigned m = __ballot_sync(kFull, surv);
+            if (m) {
+                if (surv) q[qn + __popc(m & lt_mask)] = (unsigned)pos;
+                qn += __popc(m);
+                if (qn >= 32) {   // qn < 64: evaluate the top 32 entries with all lanes
+                    __syncwarp();
+                    const unsigned ent = q[qn - 32 + lane];
+                    __syncwarp();
+                    qn -= 32;
+                    evaluate((int)ent);
+                }
             }
-            thr = from_ordered(ob) + my_sph.w + kCullSlack;
-            if (!(thr == thr)) thr = kInf;
         }
-        unsigned tm[kTileBatch];
-        float4 pt[kTileBatch];
+    };
+    for (int s0 = 0; s0 < n_super; s0 += 32) {
+        float thr = threshold();
+        const int s = s0 + lane;
+        unsigned ms = __ballot_sync(kFull, s < n_super && reach(supers[min(s, n_super - 1)], thr));
+        while (ms) {
+            const int sidx = s0 + __ffs(ms) - 1;
+            ms &= ms - 1;
+            thr = threshold();
+            const int t = sidx * 32 + lane;
+            unsigned mt = __ballot_sync(kFull, t < n_tiles && reach(tiles[min(t, n_tiles - 1)], thr));
+            while (mt) {
+                // up to kTileBatch surviving tiles: issue their point loads together
+                int tk[kTileBatch];
+                float4 pk[kTileBatch];
+                int cnt = 0;
 #pragma unroll
-        for (int k = 0; k < kTileBatch; ++k) {
-            const int t = t0 + k;
-            bool ts = false;
-            if (has_pair && t < t_end) {
-                const float4 tc = tiles[t];
-                const float dx = tc.x - my_sph.x, dy = tc.y - my_sph.y, dz = tc.z - my_sph.z;
-                const float base = thr + tc.w;
-                ts = base >= 0.f && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= base * base;
-            }
-            tm[k] = __ballot_sync(kFull, ts);
-        }
-#pragma unroll
-        for (int k = 0; k < kTileBatch; ++k) {
-            const int pos = (t0 + k) * 32 + lane;
-            pt[k] = (tm[k] && pos < n_valid) ? __ldg(&P.sorted[pos]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int k = 0; k < kTileBatch; ++k) {
-            const int pos = (t0 + k) * 32 + lane;
-            const bool valid = pos < n_valid;
-            unsigned m_t = tm[k];
-            while (m_t) {
-                const int e = __ffs(m_t) - 1;
-                m_t &= m_t - 1;
-                const float te = __shfl_sync(kFull, thr, e);
-                const float4 s = s_sph[e / L][e % L];
-                const float dx = pt[k].x - s.x, dy = pt[k].y - s.y, dz = pt[k].z - s.z;
-                const bool surv = valid && te >= 0.f && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= te * te;
-                const unsigned m = __ballot_sync(kFull, surv);
-                if (m) {
-                    if (surv) q[qn + __popc(m & lt_mask)] = ((unsigned)pos << 8) | (unsigned)e;
-                    qn += __popc(m);
-                    if (qn >= 32) {
-                        __syncwarp();
-                        const unsigned ent = q[qn - 32 + lane];
-                        __syncwarp();
-                        qn -= 32;
-                        const int ee = (int)(ent & 255u);
-                        evaluate((int)(ent >> 8), ee / L, ee % L);
+                for (int k = 0; k < kTileBatch; ++k) {
+                    tk[k] = 0;
+                    if (mt) {
+                        tk[k] = sidx * 32 + __ffs(mt) - 1;
+                        mt &= mt - 1;
+                        cnt = k + 1;
                     }
                 }
+#pragma unroll
+                for (int k = 0; k < kTileBatch; ++k) {
+                    const int pos = tk[k] * 32 + lane;
+                    pk[k] = (k < cnt && pos < n_valid) ? __ldg(&P.sorted[pos]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                push_points(pk, tk, cnt, threshold());
             }
         }
     }
     __syncwarp();
-    if (lane < qn) {
-        const unsigned ent = q[lane];
-        const int ee = (int)(ent & 255u);
-        evaluate((int)(ent >> 8), ee / L, ee % L);
-    }
+    if (lane < qn) evaluate((int)q[lane]);
 
-    // 4. reduce keys: warp shuffle, then shared atomics
-#pragma unroll
-    for (int i = 0; i < TW; ++i) {
-        unsigned long long k = lk[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long other = __shfl_xor_sync(kFull, k, o);
-            k = other < k ? other : k;
+    // 4. reduce: warp min, shared atomicMin, last warp of the waypoint writes
+    lk = warp_min_u64(lk);
+    if (lane == 0) {
+        if (lk != ~0ull) atomicMin(&s_key[wl], lk);
+        __threadfence_block();
+        if (atomicAdd(&s_done[wl], 1u) == (unsigned)L - 1u) {
+            __threadfence_block();
+            write_result(P, w, atomicAdd(&s_key[wl], 0ull));
         }
-        if (lane == 0 && i < nw && k != ~0ull) atomicMin(&s_key[i], k);
     }
-    __syncthreads();
-
-    if (P.splits == 1) {
-        if (threadIdx.x < nw) write_result(P, w0 + threadIdx.x, s_key[threadIdx.x]);
-        return;
-    }
-    if (threadIdx.x < nw && s_key[threadIdx.x] != ~0ull) atomicMin(&P.keys[w0 + threadIdx.x], s_key[threadIdx.x]);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned ticket = atomicAdd(&P.tickets[blockIdx.x], 1u);
-        s_last = (ticket == (unsigned)P.splits - 1u);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (threadIdx.x < nw) {
-        const int w = w0 + threadIdx.x;
-        const unsigned long long key = atomicExch(&P.keys[w], ~0ull);   // read and reset
-        write_result(P, w, key);
-    }
-    if (threadIdx.x == 0) P.tickets[blockIdx.x] = 0u;
 }
 
 __global__ void __launch_bounds__(128) fk_kernel(const __grid_constant__ LinkTable T,
@@ -634,24 +675,20 @@ cudaError_t launch_prep(const PrepParams& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t configure_kernels() {
-    const int smem = kMaxStagedTiles * (int)sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(check_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(check_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(check_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return e;
+size_t staged_bytes(int max_tiles) {
+    return (size_t)(max_tiles + (max_tiles + 31) / 32) * sizeof(float4);
 }
 
-cudaError_t launch_check(const CheckParams& p, int tw, cudaStream_t s) {
-    const dim3 block(kBlock);
-    const dim3 grid((unsigned)((p.W + tw - 1) / tw), (unsigned)p.splits);
-    const size_t smem = p.stage_tiles ? (size_t)p.max_tiles * sizeof(float4) : 0;
-    switch (tw) {
-        case 1: check_kernel<1><<<grid, block, smem, s>>>(p); break;
-        case 2: check_kernel<2><<<grid, block, smem, s>>>(p); break;
-        case 4: check_kernel<4><<<grid, block, smem, s>>>(p); break;
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t configure_kernels() {
+    return cudaFuncSetAttribute(check_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)staged_bytes(kMaxStagedTiles));
+}
+
+cudaError_t launch_check(const CheckParams& p, cudaStream_t s) {
+    const dim3 block((unsigned)(32 * p.tw * p.T.L));
+    const dim3 grid((unsigned)((p.W + p.tw - 1) / p.tw));
+    const size_t smem = p.stage ? staged_bytes(p.max_tiles) : 0;
+    check_kernel<<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -11,8 +11,7 @@
 namespace sdf {
 
 constexpr int kMaxLinks = SDF_MAX_LINKS;
-constexpr int kBlock = 512;               // threads per check block (16 warps)
-constexpr int kWarps = kBlock / 32;
+constexpr int kMaxWaypointsPerBlock = 32;  // one warp per (waypoint, link): TW * L <= 32
 // Cull slack (metres): a pair is skipped only when its bounding-sphere lower bound
 // exceeds the best distance found so far by more than this, which covers the FP32
 // rounding of the transform, the sphere centre and the interpolation (~1e-6 m).
@@ -43,6 +42,7 @@ struct PrepParams {
     int stride;               // 3 or 4
     float4* sorted;           // N: x, y, z, original index (int bits); finite points only
     float4* tiles;            // ceil(N / 32): bounding sphere of each 32-point tile
+    float4* supers;           // ceil(N / 1024): bounding sphere of each 32-tile super-tile
     int* n_valid;             // number of finite points written to `sorted`
     int* status;
 };
@@ -51,19 +51,17 @@ struct CheckParams {
     LinkTable T;
     const float* q;           // W x dof
     int W;
+    int tw;                   // waypoints per block (block = 32 * tw * L threads)
     const float4* sorted;     // from PrepParams
     const float4* tiles;
+    const float4* supers;
     const int* n_valid;
-    int splits;               // tile chunks per waypoint tile (gridDim.y)
-    int tiles_per_split;
     int max_tiles;            // ceil(N / 32): tiles the scratch can hold
-    int stage_tiles;          // 1: copy the tile spheres to shared memory (max_tiles <= kMaxStagedTiles)
+    int stage;                // 1: copy tile and super-tile spheres to shared memory
     int cull;                 // 0: evaluate every pair
     float* dist;
     int32_t* arg_link;
     int32_t* arg_point;
-    unsigned long long* keys; // W packed keys (splits > 1), all ~0 between calls
-    unsigned int* tickets;    // per waypoint tile (splits > 1), all 0 between calls
     int* status;              // device status bits
 };
 
@@ -72,7 +70,7 @@ enum StatusBits : int { kStatusNonFinite = 1, kStatusTimeout = 2 };
 // Launchers (check.cu / grid_build.cu).  Return a cudaError_t of the launch.
 cudaError_t configure_kernels();           // once per device, that device current
 cudaError_t launch_prep(const PrepParams& p, cudaStream_t s);
-cudaError_t launch_check(const CheckParams& p, int tw, cudaStream_t s);
+cudaError_t launch_check(const CheckParams& p, cudaStream_t s);
 cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status,
                       cudaStream_t s);
 cudaError_t launch_grid_build(const float* tris9, const int* comp_off, int n_comp, int n_tris,
@@ -105,18 +103,15 @@ struct sdf_ctx {
     int cull = 1;
     int point_stride = 3;
     int tw = 0;
-    int splits = 0;
     int time_kernels = 0;
     // scratch owned by the context
     float4* sorted = nullptr;
     size_t sorted_cap = 0;
     float4* tiles = nullptr;
     size_t tiles_cap = 0;
+    float4* supers = nullptr;
+    size_t supers_cap = 0;
     int* n_valid = nullptr;
-    unsigned long long* keys = nullptr;
-    size_t keys_cap = 0;
-    unsigned int* tickets = nullptr;
-    size_t tickets_cap = 0;
     int* status = nullptr;
     // staging for check_trajectory_host
     float* st_q = nullptr;

@@ -4,7 +4,7 @@
 // break the cycle deadline, or a host process whose memory was reserved up front
 // and that is not allowed to grow it afterwards.
 //
-// Its scratch (sorted cloud, tile spheres, per-waypoint keys and tickets, counters)
+// Its scratch (sorted cloud, tile and super-tile spheres, counters)
 // lives in one file-scope device array of fixed size instead of memory obtained
 // from cudaMalloc.  Every GPU that loads this library holds the array until the
 // process exits.  The kernels are the same ones check_trajectory launches.
@@ -21,9 +21,8 @@ constexpr int kNoAllocMaxPoints = 65536;
 constexpr int kNoAllocMaxWaypoints = 4096;
 constexpr size_t kSortedOff = 0;
 constexpr size_t kTilesOff = kSortedOff + (size_t)kNoAllocMaxPoints * sizeof(float4);
-constexpr size_t kKeysOff = kTilesOff + (size_t)(kNoAllocMaxPoints / 32) * sizeof(float4);
-constexpr size_t kTicketsOff = kKeysOff + (size_t)kNoAllocMaxWaypoints * sizeof(unsigned long long);
-constexpr size_t kCountOff = kTicketsOff + (size_t)kNoAllocMaxWaypoints * sizeof(unsigned);
+constexpr size_t kSupersOff = kTilesOff + (size_t)(kNoAllocMaxPoints / 32) * sizeof(float4);
+constexpr size_t kCountOff = kSupersOff + (size_t)(kNoAllocMaxPoints / 1024) * sizeof(float4);
 constexpr size_t kStatusOff = kCountOff + 256;
 constexpr size_t kScratchBytes = kStatusOff + 256;   // about 1.1 MiB
 
@@ -38,7 +37,6 @@ struct PerDevice {
     std::once_flag once;
     cudaError_t err = cudaSuccess;
     unsigned char* base = nullptr;   // device address of g_noalloc_scratch on this device
-    int num_sms = 0;
 };
 constexpr int kMaxDevices = 64;
 PerDevice g_per_device[kMaxDevices];
@@ -46,8 +44,8 @@ PerDevice g_per_device[kMaxDevices];
 // Once per device, with that device current: look up the array's device address
 // and set the kernels' shared-memory limit (neither allocates).
 void setup_device(int dev, PerDevice* pd) {
+    (void)dev;
     pd->err = cudaGetSymbolAddress((void**)&pd->base, g_noalloc_scratch);
-    if (pd->err == cudaSuccess) pd->err = cudaDeviceGetAttribute(&pd->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (pd->err == cudaSuccess) pd->err = sdf::configure_kernels();
 }
 
@@ -76,20 +74,13 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
     if (rc == SDF_OK) {
         const cudaStream_t stream = (cudaStream_t)cuda_stream;
         const int L = R->table.L;
-        const int tw = (4 * L <= 32) ? 4 : (2 * L <= 32 ? 2 : 1);
-        const int wt = (W + tw - 1) / tw;
+        const int tw = 32 / L >= 2 ? 2 : 1;
         const int n_tiles = std::max(1, (N + 31) / 32);
-        int splits = std::min(std::max(1, (2 * pd->num_sms + wt - 1) / wt), n_tiles);
-        const int per = (n_tiles + splits - 1) / splits;
-        splits = (n_tiles + per - 1) / per;
-
-        unsigned long long* keys = reinterpret_cast<unsigned long long*>(pd->base + kKeysOff);
-        unsigned* tickets = reinterpret_cast<unsigned*>(pd->base + kTicketsOff);
         int* status = status_dev ? status_dev : reinterpret_cast<int*>(pd->base + kStatusOff);
-        // the array keeps the previous call's contents: reset what must start cleared
+        // the array keeps the previous call's contents: the prep kernel rewrites the
+        // sorted cloud, spheres and count before the check reads them; the status
+        // word must start cleared
         cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), stream);
-        if (e == cudaSuccess && splits > 1) e = cudaMemsetAsync(keys, 0xff, (size_t)W * sizeof(*keys), stream);
-        if (e == cudaSuccess && splits > 1) e = cudaMemsetAsync(tickets, 0, (size_t)wt * sizeof(*tickets), stream);
 
         sdf::PrepParams pp;
         pp.points = points_dev;
@@ -97,6 +88,7 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         pp.stride = 3;
         pp.sorted = reinterpret_cast<float4*>(pd->base + kSortedOff);
         pp.tiles = reinterpret_cast<float4*>(pd->base + kTilesOff);
+        pp.supers = reinterpret_cast<float4*>(pd->base + kSupersOff);
         pp.n_valid = reinterpret_cast<int*>(pd->base + kCountOff);
         pp.status = status;
 
@@ -104,23 +96,21 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         p.T = R->table;
         p.q = q_dev;
         p.W = W;
+        p.tw = tw;
         p.sorted = pp.sorted;
         p.tiles = pp.tiles;
+        p.supers = pp.supers;
         p.n_valid = pp.n_valid;
-        p.splits = splits;
-        p.tiles_per_split = per;
         p.max_tiles = n_tiles;
-        p.stage_tiles = n_tiles <= sdf::kMaxStagedTiles ? 1 : 0;
+        p.stage = n_tiles <= sdf::kMaxStagedTiles ? 1 : 0;
         p.cull = 1;
         p.dist = dist_dev;
         p.arg_link = argmin_link_dev;
         p.arg_point = argmin_point_dev;
-        p.keys = splits > 1 ? keys : nullptr;
-        p.tickets = splits > 1 ? tickets : nullptr;
         p.status = status;
 
         if (e == cudaSuccess) e = sdf::launch_prep(pp, stream);
-        if (e == cudaSuccess) e = sdf::launch_check(p, tw, stream);
+        if (e == cudaSuccess) e = sdf::launch_check(p, stream);
         if (e != cudaSuccess) rc = SDF_ERR_CUDA;
     }
     if (prev >= 0 && prev != R->device) cudaSetDevice(prev);
