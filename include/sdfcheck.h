@@ -52,6 +52,7 @@ extern "C" {
 #define SDF_MAX_LINKS 16          /* L = dof + 1 <= 16                                  */
 #define SDF_MAX_POINTS 16777215   /* N < 2^24 (point index packed with waypoint/link)  */
 #define SDF_MAX_RESOLUTION 512    /* grid nodes per axis                               */
+#define SDF_MAX_BATCH 128         /* trajectories per check_batch call                 */
 
 typedef struct sdf_ctx sdf_ctx;       /* device, stream, scratch, options          */
 typedef struct sdf_grids sdf_grids;   /* device Link SDF grids + per-link metadata */
@@ -103,8 +104,9 @@ const char* sdf_last_error(const sdf_ctx* ctx);
 /* Options (sdf_ctx_set_option / sdf_ctx_get_option). */
 #define SDF_OPT_CULL 1            /* 1 (default): bounding-sphere culling; 0: evaluate every pair */
 #define SDF_OPT_POINT_STRIDE 2    /* floats per point: 3 (default, x y z) or 4 (x y z pad)       */
-#define SDF_OPT_WAYPOINTS_PER_BLOCK 3 /* 0 (default) = automatic, else 1..32 with value x links <= 32 */
+#define SDF_OPT_WAYPOINTS_PER_BLOCK 3 /* waypoints per check block, 1..16; 0 (default) = 16 / links */
 #define SDF_OPT_TIME_KERNELS 6    /* 1: record CUDA events around the two kernels of a check      */
+#define SDF_OPT_STATS 7           /* 1: count culls/lookups and time kernel phases (adds atomics)  */
 int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t value);
 int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* value);
 
@@ -119,6 +121,30 @@ int sdf_ctx_synchronize(sdf_ctx* ctx);
 #define SDF_KERNEL_PREP 0
 #define SDF_KERNEL_CHECK 1
 int sdf_ctx_last_kernel_ms(sdf_ctx* ctx, int32_t kernel, float* ms);
+
+/* Statistics accumulated by checks while SDF_OPT_STATS is 1 (cleared by
+ * sdf_ctx_stats with reset != 0).  Counts are over all checks since the reset;
+ * times are sums (or maxima) over check blocks of %globaltimer nanoseconds.
+ * Fills min(n, SDF_STAT_COUNT) entries; synchronises. */
+#define SDF_STAT_PAIRS 0          /* (waypoint, link) pairs                        */
+#define SDF_STAT_SEED_LOOKUPS 1   /* lookups of the seed tiles                      */
+#define SDF_STAT_SUPER_TESTS 2    /* super-tile sphere tests                        */
+#define SDF_STAT_SUPER_PASS 3     /* super-tiles that survived                      */
+#define SDF_STAT_TILE_TESTS 4     /* tile sphere tests                              */
+#define SDF_STAT_TILE_PASS 5      /* (pair, tile) entries that survived             */
+#define SDF_STAT_POINT_TESTS 6    /* point sphere tests                             */
+#define SDF_STAT_LOOKUPS 7        /* grid lookups of surviving points (seed excluded) */
+#define SDF_STAT_LIST_OVERFLOW 8  /* entries tested in place (block list full)      */
+#define SDF_STAT_BLOCKS 9         /* check blocks                                   */
+#define SDF_STAT_NS_FK 10         /* sum over blocks: kinematics and staging        */
+#define SDF_STAT_NS_SEED 11       /* sum over blocks: seeding                       */
+#define SDF_STAT_NS_CULL 12       /* sum over blocks: super-tile and tile culls     */
+#define SDF_STAT_NS_POINTS 13     /* sum over blocks: point tests and lookups       */
+#define SDF_STAT_NS_BLOCK 14      /* sum over blocks: whole block                   */
+#define SDF_STAT_NS_BLOCK_MAX 15  /* longest block                                  */
+#define SDF_STAT_NS_SPAN 16       /* first block start to last block end (max over calls) */
+#define SDF_STAT_COUNT 20
+int sdf_ctx_stats(sdf_ctx* ctx, int64_t* out, int32_t n, int32_t reset);
 
 /* --------------------------------------------------------------------- grids */
 
@@ -174,17 +200,45 @@ int sdf_forward_kinematics(sdf_ctx* ctx, const sdf_robot* robot, const float* q_
  * smallest link; results equal to within FP32 rounding may pick either).
  *
  * q_dev: W x dof FP32 row-major.  points_dev: N x 3 FP32 (or N x 4 with
- * SDF_OPT_POINT_STRIDE = 4), 16-byte aligned.  Outputs: W entries each.
+ * SDF_OPT_POINT_STRIDE = 4, then 16-byte aligned).  Outputs: W entries each.
  * N = 0 gives dist = +inf and argmins = -1; W = 0 is a no-op.  Pairs whose value
  * is NaN are ignored; non-finite inputs also raise SDF_ERR_NONFINITE in
- * sdf_ctx_synchronize.  Asynchronous; enqueues two kernels (a spatial sort of
- * the points into 32-point tiles, then the check) and uses context-owned scratch
- * (about 17 bytes per point).
+ * sdf_ctx_synchronize.  Asynchronous: enqueues two kernels (a spatial sort of the
+ * points, then forward kinematics, culls, lookups and the reduction) and uses
+ * context-owned scratch (about 17 bytes per point), grown when a call needs more
+ * (which synchronises).
  * Errors: INVALID_ARG (NULL pointer with W, N > 0, N > SDF_MAX_POINTS, W < 0,
  * misaligned points), OOM (growing scratch), CUDA. */
 int check_trajectory(sdf_ctx* ctx, const sdf_robot* robot, const float* q_dev, int32_t W,
                      const float* points_dev, int32_t N, float* dist_dev,
                      int32_t* argmin_link_dev, int32_t* argmin_point_dev);
+
+/* One trajectory of a batch: the arguments of check_trajectory. */
+typedef struct {
+    const sdf_robot* robot;
+    const float* q_dev;
+    int32_t W;
+    const float* points_dev;
+    int32_t N;
+    float* dist_dev;
+    int32_t* argmin_link_dev;
+    int32_t* argmin_point_dev;
+} sdf_check_request;
+
+/* Batching (the paper batches all configurations of a trajectory, Sec. III-A;
+ * this batches trajectories too): n <= SDF_MAX_BATCH independent checks of
+ * uneven sizes -- each with its own robot (same device), trajectory and cloud --
+ * in one launch of the same two kernels: one cluster per request sorts its cloud,
+ * and the check blocks of all requests share one grid.
+ * Each request's results are exactly those check_trajectory gives it alone.
+ * Asynchronous; errors as check_trajectory (the message names the request). */
+int check_batch(sdf_ctx* ctx, const sdf_check_request* requests, int32_t n);
+
+/* Grow the context's scratch for launches of up to these totals (sums over a
+ * batch) so that later checks allocate nothing: a prerequisite for capturing
+ * check_trajectory / check_batch in a CUDA graph.  Synchronises. */
+int sdf_ctx_reserve(sdf_ctx* ctx, int64_t max_points, int64_t max_waypoints, int64_t max_pairs,
+                    int32_t max_requests);
 
 /* The same check on HOST buffers: copies q and points to context-owned device
  * staging buffers, runs check_trajectory, copies the three outputs back and
@@ -204,29 +258,25 @@ int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* robot, const float* q_h
  * synchronisation cudaMalloc/cudaFree can imply) would miss the cycle deadline,
  * or a process whose memory budget is fixed at start-up.  It needs no context:
  * it calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch is
- * one file-scope device array of about 1.1 MiB that every GPU loading this
+ * one file-scope device array of about 0.5 MiB that every GPU loading this
  * library holds until the process exits.
  *
- * Limits: W <= SDF_NOALLOC_MAX_WAYPOINTS and N <= SDF_NOALLOC_MAX_POINTS, else
- * SDF_ERR_INVALID_ARG (nothing is enqueued).  Points are N x 3 FP32; culling and
- * the block shape are the automatic defaults.
+ * Limits: N <= SDF_NOALLOC_MAX_POINTS, else SDF_ERR_INVALID_ARG (nothing is
+ * enqueued); W is not limited.  Points are N x 3 FP32; culling is on.
  *
  * robot: as for check_trajectory (its device is made current for the call).
  * cuda_stream: the cudaStream_t to enqueue on (NULL = legacy default stream).
  * status_dev: optional device int that the call clears and the kernels OR their
- *   status bits into (bit 0: a non-finite input was seen, bit 1: a bounded wait
- *   gave up and the results are invalid); NULL = not reported.
+ *   status bits into (bit 0: a non-finite input was seen); NULL = not reported.
  * Returns SDF_OK after enqueueing (asynchronous), SDF_ERR_INVALID_ARG or
  * SDF_ERR_CUDA (launch or set-up failure).
  *
- * The first call on each device looks up the array's device address and sets the
- * kernels' shared-memory limit; make that first call before any stream capture.
- * Every call shares the one array and it keeps the previous call's contents (the
- * call resets what must start cleared), so calls whose work overlaps on the GPU --
- * on different streams, or from different host threads -- race and must be
- * serialised by the caller. */
-#define SDF_NOALLOC_MAX_POINTS 65536
-#define SDF_NOALLOC_MAX_WAYPOINTS 4096
+ * The first call on each device looks up the array's device address; make that
+ * first call before any stream capture.  Every call shares the one array and it
+ * keeps the previous call's contents (the call resets what must start cleared),
+ * so calls whose work overlaps on the GPU -- on different streams, or from
+ * different host threads -- race and must be serialised by the caller. */
+#define SDF_NOALLOC_MAX_POINTS 32768
 int check_trajectory_noalloc(const sdf_robot* robot, void* cuda_stream, const float* q_dev, int32_t W,
                              const float* points_dev, int32_t N, float* dist_dev,
                              int32_t* argmin_link_dev, int32_t* argmin_point_dev, int32_t* status_dev);

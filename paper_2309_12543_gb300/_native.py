@@ -24,13 +24,14 @@ SDF_ERR_UNSUPPORTED = -5
 SDF_ERR_NONFINITE = -6
 SDF_MAX_LINKS = 16
 SDF_MAX_POINTS = 16777215
-SDF_NOALLOC_MAX_POINTS = 65536
-SDF_NOALLOC_MAX_WAYPOINTS = 4096
+SDF_NOALLOC_MAX_POINTS = 32768
+SDF_MAX_BATCH = 128
 
 SDF_OPT_CULL = 1
 SDF_OPT_POINT_STRIDE = 2
 SDF_OPT_WAYPOINTS_PER_BLOCK = 3
 SDF_OPT_TIME_KERNELS = 6
+SDF_OPT_STATS = 7
 SDF_KERNEL_PREP = 0
 SDF_KERNEL_CHECK = 1
 
@@ -54,6 +55,12 @@ class sdf_dh(ctypes.Structure):
     _fields_ = [(k, ctypes.c_float) for k in ("a", "alpha", "d", "theta_offset", "q_min", "q_max")]
 
 
+class sdf_check_request(ctypes.Structure):
+    _fields_ = [("robot", ctypes.c_void_p), ("q_dev", ctypes.c_void_p), ("W", ctypes.c_int32),
+                ("points_dev", ctypes.c_void_p), ("N", ctypes.c_int32), ("dist_dev", ctypes.c_void_p),
+                ("argmin_link_dev", ctypes.c_void_p), ("argmin_point_dev", ctypes.c_void_p)]
+
+
 class sdf_grid_meta(ctypes.Structure):
     _fields_ = [("origin", ctypes.c_float * 3), ("h", ctypes.c_float), ("n", ctypes.c_int32),
                 ("center", ctypes.c_float * 3), ("radius", ctypes.c_float), ("margin", ctypes.c_float)]
@@ -73,6 +80,7 @@ def _load():
         "sdf_ctx_set_option": (ctypes.c_int, [P, i32, i64]),
         "sdf_ctx_get_option": (ctypes.c_int, [P, i32, ctypes.POINTER(i64)]),
         "sdf_ctx_synchronize": (ctypes.c_int, [P]),
+        "sdf_ctx_stats": (ctypes.c_int, [P, P, i32, i32]),
         "sdf_ctx_last_kernel_ms": (ctypes.c_int, [P, i32, ctypes.POINTER(ctypes.c_float)]),
         "sdf_build_grids": (ctypes.c_int, [P, P, i32, i32, ctypes.c_float, ctypes.POINTER(P)]),
         "sdf_grids_upload": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(P)]),
@@ -85,6 +93,8 @@ def _load():
         "check_trajectory": (ctypes.c_int, [P, P, P, i32, P, i32, P, P, P]),
         "check_trajectory_host": (ctypes.c_int, [P, P, P, i32, P, i32, P, P, P]),
         "check_trajectory_noalloc": (ctypes.c_int, [P, P, P, i32, P, i32, P, P, P, P]),
+        "check_batch": (ctypes.c_int, [P, P, i32]),
+        "sdf_ctx_reserve": (ctypes.c_int, [P, i64, i64, i64, i32]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -98,10 +108,10 @@ lib = _load()
 # the symbols include/sdfcheck.h declares (tests check the export table against it)
 EXPORTED = ("sdf_ctx_create", "sdf_ctx_destroy", "sdf_ctx_set_stream", "sdf_last_error",
             "sdf_ctx_set_option", "sdf_ctx_get_option", "sdf_ctx_synchronize",
-            "sdf_ctx_last_kernel_ms", "sdf_build_grids", "sdf_grids_upload", "sdf_grids_download",
+            "sdf_ctx_last_kernel_ms", "sdf_ctx_stats", "sdf_build_grids", "sdf_grids_upload", "sdf_grids_download",
             "sdf_grids_info", "sdf_grids_destroy", "sdf_robot_create", "sdf_robot_destroy",
             "sdf_forward_kinematics", "check_trajectory", "check_trajectory_host",
-            "check_trajectory_noalloc")
+            "check_trajectory_noalloc", "check_batch", "sdf_ctx_reserve")
 
 
 def _ptr(x) -> int:
@@ -157,6 +167,16 @@ class Context:
 
     def last_error(self) -> str:
         return lib.sdf_last_error(self.handle).decode()
+
+    STAT_NAMES = ("pairs", "seed_lookups", "super_tests", "super_pass", "tile_tests", "tile_pass",
+                  "point_tests", "lookups", "list_overflow", "blocks", "ns_fk", "ns_seed", "ns_cull",
+                  "ns_points", "ns_block", "ns_block_max", "ns_span")
+
+    def stats(self, reset: bool = False) -> dict:
+        """Counters accumulated while SDF_OPT_STATS is on (see sdfcheck.h)."""
+        out = np.zeros(20, dtype=np.int64)
+        self._check(lib.sdf_ctx_stats(self.handle, _ptr(out), 20, int(reset)), "sdf_ctx_stats")
+        return {k: int(v) for k, v in zip(self.STAT_NAMES, out)}
 
     def last_kernel_ms(self, kernel: int = 1) -> float:
         """Device ms of SDF_KERNEL_PREP (0) or SDF_KERNEL_CHECK (1) of the last check."""
@@ -290,6 +310,21 @@ def check_trajectory(ctx: Context, robot: Robot, q_dev, W: int, points_dev, N: i
     ctx._check(lib.check_trajectory(ctx.handle, robot.handle, _ptr(q_dev), int(W), _ptr(points_dev),
                                     int(N), _ptr(dist_dev), _ptr(argmin_link_dev),
                                     _ptr(argmin_point_dev)), "check_trajectory")
+
+
+def check_batch(ctx: Context, requests) -> None:
+    """requests: sequence of (robot, q_dev, W, points_dev, N, dist_dev, link_dev, point_dev)."""
+    arr = (sdf_check_request * max(len(requests), 1))()
+    for i, (robot, q, W, pts, N, d, al, ap) in enumerate(requests):
+        arr[i] = sdf_check_request(robot.handle.value if hasattr(robot.handle, "value") else robot.handle,
+                                   _ptr(q), int(W), _ptr(pts), int(N), _ptr(d), _ptr(al), _ptr(ap))
+    ctx._check(lib.check_batch(ctx.handle, ctypes.addressof(arr), len(requests)), "check_batch")
+
+
+def sdf_ctx_reserve(ctx: Context, max_points: int, max_waypoints: int, max_pairs: int,
+                    max_requests: int) -> None:
+    ctx._check(lib.sdf_ctx_reserve(ctx.handle, int(max_points), int(max_waypoints), int(max_pairs),
+                                   int(max_requests)), "sdf_ctx_reserve")
 
 
 def check_trajectory_host(ctx: Context, robot: Robot, q_host, W: int, points_host, N: int, dist_host,

@@ -88,7 +88,6 @@ int sdf_ctx_create(sdf_ctx** out, int device, void* cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
     DeviceGuard g(device);
     if (cudaMalloc((void**)&ctx->status, sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->n_valid, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess ||
         cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
         cudaEventCreate(&ctx->ev2) != cudaSuccess) {
@@ -111,6 +110,7 @@ void sdf_ctx_destroy(sdf_ctx* ctx) {
     cudaFree(ctx->tiles);
     cudaFree(ctx->supers);
     cudaFree(ctx->n_valid);
+    cudaFree(ctx->d_stats);
     cudaFree(ctx->status);
     cudaFree(ctx->st_q);
     cudaFree(ctx->st_pts);
@@ -140,10 +140,21 @@ int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t v) {
             ctx->point_stride = (int)v;
             return SDF_OK;
         case SDF_OPT_WAYPOINTS_PER_BLOCK:
-            if (v < 0 || v > 32) return fail(ctx, SDF_ERR_INVALID_ARG, "waypoints per block must be 0..32");
+            if (v < 0 || v > sdf::kCheckWarps)
+                return fail(ctx, SDF_ERR_INVALID_ARG, "waypoints per block must be 0..%d", sdf::kCheckWarps);
             ctx->tw = (int)v;
             return SDF_OK;
         case SDF_OPT_TIME_KERNELS: ctx->time_kernels = v ? 1 : 0; return SDF_OK;
+        case SDF_OPT_STATS:
+            if (v && !ctx->d_stats) {
+                DeviceGuard g(ctx->device);
+                cudaError_t e = cudaMalloc((void**)&ctx->d_stats, sdf::kStatCount * sizeof(unsigned long long));
+                if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, sdf::kStatCount * sizeof(unsigned long long));
+                if (e == cudaSuccess) e = cudaMemset(ctx->d_stats + 17, 0xff, sizeof(unsigned long long));
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "statistics buffer");
+            }
+            ctx->stats = v ? 1 : 0;
+            return SDF_OK;
         default: return fail(ctx, SDF_ERR_INVALID_ARG, "unknown option %d", (int)key);
     }
 }
@@ -155,6 +166,7 @@ int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* v) {
         case SDF_OPT_POINT_STRIDE: *v = ctx->point_stride; return SDF_OK;
         case SDF_OPT_WAYPOINTS_PER_BLOCK: *v = ctx->tw; return SDF_OK;
         case SDF_OPT_TIME_KERNELS: *v = ctx->time_kernels; return SDF_OK;
+        case SDF_OPT_STATS: *v = ctx->stats; return SDF_OK;
         default: return SDF_ERR_INVALID_ARG;
     }
 }
@@ -172,6 +184,24 @@ int sdf_ctx_synchronize(sdf_ctx* ctx) {
         if (st & sdf::kStatusNonFinite)
             return fail(ctx, SDF_ERR_NONFINITE, "non-finite joint value or point in a check");
     }
+    return SDF_OK;
+}
+
+int sdf_ctx_stats(sdf_ctx* ctx, int64_t* out, int32_t n, int32_t reset) {
+    if (!ctx || (n > 0 && !out) || n < 0) return SDF_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    unsigned long long h[sdf::kStatCount] = {0};
+    if (ctx->d_stats) {
+        SDF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        SDF_CUDA(ctx, cudaMemcpy(h, ctx->d_stats, sizeof h, cudaMemcpyDeviceToHost));
+        if (reset) {
+            SDF_CUDA(ctx, cudaMemset(ctx->d_stats, 0, sizeof h));
+            SDF_CUDA(ctx, cudaMemset(ctx->d_stats + 17, 0xff, sizeof(unsigned long long)));
+        }
+        h[16] = h[18] > h[17] ? h[18] - h[17] : 0;   // first block start to last block end
+        h[17] = h[18] = 0;
+    }
+    for (int i = 0; i < n && i < sdf::kStatCount; ++i) out[i] = (int64_t)h[i];
     return SDF_OK;
 }
 
@@ -407,11 +437,25 @@ int sdf_robot_create(sdf_ctx* ctx, const sdf_dh* dh, int32_t dof, const float* b
         T.grid_h[l] = m.h;
     }
     T.values = grids->values;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaMalloc((void**)&R->d_table, sizeof(sdf::LinkTable));
+    if (e == cudaSuccess) e = cudaMemcpy(R->d_table, &T, sizeof(sdf::LinkTable), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        sdf_robot_destroy(R);
+        return cuda_fail(ctx, e, "robot table upload");
+    }
     *out = R;
     return SDF_OK;
 }
 
-void sdf_robot_destroy(sdf_robot* R) { delete R; }
+void sdf_robot_destroy(sdf_robot* R) {
+    if (!R) return;
+    if (R->d_table) {
+        DeviceGuard g(R->device);
+        cudaFree(R->d_table);
+    }
+    delete R;
+}
 
 int sdf_forward_kinematics(sdf_ctx* ctx, const sdf_robot* R, const float* q_dev, int32_t W, float* out_dev) {
     if (!ctx || !R || W < 0) return SDF_ERR_INVALID_ARG;
@@ -426,72 +470,132 @@ int sdf_forward_kinematics(sdf_ctx* ctx, const sdf_robot* R, const float* q_dev,
 
 // -------------------------------------------------------------------- check
 
-// Waypoints per block (one warp per waypoint and link, so TW * L <= 32).
-static int choose_tw(const sdf_ctx* ctx, int L) {
-    if (ctx->tw > 0) return ctx->tw;
-    return 32 / L >= 2 ? 2 : 1;
+// ------------------------------------------------------------------ batches
+
+static int validate_request(sdf_ctx* ctx, const sdf_check_request& r, int idx) {
+    if (!r.robot) return fail(ctx, SDF_ERR_INVALID_ARG, "request %d: null robot", idx);
+    if (r.robot->device != ctx->device) return fail(ctx, SDF_ERR_INVALID_ARG, "request %d: robot on another device", idx);
+    if (r.W < 0 || r.N < 0) return fail(ctx, SDF_ERR_INVALID_ARG, "request %d: negative size", idx);
+    if (r.N > SDF_MAX_POINTS) return fail(ctx, SDF_ERR_INVALID_ARG, "request %d: N > %d", idx, SDF_MAX_POINTS);
+    if (r.W == 0) return SDF_OK;
+    if (!r.dist_dev || !r.argmin_link_dev || !r.argmin_point_dev || (r.robot->dof > 0 && !r.q_dev) ||
+        (r.N > 0 && !r.points_dev))
+        return fail(ctx, SDF_ERR_INVALID_ARG, "request %d: null buffer", idx);
+    const uintptr_t pa = reinterpret_cast<uintptr_t>(r.points_dev);
+    if ((ctx->point_stride == 4 && (pa & 15u) != 0) || (pa & 3u) != 0)
+        return fail(ctx, SDF_ERR_INVALID_ARG, "request %d: points misaligned", idx);
+    return SDF_OK;
+}
+
+// Scratch for up to the given totals; growth synchronises the device, so a launch
+// that fits needs no allocation (and can be captured in a CUDA graph).
+static int reserve_scratch(sdf_ctx* ctx, size_t points, size_t tiles, size_t supers, size_t instances) {
+    int rc = grow(ctx, &ctx->sorted, &ctx->sorted_cap, std::max<size_t>(points, 1), false);
+    if (rc == SDF_OK) rc = grow(ctx, &ctx->tiles, &ctx->tiles_cap, std::max<size_t>(tiles, 1), false);
+    if (rc == SDF_OK) rc = grow(ctx, &ctx->supers, &ctx->supers_cap, std::max<size_t>(supers, 1), false);
+    if (rc == SDF_OK) rc = grow(ctx, &ctx->n_valid, &ctx->n_valid_cap, std::max<size_t>(instances, 1), false);
+    return rc;
+}
+
+int sdf_ctx_reserve(sdf_ctx* ctx, int64_t max_points, int64_t max_waypoints, int64_t max_pairs, int32_t max_requests) {
+    if (!ctx || max_points < 0 || max_waypoints < 0 || max_pairs < 0 || max_requests < 0 || max_requests > SDF_MAX_BATCH)
+        return SDF_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    const size_t P = (size_t)max_points, R = (size_t)std::max(max_requests, 1);
+    const size_t tiles = (P + 31) / 32 + R, supers = tiles / 32 + R;
+    return reserve_scratch(ctx, P, tiles, supers, R);
+}
+
+// Waypoints per check block for a robot with L links: one warp per (waypoint, link).
+static int block_waypoints(const sdf_ctx* ctx, int L) {
+    const int fit = std::max(1, sdf::kCheckWarps / L);
+    return ctx->tw > 0 ? std::min(ctx->tw, fit) : fit;
+}
+
+int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
+    if (!ctx) return SDF_ERR_INVALID_ARG;
+    if (n < 0 || n > SDF_MAX_BATCH) return fail(ctx, SDF_ERR_INVALID_ARG, "batch size must be 0..%d", SDF_MAX_BATCH);
+    if (n > 0 && !reqs) return fail(ctx, SDF_ERR_INVALID_ARG, "null request array");
+    for (int i = 0; i < n; ++i) {
+        const int rc = validate_request(ctx, reqs[i], i);
+        if (rc != SDF_OK) return rc;
+    }
+    sdf::BatchParams* p = new (std::nothrow) sdf::BatchParams();
+    if (!p) return fail(ctx, SDF_ERR_OOM, "host allocation");
+    size_t points = 0, tiles = 0, supers = 0, blocks = 0, max_tiles = 0;
+    int k = 0;
+    for (int i = 0; i < n; ++i) {
+        const sdf_check_request& r = reqs[i];
+        if (r.W == 0) continue;
+        sdf::InstDesc& I = p->inst[k++];
+        I.robot = r.robot->d_table;
+        I.q = r.q_dev;
+        I.points = r.points_dev;
+        I.dist = r.dist_dev;
+        I.arg_link = r.argmin_link_dev;
+        I.arg_point = r.argmin_point_dev;
+        I.W = r.W;
+        I.N = r.N;
+        I.L = r.robot->table.L;
+        I.dof = r.robot->dof;
+        I.point_base = (int)points;
+        I.tile_base = (int)tiles;
+        I.super_base = (int)supers;
+        I.tw = block_waypoints(ctx, I.L);
+        I.block_base = (int)blocks;
+        const size_t nt = ((size_t)r.N + 31) / 32;
+        points += (size_t)r.N;
+        tiles += nt;
+        supers += (nt + 31) / 32;
+        blocks += ((size_t)r.W + I.tw - 1) / I.tw;
+        max_tiles = std::max(max_tiles, nt);
+    }
+    if (k == 0 || points > (size_t)INT32_MAX || blocks > (size_t)INT32_MAX) {
+        delete p;
+        return k == 0 ? SDF_OK : fail(ctx, SDF_ERR_INVALID_ARG, "batch too large");
+    }
+    DeviceGuard g(ctx->device);
+    int rc = reserve_scratch(ctx, points, tiles, supers, (size_t)k);
+    if (rc != SDF_OK) {
+        delete p;
+        return rc;
+    }
+    p->n_inst = k;
+    p->n_blocks = (int)blocks;
+    p->stride = ctx->point_stride;
+    p->cull = ctx->cull;
+    p->stage_tiles = (int)std::min<size_t>(max_tiles, (size_t)sdf::kMaxStagedTiles);
+    p->sorted = ctx->sorted;
+    p->tiles = ctx->tiles;
+    p->supers = ctx->supers;
+    p->n_valid = ctx->n_valid;
+    p->status = ctx->status;
+    p->stats = ctx->stats ? ctx->d_stats : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (ctx->time_kernels) e = cudaEventRecord(ctx->ev0, ctx->stream);
+    if (e == cudaSuccess) e = sdf::launch_batch(*p, ctx->stream, ctx->time_kernels ? ctx->ev1 : nullptr);
+    if (e == cudaSuccess && ctx->time_kernels) {
+        e = cudaEventRecord(ctx->ev2, ctx->stream);
+        ctx->timed_valid = true;
+    }
+    delete p;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "check launch");
+    return SDF_OK;
 }
 
 int check_trajectory(sdf_ctx* ctx, const sdf_robot* R, const float* q_dev, int32_t W, const float* points_dev,
                      int32_t N, float* dist_dev, int32_t* argmin_link_dev, int32_t* argmin_point_dev) {
     if (!ctx || !R) return SDF_ERR_INVALID_ARG;
-    if (W < 0 || N < 0) return fail(ctx, SDF_ERR_INVALID_ARG, "negative size");
-    if (N > SDF_MAX_POINTS) return fail(ctx, SDF_ERR_INVALID_ARG, "N > %d", SDF_MAX_POINTS);
-    if (W == 0) return SDF_OK;
-    if (!dist_dev || !argmin_link_dev || !argmin_point_dev || (R->dof > 0 && !q_dev) || (N > 0 && !points_dev))
-        return fail(ctx, SDF_ERR_INVALID_ARG, "null buffer");
-    if (ctx->point_stride == 4 && (reinterpret_cast<uintptr_t>(points_dev) & 15u) != 0)
-        return fail(ctx, SDF_ERR_INVALID_ARG, "points must be 16-byte aligned");
-    if ((reinterpret_cast<uintptr_t>(points_dev) & 3u) != 0)
-        return fail(ctx, SDF_ERR_INVALID_ARG, "points must be 4-byte aligned");
-    const int L = R->table.L;
-    const int tw = choose_tw(ctx, L);
-    if (tw * L > 32)
-        return fail(ctx, SDF_ERR_INVALID_ARG, "%d waypoints per block x %d links exceeds 32 warps", tw, L);
-    DeviceGuard g(ctx->device);
-    const size_t n_tiles = (size_t)std::max(1, (N + 31) / 32);
-    const size_t n_super = (n_tiles + 31) / 32;
-    int rc = grow(ctx, &ctx->sorted, &ctx->sorted_cap, (size_t)std::max(N, 1), false);
-    if (rc == SDF_OK) rc = grow(ctx, &ctx->tiles, &ctx->tiles_cap, n_tiles, false);
-    if (rc == SDF_OK) rc = grow(ctx, &ctx->supers, &ctx->supers_cap, n_super, false);
-    if (rc != SDF_OK) return rc;
-
-    sdf::PrepParams pp;
-    pp.points = points_dev;
-    pp.N = N;
-    pp.stride = ctx->point_stride;
-    pp.sorted = ctx->sorted;
-    pp.tiles = ctx->tiles;
-    pp.supers = ctx->supers;
-    pp.n_valid = ctx->n_valid;
-    pp.status = ctx->status;
-
-    sdf::CheckParams p;
-    p.T = R->table;
-    p.q = q_dev;
-    p.W = W;
-    p.tw = tw;
-    p.sorted = ctx->sorted;
-    p.tiles = ctx->tiles;
-    p.supers = ctx->supers;
-    p.n_valid = ctx->n_valid;
-    p.max_tiles = (int)n_tiles;
-    p.stage = n_tiles <= (size_t)sdf::kMaxStagedTiles ? 1 : 0;
-    p.cull = ctx->cull;
-    p.dist = dist_dev;
-    p.arg_link = argmin_link_dev;
-    p.arg_point = argmin_point_dev;
-    p.status = ctx->status;
-
-    if (ctx->time_kernels) SDF_CUDA(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
-    SDF_CUDA(ctx, sdf::launch_prep(pp, ctx->stream));
-    if (ctx->time_kernels) SDF_CUDA(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
-    SDF_CUDA(ctx, sdf::launch_check(p, ctx->stream));
-    if (ctx->time_kernels) {
-        SDF_CUDA(ctx, cudaEventRecord(ctx->ev2, ctx->stream));
-        ctx->timed_valid = true;
-    }
-    return SDF_OK;
+    sdf_check_request r;
+    r.robot = R;
+    r.q_dev = q_dev;
+    r.W = W;
+    r.points_dev = points_dev;
+    r.N = N;
+    r.dist_dev = dist_dev;
+    r.argmin_link_dev = argmin_link_dev;
+    r.argmin_point_dev = argmin_point_dev;
+    return check_batch(ctx, &r, 1);
 }
 
 int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* R, const float* q_host, int32_t W,

@@ -1,39 +1,35 @@
-// Runtime distance check for sm_103a: a spatial sort of the obstacle cloud, then
-// one fused kernel for forward kinematics, culling, transform, lookup and the
-// per-waypoint min.
+// Runtime distance check for sm_103a, for one trajectory or a batch of them.
+// Two kernels per launch:
 //
-// cloud_prep_kernel (one cluster of 8 CTAs x 1024 threads) orders the points in
-// space: bounding box, 32^3-cell Morton key per point, counting sort of the keys
-// in distributed shared memory, scatter into a float4 array (x, y, z, original
-// index), then a bounding sphere per tile of 32 consecutive sorted points and per
-// super-tile of 32 consecutive tiles.  Non-finite points are dropped from the
-// sorted cloud (and flagged), so they can never be a minimum.
+// prep_kernel -- one thread-block cluster (8 CTAs x 1024 threads) per trajectory
+//   sorts its obstacle points in space: bounding box, 32^3-cell Morton key,
+//   counting sort in distributed shared memory, scatter into float4 (x, y, z,
+//   original index); then a bounding sphere per tile of 32 sorted points and per
+//   super-tile of 32 tiles.  Non-finite points are dropped (and flagged).
+// check_kernel -- one block per (trajectory, group of waypoints); the trajectory's
+//   tile and super-tile spheres reach shared memory by one TMA bulk copy that
+//   completes on an mbarrier (bounded wait).
+//   Phase A, one warp per (waypoint, link) pair:
+//   * forward kinematics (Sec. III-A "parallel forward kinematics"): lanes build
+//     the DH joint transforms and a warp scan composes them; the pair's
+//     link-from-world transform and world bounding sphere go to shared memory;
+//   * seed: the tile whose farthest point is nearest to the link's sphere centre
+//     is evaluated in full, which makes the waypoint's best value (a shared-memory
+//     atomic shared by the waypoint's warps) a tight upper bound early;
+//   * culls super-tiles, then tiles, with ||c - c_link|| - r - R_link > best + slack
+//     (the analogue of the paper's "grids in sphere", Sec. III-B); every surviving
+//     (pair, tile) goes to a block-wide list in shared memory.
+//   Phase B, all warps of the block: entries are taken from the list a few at a time
+//   (loads issued together), the tile's points are tested against the pair's
+//   sphere, survivors are compacted into a per-warp queue and evaluated 32 at a
+//   time: transform into the link frame (the per-point form of Sec. II-B / Fig.
+//   2), trilinear lookup in the FP32 link grid (the grid-sample interpolation of
+//   Sec. III-A), distance to the grid box outside it.  Each value is folded into
+//   the waypoint's minimum (Sec. III-A) as a 64-bit key whose unsigned order is
+//   (distance, point, link), so atomicMin gives a deterministic arg-min.
 //
-// check_kernel: one warp per (waypoint, link) pair; a block holds the pairs of TW
-// waypoints.  Each warp, with no block-wide barrier after set-up:
-//   1. forward kinematics (Sec. III-A "parallel forward kinematics"): lanes build
-//      one DH joint transform each and a warp scan composes them; the warp keeps
-//      its link's link-from-world transform and world bounding-sphere centre in
-//      registers;
-//   2. seed: evaluates the tile whose farthest point is nearest to its link's
-//      sphere centre, which makes the waypoint's best value (shared by the
-//      waypoint's warps through a shared-memory atomic) a tight upper bound;
-//   3. walks super-tiles -> tiles -> points, lanes over the children, skipping
-//      every sphere with ||c - c_link|| - r - R_link > best + slack (the analogue
-//      of the paper's "grids in sphere", Sec. III-B).  Surviving points are
-//      compacted into a per-warp queue and evaluated 32 at a time: transform into
-//      the link frame (the per-point form of Sec. II-B / Fig. 2), trilinear lookup
-//      in the FP32 link grid (the grid-sample interpolation of Sec. III-A),
-//      distance to the grid box outside it;
-//   4. reduction with min per waypoint (Sec. III-A): each value is packed with its
-//      original point index and link into one 64-bit key whose unsigned order is
-//      (distance, point, link); warp shuffles, a shared-memory atomicMin, and the
-//      waypoint's last warp writes the decoded result.
-// The tile and super-tile spheres reach shared memory by one TMA bulk copy that
-// completes on an mbarrier (with a bounded wait).
-//
-// The culls are exact: a skipped pair's interpolated distance exceeds the best
-// value already found by more than the FP32 rounding of the bound, so culled and
+// The culls are exact: a skipped pair's interpolated distance exceeds a value
+// already found by more than the FP32 rounding of the bound, so culled and
 // unculled runs give bit-identical results.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -48,6 +44,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kOrderedInf = 0xff800000u;   // ordered_bits(+inf): "no value yet"
+constexpr int kCells = 32768;                       // 32^3 Morton cells for the cloud sort
 constexpr int kPrepThreads = 1024;
 constexpr int kPrepCtas = 8;                        // one portable-size cluster
 constexpr int kBinsPerCta = kCells / kPrepCtas;
@@ -171,27 +168,6 @@ __device__ __forceinline__ unsigned long long pack_key(float g, int point, int l
     return ((unsigned long long)ordered_bits(g) << 32) | ((unsigned)point << 4) | (unsigned)link;
 }
 
-__device__ __forceinline__ void write_result(const CheckParams& P, int w, unsigned long long key) {
-    if (key == ~0ull) {
-        P.dist[w] = __int_as_float(0x7f800000);
-        P.arg_link[w] = -1;
-        P.arg_point[w] = -1;
-    } else {
-        P.dist[w] = from_ordered((unsigned)(key >> 32));
-        P.arg_link[w] = (int)(key & 15u);
-        P.arg_point[w] = (int)((key & 0xffffffffu) >> 4);
-    }
-}
-
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(kFull, k, o);
-        k = other < k ? other : k;
-    }
-    return k;
-}
-
 // (score, index) arg-min across the warp; ties go to the smaller index.
 __device__ __forceinline__ int warp_argmin(float s, int idx) {
 #pragma unroll
@@ -236,14 +212,19 @@ __device__ __forceinline__ float block_reduce(float v, float* s_tmp, Op op) {
 struct FMin { __device__ float operator()(float a, float b) const { return fminf(a, b); } };
 struct FMax { __device__ float operator()(float a, float b) const { return fmaxf(a, b); } };
 
-// Spatial sort of the cloud by one thread-block cluster: the 32^3 cell counters
-// are spread over the CTAs' shared memory (distributed shared memory), so every
-// phase is one pass over the points with cluster barriers in between.  Up to
-// kPrepCached points per thread stay in registers between the passes.
+
+// ------------------------------------------------------------------ prep kernel
+
+// One cluster per trajectory sorts its cloud: 32^3 cell counters spread over the
+// CTAs' shared memory, every phase one pass over the points with cluster barriers
+// in between; up to kPrepCached points per thread stay in registers between the
+// passes.
 __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads, 1)
-    cloud_prep_kernel(const __grid_constant__ PrepParams P) {
+    prep_kernel(const __grid_constant__ BatchParams P) {
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned rank = cluster.block_rank();
+    const int inst = blockIdx.x / kPrepCtas;
+    const InstDesc& I = P.inst[inst];
     __shared__ unsigned s_bins[kBinsPerCta];     // counters, then cursors, of this CTA's cells
     __shared__ float s_tmp[32];
     __shared__ float s_box[6];
@@ -252,26 +233,28 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gtid = (int)rank * kPrepThreads + tid;
     constexpr int kStride = kPrepCtas * kPrepThreads;
+    constexpr int kClusterWarps = kPrepCtas * (kPrepThreads / 32);
     const float kInf = __int_as_float(0x7f800000);
-    const bool cached = P.N <= kStride * kPrepCached;
+    const int N = I.N;
+    const float* pts = I.points;
+    const bool cached = N <= kStride * kPrepCached;
 
     float3 pc[kPrepCached];
 #pragma unroll
     for (int k = 0; k < kPrepCached; ++k) {
         const int i = gtid + k * kStride;
-        pc[k] = (cached && i < P.N) ? load_point(P.points, P.stride, i) : make_float3(0.f, 0.f, 0.f);
+        pc[k] = (cached && i < N) ? load_point(pts, P.stride, i) : make_float3(0.f, 0.f, 0.f);
     }
-    auto point_at = [&](int k, int i) -> float3 { return cached ? pc[k] : load_point(P.points, P.stride, i); };
-    // visits every point index of this thread: f(point, index)
+
     auto for_each_point = [&](auto&& f) {
         if (cached) {
 #pragma unroll
             for (int k = 0; k < kPrepCached; ++k) {
                 const int i = gtid + k * kStride;
-                if (i < P.N) f(point_at(k, i), i);
+                if (i < N) f(pc[k], i);
             }
         } else {
-            for (int i = gtid; i < P.N; i += kStride) f(load_point(P.points, P.stride, i), i);
+            for (int i = gtid; i < N; i += kStride) f(load_point(pts, P.stride, i), i);
         }
     };
 
@@ -315,7 +298,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     cluster.sync();
 
     // 3. exclusive scan of this CTA's cells (warp w owns a contiguous run), then
-    //    the CTA totals of lower ranks give the CTA's global offset
+    //    the CTA totals of lower ranks give the CTA's offset
     constexpr int kPerWarp = kBinsPerCta / (kPrepThreads / 32);
     unsigned running = 0;
     for (int k = 0; k < kPerWarp; k += 32) {
@@ -357,23 +340,23 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     cluster.sync();
 
     // 4. scatter (order inside a cell is arbitrary; keys carry the original index)
+    float4* sorted = P.sorted + I.point_base;
     for_each_point([&](float3 p, int i) {
         if (finite3(p)) {
             const unsigned c = cell_key(p, blo, inv);
             const unsigned pos = atomicAdd(cluster.map_shared_rank(&s_bins[c % kBinsPerCta], (int)(c / kBinsPerCta)), 1u);
-            P.sorted[pos] = make_float4(p.x, p.y, p.z, __int_as_float(i));
+            sorted[pos] = make_float4(p.x, p.y, p.z, __int_as_float(i));
         }
     });
-    // the cluster barrier orders these writes before the reads below (cluster scope)
-    cluster.sync();
+    cluster.sync();   // orders the scatter before the reads below (cluster scope)
 
     // 5. tile spheres: centre of the tile's box, radius to its farthest point
     const int n_tiles = (n_valid + 31) >> 5;
-    constexpr int kClusterWarps = kPrepCtas * (kPrepThreads / 32);
+    float4* tiles = P.tiles + I.tile_base;
     for (int t = (int)rank * (kPrepThreads / 32) + warp; t < n_tiles; t += kClusterWarps) {
         const int i = t * 32 + lane;
         const bool v = i < n_valid;
-        const float4 p = v ? __ldcg(&P.sorted[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 p = v ? __ldcg(&sorted[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
         float mn[3] = {v ? p.x : kInf, v ? p.y : kInf, v ? p.z : kInf};
         float mx[3] = {v ? p.x : -kInf, v ? p.y : -kInf, v ? p.z : -kInf};
 #pragma unroll
@@ -387,17 +370,18 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         float r2 = v ? (p.x - cx) * (p.x - cx) + (p.y - cy) * (p.y - cy) + (p.z - cz) * (p.z - cz) : 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(kFull, r2, o));
-        if (lane == 0) P.tiles[t] = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-6f) + 1e-7f);
+        if (lane == 0) tiles[t] = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-6f) + 1e-7f);
     }
     cluster.sync();
 
     // 6. super-tile spheres over 32 consecutive tiles: box of the tile spheres,
     //    radius to the farthest tile sphere
     const int n_super = (n_tiles + 31) >> 5;
+    float4* supers = P.supers + I.super_base;
     for (int s = (int)rank * (kPrepThreads / 32) + warp; s < n_super; s += kClusterWarps) {
         const int t = s * 32 + lane;
         const bool v = t < n_tiles;
-        const float4 c = v ? __ldcg(&P.tiles[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 c = v ? __ldcg(&tiles[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
         float mn[3] = {v ? c.x - c.w : kInf, v ? c.y - c.w : kInf, v ? c.z - c.w : kInf};
         float mx[3] = {v ? c.x + c.w : -kInf, v ? c.y + c.w : -kInf, v ? c.z + c.w : -kInf};
 #pragma unroll
@@ -411,9 +395,9 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         float r = v ? sqrtf((c.x - cx) * (c.x - cx) + (c.y - cy) * (c.y - cy) + (c.z - cz) * (c.z - cz)) + c.w : 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(kFull, r, o));
-        if (lane == 0) P.supers[s] = make_float4(cx, cy, cz, r * (1.f + 1e-6f) + 1e-7f);
+        if (lane == 0) supers[s] = make_float4(cx, cy, cz, r * (1.f + 1e-6f) + 1e-7f);
     }
-    if (rank == 0 && tid == 0) *P.n_valid = n_valid;
+    if (rank == 0 && tid == 0) P.n_valid[inst] = n_valid;
 }
 
 // ---- TMA bulk copy (global -> shared) completing on an mbarrier ----------------
@@ -452,7 +436,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
-// The link-from-world rows and world sphere of link l for waypoint w, computed by
+// The link-from-world rows and world sphere of link l for one waypoint, computed by
 // the whole warp (every lane ends with the same values).
 __device__ __forceinline__ void warp_link_pose(const LinkTable& T, const float* qw, int lane, int l,
                                                float4* rows, float4* sph) {
@@ -467,182 +451,374 @@ __device__ __forceinline__ void warp_link_pose(const LinkTable& T, const float* 
     store_link(M, T.sph_local[l], rows, sph);
 }
 
-// One warp per (waypoint, link) pair; blockDim.x = 32 * TW * L.
-__global__ void __launch_bounds__(1024, 1) check_kernel(const __grid_constant__ CheckParams P) {
-    extern __shared__ float4 s_spheres[];        // tiles, then super-tiles (one bulk copy)
-    __shared__ unsigned s_best[kMaxWaypointsPerBlock];
-    __shared__ unsigned long long s_key[kMaxWaypointsPerBlock];
-    __shared__ unsigned s_done[kMaxWaypointsPerBlock];
-    __shared__ unsigned s_queue[32][64];
-    __shared__ __align__(8) uint64_t s_mbar;
+// ------------------------------------------------------------------ check kernel
 
-    const LinkTable& T = P.T;
-    const int L = T.L;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tw = P.tw;
-    const int wl = warp / L, l = warp - wl * L;
-    const int w = blockIdx.x * tw + wl;
-    const int nw = min(tw, P.W - (int)blockIdx.x * tw);
-    const int n_valid = *P.n_valid;
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// per-warp statistics rows (SDF_OPT_STATS), written by lane 0 of their warp
+enum WarpStat { kWsSeed, kWsSuperT, kWsSuperP, kWsTileT, kWsTileP, kWsPointT, kWsLookups, kWsOver, kWsCount };
+enum WarpNs { kWnSeed, kWnCull, kWnPoints, kWnCount };
+
+constexpr unsigned kTileMask = (1u << 28) - 1u;     // tile index of a list entry
+
+struct BlockState {
+    const float4* sorted;      // this trajectory's sorted points
+    const float* values;       // this robot's grids
+    int n, L, n_valid;
+    float4 (*pose)[4];         // per pair: rows[3], sphere
+    const float4* grid_o;      // per link (shared memory)
+    const float* grid_h;
+    unsigned* best;            // per waypoint of the block
+    unsigned long long* key;
+    int cull;
+    unsigned* stat;            // this warp's statistics row, or null
+};
+
+__device__ __forceinline__ void stat_add(const BlockState& B, int idx, unsigned v, int lane) {
+    if (B.stat && lane == 0) B.stat[idx] += v;
+}
+
+__device__ __forceinline__ float pair_threshold(const BlockState& B, int pair) {
+    if (!B.cull) return __int_as_float(0x7f800000);
+    const float t = from_ordered(B.best[pair / B.L]) + B.pose[pair][3].w + kCullSlack;
+    return (t == t) ? t : __int_as_float(0x7f800000);
+}
+
+__device__ __forceinline__ bool sphere_reaches(float4 c, float4 sph, float thr) {
+    const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
+    const float base = thr + c.w;
+    return base >= 0.f && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= base * base;
+}
+
+// Interpolated distance of sorted point `pos` for block pair `pair`, folded into
+// the waypoint's best value and key when it can still be the minimum.
+__device__ __forceinline__ void evaluate(const BlockState& B, int pos, int pair) {
+    const float4 p = __ldg(&B.sorted[pos]);
+    const float4 r0 = B.pose[pair][0], r1 = B.pose[pair][1], r2 = B.pose[pair][2];
+    const int wl = pair / B.L, l = pair - wl * B.L;
+    const float lx = fmaf(r0.x, p.x, fmaf(r0.y, p.y, fmaf(r0.z, p.z, r0.w)));
+    const float ly = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
+    const float lz = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
+    const float g = grid_lookup(B.values + (size_t)l * B.n * B.n * B.n, B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz);
+    const unsigned long long key = pack_key(g, __float_as_int(p.w), l);
+    const unsigned ob = (unsigned)(key >> 32);
+    if (ob <= B.best[wl]) {
+        atomicMin(&B.best[wl], ob);
+        atomicMin(&B.key[wl], key);
+    }
+}
+
+// Per-warp queue of (sorted point, pair) entries; 32 entries are evaluated at once.
+struct WarpQueue {
+    uint2* q;      // 64 slots in shared memory
+    int n;
+};
+
+__device__ __forceinline__ void queue_push(const BlockState& B, WarpQueue& Q, bool surv, int pos, int pair,
+                                           int lane) {
+    const unsigned m = __ballot_sync(kFull, surv);
+    if (!m) return;
+    stat_add(B, kWsLookups, (unsigned)__popc(m), lane);
+    if (surv) Q.q[Q.n + __popc(m & ((1u << lane) - 1u))] = make_uint2((unsigned)pos, (unsigned)pair);
+    Q.n += __popc(m);
+    if (Q.n >= 32) {   // Q.n < 64: evaluate the top 32 entries with all lanes
+        __syncwarp();
+        const uint2 e = Q.q[Q.n - 32 + lane];
+        __syncwarp();
+        Q.n -= 32;
+        evaluate(B, (int)e.x, (int)e.y);
+    }
+}
+
+__device__ __forceinline__ void queue_flush(const BlockState& B, WarpQueue& Q, int lane) {
+    __syncwarp();
+    if (lane < Q.n) {
+        const uint2 e = Q.q[lane];
+        evaluate(B, (int)e.x, (int)e.y);
+    }
+    __syncwarp();
+    Q.n = 0;
+}
+
+// Point tests of up to kTileBatch (pair, tile) entries, the point loads issued together.
+__device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, const unsigned (&ent)[kTileBatch],
+                                           int cnt, int lane) {
+    float4 pt[kTileBatch];
+    int pos[kTileBatch];
+#pragma unroll
+    for (int k = 0; k < kTileBatch; ++k) {
+        pos[k] = (int)(ent[k] & kTileMask) * 32 + lane;
+        pt[k] = (k < cnt && pos[k] < B.n_valid) ? __ldg(&B.sorted[pos[k]]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < kTileBatch; ++k) {
+        if (k >= cnt) break;
+        const int pair = (int)(ent[k] >> 28);
+        const float4 sph = B.pose[pair][3];
+        const float thr = pair_threshold(B, pair);
+        const float dx = pt[k].x - sph.x, dy = pt[k].y - sph.y, dz = pt[k].z - sph.z;
+        const bool surv = pos[k] < B.n_valid && thr >= 0.f && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= thr * thr;
+        if (B.stat) stat_add(B, kWsPointT, (unsigned)__popc(__ballot_sync(kFull, pos[k] < B.n_valid)), lane);
+        queue_push(B, Q, surv, pos[k], pair, lane);
+    }
+}
+
+__global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid_constant__ BatchParams P) {
+    extern __shared__ float4 s_spheres[];            // tiles [stage_tiles], then super-tiles
+    __shared__ float4 s_pose[kCheckWarps][4];
+    __shared__ float4 s_grid_o[kMaxLinks];
+    __shared__ float s_grid_h[kMaxLinks];
+    __shared__ unsigned s_best[kCheckWarps];
+    __shared__ unsigned long long s_key[kCheckWarps];
+    __shared__ unsigned s_list[kBlockList];
+    __shared__ unsigned s_list_n, s_list_next;
+    __shared__ uint2 s_queue[kCheckWarps][64];
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ unsigned s_stat[kCheckWarps][kWsCount];
+    __shared__ unsigned long long s_stat_ns[kCheckWarps][kWnCount];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool stats = P.stats != nullptr;
+    unsigned long long t_block0 = 0;
+    if (stats) {
+        if (tid == 0) t_block0 = global_ns();
+        if (lane < kWsCount) s_stat[warp][lane] = 0u;
+        if (lane < kWnCount) s_stat_ns[warp][lane] = 0ull;
+    }
+    // block -> trajectory (block_base is increasing)
+    int lo = 0, hi = P.n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.inst[mid].block_base <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const InstDesc& I = P.inst[lo];
+    const LinkTable& T = *I.robot;
+    const int L = I.L;
+    const int w0 = ((int)blockIdx.x - I.block_base) * I.tw;
+    const int nw = min(I.tw, I.W - w0);
+    const int n_pair = nw * L;
+    const int n_valid = P.n_valid[lo];
     const int n_tiles = (n_valid + 31) >> 5;
     const int n_super = (n_tiles + 31) >> 5;
-    const bool staged = P.stage && n_tiles > 0;
+    const bool staged = n_tiles > 0 && n_tiles <= P.stage_tiles;
 
-    // 0. one thread starts the copy of all tile and super-tile spheres
-    if (staged && threadIdx.x == 0) {
+    if (staged && tid == 0) {
         mbar_init(&s_mbar, 1);
         const unsigned tb = (unsigned)n_tiles * (unsigned)sizeof(float4);
         const unsigned sb = (unsigned)n_super * (unsigned)sizeof(float4);
         mbar_expect_tx(&s_mbar, tb + sb);
-        bulk_copy_g2s(s_spheres, P.tiles, tb, &s_mbar);
-        bulk_copy_g2s(s_spheres + P.max_tiles, P.supers, sb, &s_mbar);
+        bulk_copy_g2s(s_spheres, P.tiles + I.tile_base, tb, &s_mbar);
+        bulk_copy_g2s(s_spheres + P.stage_tiles, P.supers + I.super_base, sb, &s_mbar);
     }
-    if (threadIdx.x < kMaxWaypointsPerBlock) {
-        s_best[threadIdx.x] = kOrderedInf;
-        s_key[threadIdx.x] = ~0ull;
-        s_done[threadIdx.x] = 0u;
+    if (tid < kCheckWarps) {
+        s_best[tid] = kOrderedInf;
+        s_key[tid] = ~0ull;
     }
-    __syncthreads();   // the only block-wide barrier
-    if (wl >= nw) return;
-
-    // 1. forward kinematics; this warp keeps link l's pose in registers
-    const float* qw = P.q + (size_t)w * T.dof;
-    if (l == 0 && lane < T.dof && !isfinite(qw[lane])) atomicOr(P.status, kStatusNonFinite);
-    float4 rows[3], sph;
-    warp_link_pose(T, qw, lane, l, rows, &sph);
-    const float* G = T.values + (size_t)l * T.n * T.n * T.n;
-    const float4 g_o = T.grid_o[l];
-    const float g_h = T.grid_h[l];
-
-    if (staged && !mbar_wait_bounded(&s_mbar, 0)) {
-        // the copy did not complete in time: report, then leave this warp (the block
-        // stays resident until every warp has waited the same bounded time)
-        if (lane == 0) atomicOr(P.status, kStatusTimeout);
-        return;
+    if (tid < L) {
+        s_grid_o[tid] = T.grid_o[tid];
+        s_grid_h[tid] = T.grid_h[tid];
     }
-    const float4* tiles = staged ? s_spheres : P.tiles;
-    const float4* supers = staged ? s_spheres + P.max_tiles : P.supers;
+    if (tid == 0) {
+        s_list_n = 0u;
+        s_list_next = 0u;
+    }
 
-    unsigned long long lk = ~0ull;
-    auto evaluate = [&](int pos) {
-        const float4 p = __ldg(&P.sorted[pos]);
-        const float lx = fmaf(rows[0].x, p.x, fmaf(rows[0].y, p.y, fmaf(rows[0].z, p.z, rows[0].w)));
-        const float ly = fmaf(rows[1].x, p.x, fmaf(rows[1].y, p.y, fmaf(rows[1].z, p.z, rows[1].w)));
-        const float lz = fmaf(rows[2].x, p.x, fmaf(rows[2].y, p.y, fmaf(rows[2].z, p.z, rows[2].w)));
-        const float g = grid_lookup(G, T.n, g_o, g_h, lx, ly, lz);
-        const unsigned long long key = pack_key(g, __float_as_int(p.w), l);
-        if (key < lk) lk = key;
-        const unsigned ob = (unsigned)(key >> 32);
-        if (ob < s_best[wl]) atomicMin(&s_best[wl], ob);
-    };
+    // phase A.1: forward kinematics, one warp per pair (overlaps the copy)
+    const bool pair_warp = warp < n_pair;
+    const int wl = pair_warp ? warp / L : 0, l = pair_warp ? warp - wl * L : 0;
+    float4 sph = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pair_warp) {
+        const float* qw = I.q + (size_t)(w0 + wl) * I.dof;
+        if (l == 0 && lane < I.dof && !isfinite(qw[lane])) atomicOr(P.status, kStatusNonFinite);
+        float4 rows[3];
+        warp_link_pose(T, qw, lane, l, rows, &sph);
+        if (lane == 0) {
+            s_pose[warp][0] = rows[0];
+            s_pose[warp][1] = rows[1];
+            s_pose[warp][2] = rows[2];
+            s_pose[warp][3] = sph;
+        }
+    }
+    __syncthreads();
+    if (staged) {
+        const bool ok = mbar_wait_bounded(&s_mbar, 0);
+        if (!__syncthreads_and(ok)) {
+            // the copy did not complete in time: report it and leave; one more
+            // bounded wait first so no transfer into this block is left in flight
+            if (tid == 0) {
+                atomicOr(P.status, kStatusTimeout);
+                mbar_wait_bounded(&s_mbar, 0);
+            }
+            return;
+        }
+    }
+    const float4* tiles = staged ? s_spheres : P.tiles + I.tile_base;
+    const float4* supers = staged ? s_spheres + P.stage_tiles : P.supers + I.super_base;
+    const unsigned long long t_fk = (stats && tid == 0) ? global_ns() : 0ull;
+
+    BlockState B;
+    B.sorted = P.sorted + I.point_base;
+    B.values = T.values;
+    B.n = T.n;
+    B.L = L;
+    B.n_valid = n_valid;
+    B.pose = s_pose;
+    B.grid_o = s_grid_o;
+    B.grid_h = s_grid_h;
+    B.best = s_best;
+    B.key = s_key;
+    B.cull = P.cull;
+    B.stat = stats ? s_stat[warp] : nullptr;
+    WarpQueue Q{s_queue[warp], 0};
     const float kInf = __int_as_float(0x7f800000);
-    auto threshold = [&]() -> float {   // best + R + slack: a distance from the sphere centre
-        if (!P.cull) return kInf;
-        const float t = from_ordered(s_best[wl]) + sph.w + kCullSlack;
-        return (t == t) ? t : kInf;
-    };
-    auto reach = [&](float4 c, float thr) -> bool {   // sphere c may hold a pair below the bound
-        const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
-        const float base = thr + c.w;
-        return base >= 0.f && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= base * base;
-    };
 
-    // 2. seed: nearest super-tile, nearest tile in it, all its points
-    if (P.cull && n_tiles > 0) {
-        float bs = kInf;
-        int bi = 0x7fffffff;
+    if (pair_warp) {
+        unsigned long long t_a = stats ? global_ns() : 0ull;
+        // phase A.2: seed -- nearest super-tile, nearest tile in it, all its points
+        if (P.cull && n_tiles > 0) {
+            float bs = kInf;
+            int bi = 0x7fffffff;
+            for (int s0 = 0; s0 < n_super; s0 += 32) {
+                const int s = s0 + lane;
+                if (s < n_super) {
+                    const float4 c = supers[s];
+                    const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
+                    const float sc = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + c.w;
+                    if (sc < bs) { bs = sc; bi = s; }
+                }
+            }
+            const int s_seed = warp_argmin(bs, bi);   // >= n_super when every score is NaN
+            if (s_seed < n_super) {
+                const int t = s_seed * 32 + lane;
+                float ts = kInf;
+                if (t < n_tiles) {
+                    const float4 c = tiles[t];
+                    const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
+                    ts = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + c.w;
+                }
+                const int t_seed = warp_argmin(ts, t < n_tiles ? t : 0x7fffffff);
+                const bool ev = t_seed < n_tiles && t_seed * 32 + lane < n_valid;
+                if (stats) stat_add(B, kWsSeed, (unsigned)__popc(__ballot_sync(kFull, ev)), lane);
+                if (ev) evaluate(B, t_seed * 32 + lane, warp);
+            }
+        }
+        if (stats) {
+            const unsigned long long t_b = global_ns();
+            if (lane == 0) s_stat_ns[warp][kWnSeed] += t_b - t_a;
+            t_a = t_b;
+        }
+        // phase A.3: cull super-tiles, then tiles; survivors go to the block list,
+        // or are tested here when the list is full
+        unsigned over_ent[kTileBatch];
+        int over_n = 0;
         for (int s0 = 0; s0 < n_super; s0 += 32) {
             const int s = s0 + lane;
-            if (s < n_super) {
-                const float4 c = supers[s];
-                const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
-                const float sc = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + c.w;
-                if (sc < bs) { bs = sc; bi = s; }
+            float thr = pair_threshold(B, warp);
+            unsigned ms = __ballot_sync(kFull, s < n_super && sphere_reaches(supers[min(s, n_super - 1)], sph, thr));
+            if (stats) {
+                stat_add(B, kWsSuperT, (unsigned)min(32, n_super - s0), lane);
+                stat_add(B, kWsSuperP, (unsigned)__popc(ms), lane);
             }
-        }
-        const int s_seed = warp_argmin(bs, bi);   // n_super..INT_MAX when every score is NaN
-        if (s_seed < n_super) {
-            const int t = s_seed * 32 + lane;
-            float ts = kInf;
-            if (t < n_tiles) {
-                const float4 c = tiles[t];
-                const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
-                ts = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + c.w;
-            }
-            const int t_seed = warp_argmin(ts, t < n_tiles ? t : 0x7fffffff);
-            if (t_seed < n_tiles && t_seed * 32 + lane < n_valid) evaluate(t_seed * 32 + lane);
-        }
-    }
-
-    // 3. hierarchical sweep with survivor compaction
-    unsigned* q = s_queue[warp];
-    int qn = 0;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    auto push_points = [&](const float4 (&pk)[kTileBatch], const int (&tk)[kTileBatch], int cnt, float thr) {
-#pragma unroll
-        for (int k = 0; k < kTileBatch; ++k) {
-            if (k >= cnt) break;
-            const int pos = tk[k] * 32 + lane;
-            const float dx = pk[k].x - sph.x, dy = pk[k].y - sph.y, dz = pk[k].z - sph.z;
-            const bool surv = pos < n_valid && thr >= 0.f && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= thr * thr;
-            const unsigned m = __ballot_sync(kFull, surv);
-            if (m) {
-                if (surv) q[qn + __popc(m & lt_mask)] = (unsigned)pos;
-                qn += __popc(m);
-                if (qn >= 32) {   // qn < 64: evaluate the top 32 entries with all lanes
-                    __syncwarp();
-                    const unsigned ent = q[qn - 32 + lane];
-                    __syncwarp();
-                    qn -= 32;
-                    evaluate((int)ent);
+            while (ms) {
+                const int sidx = s0 + __ffs(ms) - 1;
+                ms &= ms - 1;
+                thr = pair_threshold(B, warp);
+                const int t = sidx * 32 + lane;
+                const unsigned mt = __ballot_sync(kFull, t < n_tiles && sphere_reaches(tiles[min(t, n_tiles - 1)], sph, thr));
+                if (stats) {
+                    stat_add(B, kWsTileT, (unsigned)min(32, n_tiles - sidx * 32), lane);
+                    stat_add(B, kWsTileP, (unsigned)__popc(mt), lane);
                 }
-            }
-        }
-    };
-    for (int s0 = 0; s0 < n_super; s0 += 32) {
-        float thr = threshold();
-        const int s = s0 + lane;
-        unsigned ms = __ballot_sync(kFull, s < n_super && reach(supers[min(s, n_super - 1)], thr));
-        while (ms) {
-            const int sidx = s0 + __ffs(ms) - 1;
-            ms &= ms - 1;
-            thr = threshold();
-            const int t = sidx * 32 + lane;
-            unsigned mt = __ballot_sync(kFull, t < n_tiles && reach(tiles[min(t, n_tiles - 1)], thr));
-            while (mt) {
-                // up to kTileBatch surviving tiles: issue their point loads together
-                int tk[kTileBatch];
-                float4 pk[kTileBatch];
-                int cnt = 0;
-#pragma unroll
-                for (int k = 0; k < kTileBatch; ++k) {
-                    tk[k] = 0;
-                    if (mt) {
-                        tk[k] = sidx * 32 + __ffs(mt) - 1;
-                        mt &= mt - 1;
-                        cnt = k + 1;
+                if (!mt) continue;
+                unsigned base = 0;
+                if (lane == 0) base = atomicAdd(&s_list_n, (unsigned)__popc(mt));
+                base = __shfl_sync(kFull, base, 0);
+                const bool mine = (mt >> lane) & 1u;
+                const unsigned slot = base + __popc(mt & ((1u << lane) - 1u));
+                const unsigned ent = ((unsigned)warp << 28) | (unsigned)t;
+                if (mine && slot < (unsigned)kBlockList) s_list[slot] = ent;
+                unsigned over = __ballot_sync(kFull, mine && slot >= (unsigned)kBlockList);
+                if (stats) stat_add(B, kWsOver, (unsigned)__popc(over), lane);
+                while (over) {   // the list is full: test these tiles here
+                    over_ent[over_n] = ((unsigned)warp << 28) | (unsigned)(sidx * 32 + __ffs(over) - 1);
+                    over &= over - 1;
+                    if (++over_n == kTileBatch) {
+                        test_tiles(B, Q, over_ent, over_n, lane);
+                        over_n = 0;
                     }
                 }
-#pragma unroll
-                for (int k = 0; k < kTileBatch; ++k) {
-                    const int pos = tk[k] * 32 + lane;
-                    pk[k] = (k < cnt && pos < n_valid) ? __ldg(&P.sorted[pos]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                push_points(pk, tk, cnt, threshold());
             }
         }
+        if (over_n) test_tiles(B, Q, over_ent, over_n, lane);
+        if (stats && lane == 0) s_stat_ns[warp][kWnCull] += global_ns() - t_a;
     }
-    __syncwarp();
-    if (lane < qn) evaluate((int)q[lane]);
+    __syncthreads();
+    const unsigned long long t_b0 = stats ? global_ns() : 0ull;
 
-    // 4. reduce: warp min, shared atomicMin, last warp of the waypoint writes
-    lk = warp_min_u64(lk);
-    if (lane == 0) {
-        if (lk != ~0ull) atomicMin(&s_key[wl], lk);
-        __threadfence_block();
-        if (atomicAdd(&s_done[wl], 1u) == (unsigned)L - 1u) {
-            __threadfence_block();
-            write_result(P, w, atomicAdd(&s_key[wl], 0ull));
+    // phase B: every warp takes list entries a few at a time
+    const unsigned n_list = min(s_list_n, (unsigned)kBlockList);
+    for (;;) {
+        unsigned k0 = 0;
+        if (lane == 0) k0 = atomicAdd(&s_list_next, (unsigned)kTileBatch);
+        k0 = __shfl_sync(kFull, k0, 0);
+        if (k0 >= n_list) break;
+        unsigned ent[kTileBatch];
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < kTileBatch; ++k) {
+            ent[k] = 0u;
+            if (k0 + k < n_list) {
+                ent[k] = s_list[k0 + k];
+                cnt = k + 1;
+            }
+        }
+        test_tiles(B, Q, ent, cnt, lane);
+    }
+    queue_flush(B, Q, lane);
+    if (stats && lane == 0) s_stat_ns[warp][kWnPoints] += global_ns() - t_b0;
+    __syncthreads();
+    if (stats) {
+        // block sums of the warp rows, one global atomic per counter
+        if (tid < kWsCount) {
+            unsigned long long v = 0;
+            for (int k = 0; k < kCheckWarps; ++k) v += s_stat[k][tid];
+            const int dst[kWsCount] = {1, 2, 3, 4, 5, 6, 7, 8};
+            atomicAdd(&P.stats[dst[tid]], v);
+        } else if (tid >= 32 && tid < 32 + kWnCount) {
+            unsigned long long v = 0;
+            for (int k = 0; k < kCheckWarps; ++k) v += s_stat_ns[k][tid - 32];
+            atomicAdd(&P.stats[11 + (tid - 32)], v);
+        } else if (tid == 64) {
+            const unsigned long long t_end = global_ns();
+            atomicAdd(&P.stats[0], (unsigned long long)n_pair);
+            atomicAdd(&P.stats[9], 1ull);
+        }
+        if (tid == 0) {
+            const unsigned long long t_end = global_ns();
+            atomicAdd(&P.stats[10], t_fk - t_block0);
+            atomicAdd(&P.stats[14], t_end - t_block0);
+            atomicMax(&P.stats[15], t_end - t_block0);
+            atomicMin(&P.stats[17], t_block0);
+            atomicMax(&P.stats[18], t_end);
+        }
+    }
+
+    // results of the block's waypoints
+    if (tid < nw) {
+        const int w = w0 + tid;
+        const unsigned long long key = s_key[tid];
+        if (key == ~0ull) {
+            I.dist[w] = kInf;
+            I.arg_link[w] = -1;
+            I.arg_point[w] = -1;
+        } else {
+            I.dist[w] = from_ordered((unsigned)(key >> 32));
+            I.arg_link[w] = (int)(key & 15u);
+            I.arg_point[w] = (int)((key & 0xffffffffu) >> 4);
         }
     }
 }
@@ -670,13 +846,8 @@ __global__ void __launch_bounds__(128) fk_kernel(const __grid_constant__ LinkTab
 
 }  // namespace
 
-cudaError_t launch_prep(const PrepParams& p, cudaStream_t s) {
-    cloud_prep_kernel<<<kPrepCtas, kPrepThreads, 0, s>>>(p);
-    return cudaGetLastError();
-}
-
-size_t staged_bytes(int max_tiles) {
-    return (size_t)(max_tiles + (max_tiles + 31) / 32) * sizeof(float4);
+size_t staged_bytes(int stage_tiles) {
+    return stage_tiles > 0 ? (size_t)(stage_tiles + stage_tiles / 32 + 1) * sizeof(float4) : 0;
 }
 
 cudaError_t configure_kernels() {
@@ -684,16 +855,20 @@ cudaError_t configure_kernels() {
                                 (int)staged_bytes(kMaxStagedTiles));
 }
 
-cudaError_t launch_check(const CheckParams& p, cudaStream_t s) {
-    const dim3 block((unsigned)(32 * p.tw * p.T.L));
-    const dim3 grid((unsigned)((p.W + p.tw - 1) / p.tw));
-    const size_t smem = p.stage ? staged_bytes(p.max_tiles) : 0;
-    check_kernel<<<grid, block, smem, s>>>(p);
+cudaError_t launch_batch(const BatchParams& p, cudaStream_t s, cudaEvent_t ev_mid) {
+    if (p.n_inst <= 0 || p.n_blocks <= 0) return cudaSuccess;
+    prep_kernel<<<kPrepCtas * p.n_inst, kPrepThreads, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ev_mid) {
+        e = cudaEventRecord(ev_mid, s);
+        if (e != cudaSuccess) return e;
+    }
+    check_kernel<<<p.n_blocks, kCheckWarps * 32, staged_bytes(p.stage_tiles), s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status,
-                      cudaStream_t s) {
+cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status, cudaStream_t s) {
     fk_kernel<<<(unsigned)((W + 3) / 4), 128, 0, s>>>(T, q, W, out, status);
     return cudaGetLastError();
 }

@@ -11,13 +11,17 @@
 namespace sdf {
 
 constexpr int kMaxLinks = SDF_MAX_LINKS;
-constexpr int kMaxWaypointsPerBlock = 32;  // one warp per (waypoint, link): TW * L <= 32
-// Cull slack (metres): a pair is skipped only when its bounding-sphere lower bound
-// exceeds the best distance found so far by more than this, which covers the FP32
-// rounding of the transform, the sphere centre and the interpolation (~1e-6 m).
+// Cull slack (metres): a sphere is skipped only when its lower bound exceeds the
+// best distance found so far by more than this, which covers the FP32 rounding of
+// the transform, the sphere centre and the interpolation (~1e-6 m).
 constexpr float kCullSlack = 1e-4f;
+constexpr int kMaxBatch = 128;            // trajectories per launch (kernel-parameter table)
+constexpr int kCheckWarps = 16;           // warps per check block
+constexpr int kTileBatch = 4;             // (pair, tile) entries per warp step, loads issued together
+constexpr int kBlockList = 2048;          // (pair, tile) entries a block can queue in shared memory
+constexpr int kMaxStagedTiles = 4096;     // tile spheres a block can stage in shared memory
 
-// Robot + grids as the kernels see them (passed by value as a kernel parameter).
+// Robot + grids as the kernels see them.  The robot keeps a device copy.
 struct LinkTable {
     int L;                    // links = dof + 1
     int dof;
@@ -31,51 +35,50 @@ struct LinkTable {
     const float* values;           // L grids of n^3 floats, x fastest
 };
 
-constexpr int kCells = 32768;             // 32^3 Morton cells for the cloud sort
-constexpr int kMaxStagedTiles = 4096;     // tile spheres staged in shared memory (64 KiB)
-constexpr int kTileBatch = 4;             // tiles per warp step in the sweep
-
-// Spatial sort of the obstacle points (cloud_prep_kernel).
-struct PrepParams {
-    const float* points;      // N x stride, caller's layout
-    int N;
-    int stride;               // 3 or 4
-    float4* sorted;           // N: x, y, z, original index (int bits); finite points only
-    float4* tiles;            // ceil(N / 32): bounding sphere of each 32-point tile
-    float4* supers;           // ceil(N / 1024): bounding sphere of each 32-tile super-tile
-    int* n_valid;             // number of finite points written to `sorted`
-    int* status;
-};
-
-struct CheckParams {
-    LinkTable T;
+// One trajectory check inside a launch.  Offsets index the batch-wide scratch.
+struct InstDesc {
+    const LinkTable* robot;   // device copy
     const float* q;           // W x dof
-    int W;
-    int tw;                   // waypoints per block (block = 32 * tw * L threads)
-    const float4* sorted;     // from PrepParams
-    const float4* tiles;
-    const float4* supers;
-    const int* n_valid;
-    int max_tiles;            // ceil(N / 32): tiles the scratch can hold
-    int stage;                // 1: copy tile and super-tile spheres to shared memory
-    int cull;                 // 0: evaluate every pair
+    const float* points;      // N x stride
     float* dist;
     int32_t* arg_link;
     int32_t* arg_point;
+    int W, N, L, dof;
+    int point_base;           // sorted points (N)
+    int tile_base;            // ceil(N / 32) tile spheres
+    int super_base;           // ceil(N / 1024) super-tile spheres
+    int tw;                   // waypoints per check block (tw * L <= kCheckWarps)
+    int block_base;           // first check block of this trajectory
+};
+
+struct BatchParams {
+    int n_inst;
+    int n_blocks;             // check blocks over all trajectories
+    int stride;               // floats per point: 3 or 4
+    int cull;                 // 0: evaluate every pair
+    int stage_tiles;          // tile spheres the dynamic shared memory holds (0: no staging)
+    float4* sorted;           // finite points, spatially sorted: x, y, z, original index bits
+    float4* tiles;            // sphere of each 32-point tile
+    float4* supers;           // sphere of each 32-tile super-tile
+    int* n_valid;             // finite points per trajectory
     int* status;              // device status bits
+    unsigned long long* stats;  // kStatCount counters, or null (statistics off)
+    InstDesc inst[kMaxBatch];
 };
 
 enum StatusBits : int { kStatusNonFinite = 1, kStatusTimeout = 2 };
 
-// Launchers (check.cu / grid_build.cu).  Return a cudaError_t of the launch.
+// Statistics counters (SDF_OPT_STATS); indices match SDF_STAT_* in sdfcheck.h.
+constexpr int kStatCount = 20;
+
+// Launchers (check.cu / grid_build.cu).  Each returns the launch's cudaError_t.
 cudaError_t configure_kernels();           // once per device, that device current
-cudaError_t launch_prep(const PrepParams& p, cudaStream_t s);
-cudaError_t launch_check(const CheckParams& p, cudaStream_t s);
-cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status,
-                      cudaStream_t s);
-cudaError_t launch_grid_build(const float* tris9, const int* comp_off, int n_comp, int n_tris,
-                              float ox, float oy, float oz, float h, int n, float* out,
-                              cudaStream_t s);
+// Enqueues the two kernels of one batch (spatial sort, check); ev_mid (may be null)
+// is recorded between them.
+cudaError_t launch_batch(const BatchParams& p, cudaStream_t s, cudaEvent_t ev_mid);
+cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status, cudaStream_t s);
+cudaError_t launch_grid_build(const float* tris9, const int* comp_off, int n_comp, int n_tris, float ox,
+                              float oy, float oz, float h, int n, float* out, cudaStream_t s);
 
 }  // namespace sdf
 
@@ -91,7 +94,8 @@ struct sdf_robot {
     int device = 0;
     int dof = 0;
     const sdf_grids* grids = nullptr;
-    sdf::LinkTable table;
+    sdf::LinkTable table;                  // host copy
+    sdf::LinkTable* d_table = nullptr;     // device copy read by the kernels
 };
 
 struct sdf_ctx {
@@ -102,9 +106,11 @@ struct sdf_ctx {
     // options
     int cull = 1;
     int point_stride = 3;
-    int tw = 0;
     int time_kernels = 0;
-    // scratch owned by the context
+    int stats = 0;
+    unsigned long long* d_stats = nullptr;  // kStatCount counters on the device
+    int tw = 0;                            // waypoints per check block (0: as many as fit)
+    // scratch owned by the context (grown on demand, or up front by sdf_ctx_reserve)
     float4* sorted = nullptr;
     size_t sorted_cap = 0;
     float4* tiles = nullptr;
@@ -112,6 +118,7 @@ struct sdf_ctx {
     float4* supers = nullptr;
     size_t supers_cap = 0;
     int* n_valid = nullptr;
+    size_t n_valid_cap = 0;
     int* status = nullptr;
     // staging for check_trajectory_host
     float* st_q = nullptr;

@@ -76,9 +76,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(sdf):
     big = sdf.SDF_NOALLOC_MAX_POINTS + 1
     pts = torch.zeros((big, 3), device="cuda")
     q = torch.zeros((4, 6), device="cuda")
-    d = torch.empty(sdf.SDF_NOALLOC_MAX_WAYPOINTS + 1, device="cuda")
-    i = torch.empty(sdf.SDF_NOALLOC_MAX_WAYPOINTS + 1, dtype=torch.int32, device="cuda")
+    d = torch.empty(4, device="cuda")
+    i = torch.empty(4, dtype=torch.int32, device="cuda")
     assert sdf.check_trajectory_noalloc(robot, stream, q, 4, pts, big, d, i, i) == sdf.SDF_ERR_INVALID_ARG
-    qb = torch.zeros((sdf.SDF_NOALLOC_MAX_WAYPOINTS + 1, 6), device="cuda")
-    assert sdf.check_trajectory_noalloc(robot, stream, qb, qb.shape[0], pts, 10, d, i, i) == \
-        sdf.SDF_ERR_INVALID_ARG
+    assert sdf.check_trajectory_noalloc(robot, stream, q, -1, pts, 10, d, i, i) == sdf.SDF_ERR_INVALID_ARG
