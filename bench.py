@@ -259,7 +259,6 @@ def run_ours(args):
     al = torch.empty(W, dtype=torch.int32, device=dev)
     ap = torch.empty(W, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    ctx.set_option(sdf.SDF_OPT_TIME_KERNELS, 1)
 
     def step():
         sdf.check_trajectory(ctx, robot, q, W, pts, N, dist_o, al, ap)
@@ -271,9 +270,10 @@ def run_ours(args):
     if rc != 0:
         raise RuntimeError(f"warm-up check failed: {ctx.last_error()}")
 
+    # timed steps: the check's two kernels overlap (programmatic dependent launch);
+    # one event pair per step brackets both
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    kernel_ms, prep_ms = [], []
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -285,11 +285,6 @@ def run_ours(args):
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
-        if i % 16 == 15 or i == args.steps - 1:
-            # kernel events live in the library (one pair per context): read them
-            # for the last step of each group of 16
-            kernel_ms.append(ctx.last_kernel_ms(sdf.SDF_KERNEL_CHECK))
-            prep_ms.append(ctx.last_kernel_ms(sdf.SDF_KERNEL_PREP))
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     if ws > 1:
@@ -299,6 +294,17 @@ def run_ours(args):
     rc = ctx.synchronize()
     if rc != 0:
         raise RuntimeError(f"timed checks failed: {ctx.last_error()}")
+
+    # per-kernel device times for the roofline: the same steps with the library's
+    # events around each kernel (the kernels then run back to back, not overlapped)
+    ctx.set_option(sdf.SDF_OPT_TIME_KERNELS, 1)
+    kernel_ms, prep_ms = [], []
+    for i in range(args.steps):
+        flush.zero_()
+        step()
+        kernel_ms.append(ctx.last_kernel_ms(sdf.SDF_KERNEL_CHECK))
+        prep_ms.append(ctx.last_kernel_ms(sdf.SDF_KERNEL_PREP))
+    ctx.set_option(sdf.SDF_OPT_TIME_KERNELS, 0)
 
     # end to end through the host-buffer entry point (pinned host memory)
     qh = torch.tensor(scene.q, dtype=torch.float32).pin_memory().numpy()

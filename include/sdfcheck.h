@@ -142,8 +142,14 @@ int sdf_ctx_last_kernel_ms(sdf_ctx* ctx, int32_t kernel, float* ms);
 #define SDF_STAT_NS_POINTS 13     /* sum over blocks: point tests and lookups       */
 #define SDF_STAT_NS_BLOCK 14      /* sum over blocks: whole block                   */
 #define SDF_STAT_NS_BLOCK_MAX 15  /* longest block                                  */
-#define SDF_STAT_NS_SPAN 16       /* first block start to last block end (max over calls) */
-#define SDF_STAT_COUNT 20
+#define SDF_STAT_NS_SPAN 16       /* first block start to last block end, over the calls */
+#define SDF_STAT_NS_SORT_BOX 20   /* sort phases, first cluster only: bounding box    */
+#define SDF_STAT_NS_SORT_HIST 21  /* histogram                                      */
+#define SDF_STAT_NS_SORT_SCAN 22  /* scan                                           */
+#define SDF_STAT_NS_SORT_SCATTER 23 /* scatter                                      */
+#define SDF_STAT_NS_SORT_TILES 24 /* tile spheres                                   */
+#define SDF_STAT_NS_SORT_SUPERS 25 /* super-tile spheres                            */
+#define SDF_STAT_COUNT 32
 int sdf_ctx_stats(sdf_ctx* ctx, int64_t* out, int32_t n, int32_t reset);
 
 /* --------------------------------------------------------------------- grids */

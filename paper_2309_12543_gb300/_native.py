@@ -170,13 +170,14 @@ class Context:
 
     STAT_NAMES = ("pairs", "seed_lookups", "super_tests", "super_pass", "tile_tests", "tile_pass",
                   "point_tests", "lookups", "list_overflow", "blocks", "ns_fk", "ns_seed", "ns_cull",
-                  "ns_points", "ns_block", "ns_block_max", "ns_span")
+                  "ns_points", "ns_block", "ns_block_max", "ns_span", "_17", "_18", "_19", "ns_sort_box",
+                  "ns_sort_hist", "ns_sort_scan", "ns_sort_scatter", "ns_sort_tiles", "ns_sort_supers")
 
     def stats(self, reset: bool = False) -> dict:
         """Counters accumulated while SDF_OPT_STATS is on (see sdfcheck.h)."""
-        out = np.zeros(20, dtype=np.int64)
-        self._check(lib.sdf_ctx_stats(self.handle, _ptr(out), 20, int(reset)), "sdf_ctx_stats")
-        return {k: int(v) for k, v in zip(self.STAT_NAMES, out)}
+        out = np.zeros(32, dtype=np.int64)
+        self._check(lib.sdf_ctx_stats(self.handle, _ptr(out), 32, int(reset)), "sdf_ctx_stats")
+        return {k: int(v) for k, v in zip(self.STAT_NAMES, out) if not k.startswith("_")}
 
     def last_kernel_ms(self, kernel: int = 1) -> float:
         """Device ms of SDF_KERNEL_PREP (0) or SDF_KERNEL_CHECK (1) of the last check."""

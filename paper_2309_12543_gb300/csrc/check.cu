@@ -215,6 +215,13 @@ struct FMax { __device__ float operator()(float a, float b) const { return fmaxf
 
 // ------------------------------------------------------------------ prep kernel
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+
 // One cluster per trajectory sorts its cloud: 32^3 cell counters spread over the
 // CTAs' shared memory, every phase one pass over the points with cluster barriers
 // in between; up to kPrepCached points per thread stay in registers between the
@@ -225,6 +232,8 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     const unsigned rank = cluster.block_rank();
     const int inst = blockIdx.x / kPrepCtas;
     const InstDesc& I = P.inst[inst];
+    // the check grid may start now: its set-up reads nothing this kernel writes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ unsigned s_bins[kBinsPerCta];     // counters, then cursors, of this CTA's cells
     __shared__ float s_tmp[32];
     __shared__ float s_box[6];
@@ -238,6 +247,16 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     const int N = I.N;
     const float* pts = I.points;
     const bool cached = N <= kStride * kPrepCached;
+    // phase timestamps of the first CTA (SDF_OPT_STATS)
+    const bool clock = P.stats != nullptr && rank == 0 && tid == 0;
+    unsigned long long t_mark = clock ? global_ns() : 0ull;
+    auto mark = [&](int slot) {
+        if (clock) {
+            const unsigned long long t = global_ns();
+            atomicAdd(&P.stats[slot], t - t_mark);
+            t_mark = t;
+        }
+    };
 
     float3 pc[kPrepCached];
 #pragma unroll
@@ -287,6 +306,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     }
     const float3 inv = make_float3(32.f / fmaxf(bhi.x - blo.x, 1e-6f), 32.f / fmaxf(bhi.y - blo.y, 1e-6f),
                                    32.f / fmaxf(bhi.z - blo.z, 1e-6f));
+    mark(20);
 
     // 2. histogram: cell c is counted in CTA c / kBinsPerCta
     for_each_point([&](float3 p, int) {
@@ -296,6 +316,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         }
     });
     cluster.sync();
+    mark(21);
 
     // 3. exclusive scan of this CTA's cells (warp w owns a contiguous run), then
     //    the CTA totals of lower ranks give the CTA's offset
@@ -338,6 +359,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     for (int k = 0; k < kPerWarp; k += 32) s_bins[warp * kPerWarp + k + lane] += off;
     const int n_valid = (int)total;
     cluster.sync();
+    mark(22);
 
     // 4. scatter (order inside a cell is arbitrary; keys carry the original index)
     float4* sorted = P.sorted + I.point_base;
@@ -349,6 +371,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         }
     });
     cluster.sync();   // orders the scatter before the reads below (cluster scope)
+    mark(23);
 
     // 5. tile spheres: centre of the tile's box, radius to its farthest point
     const int n_tiles = (n_valid + 31) >> 5;
@@ -373,6 +396,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         if (lane == 0) tiles[t] = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-6f) + 1e-7f);
     }
     cluster.sync();
+    mark(24);
 
     // 6. super-tile spheres over 32 consecutive tiles: box of the tile spheres,
     //    radius to the farthest tile sphere
@@ -398,6 +422,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         if (lane == 0) supers[s] = make_float4(cx, cy, cz, r * (1.f + 1e-6f) + 1e-7f);
     }
     if (rank == 0 && tid == 0) P.n_valid[inst] = n_valid;
+    mark(25);
 }
 
 // ---- TMA bulk copy (global -> shared) completing on an mbarrier ----------------
@@ -436,28 +461,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
-// The link-from-world rows and world sphere of link l for one waypoint, computed by
-// the whole warp (every lane ends with the same values).
-__device__ __forceinline__ void warp_link_pose(const LinkTable& T, const float* qw, int lane, int l,
-                                               float4* rows, float4* sph) {
-    float M[12];
-    fk_warp(T, qw, lane, M);
-    const int src = l > 0 ? l - 1 : 0;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const float v = __shfl_sync(kFull, M[k], src);
-        M[k] = l > 0 ? v : T.base[k];
-    }
-    store_link(M, T.sph_local[l], rows, sph);
-}
-
 // ------------------------------------------------------------------ check kernel
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // per-warp statistics rows (SDF_OPT_STATS), written by lane 0 of their warp
 enum WarpStat { kWsSeed, kWsSuperT, kWsSuperP, kWsTileT, kWsTileP, kWsPointT, kWsLookups, kWsOver, kWsCount };
@@ -601,19 +605,6 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
     const int w0 = ((int)blockIdx.x - I.block_base) * I.tw;
     const int nw = min(I.tw, I.W - w0);
     const int n_pair = nw * L;
-    const int n_valid = P.n_valid[lo];
-    const int n_tiles = (n_valid + 31) >> 5;
-    const int n_super = (n_tiles + 31) >> 5;
-    const bool staged = n_tiles > 0 && n_tiles <= P.stage_tiles;
-
-    if (staged && tid == 0) {
-        mbar_init(&s_mbar, 1);
-        const unsigned tb = (unsigned)n_tiles * (unsigned)sizeof(float4);
-        const unsigned sb = (unsigned)n_super * (unsigned)sizeof(float4);
-        mbar_expect_tx(&s_mbar, tb + sb);
-        bulk_copy_g2s(s_spheres, P.tiles + I.tile_base, tb, &s_mbar);
-        bulk_copy_g2s(s_spheres + P.stage_tiles, P.supers + I.super_base, sb, &s_mbar);
-    }
     if (tid < kCheckWarps) {
         s_best[tid] = kOrderedInf;
         s_key[tid] = ~0ull;
@@ -627,21 +618,45 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
         s_list_next = 0u;
     }
 
-    // phase A.1: forward kinematics, one warp per pair (overlaps the copy)
-    const bool pair_warp = warp < n_pair;
-    const int wl = pair_warp ? warp / L : 0, l = pair_warp ? warp - wl * L : 0;
-    float4 sph = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (pair_warp) {
-        const float* qw = I.q + (size_t)(w0 + wl) * I.dof;
-        if (l == 0 && lane < I.dof && !isfinite(qw[lane])) atomicOr(P.status, kStatusNonFinite);
-        float4 rows[3];
-        warp_link_pose(T, qw, lane, l, rows, &sph);
-        if (lane == 0) {
-            s_pose[warp][0] = rows[0];
-            s_pose[warp][1] = rows[1];
-            s_pose[warp][2] = rows[2];
-            s_pose[warp][3] = sph;
+    // phase A.1: forward kinematics, one warp per waypoint (before the sort is
+    // waited for); lane j writes link j's pose
+    if (warp < nw) {
+        const float* qw = I.q + (size_t)(w0 + warp) * I.dof;
+        if (lane < I.dof && !isfinite(qw[lane])) atomicOr(P.status, kStatusNonFinite);
+        float M[12];
+        fk_warp(T, qw, lane, M);
+        float Mj[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const float v = __shfl_up_sync(kFull, M[k], 1);
+            Mj[k] = lane == 0 ? T.base[k] : v;
         }
+        if (lane < L) {
+            float4 rows[3], sp;
+            store_link(Mj, T.sph_local[lane], rows, &sp);
+            float4* dst = s_pose[warp * L + lane];
+            dst[0] = rows[0];
+            dst[1] = rows[1];
+            dst[2] = rows[2];
+            dst[3] = sp;
+        }
+    }
+    const bool pair_warp = warp < n_pair;
+
+    // wait for the sort (a no-op without programmatic dependent launch), then stage
+    // this trajectory's tile and super-tile spheres
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int n_valid = P.n_valid[lo];
+    const int n_tiles = (n_valid + 31) >> 5;
+    const int n_super = (n_tiles + 31) >> 5;
+    const bool staged = n_tiles > 0 && n_tiles <= P.stage_tiles;
+    if (staged && tid == 0) {
+        mbar_init(&s_mbar, 1);
+        const unsigned tb = (unsigned)n_tiles * (unsigned)sizeof(float4);
+        const unsigned sb = (unsigned)n_super * (unsigned)sizeof(float4);
+        mbar_expect_tx(&s_mbar, tb + sb);
+        bulk_copy_g2s(s_spheres, P.tiles + I.tile_base, tb, &s_mbar);
+        bulk_copy_g2s(s_spheres + P.stage_tiles, P.supers + I.super_base, sb, &s_mbar);
     }
     __syncthreads();
     if (staged) {
@@ -659,6 +674,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
     const float4* tiles = staged ? s_spheres : P.tiles + I.tile_base;
     const float4* supers = staged ? s_spheres + P.stage_tiles : P.supers + I.super_base;
     const unsigned long long t_fk = (stats && tid == 0) ? global_ns() : 0ull;
+    const float4 sph = s_pose[pair_warp ? warp : 0][3];
 
     BlockState B;
     B.sorted = P.sorted + I.point_base;
@@ -860,12 +876,23 @@ cudaError_t launch_batch(const BatchParams& p, cudaStream_t s, cudaEvent_t ev_mi
     prep_kernel<<<kPrepCtas * p.n_inst, kPrepThreads, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (ev_mid) {
+    if (ev_mid) {   // a timing event between the kernels; the check then starts after the sort ends
         e = cudaEventRecord(ev_mid, s);
         if (e != cudaSuccess) return e;
     }
-    check_kernel<<<p.n_blocks, kCheckWarps * 32, staged_bytes(p.stage_tiles), s>>>(p);
-    return cudaGetLastError();
+    // programmatic dependent launch: the check grid starts while the sort finishes,
+    // runs its forward kinematics, then waits (griddepcontrol.wait) for the sort
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)p.n_blocks);
+    cfg.blockDim = dim3(kCheckWarps * 32);
+    cfg.dynamicSmemBytes = staged_bytes(p.stage_tiles);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = ev_mid ? 0 : 1;
+    return cudaLaunchKernelEx(&cfg, check_kernel, p);
 }
 
 cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status, cudaStream_t s) {

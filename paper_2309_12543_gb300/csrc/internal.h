@@ -69,7 +69,7 @@ struct BatchParams {
 enum StatusBits : int { kStatusNonFinite = 1, kStatusTimeout = 2 };
 
 // Statistics counters (SDF_OPT_STATS); indices match SDF_STAT_* in sdfcheck.h.
-constexpr int kStatCount = 20;
+constexpr int kStatCount = 32;
 
 // Launchers (check.cu / grid_build.cu).  Each returns the launch's cudaError_t.
 cudaError_t configure_kernels();           // once per device, that device current
