@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="paper", choices=["paper", "tiny"])
+    ap.add_argument("--config", default="paper", choices=["paper", "tiny", "batched"])
     ap.add_argument("--order", default="voxel", choices=["voxel", "random"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100)
@@ -367,10 +367,107 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------------------ batched
+
+BATCH_METRIC = "µs per batch of 64 uneven trajectory checks (one graph replay)"
+
+
+def run_batched(args):
+    """64 independent checks (W ~ U[50,1000], N log-uniform [1k,100k], 6- and 7-DoF
+    arms with 96^3 grids) in one graph-captured launch of the batched engine."""
+    import torch
+    import paper_2309_12543_gb300 as sdf
+    import scenegen
+    from paper_2309_12543_gb300 import build as pkg_build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg_build.build()
+    bs = scenegen.make_batched(order=args.order)
+    stream = torch.cuda.Stream(dev)
+    ctx = sdf.Context(local, stream)
+    robots = []
+    for arm in bs.arms:
+        g = sdf.sdf_build_grids(ctx, arm.meshes, arm.resolution, arm.margin)
+        robots.append(sdf.Robot(ctx, arm.dh, g, arm.base))
+    reqs, outs = [], []
+    for a, q, p in bs.instances:
+        W, N = q.shape[0], p.shape[0]
+        o = (torch.empty(W, device=dev), torch.empty(W, dtype=torch.int32, device=dev),
+             torch.empty(W, dtype=torch.int32, device=dev))
+        outs.append(o)
+        reqs.append((robots[a], torch.tensor(q, dtype=torch.float32, device=dev), W,
+                     torch.tensor(p, dtype=torch.float32, device=dev), N, *o))
+    tot_w = sum(r[2] for r in reqs)
+    tot_n = sum(r[4] for r in reqs)
+    tot_pairs = sum(r[2] * r[0].n_links for r in reqs)
+    sdf.sdf_ctx_reserve(ctx, tot_n, tot_w, tot_pairs, len(reqs))
+    tw, tb, tuned_us = sdf.sdf_autotune(ctx, reqs, repeats=5)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            sdf.check_batch(ctx, reqs)
+    if ctx.synchronize() != 0:
+        raise RuntimeError(ctx.last_error())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        sdf.check_batch(ctx, reqs)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    main = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        graph.replay()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(main)
+        graph.replay()
+        ev[i][1].record(main)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    step_ms = [x.elapsed_time(y) for x, y in ev]
+    total_ms = max_over_ranks(float(sum(step_ms)))
+    if ctx.synchronize() != 0:
+        raise RuntimeError(ctx.last_error())
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    value = total_ms * 1e3 / (ws * args.steps)
+    out = {
+        "metric": BATCH_METRIC, "value": value, "unit": "µs per batch", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched: {len(reqs)} checks, W in [{min(r[2] for r in reqs)}, "
+                               f"{max(r[2] for r in reqs)}] (total {tot_w}), N in [{min(r[4] for r in reqs)}, "
+                               f"{max(r[4] for r in reqs)}] (total {tot_n}), 6-DoF and 7-DoF arms, "
+                               f"96^3 grids, one CUDA graph", "requests": len(reqs),
+                   "waypoints": tot_w, "points": tot_n, "autotuned": {"waypoints_per_block": tw, "tile_batch": tb,
+                                                                      "median_us_warm": tuned_us},
+                   "l2": "flushed before every timed step (256 MiB write)"},
+        "p50_us": percentile([x * 1e3 for x in step_ms], 50), "p99_us": percentile([x * 1e3 for x in step_ms], 99),
+        "checks_per_s": len(reqs) / (value * 1e-6), "waypoints_per_s": tot_w / (value * 1e-6),
+        "gpu_launches": 2 * args.steps, "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

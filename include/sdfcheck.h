@@ -104,7 +104,8 @@ const char* sdf_last_error(const sdf_ctx* ctx);
 /* Options (sdf_ctx_set_option / sdf_ctx_get_option). */
 #define SDF_OPT_CULL 1            /* 1 (default): bounding-sphere culling; 0: evaluate every pair */
 #define SDF_OPT_POINT_STRIDE 2    /* floats per point: 3 (default, x y z) or 4 (x y z pad)       */
-#define SDF_OPT_WAYPOINTS_PER_BLOCK 3 /* waypoints per check block, 1..16; 0 (default) = 16 / links */
+#define SDF_OPT_WAYPOINTS_PER_BLOCK 3 /* waypoints per check block, 1..16; 0 (default) = tuned or 16 / links */
+#define SDF_OPT_TILE_BATCH 4      /* list entries per warp step: 2, 4 or 8; 0 (default) = tuned or 4  */
 #define SDF_OPT_TIME_KERNELS 6    /* 1: record CUDA events around the two kernels of a check      */
 #define SDF_OPT_STATS 7           /* 1: count culls/lookups and time kernel phases (adds atomics)  */
 int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t value);
@@ -239,6 +240,16 @@ typedef struct {
  * Each request's results are exactly those check_trajectory gives it alone.
  * Asynchronous; errors as check_trajectory (the message names the request). */
 int check_batch(sdf_ctx* ctx, const sdf_check_request* requests, int32_t n);
+
+/* Autotuner: times every launch shape (waypoints per block 1..16/links x list
+ * entries per warp step 2, 4, 8) on these requests, `repeats` runs each (median,
+ * caches warm), and remembers the fastest for launches of the same shape -- the
+ * request count, the largest link count and the power-of-two buckets of the total
+ * waypoints and points.  Later check_trajectory / check_batch calls of that shape
+ * use it unless SDF_OPT_WAYPOINTS_PER_BLOCK / SDF_OPT_TILE_BATCH are set.  Runs the
+ * checks (their outputs are overwritten) and synchronises.  Outputs may be NULL. */
+int sdf_autotune(sdf_ctx* ctx, const sdf_check_request* requests, int32_t n, int32_t repeats,
+                 int32_t* best_waypoints_per_block, int32_t* best_tile_batch, float* best_us);
 
 /* Grow the context's scratch for launches of up to these totals (sums over a
  * batch) so that later checks allocate nothing: a prerequisite for capturing

@@ -30,6 +30,7 @@ SDF_MAX_BATCH = 128
 SDF_OPT_CULL = 1
 SDF_OPT_POINT_STRIDE = 2
 SDF_OPT_WAYPOINTS_PER_BLOCK = 3
+SDF_OPT_TILE_BATCH = 4
 SDF_OPT_TIME_KERNELS = 6
 SDF_OPT_STATS = 7
 SDF_KERNEL_PREP = 0
@@ -94,6 +95,7 @@ def _load():
         "check_trajectory_host": (ctypes.c_int, [P, P, P, i32, P, i32, P, P, P]),
         "check_trajectory_noalloc": (ctypes.c_int, [P, P, P, i32, P, i32, P, P, P, P]),
         "check_batch": (ctypes.c_int, [P, P, i32]),
+        "sdf_autotune": (ctypes.c_int, [P, P, i32, i32, P, P, P]),
         "sdf_ctx_reserve": (ctypes.c_int, [P, i64, i64, i64, i32]),
     }
     for name, (res, args) in sigs.items():
@@ -111,7 +113,7 @@ EXPORTED = ("sdf_ctx_create", "sdf_ctx_destroy", "sdf_ctx_set_stream", "sdf_last
             "sdf_ctx_last_kernel_ms", "sdf_ctx_stats", "sdf_build_grids", "sdf_grids_upload", "sdf_grids_download",
             "sdf_grids_info", "sdf_grids_destroy", "sdf_robot_create", "sdf_robot_destroy",
             "sdf_forward_kinematics", "check_trajectory", "check_trajectory_host",
-            "check_trajectory_noalloc", "check_batch", "sdf_ctx_reserve")
+            "check_trajectory_noalloc", "check_batch", "sdf_ctx_reserve", "sdf_autotune")
 
 
 def _ptr(x) -> int:
@@ -313,13 +315,28 @@ def check_trajectory(ctx: Context, robot: Robot, q_dev, W: int, points_dev, N: i
                                     _ptr(argmin_point_dev)), "check_trajectory")
 
 
-def check_batch(ctx: Context, requests) -> None:
-    """requests: sequence of (robot, q_dev, W, points_dev, N, dist_dev, link_dev, point_dev)."""
+def _requests(requests):
     arr = (sdf_check_request * max(len(requests), 1))()
     for i, (robot, q, W, pts, N, d, al, ap) in enumerate(requests):
         arr[i] = sdf_check_request(robot.handle.value if hasattr(robot.handle, "value") else robot.handle,
                                    _ptr(q), int(W), _ptr(pts), int(N), _ptr(d), _ptr(al), _ptr(ap))
+    return arr
+
+
+def check_batch(ctx: Context, requests) -> None:
+    """requests: sequence of (robot, q_dev, W, points_dev, N, dist_dev, link_dev, point_dev)."""
+    arr = _requests(requests)
     ctx._check(lib.check_batch(ctx.handle, ctypes.addressof(arr), len(requests)), "check_batch")
+
+
+def sdf_autotune(ctx: Context, requests, repeats: int = 5):
+    """Time the launch shapes on these requests; returns (waypoints per block,
+    tile batch, median microseconds) of the fastest, which later calls reuse."""
+    arr = _requests(requests)
+    tw, tb, us = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    ctx._check(lib.sdf_autotune(ctx.handle, ctypes.addressof(arr), len(requests), int(repeats), ctypes.byref(tw),
+                                ctypes.byref(tb), ctypes.byref(us)), "sdf_autotune")
+    return int(tw.value), int(tb.value), float(us.value)
 
 
 def sdf_ctx_reserve(ctx: Context, max_points: int, max_waypoints: int, max_pairs: int,

@@ -144,6 +144,11 @@ int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t v) {
                 return fail(ctx, SDF_ERR_INVALID_ARG, "waypoints per block must be 0..%d", sdf::kCheckWarps);
             ctx->tw = (int)v;
             return SDF_OK;
+        case SDF_OPT_TILE_BATCH:
+            if (v != 0 && v != 2 && v != 4 && v != 8)
+                return fail(ctx, SDF_ERR_INVALID_ARG, "tile batch must be 0, 2, 4 or 8");
+            ctx->tile_batch = (int)v;
+            return SDF_OK;
         case SDF_OPT_TIME_KERNELS: ctx->time_kernels = v ? 1 : 0; return SDF_OK;
         case SDF_OPT_STATS:
             if (v && !ctx->d_stats) {
@@ -165,6 +170,7 @@ int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* v) {
         case SDF_OPT_CULL: *v = ctx->cull; return SDF_OK;
         case SDF_OPT_POINT_STRIDE: *v = ctx->point_stride; return SDF_OK;
         case SDF_OPT_WAYPOINTS_PER_BLOCK: *v = ctx->tw; return SDF_OK;
+        case SDF_OPT_TILE_BATCH: *v = ctx->tile_batch; return SDF_OK;
         case SDF_OPT_TIME_KERNELS: *v = ctx->time_kernels; return SDF_OK;
         case SDF_OPT_STATS: *v = ctx->stats; return SDF_OK;
         default: return SDF_ERR_INVALID_ARG;
@@ -506,10 +512,34 @@ int sdf_ctx_reserve(sdf_ctx* ctx, int64_t max_points, int64_t max_waypoints, int
     return reserve_scratch(ctx, P, tiles, supers, R);
 }
 
-// Waypoints per check block for a robot with L links: one warp per (waypoint, link).
-static int block_waypoints(const sdf_ctx* ctx, int L) {
+// Launch-shape key of a batch for the tuning cache: request count, the largest
+// link count, and power-of-two buckets of the total waypoints and points.
+static uint64_t shape_key(const sdf_check_request* reqs, int n) {
+    uint64_t W = 0, N = 0, L = 0, k = 0;
+    for (int i = 0; i < n; ++i) {
+        if (reqs[i].W == 0) continue;
+        ++k;
+        W += (uint64_t)reqs[i].W;
+        N += (uint64_t)reqs[i].N;
+        L = std::max<uint64_t>(L, (uint64_t)reqs[i].robot->table.L);
+    }
+    auto lg = [](uint64_t v) { uint64_t b = 0; while (v > 1) { v >>= 1; ++b; } return b; };
+    return (k << 40) | (L << 32) | (lg(W) << 16) | lg(N);
+}
+
+// Waypoints per check block for a robot with L links (one warp per waypoint and
+// link) and list entries per warp step: explicit options first, then a tuned
+// configuration for this launch shape, then the defaults.
+static void launch_shape(const sdf_ctx* ctx, uint64_t key, int L, int* tw, int* tb) {
     const int fit = std::max(1, sdf::kCheckWarps / L);
-    return ctx->tw > 0 ? std::min(ctx->tw, fit) : fit;
+    int t = ctx->tw, b = ctx->tile_batch;
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+        if (t == 0) t = it->second.first;
+        if (b == 0) b = it->second.second;
+    }
+    *tw = t > 0 ? std::min(t, fit) : fit;
+    *tb = b > 0 ? b : sdf::kDefaultTileBatch;
 }
 
 int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
@@ -522,6 +552,8 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     }
     sdf::BatchParams* p = new (std::nothrow) sdf::BatchParams();
     if (!p) return fail(ctx, SDF_ERR_OOM, "host allocation");
+    const uint64_t key = shape_key(reqs, n);
+    int tile_batch = sdf::kDefaultTileBatch;
     size_t points = 0, tiles = 0, supers = 0, blocks = 0, max_tiles = 0;
     int k = 0;
     for (int i = 0; i < n; ++i) {
@@ -541,7 +573,7 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
         I.point_base = (int)points;
         I.tile_base = (int)tiles;
         I.super_base = (int)supers;
-        I.tw = block_waypoints(ctx, I.L);
+        launch_shape(ctx, key, I.L, &I.tw, &tile_batch);
         I.block_base = (int)blocks;
         const size_t nt = ((size_t)r.N + 31) / 32;
         points += (size_t)r.N;
@@ -573,13 +605,72 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     p->stats = ctx->stats ? ctx->d_stats : nullptr;
     cudaError_t e = cudaSuccess;
     if (ctx->time_kernels) e = cudaEventRecord(ctx->ev0, ctx->stream);
-    if (e == cudaSuccess) e = sdf::launch_batch(*p, ctx->stream, ctx->time_kernels ? ctx->ev1 : nullptr);
+    if (e == cudaSuccess) e = sdf::launch_batch(*p, tile_batch, ctx->stream, ctx->time_kernels ? ctx->ev1 : nullptr);
     if (e == cudaSuccess && ctx->time_kernels) {
         e = cudaEventRecord(ctx->ev2, ctx->stream);
         ctx->timed_valid = true;
     }
     delete p;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "check launch");
+    return SDF_OK;
+}
+
+int sdf_autotune(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n, int32_t repeats, int32_t* best_tw,
+                 int32_t* best_tile_batch, float* best_us) {
+    if (!ctx || repeats < 1) return SDF_ERR_INVALID_ARG;
+    if (n < 1 || n > SDF_MAX_BATCH || !reqs) return fail(ctx, SDF_ERR_INVALID_ARG, "autotune needs 1..%d requests", SDF_MAX_BATCH);
+    int Lmin = sdf::kMaxLinks;
+    for (int i = 0; i < n; ++i) {
+        const int rc = validate_request(ctx, reqs[i], i);
+        if (rc != SDF_OK) return rc;
+        if (reqs[i].W > 0) Lmin = std::min(Lmin, reqs[i].robot->table.L);
+    }
+    DeviceGuard g(ctx->device);
+    const uint64_t key = shape_key(reqs, n);
+    const int save_tw = ctx->tw, save_tb = ctx->tile_batch, save_time = ctx->time_kernels;
+    ctx->time_kernels = 0;
+    ctx->tuned.erase(key);
+    cudaEvent_t a = nullptr, b = nullptr;
+    SDF_CUDA(ctx, cudaEventCreate(&a));
+    SDF_CUDA(ctx, cudaEventCreate(&b));
+    float best = INFINITY;
+    int btw = 0, btb = 0, rc = SDF_OK;
+    const int tbs[3] = {2, 4, 8};
+    const int fit = std::max(1, sdf::kCheckWarps / Lmin);
+    for (int tw = 1; tw <= fit && rc == SDF_OK; ++tw) {
+        for (int tb : tbs) {
+            ctx->tw = tw;
+            ctx->tile_batch = tb;
+            rc = check_batch(ctx, reqs, n);   // warm-up, grows scratch if needed
+            std::vector<float> ms;
+            for (int r = 0; r < repeats && rc == SDF_OK; ++r) {
+                cudaEventRecord(a, ctx->stream);
+                rc = check_batch(ctx, reqs, n);
+                cudaEventRecord(b, ctx->stream);
+                float t = 0.f;
+                if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess) rc = SDF_ERR_CUDA;
+                ms.push_back(t);
+            }
+            if (rc != SDF_OK) break;
+            std::nth_element(ms.begin(), ms.begin() + ms.size() / 2, ms.end());
+            const float med = ms[ms.size() / 2];
+            if (med < best) {
+                best = med;
+                btw = tw;
+                btb = tb;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->tw = save_tw;
+    ctx->tile_batch = save_tb;
+    ctx->time_kernels = save_time;
+    if (rc != SDF_OK) return rc;
+    ctx->tuned[key] = std::make_pair(btw, btb);
+    if (best_tw) *best_tw = btw;
+    if (best_tile_batch) *best_tile_batch = btb;
+    if (best_us) *best_us = best * 1e3f;
     return SDF_OK;
 }
 

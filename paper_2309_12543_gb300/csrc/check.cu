@@ -548,18 +548,19 @@ __device__ __forceinline__ void queue_flush(const BlockState& B, WarpQueue& Q, i
     Q.n = 0;
 }
 
-// Point tests of up to kTileBatch (pair, tile) entries, the point loads issued together.
-__device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, const unsigned (&ent)[kTileBatch],
+// Point tests of up to TB (pair, tile) entries, the point loads issued together.
+template <int TB>
+__device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, const unsigned (&ent)[TB],
                                            int cnt, int lane) {
-    float4 pt[kTileBatch];
-    int pos[kTileBatch];
+    float4 pt[TB];
+    int pos[TB];
 #pragma unroll
-    for (int k = 0; k < kTileBatch; ++k) {
+    for (int k = 0; k < TB; ++k) {
         pos[k] = (int)(ent[k] & kTileMask) * 32 + lane;
         pt[k] = (k < cnt && pos[k] < B.n_valid) ? __ldg(&B.sorted[pos[k]]) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int k = 0; k < kTileBatch; ++k) {
+    for (int k = 0; k < TB; ++k) {
         if (k >= cnt) break;
         const int pair = (int)(ent[k] >> 28);
         const float4 sph = B.pose[pair][3];
@@ -571,6 +572,8 @@ __device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, co
     }
 }
 
+// TB: list entries a warp takes per step in phase B (their point loads go out together).
+template <int TB>
 __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid_constant__ BatchParams P) {
     extern __shared__ float4 s_spheres[];            // tiles [stage_tiles], then super-tiles
     __shared__ float4 s_pose[kCheckWarps][4];
@@ -729,7 +732,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
         }
         // phase A.3: cull super-tiles, then tiles; survivors go to the block list,
         // or are tested here when the list is full
-        unsigned over_ent[kTileBatch];
+        unsigned over_ent[TB];
         int over_n = 0;
         for (int s0 = 0; s0 < n_super; s0 += 32) {
             const int s = s0 + lane;
@@ -762,14 +765,14 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
                 while (over) {   // the list is full: test these tiles here
                     over_ent[over_n] = ((unsigned)warp << 28) | (unsigned)(sidx * 32 + __ffs(over) - 1);
                     over &= over - 1;
-                    if (++over_n == kTileBatch) {
-                        test_tiles(B, Q, over_ent, over_n, lane);
+                    if (++over_n == TB) {
+                        test_tiles<TB>(B, Q, over_ent, over_n, lane);
                         over_n = 0;
                     }
                 }
             }
         }
-        if (over_n) test_tiles(B, Q, over_ent, over_n, lane);
+        if (over_n) test_tiles<TB>(B, Q, over_ent, over_n, lane);
         if (stats && lane == 0) s_stat_ns[warp][kWnCull] += global_ns() - t_a;
     }
     __syncthreads();
@@ -779,20 +782,20 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
     const unsigned n_list = min(s_list_n, (unsigned)kBlockList);
     for (;;) {
         unsigned k0 = 0;
-        if (lane == 0) k0 = atomicAdd(&s_list_next, (unsigned)kTileBatch);
+        if (lane == 0) k0 = atomicAdd(&s_list_next, (unsigned)TB);
         k0 = __shfl_sync(kFull, k0, 0);
         if (k0 >= n_list) break;
-        unsigned ent[kTileBatch];
+        unsigned ent[TB];
         int cnt = 0;
 #pragma unroll
-        for (int k = 0; k < kTileBatch; ++k) {
+        for (int k = 0; k < TB; ++k) {
             ent[k] = 0u;
             if (k0 + k < n_list) {
                 ent[k] = s_list[k0 + k];
                 cnt = k + 1;
             }
         }
-        test_tiles(B, Q, ent, cnt, lane);
+        test_tiles<TB>(B, Q, ent, cnt, lane);
     }
     queue_flush(B, Q, lane);
     if (stats && lane == 0) s_stat_ns[warp][kWnPoints] += global_ns() - t_b0;
@@ -867,11 +870,14 @@ size_t staged_bytes(int stage_tiles) {
 }
 
 cudaError_t configure_kernels() {
-    return cudaFuncSetAttribute(check_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)staged_bytes(kMaxStagedTiles));
+    const int smem = (int)staged_bytes(kMaxStagedTiles);
+    cudaError_t e = cudaFuncSetAttribute(check_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(check_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(check_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
 }
 
-cudaError_t launch_batch(const BatchParams& p, cudaStream_t s, cudaEvent_t ev_mid) {
+cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, cudaEvent_t ev_mid) {
     if (p.n_inst <= 0 || p.n_blocks <= 0) return cudaSuccess;
     prep_kernel<<<kPrepCtas * p.n_inst, kPrepThreads, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
@@ -892,7 +898,12 @@ cudaError_t launch_batch(const BatchParams& p, cudaStream_t s, cudaEvent_t ev_mi
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = ev_mid ? 0 : 1;
-    return cudaLaunchKernelEx(&cfg, check_kernel, p);
+    switch (tile_batch) {
+        case 2: return cudaLaunchKernelEx(&cfg, check_kernel<2>, p);
+        case 4: return cudaLaunchKernelEx(&cfg, check_kernel<4>, p);
+        case 8: return cudaLaunchKernelEx(&cfg, check_kernel<8>, p);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status, cudaStream_t s) {

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <utility>
 
 #include "sdfcheck.h"
 
@@ -17,7 +19,7 @@ constexpr int kMaxLinks = SDF_MAX_LINKS;
 constexpr float kCullSlack = 1e-4f;
 constexpr int kMaxBatch = 128;            // trajectories per launch (kernel-parameter table)
 constexpr int kCheckWarps = 16;           // warps per check block
-constexpr int kTileBatch = 4;             // (pair, tile) entries per warp step, loads issued together
+constexpr int kDefaultTileBatch = 4;      // (pair, tile) entries per warp step (2, 4 or 8)
 constexpr int kBlockList = 2048;          // (pair, tile) entries a block can queue in shared memory
 constexpr int kMaxStagedTiles = 4096;     // tile spheres a block can stage in shared memory
 
@@ -75,7 +77,7 @@ constexpr int kStatCount = 32;
 cudaError_t configure_kernels();           // once per device, that device current
 // Enqueues the two kernels of one batch (spatial sort, check); ev_mid (may be null)
 // is recorded between them.
-cudaError_t launch_batch(const BatchParams& p, cudaStream_t s, cudaEvent_t ev_mid);
+cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, cudaEvent_t ev_mid);
 cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status, cudaStream_t s);
 cudaError_t launch_grid_build(const float* tris9, const int* comp_off, int n_comp, int n_tris, float ox,
                               float oy, float oz, float h, int n, float* out, cudaStream_t s);
@@ -109,7 +111,9 @@ struct sdf_ctx {
     int time_kernels = 0;
     int stats = 0;
     unsigned long long* d_stats = nullptr;  // kStatCount counters on the device
-    int tw = 0;                            // waypoints per check block (0: as many as fit)
+    int tw = 0;                            // waypoints per check block (0: tuned or as many as fit)
+    int tile_batch = 0;                    // list entries per warp step (0: tuned or 4)
+    std::map<uint64_t, std::pair<int, int>> tuned;   // launch shape key -> (tw, tile batch)
     // scratch owned by the context (grown on demand, or up front by sdf_ctx_reserve)
     float4* sorted = nullptr;
     size_t sorted_cap = 0;

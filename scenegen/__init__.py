@@ -333,14 +333,9 @@ def human_capsules(rng: np.random.Generator, dist_range=(0.2, 1.5),
     return [(c + rot @ p0, c + rot @ p1, r) for (p0, p1, r) in caps]
 
 
-def cloud_humans(rng: np.random.Generator, N: int, n_clusters: int = 3, voxel: float = 0.02,
-                 order: str = "voxel", clusters=None) -> np.ndarray:
-    """Occupied ``voxel``-sized voxel centres of ``n_clusters`` human-like clusters,
-    sampled without replacement down to N points.
-
-    order = "voxel": points sorted by linear voxel index (x fastest), the order in
-    which a voxeliser emits occupied cells; "random": shuffled.
-    """
+def human_voxels(rng: np.random.Generator, n_clusters: int = 3, voxel: float = 0.02, clusters=None) -> np.ndarray:
+    """Integer cells of the occupied ``voxel``-sized voxels of ``n_clusters``
+    human-like clusters (unique, unordered)."""
     if clusters is None:
         clusters = [human_capsules(rng) for _ in range(n_clusters)]
     keys = []
@@ -356,19 +351,36 @@ def cloud_humans(rng: np.random.Generator, N: int, n_clusters: int = 3, voxel: f
         for (p0, p1, r) in caps:
             occ |= _capsule_contains(x, p0, p1, r)
         keys.append(gi[occ])
-    cells = np.unique(np.concatenate(keys), axis=0)
+    return np.unique(np.concatenate(keys), axis=0)
+
+
+def sample_voxels(rng: np.random.Generator, cells: np.ndarray, N: int, voxel: float = 0.02,
+                  order: str = "voxel") -> np.ndarray:
+    """N voxel centres drawn without replacement from integer cells.
+
+    order = "voxel": sorted by linear voxel index (x fastest), the order in which a
+    voxeliser emits occupied cells; "random": shuffled.
+    """
     if N > cells.shape[0]:
         raise ValueError(f"only {cells.shape[0]} occupied voxels, {N} requested")
     pick = rng.choice(cells.shape[0], size=N, replace=False)
     cells = cells[pick]
-    if order == "voxel":
+    if order == "voxel" and N > 0:
         off = cells - cells.min(axis=0)
         ext = off.max(axis=0) + 1
         lin = off[:, 0] + ext[0] * (off[:, 1] + ext[1] * off[:, 2])
         cells = cells[np.argsort(lin, kind="stable")]
-    elif order != "random":
+    elif order not in ("voxel", "random"):
         raise ValueError(order)
     return (cells + 0.5) * voxel
+
+
+def cloud_humans(rng: np.random.Generator, N: int, n_clusters: int = 3, voxel: float = 0.02,
+                 order: str = "voxel", clusters=None) -> np.ndarray:
+    """N occupied ``voxel``-sized voxel centres of ``n_clusters`` human-like
+    clusters, sampled without replacement (see ``sample_voxels`` for the order)."""
+    cells = human_voxels(rng, n_clusters, voxel, clusters)
+    return sample_voxels(rng, cells, N, voxel, order)
 
 
 # ------------------------------------------------------------------------ configs
@@ -400,3 +412,38 @@ def make_scene(name: str, **override) -> Scene:
         pts = cloud_humans(rng, cfg["N"], order=cfg.get("order", "voxel"))
     base = np.hstack([np.eye(3), np.zeros((3, 1))])
     return Scene(name, dh, base, meshes, cfg["resolution"], cfg["margin"], q, pts)
+
+
+# ------------------------------------------------------------ batched workload
+
+@dataclasses.dataclass
+class BatchedScene:
+    arms: list                 # Scene per arm model (meshes, grid parameters, DH); q/points unused
+    instances: list            # (arm index, q (W x dof), points (N x 3))
+
+
+def make_batched(seed: int = 3, n: int = 64, W_range=(50, 1000), N_range=(1000, 100000),
+                 resolution: int = 96, layouts: int = 8, order: str = "voxel") -> BatchedScene:
+    """Independent checks of uneven sizes for one batched launch: a pool of two arm
+    models (6- and 7-DoF, capsule+box links, ``resolution``^3 grids), trajectories of
+    W ~ U(W_range) waypoints through 5 configurations, clouds of N log-uniform in
+    N_range points drawn from a pool of ``layouts`` three-human voxel layouts."""
+    rng = np.random.default_rng(seed)
+    arms = []
+    for dof in (6, 7):
+        dh = gen_arm(rng, dof)
+        meshes = link_meshes(rng, dh, "capsule_box", 32, 15)
+        base = np.hstack([np.eye(3), np.zeros((3, 1))])
+        arms.append(Scene(f"arm{dof}", dh, base, meshes, resolution, 0.05, np.zeros((0, dof)),
+                          np.zeros((0, 3))))
+    pool = [human_voxels(rng) for _ in range(layouts)]
+    insts = []
+    for i in range(n):
+        a = int(rng.integers(0, 2))
+        W = int(rng.integers(W_range[0], W_range[1] + 1))
+        N = int(round(math.exp(rng.uniform(math.log(N_range[0]), math.log(N_range[1])))))
+        cells = pool[int(rng.integers(0, layouts))]
+        N = min(N, cells.shape[0])
+        q = spline_trajectory(rng, arms[a].dh, 5, W)
+        insts.append((a, q, sample_voxels(rng, cells, N, order=order)))
+    return BatchedScene(arms, insts)
