@@ -48,6 +48,7 @@ extern "C" {
 #define SDF_ERR_TIMEOUT (-4)      /* a bounded device wait gave up                     */
 #define SDF_ERR_UNSUPPORTED (-5)  /* device or option not supported by this build      */
 #define SDF_ERR_NONFINITE (-6)    /* a NaN/Inf joint value or point was seen           */
+#define SDF_PENDING 1             /* sdf_server_poll: the request is not finished yet  */
 
 #define SDF_MAX_LINKS 16          /* L = dof + 1 <= 16                                  */
 #define SDF_MAX_POINTS 16777215   /* N < 2^24 (point index packed with waypoint/link)  */
@@ -264,6 +265,66 @@ int sdf_ctx_reserve(sdf_ctx* ctx, int64_t max_points, int64_t max_waypoints, int
 int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* robot, const float* q_host, int32_t W,
                           const float* points_host, int32_t N, float* dist_host,
                           int32_t* argmin_link_host, int32_t* argmin_point_host);
+
+/* ------------------------------------------------------------------- serving */
+
+/* A serving engine for the paper's use: the controller needs the distances along
+ * the executing trajectory every control cycle (about 10 ms, 8 ms for the b-CAP
+ * protocol; Sec. I).  Clients publish the latest obstacle cloud and submit
+ * trajectories from any thread; an engine thread batches the requests as they
+ * arrive (continuous batching): whenever one of `slots` in-flight slots is free it
+ * takes waiting requests in arrival order while the batch fits the slot
+ * (max_batch requests, max_waypoints in total) and the device-memory budget
+ * (the request buffers and sort scratch of every in-flight batch count against
+ * it), and launches it with check_batch on the slot's own stream, so batches
+ * overlap on the device.  Every request of a batch is checked against the cloud
+ * current when the batch forms.  Robots (grids) stay resident; the server owns
+ * its streams, buffers and contexts. */
+typedef struct sdf_server sdf_server;
+typedef struct {
+    int32_t device;
+    int64_t memory_budget_bytes;  /* 0 = a quarter of the device's free memory          */
+    int32_t slots;                /* batches in flight at once, 1..16                    */
+    int32_t max_batch;            /* requests per batch, 1..SDF_MAX_BATCH                */
+    int32_t max_waypoints;        /* waypoints per batch (and per request)               */
+    int32_t max_points;           /* points per published cloud                          */
+    int32_t max_dof;              /* largest robot dof submitted                         */
+    int32_t batch_window_us;      /* 0: launch as soon as a slot is free; > 0: a batch
+                                     short of max_batch waits until its oldest request
+                                     has waited this long (more requests per batch)      */
+} sdf_server_config;
+
+/* Allocates every buffer up front (errors: INVALID_ARG, OOM, CUDA). */
+int sdf_server_create(const sdf_server_config* config, sdf_server** out);
+/* Stops the engine after the batches in flight; pending requests are dropped. */
+void sdf_server_destroy(sdf_server* server);
+/* Publish a cloud (host N x 3, copied).  Requests batched after this call use it.
+ * SDF_ERR_TIMEOUT if every cloud buffer is still held by in-flight batches. */
+int sdf_server_set_cloud(sdf_server* server, const float* points_host, int32_t N);
+/* Queue one trajectory (host W x dof, copied); returns at once with a ticket.
+ * SDF_ERR_OOM if the request alone exceeds the memory budget (it is not queued),
+ * SDF_ERR_INVALID_ARG if W > max_waypoints or dof > max_dof. */
+int sdf_server_submit(sdf_server* server, const sdf_robot* robot, const float* q_host, int32_t W,
+                      uint64_t* ticket);
+/* Results of a ticket (W entries each, any output may be NULL) and its latency
+ * from submission to results in host memory.  wait_us: 0 = do not wait (returns
+ * SDF_PENDING if unfinished), > 0 = wait up to that long (SDF_ERR_TIMEOUT),
+ * < 0 = wait up to 60 s.  A finished ticket is released by this call. */
+int sdf_server_poll(sdf_server* server, uint64_t ticket, int64_t wait_us, float* dist_host,
+                    int32_t* argmin_link_host, int32_t* argmin_point_host, double* latency_us);
+/* Statistics since creation or the last reset. */
+#define SDF_SERVER_STAT_P50_US 0
+#define SDF_SERVER_STAT_P99_US 1
+#define SDF_SERVER_STAT_MEAN_US 2
+#define SDF_SERVER_STAT_COMPLETED 3
+#define SDF_SERVER_STAT_REJECTED 4
+#define SDF_SERVER_STAT_BATCHES 5
+#define SDF_SERVER_STAT_MEAN_BATCH 6
+#define SDF_SERVER_STAT_PEAK_IN_FLIGHT 7
+#define SDF_SERVER_STAT_PENDING 8
+#define SDF_SERVER_STAT_MAX_US 9
+#define SDF_SERVER_STAT_COUNT 10
+int sdf_server_stats(sdf_server* server, double* out, int32_t n, int32_t reset);
 
 /* ----------------------------------------------------------- allocation-free check */
 

@@ -22,6 +22,7 @@ SDF_ERR_CUDA = -3
 SDF_ERR_TIMEOUT = -4
 SDF_ERR_UNSUPPORTED = -5
 SDF_ERR_NONFINITE = -6
+SDF_PENDING = 1
 SDF_MAX_LINKS = 16
 SDF_MAX_POINTS = 16777215
 SDF_NOALLOC_MAX_POINTS = 32768
@@ -62,6 +63,12 @@ class sdf_check_request(ctypes.Structure):
                 ("argmin_link_dev", ctypes.c_void_p), ("argmin_point_dev", ctypes.c_void_p)]
 
 
+class sdf_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("memory_budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("max_waypoints", ctypes.c_int32), ("max_points", ctypes.c_int32),
+                ("max_dof", ctypes.c_int32), ("batch_window_us", ctypes.c_int32)]
+
+
 class sdf_grid_meta(ctypes.Structure):
     _fields_ = [("origin", ctypes.c_float * 3), ("h", ctypes.c_float), ("n", ctypes.c_int32),
                 ("center", ctypes.c_float * 3), ("radius", ctypes.c_float), ("margin", ctypes.c_float)]
@@ -96,6 +103,12 @@ def _load():
         "check_trajectory_noalloc": (ctypes.c_int, [P, P, P, i32, P, i32, P, P, P, P]),
         "check_batch": (ctypes.c_int, [P, P, i32]),
         "sdf_autotune": (ctypes.c_int, [P, P, i32, i32, P, P, P]),
+        "sdf_server_create": (ctypes.c_int, [P, ctypes.POINTER(P)]),
+        "sdf_server_destroy": (None, [P]),
+        "sdf_server_set_cloud": (ctypes.c_int, [P, P, i32]),
+        "sdf_server_submit": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(ctypes.c_uint64)]),
+        "sdf_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, i64, P, P, P, ctypes.POINTER(ctypes.c_double)]),
+        "sdf_server_stats": (ctypes.c_int, [P, P, i32, i32]),
         "sdf_ctx_reserve": (ctypes.c_int, [P, i64, i64, i64, i32]),
     }
     for name, (res, args) in sigs.items():
@@ -113,7 +126,9 @@ EXPORTED = ("sdf_ctx_create", "sdf_ctx_destroy", "sdf_ctx_set_stream", "sdf_last
             "sdf_ctx_last_kernel_ms", "sdf_ctx_stats", "sdf_build_grids", "sdf_grids_upload", "sdf_grids_download",
             "sdf_grids_info", "sdf_grids_destroy", "sdf_robot_create", "sdf_robot_destroy",
             "sdf_forward_kinematics", "check_trajectory", "check_trajectory_host",
-            "check_trajectory_noalloc", "check_batch", "sdf_ctx_reserve", "sdf_autotune")
+            "check_trajectory_noalloc", "check_batch", "sdf_ctx_reserve", "sdf_autotune",
+            "sdf_server_create", "sdf_server_destroy", "sdf_server_set_cloud", "sdf_server_submit",
+            "sdf_server_poll", "sdf_server_stats")
 
 
 def _ptr(x) -> int:
@@ -364,3 +379,67 @@ def check_trajectory_noalloc(robot: Robot, stream, q_dev, W: int, points_dev, N:
     return int(lib.check_trajectory_noalloc(robot.handle, _stream_handle(stream), _ptr(q_dev), int(W),
                                             _ptr(points_dev), int(N), _ptr(dist_dev), _ptr(argmin_link_dev),
                                             _ptr(argmin_point_dev), _ptr(status_dev)))
+
+
+class Server:
+    """Serving engine (continuous batching of trajectory checks on one device)."""
+
+    STAT_NAMES = ("p50_us", "p99_us", "mean_us", "completed", "rejected", "batches", "mean_batch",
+                  "peak_in_flight", "pending", "max_us")
+
+    def __init__(self, device: int = 0, memory_budget_bytes: int = 0, slots: int = 4, max_batch: int = 64,
+                 max_waypoints: int = 16384, max_points: int = 100000, max_dof: int = 7,
+                 batch_window_us: int = 0):
+        cfg = sdf_server_config(int(device), int(memory_budget_bytes), int(slots), int(max_batch),
+                                int(max_waypoints), int(max_points), int(max_dof), int(batch_window_us))
+        h = ctypes.c_void_p()
+        rc = lib.sdf_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != SDF_OK:
+            raise SdfError(rc, "sdf_server_create failed")
+        self.handle = h
+
+    def set_cloud(self, points) -> int:
+        p = np.ascontiguousarray(points, dtype=np.float32).reshape(-1, 3)
+        return int(lib.sdf_server_set_cloud(self.handle, _ptr(p), int(p.shape[0])))
+
+    def submit(self, robot: "Robot", q) -> int:
+        """Queue a trajectory; returns its ticket (raises if rejected)."""
+        qa = np.ascontiguousarray(q, dtype=np.float32).reshape(-1, robot.dof)
+        t = ctypes.c_uint64()
+        rc = lib.sdf_server_submit(self.handle, robot.handle, _ptr(qa), int(qa.shape[0]), ctypes.byref(t))
+        if rc != SDF_OK:
+            raise SdfError(rc, "sdf_server_submit")
+        self._w = getattr(self, "_w", {})
+        self._w[int(t.value)] = int(qa.shape[0])
+        return int(t.value)
+
+    def poll(self, ticket: int, wait_us: int = -1):
+        """(status, dist, link, point, latency_us); status SDF_PENDING while unfinished."""
+        W = self._w[ticket]
+        d = np.empty(W, np.float32)
+        l = np.empty(W, np.int32)
+        p = np.empty(W, np.int32)
+        lat = ctypes.c_double()
+        rc = int(lib.sdf_server_poll(self.handle, ctypes.c_uint64(ticket), int(wait_us), _ptr(d), _ptr(l), _ptr(p),
+                                     ctypes.byref(lat)))
+        if rc != SDF_PENDING and rc != SDF_ERR_TIMEOUT:
+            self._w.pop(ticket, None)
+        return rc, d, l, p, float(lat.value)
+
+    def stats(self, reset: bool = False) -> dict:
+        out = np.zeros(10, dtype=np.float64)
+        rc = lib.sdf_server_stats(self.handle, _ptr(out), 10, int(reset))
+        if rc != SDF_OK:
+            raise SdfError(rc, "sdf_server_stats")
+        return dict(zip(self.STAT_NAMES, out.tolist()))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.sdf_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

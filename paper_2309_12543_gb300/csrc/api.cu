@@ -555,44 +555,52 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     const uint64_t key = shape_key(reqs, n);
     int tile_batch = sdf::kDefaultTileBatch;
     size_t points = 0, tiles = 0, supers = 0, blocks = 0, max_tiles = 0;
-    int k = 0;
+    int k = 0, nc = 0;
     for (int i = 0; i < n; ++i) {
         const sdf_check_request& r = reqs[i];
         if (r.W == 0) continue;
+        // requests passing the same cloud share its sort
+        int c = 0;
+        while (c < nc && !(p->cloud[c].points == r.points_dev && p->cloud[c].N == r.N)) ++c;
+        if (c == nc) {
+            sdf::CloudDesc& C = p->cloud[nc++];
+            C.points = r.points_dev;
+            C.N = r.N;
+            C.point_base = (int)points;
+            C.tile_base = (int)tiles;
+            C.super_base = (int)supers;
+            const size_t nt = ((size_t)r.N + 31) / 32;
+            points += (size_t)r.N;
+            tiles += nt;
+            supers += (nt + 31) / 32;
+            max_tiles = std::max(max_tiles, nt);
+        }
         sdf::InstDesc& I = p->inst[k++];
         I.robot = r.robot->d_table;
         I.q = r.q_dev;
-        I.points = r.points_dev;
         I.dist = r.dist_dev;
         I.arg_link = r.argmin_link_dev;
         I.arg_point = r.argmin_point_dev;
         I.W = r.W;
-        I.N = r.N;
         I.L = r.robot->table.L;
         I.dof = r.robot->dof;
-        I.point_base = (int)points;
-        I.tile_base = (int)tiles;
-        I.super_base = (int)supers;
+        I.cloud = c;
         launch_shape(ctx, key, I.L, &I.tw, &tile_batch);
         I.block_base = (int)blocks;
-        const size_t nt = ((size_t)r.N + 31) / 32;
-        points += (size_t)r.N;
-        tiles += nt;
-        supers += (nt + 31) / 32;
         blocks += ((size_t)r.W + I.tw - 1) / I.tw;
-        max_tiles = std::max(max_tiles, nt);
     }
     if (k == 0 || points > (size_t)INT32_MAX || blocks > (size_t)INT32_MAX) {
         delete p;
         return k == 0 ? SDF_OK : fail(ctx, SDF_ERR_INVALID_ARG, "batch too large");
     }
     DeviceGuard g(ctx->device);
-    int rc = reserve_scratch(ctx, points, tiles, supers, (size_t)k);
+    int rc = reserve_scratch(ctx, points, tiles, supers, (size_t)nc);
     if (rc != SDF_OK) {
         delete p;
         return rc;
     }
     p->n_inst = k;
+    p->n_cloud = nc;
     p->n_blocks = (int)blocks;
     p->stride = ctx->point_stride;
     p->cull = ctx->cull;

@@ -222,7 +222,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 
-// One cluster per trajectory sorts its cloud: 32^3 cell counters spread over the
+// One cluster per cloud sorts it: 32^3 cell counters spread over the
 // CTAs' shared memory, every phase one pass over the points with cluster barriers
 // in between; up to kPrepCached points per thread stay in registers between the
 // passes.
@@ -230,8 +230,8 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     prep_kernel(const __grid_constant__ BatchParams P) {
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned rank = cluster.block_rank();
-    const int inst = blockIdx.x / kPrepCtas;
-    const InstDesc& I = P.inst[inst];
+    const int cidx = blockIdx.x / kPrepCtas;
+    const CloudDesc& C = P.cloud[cidx];
     // the check grid may start now: its set-up reads nothing this kernel writes
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ unsigned s_bins[kBinsPerCta];     // counters, then cursors, of this CTA's cells
@@ -244,8 +244,8 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     constexpr int kStride = kPrepCtas * kPrepThreads;
     constexpr int kClusterWarps = kPrepCtas * (kPrepThreads / 32);
     const float kInf = __int_as_float(0x7f800000);
-    const int N = I.N;
-    const float* pts = I.points;
+    const int N = C.N;
+    const float* pts = C.points;
     const bool cached = N <= kStride * kPrepCached;
     // phase timestamps of the first CTA (SDF_OPT_STATS)
     const bool clock = P.stats != nullptr && rank == 0 && tid == 0;
@@ -362,7 +362,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     mark(22);
 
     // 4. scatter (order inside a cell is arbitrary; keys carry the original index)
-    float4* sorted = P.sorted + I.point_base;
+    float4* sorted = P.sorted + C.point_base;
     for_each_point([&](float3 p, int i) {
         if (finite3(p)) {
             const unsigned c = cell_key(p, blo, inv);
@@ -375,7 +375,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
 
     // 5. tile spheres: centre of the tile's box, radius to its farthest point
     const int n_tiles = (n_valid + 31) >> 5;
-    float4* tiles = P.tiles + I.tile_base;
+    float4* tiles = P.tiles + C.tile_base;
     for (int t = (int)rank * (kPrepThreads / 32) + warp; t < n_tiles; t += kClusterWarps) {
         const int i = t * 32 + lane;
         const bool v = i < n_valid;
@@ -401,7 +401,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     // 6. super-tile spheres over 32 consecutive tiles: box of the tile spheres,
     //    radius to the farthest tile sphere
     const int n_super = (n_tiles + 31) >> 5;
-    float4* supers = P.supers + I.super_base;
+    float4* supers = P.supers + C.super_base;
     for (int s = (int)rank * (kPrepThreads / 32) + warp; s < n_super; s += kClusterWarps) {
         const int t = s * 32 + lane;
         const bool v = t < n_tiles;
@@ -421,7 +421,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(kFull, r, o));
         if (lane == 0) supers[s] = make_float4(cx, cy, cz, r * (1.f + 1e-6f) + 1e-7f);
     }
-    if (rank == 0 && tid == 0) P.n_valid[inst] = n_valid;
+    if (rank == 0 && tid == 0) P.n_valid[cidx] = n_valid;
     mark(25);
 }
 
@@ -603,6 +603,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
         if (P.inst[mid].block_base <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
     }
     const InstDesc& I = P.inst[lo];
+    const CloudDesc& C = P.cloud[I.cloud];
     const LinkTable& T = *I.robot;
     const int L = I.L;
     const int w0 = ((int)blockIdx.x - I.block_base) * I.tw;
@@ -649,7 +650,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
     // wait for the sort (a no-op without programmatic dependent launch), then stage
     // this trajectory's tile and super-tile spheres
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int n_valid = P.n_valid[lo];
+    const int n_valid = P.n_valid[I.cloud];
     const int n_tiles = (n_valid + 31) >> 5;
     const int n_super = (n_tiles + 31) >> 5;
     const bool staged = n_tiles > 0 && n_tiles <= P.stage_tiles;
@@ -658,8 +659,8 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
         const unsigned tb = (unsigned)n_tiles * (unsigned)sizeof(float4);
         const unsigned sb = (unsigned)n_super * (unsigned)sizeof(float4);
         mbar_expect_tx(&s_mbar, tb + sb);
-        bulk_copy_g2s(s_spheres, P.tiles + I.tile_base, tb, &s_mbar);
-        bulk_copy_g2s(s_spheres + P.stage_tiles, P.supers + I.super_base, sb, &s_mbar);
+        bulk_copy_g2s(s_spheres, P.tiles + C.tile_base, tb, &s_mbar);
+        bulk_copy_g2s(s_spheres + P.stage_tiles, P.supers + C.super_base, sb, &s_mbar);
     }
     __syncthreads();
     if (staged) {
@@ -674,13 +675,13 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
             return;
         }
     }
-    const float4* tiles = staged ? s_spheres : P.tiles + I.tile_base;
-    const float4* supers = staged ? s_spheres + P.stage_tiles : P.supers + I.super_base;
+    const float4* tiles = staged ? s_spheres : P.tiles + C.tile_base;
+    const float4* supers = staged ? s_spheres + P.stage_tiles : P.supers + C.super_base;
     const unsigned long long t_fk = (stats && tid == 0) ? global_ns() : 0ull;
     const float4 sph = s_pose[pair_warp ? warp : 0][3];
 
     BlockState B;
-    B.sorted = P.sorted + I.point_base;
+    B.sorted = P.sorted + C.point_base;
     B.values = T.values;
     B.n = T.n;
     B.L = L;
@@ -879,7 +880,7 @@ cudaError_t configure_kernels() {
 
 cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, cudaEvent_t ev_mid) {
     if (p.n_inst <= 0 || p.n_blocks <= 0) return cudaSuccess;
-    prep_kernel<<<kPrepCtas * p.n_inst, kPrepThreads, 0, s>>>(p);
+    prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev_mid) {   // a timing event between the kernels; the check then starts after the sort ends

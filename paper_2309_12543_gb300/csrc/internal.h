@@ -37,24 +37,31 @@ struct LinkTable {
     const float* values;           // L grids of n^3 floats, x fastest
 };
 
-// One trajectory check inside a launch.  Offsets index the batch-wide scratch.
-struct InstDesc {
-    const LinkTable* robot;   // device copy
-    const float* q;           // W x dof
+// One obstacle cloud of a launch (requests that pass the same cloud share it).
+struct CloudDesc {
     const float* points;      // N x stride
-    float* dist;
-    int32_t* arg_link;
-    int32_t* arg_point;
-    int W, N, L, dof;
+    int N;
     int point_base;           // sorted points (N)
     int tile_base;            // ceil(N / 32) tile spheres
     int super_base;           // ceil(N / 1024) super-tile spheres
+};
+
+// One trajectory check inside a launch.
+struct InstDesc {
+    const LinkTable* robot;   // device copy
+    const float* q;           // W x dof
+    float* dist;
+    int32_t* arg_link;
+    int32_t* arg_point;
+    int W, L, dof;
+    int cloud;                // index into BatchParams::cloud
     int tw;                   // waypoints per check block (tw * L <= kCheckWarps)
     int block_base;           // first check block of this trajectory
 };
 
 struct BatchParams {
     int n_inst;
+    int n_cloud;
     int n_blocks;             // check blocks over all trajectories
     int stride;               // floats per point: 3 or 4
     int cull;                 // 0: evaluate every pair
@@ -62,9 +69,10 @@ struct BatchParams {
     float4* sorted;           // finite points, spatially sorted: x, y, z, original index bits
     float4* tiles;            // sphere of each 32-point tile
     float4* supers;           // sphere of each 32-tile super-tile
-    int* n_valid;             // finite points per trajectory
+    int* n_valid;             // finite points per cloud
     int* status;              // device status bits
     unsigned long long* stats;  // kStatCount counters, or null (statistics off)
+    CloudDesc cloud[kMaxBatch];
     InstDesc inst[kMaxBatch];
 };
 

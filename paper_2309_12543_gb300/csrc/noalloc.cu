@@ -83,22 +83,25 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), stream);
 
         sdf::BatchParams& p = t_params;
+        sdf::CloudDesc& C = p.cloud[0];
+        C.points = points_dev;
+        C.N = N;
+        C.point_base = C.tile_base = C.super_base = 0;
         sdf::InstDesc& I = p.inst[0];
         I.robot = R->d_table;
         I.q = q_dev;
-        I.points = points_dev;
         I.dist = dist_dev;
         I.arg_link = argmin_link_dev;
         I.arg_point = argmin_point_dev;
         I.W = W;
-        I.N = N;
         I.L = R->table.L;
         I.dof = R->dof;
-        I.point_base = I.tile_base = I.super_base = 0;
+        I.cloud = 0;
         I.tw = sdf::kCheckWarps / I.L > 0 ? sdf::kCheckWarps / I.L : 1;
         I.block_base = 0;
         const int n_tiles = (N + 31) / 32;
         p.n_inst = 1;
+        p.n_cloud = 1;
         p.n_blocks = (W + I.tw - 1) / I.tw;
         p.stride = 3;
         p.cull = 1;

@@ -1,0 +1,411 @@
+// Serving engine: a request loop that batches incoming trajectory checks as they
+// arrive (continuous batching) against the latest published obstacle cloud.
+//
+// The paper's controller needs distances along the executing trajectory in every
+// control cycle (about 10 ms; 8 ms for the b-CAP protocol, Sec. I).  Clients submit
+// trajectories from any thread; one engine thread forms batches whenever one of
+// `slots` in-flight slots is free and the device-memory budget admits the batch,
+// launches it with check_batch on the slot's own stream (so batches overlap on the
+// device), and a host callback marks its requests done when the results are back
+// in host memory.  Grids, robots and the latest cloud stay resident on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    const sdf_robot* robot = nullptr;
+    std::vector<float> q;            // W x dof
+    int W = 0;
+    size_t bytes = 0;                // device footprint of its buffers
+    Clock::time_point submitted;
+    int state = 0;                   // 0 pending, 1 in flight, 2 done
+    int status = SDF_OK;
+    std::vector<float> dist;
+    std::vector<int32_t> link, point;
+    double latency_us = 0.0;
+};
+
+struct CloudBuf {
+    float* d = nullptr;              // device, max_points x 3
+    float* h = nullptr;              // pinned staging
+    int N = 0;
+    int refs = 0;                    // in-flight batches using it
+    cudaEvent_t ready = nullptr;     // its upload finished
+};
+
+struct Slot {
+    sdf_server* srv = nullptr;
+    sdf_ctx* ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    float* d_q = nullptr;            // max_waypoints x max_dof
+    float* h_q = nullptr;            // pinned
+    float* d_out = nullptr;          // dist | link | point, max_waypoints each
+    float* h_out = nullptr;          // pinned
+    std::vector<std::shared_ptr<Request>> reqs;
+    int cloud = -1;
+    size_t bytes = 0;
+    std::atomic<bool> finished{false};
+    bool busy = false;
+};
+
+}  // namespace
+
+struct sdf_server {
+    sdf_server_config cfg;
+    std::vector<std::unique_ptr<Slot>> slots;
+    std::vector<CloudBuf> clouds;
+    cudaStream_t upload = nullptr;
+    int current_cloud = -1;
+    std::mutex mu;
+    std::condition_variable cv;      // engine wake-up and client wake-up
+    std::deque<std::shared_ptr<Request>> pending;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> by_ticket;
+    uint64_t next_ticket = 1;
+    size_t in_flight_bytes = 0;
+    size_t scratch_bytes = 0;        // per batch: sorted cloud and spheres
+    bool stop = false;
+    std::thread engine;
+    // statistics
+    std::vector<double> latencies;
+    uint64_t completed = 0, rejected = 0, batches = 0, batched_requests = 0;
+    int in_flight = 0, peak_in_flight = 0;
+    std::string err;
+};
+
+namespace {
+
+// Runs on a CUDA-internal thread once the batch's results are in host memory.  It
+// makes no CUDA call and takes no lock (the engine may hold the lock while it
+// synchronises this stream); the engine also wakes on its own every 200 us.
+void CUDART_CB on_batch_done(void* arg) {
+    Slot* s = static_cast<Slot*>(arg);
+    s->finished.store(true, std::memory_order_release);
+    s->srv->cv.notify_all();
+}
+
+size_t request_bytes(const sdf_server* S, int W, int dof) {
+    (void)S;
+    return (size_t)W * ((size_t)dof * sizeof(float) + sizeof(float) + 2 * sizeof(int32_t));
+}
+
+// Retire finished batches: results to their requests, memory and cloud released.
+void retire(sdf_server* S, std::unique_lock<std::mutex>& lk) {
+    (void)lk;
+    for (auto& sp : S->slots) {
+        Slot& s = *sp;
+        if (!s.busy || !s.finished.load(std::memory_order_acquire)) continue;
+        const int rc = sdf_ctx_synchronize(s.ctx);
+        const auto now = Clock::now();
+        const int maxw = S->cfg.max_waypoints;
+        int off = 0;
+        for (auto& r : s.reqs) {
+            r->dist.assign(s.h_out + off, s.h_out + off + r->W);
+            const int32_t* li = reinterpret_cast<const int32_t*>(s.h_out + maxw);
+            const int32_t* pi = reinterpret_cast<const int32_t*>(s.h_out + 2 * maxw);
+            r->link.assign(li + off, li + off + r->W);
+            r->point.assign(pi + off, pi + off + r->W);
+            if (r->status == SDF_OK) r->status = rc;
+            r->latency_us = std::chrono::duration<double, std::micro>(now - r->submitted).count();
+            r->state = 2;
+            S->latencies.push_back(r->latency_us);
+            ++S->completed;
+            off += r->W;
+        }
+        s.reqs.clear();
+        S->in_flight_bytes -= s.bytes;
+        S->clouds[s.cloud].refs--;
+        s.busy = false;
+        s.finished.store(false, std::memory_order_relaxed);
+        --S->in_flight;
+    }
+}
+
+// Form and launch batches while a slot is free and requests are waiting.
+void launch(sdf_server* S) {
+    while (!S->pending.empty() && S->current_cloud >= 0) {
+        Slot* slot = nullptr;
+        for (auto& sp : S->slots)
+            if (!sp->busy) { slot = sp.get(); break; }
+        if (!slot) return;
+        if (S->cfg.batch_window_us > 0 && (int)S->pending.size() < S->cfg.max_batch) {
+            const auto waited = std::chrono::duration_cast<std::chrono::microseconds>(
+                Clock::now() - S->pending.front()->submitted).count();
+            if (waited < S->cfg.batch_window_us) return;   // the engine wakes every 200 us
+        }
+        // admission: requests in arrival order while the batch fits the slot and the
+        // memory budget (in-flight batches included)
+        size_t bytes = S->scratch_bytes;
+        int W = 0, n = 0;
+        for (auto& r : S->pending) {
+            if (n == S->cfg.max_batch || W + r->W > S->cfg.max_waypoints) break;
+            if (S->in_flight_bytes + bytes + r->bytes > (size_t)S->cfg.memory_budget_bytes) break;
+            bytes += r->bytes;
+            W += r->W;
+            ++n;
+        }
+        if (n == 0) return;   // wait for memory to be released
+        Slot& s = *slot;
+        s.reqs.assign(S->pending.begin(), S->pending.begin() + n);
+        S->pending.erase(S->pending.begin(), S->pending.begin() + n);
+        CloudBuf& cb = S->clouds[S->current_cloud];
+        s.cloud = S->current_cloud;
+        cb.refs++;
+        // pack joint values, enqueue copy, check, copy back, completion callback
+        const int maxw = S->cfg.max_waypoints;
+        std::vector<sdf_check_request> req(n);
+        size_t qoff = 0;
+        int woff = 0;
+        for (int i = 0; i < n; ++i) {
+            Request& r = *s.reqs[i];
+            std::memcpy(s.h_q + qoff, r.q.data(), r.q.size() * sizeof(float));
+            req[i].robot = r.robot;
+            req[i].q_dev = s.d_q + qoff;
+            req[i].W = r.W;
+            req[i].points_dev = cb.d;
+            req[i].N = cb.N;
+            req[i].dist_dev = s.d_out + woff;
+            req[i].argmin_link_dev = reinterpret_cast<int32_t*>(s.d_out + maxw) + woff;
+            req[i].argmin_point_dev = reinterpret_cast<int32_t*>(s.d_out + 2 * maxw) + woff;
+            qoff += r.q.size();
+            woff += r.W;
+            r.state = 1;
+        }
+        int rc = SDF_OK;
+        if (cudaMemcpyAsync(s.d_q, s.h_q, qoff * sizeof(float), cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
+            cudaStreamWaitEvent(s.stream, cb.ready, 0) != cudaSuccess)
+            rc = SDF_ERR_CUDA;
+        if (rc == SDF_OK) rc = check_batch(s.ctx, req.data(), n);
+        for (int part = 0; part < 3 && rc == SDF_OK; ++part)
+            if (cudaMemcpyAsync(s.h_out + part * maxw, s.d_out + part * maxw, (size_t)woff * sizeof(float),
+                                cudaMemcpyDeviceToHost, s.stream) != cudaSuccess)
+                rc = SDF_ERR_CUDA;
+        s.bytes = bytes;
+        s.busy = true;
+        S->in_flight_bytes += bytes;
+        S->in_flight++;
+        S->peak_in_flight = std::max(S->peak_in_flight, S->in_flight);
+        S->batches++;
+        S->batched_requests += (uint64_t)n;
+        if (rc == SDF_OK && cudaLaunchHostFunc(s.stream, on_batch_done, &s) != cudaSuccess) rc = SDF_ERR_CUDA;
+        if (rc != SDF_OK) {
+            // report the failure on these requests; the slot is released at once
+            for (auto& r : s.reqs) r->status = rc;
+            s.finished.store(true, std::memory_order_release);
+        }
+    }
+}
+
+void engine_loop(sdf_server* S) {
+    cudaSetDevice(S->cfg.device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        retire(S, lk);
+        launch(S);
+        S->cv.notify_all();   // clients waiting on results
+        S->cv.wait_for(lk, std::chrono::microseconds(200));
+    }
+}
+
+void free_server(sdf_server* S) {
+    for (auto& sp : S->slots) {
+        Slot& s = *sp;
+        if (s.stream) cudaStreamSynchronize(s.stream);
+        cudaFree(s.d_q);
+        cudaFree(s.d_out);
+        cudaFreeHost(s.h_q);
+        cudaFreeHost(s.h_out);
+        if (s.ctx) sdf_ctx_destroy(s.ctx);
+        if (s.stream) cudaStreamDestroy(s.stream);
+    }
+    for (auto& c : S->clouds) {
+        cudaFree(c.d);
+        cudaFreeHost(c.h);
+        if (c.ready) cudaEventDestroy(c.ready);
+    }
+    if (S->upload) cudaStreamDestroy(S->upload);
+    delete S;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdf_server_create(const sdf_server_config* cfg, sdf_server** out) {
+    if (!cfg || !out) return SDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    sdf_server_config c = *cfg;
+    if (c.slots < 1 || c.slots > 16 || c.max_batch < 1 || c.max_batch > SDF_MAX_BATCH || c.max_waypoints < 1 ||
+        c.max_points < 0 || c.max_points > SDF_MAX_POINTS || c.max_dof < 0 || c.max_dof + 1 > SDF_MAX_LINKS ||
+        c.memory_budget_bytes < 0 || c.batch_window_us < 0)
+        return SDF_ERR_INVALID_ARG;
+    if (cudaSetDevice(c.device) != cudaSuccess) return SDF_ERR_INVALID_ARG;
+    if (c.memory_budget_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return SDF_ERR_CUDA;
+        c.memory_budget_bytes = (int64_t)(fr / 4);
+    }
+    sdf_server* S = new (std::nothrow) sdf_server();
+    if (!S) return SDF_ERR_OOM;
+    S->cfg = c;
+    const size_t np = (size_t)std::max(c.max_points, 1);
+    S->scratch_bytes = np * sizeof(float4) + (np / 32 + 2) * sizeof(float4) * 2 + 64;
+    int rc = SDF_OK;
+    if (cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking) != cudaSuccess) rc = SDF_ERR_CUDA;
+    const int kClouds = c.slots + 2;   // enough that a free buffer exists while slots hold theirs
+    S->clouds.resize(kClouds);
+    for (auto& cb : S->clouds) {
+        if (rc != SDF_OK) break;
+        if (cudaMalloc((void**)&cb.d, np * 3 * sizeof(float)) != cudaSuccess ||
+            cudaMallocHost((void**)&cb.h, np * 3 * sizeof(float)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&cb.ready, cudaEventDisableTiming) != cudaSuccess)
+            rc = SDF_ERR_OOM;
+    }
+    const size_t qn = (size_t)c.max_waypoints * std::max(c.max_dof, 1);
+    for (int i = 0; i < c.slots && rc == SDF_OK; ++i) {
+        S->slots.emplace_back(new Slot());
+        Slot& s = *S->slots.back();
+        s.srv = S;
+        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) { rc = SDF_ERR_CUDA; break; }
+        rc = sdf_ctx_create(&s.ctx, c.device, s.stream);
+        if (rc != SDF_OK) break;
+        rc = sdf_ctx_reserve(s.ctx, c.max_points, c.max_waypoints, (int64_t)c.max_waypoints * (c.max_dof + 1),
+                             c.max_batch);
+        if (rc != SDF_OK) break;
+        if (cudaMalloc((void**)&s.d_q, qn * sizeof(float)) != cudaSuccess ||
+            cudaMallocHost((void**)&s.h_q, qn * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&s.d_out, 3 * (size_t)c.max_waypoints * sizeof(float)) != cudaSuccess ||
+            cudaMallocHost((void**)&s.h_out, 3 * (size_t)c.max_waypoints * sizeof(float)) != cudaSuccess)
+            rc = SDF_ERR_OOM;
+    }
+    if (rc != SDF_OK) {
+        free_server(S);
+        return rc;
+    }
+    S->engine = std::thread(engine_loop, S);
+    *out = S;
+    return SDF_OK;
+}
+
+void sdf_server_destroy(sdf_server* S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv.notify_all();
+    }
+    if (S->engine.joinable()) S->engine.join();
+    cudaSetDevice(S->cfg.device);
+    free_server(S);
+}
+
+int sdf_server_set_cloud(sdf_server* S, const float* points_host, int32_t N) {
+    if (!S || N < 0 || N > S->cfg.max_points || (N > 0 && !points_host)) return SDF_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    int pick = -1;
+    for (int i = 0; i < (int)S->clouds.size(); ++i)
+        if (i != S->current_cloud && S->clouds[i].refs == 0) { pick = i; break; }
+    if (pick < 0) return SDF_ERR_TIMEOUT;   // every buffer is held by in-flight batches
+    CloudBuf& cb = S->clouds[pick];
+    // the previous upload into this buffer is complete once no batch holds it and its
+    // own upload event has fired
+    if (cudaEventSynchronize(cb.ready) != cudaSuccess) return SDF_ERR_CUDA;
+    cudaSetDevice(S->cfg.device);
+    std::memcpy(cb.h, points_host, (size_t)N * 3 * sizeof(float));
+    cb.N = N;
+    if (N > 0 && cudaMemcpyAsync(cb.d, cb.h, (size_t)N * 3 * sizeof(float), cudaMemcpyHostToDevice, S->upload) !=
+                     cudaSuccess)
+        return SDF_ERR_CUDA;
+    if (cudaEventRecord(cb.ready, S->upload) != cudaSuccess) return SDF_ERR_CUDA;
+    S->current_cloud = pick;
+    S->cv.notify_all();
+    return SDF_OK;
+}
+
+int sdf_server_submit(sdf_server* S, const sdf_robot* robot, const float* q_host, int32_t W, uint64_t* ticket) {
+    if (!S || !robot || !ticket || W < 1 || (robot->dof > 0 && !q_host)) return SDF_ERR_INVALID_ARG;
+    if (robot->device != S->cfg.device || robot->dof > S->cfg.max_dof || W > S->cfg.max_waypoints)
+        return SDF_ERR_INVALID_ARG;
+    auto r = std::make_shared<Request>();
+    r->robot = robot;
+    r->W = W;
+    r->q.assign(q_host, q_host + (size_t)W * robot->dof);
+    r->bytes = request_bytes(S, W, robot->dof);
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (r->bytes + S->scratch_bytes > (size_t)S->cfg.memory_budget_bytes) {
+        ++S->rejected;
+        return SDF_ERR_OOM;   // could never be admitted
+    }
+    r->ticket = S->next_ticket++;
+    r->submitted = Clock::now();
+    S->pending.push_back(r);
+    S->by_ticket[r->ticket] = r;
+    *ticket = r->ticket;
+    S->cv.notify_all();
+    return SDF_OK;
+}
+
+int sdf_server_poll(sdf_server* S, uint64_t ticket, int64_t wait_us, float* dist, int32_t* link, int32_t* point,
+                    double* latency_us) {
+    if (!S) return SDF_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->by_ticket.find(ticket);
+    if (it == S->by_ticket.end()) return SDF_ERR_INVALID_ARG;
+    std::shared_ptr<Request> r = it->second;
+    if (r->state != 2 && wait_us != 0) {
+        const auto until = Clock::now() + std::chrono::microseconds(wait_us < 0 ? 60000000 : wait_us);
+        S->cv.wait_until(lk, until, [&] { return r->state == 2 || S->stop; });
+    }
+    if (r->state != 2) return wait_us != 0 ? SDF_ERR_TIMEOUT : SDF_PENDING;
+    if (dist) std::memcpy(dist, r->dist.data(), (size_t)r->W * sizeof(float));
+    if (link) std::memcpy(link, r->link.data(), (size_t)r->W * sizeof(int32_t));
+    if (point) std::memcpy(point, r->point.data(), (size_t)r->W * sizeof(int32_t));
+    if (latency_us) *latency_us = r->latency_us;
+    S->by_ticket.erase(it);
+    return r->status;
+}
+
+int sdf_server_stats(sdf_server* S, double* out, int32_t n, int32_t reset) {
+    if (!S || n < 0 || (n > 0 && !out)) return SDF_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::vector<double> v = S->latencies;
+    auto pct = [&](double p) -> double {
+        if (v.empty()) return 0.0;
+        const size_t k = std::min(v.size() - 1, (size_t)(p * (double)(v.size() - 1) + 0.5));
+        std::nth_element(v.begin(), v.begin() + k, v.end());
+        return v[k];
+    };
+    double mean = 0.0;
+    for (double x : S->latencies) mean += x;
+    if (!S->latencies.empty()) mean /= (double)S->latencies.size();
+    const double vals[SDF_SERVER_STAT_COUNT] = {
+        pct(0.50), pct(0.99), mean, (double)S->completed, (double)S->rejected, (double)S->batches,
+        S->batches ? (double)S->batched_requests / (double)S->batches : 0.0, (double)S->peak_in_flight,
+        (double)S->pending.size(), v.empty() ? 0.0 : *std::max_element(S->latencies.begin(), S->latencies.end())};
+    for (int i = 0; i < n && i < SDF_SERVER_STAT_COUNT; ++i) out[i] = vals[i];
+    if (reset) {
+        S->latencies.clear();
+        S->completed = S->rejected = S->batches = S->batched_requests = 0;
+        S->peak_in_flight = S->in_flight;
+    }
+    return SDF_OK;
+}
+
+}  // extern "C"

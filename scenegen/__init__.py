@@ -447,3 +447,24 @@ def make_batched(seed: int = 3, n: int = 64, W_range=(50, 1000), N_range=(1000, 
         q = spline_trajectory(rng, arms[a].dh, 5, W)
         insts.append((a, q, sample_voxels(rng, cells, N, order=order)))
     return BatchedScene(arms, insts)
+
+
+# ------------------------------------------------------------- serving workload
+
+def drifting_clouds(seed: int = 5, cycles: int = 250, N_range=(5000, 80000), sigma: float = 0.005,
+                    voxel: float = 0.02, order: str = "voxel"):
+    """Clouds for a control-cycle stream: three human clusters whose positions take
+    a Gaussian random walk (``sigma`` metres per axis per cycle, so about 0.9 cm
+    per cycle on average), voxelised at ``voxel`` and sampled to N ~ U(N_range)
+    points each cycle."""
+    rng = np.random.default_rng(seed)
+    clusters = [human_voxels(rng, 1, voxel) for _ in range(3)]
+    offs = np.zeros((3, 3))
+    out = []
+    for _ in range(cycles):
+        offs += rng.normal(0.0, sigma, size=(3, 3))
+        shift = np.round(offs / voxel).astype(np.int64)
+        cells = np.unique(np.concatenate([c + shift[i] for i, c in enumerate(clusters)]), axis=0)
+        N = min(int(rng.integers(N_range[0], N_range[1] + 1)), cells.shape[0])
+        out.append(sample_voxels(rng, cells, N, voxel, order).astype(np.float32))
+    return out

@@ -1,0 +1,130 @@
+"""Serving engine: continuous batching of trajectory checks against the latest
+cloud.  Each result must be the same alone (check_trajectory on the same cloud)
+and in the mix, bit for bit; admission respects the memory budget; requests use
+the cloud that was current when their batch formed."""
+import numpy as np
+import pytest
+
+import scenegen as sg
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sdf():
+    from paper_2309_12543_gb300 import build
+    build.build()
+    import paper_2309_12543_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def world(sdf):
+    ctx = sdf.Context(0, torch.cuda.current_stream())
+    arms = []
+    for dof, seed in ((6, 31), (7, 32)):
+        sc = sg.make_scene("tiny", dof=dof, seed=seed, resolution=24)
+        g = sdf.sdf_build_grids(ctx, sc.meshes, sc.resolution, sc.margin)
+        arms.append((sc, sdf.Robot(ctx, sc.dh, g, sc.base)))
+    return ctx, arms
+
+
+def _alone(sdf, ctx, robot, q, pts):
+    W, N = q.shape[0], pts.shape[0]
+    out = tuple(torch.empty(W, dtype=dt, device="cuda") for dt in (torch.float32, torch.int32, torch.int32))
+    sdf.check_trajectory(ctx, robot, torch.tensor(q, dtype=torch.float32, device="cuda"), W,
+                         torch.tensor(pts, dtype=torch.float32, device="cuda"), N, *out)
+    assert ctx.synchronize() == 0
+    return tuple(t.cpu().numpy() for t in out)
+
+
+def test_results_alone_equal_in_the_mix(sdf, world):
+    ctx, arms = world
+    rng = np.random.default_rng(41)
+    pts = sg.cloud_uniform(rng, 3000).astype(np.float32)
+    # a 20 ms batch window: batches fill to max_batch (the last one waits out the window)
+    srv = sdf.Server(0, slots=3, max_batch=8, max_waypoints=4096, max_points=5000, max_dof=7,
+                     batch_window_us=20000)
+    assert srv.set_cloud(pts) == sdf.SDF_OK
+    jobs = []
+    for i in range(60):
+        sc, robot = arms[i % 2]
+        q = sg.spline_trajectory(rng, sc.dh, 3, int(rng.integers(1, 400))).astype(np.float32)
+        jobs.append((robot, q, srv.submit(robot, q)))
+    for robot, q, t in jobs:
+        rc, d, l, p, lat = srv.poll(t, wait_us=-1)
+        assert rc == sdf.SDF_OK and lat > 0
+        d0, l0, p0 = _alone(sdf, ctx, robot, q, pts)
+        assert np.array_equal(d.view(np.uint32), d0.view(np.uint32))
+        assert np.array_equal(l, l0) and np.array_equal(p, p0)
+    st = srv.stats()
+    assert st["completed"] == 60 and st["batches"] <= 60 and st["p99_us"] >= st["p50_us"] > 0
+    assert st["mean_batch"] > 1.0            # requests were batched together
+    srv.close()
+
+
+def test_batch_window_holds_a_lone_request(sdf, world):
+    ctx, arms = world
+    sc, robot = arms[0]
+    rng = np.random.default_rng(44)
+    pts = sg.cloud_uniform(rng, 1000).astype(np.float32)
+    srv = sdf.Server(0, slots=2, max_batch=4, max_waypoints=1024, max_points=2000, max_dof=7,
+                     batch_window_us=5000)
+    srv.set_cloud(pts)
+    q = sg.spline_trajectory(rng, sc.dh, 3, 50).astype(np.float32)
+    rc, d, _, _, lat = srv.poll(srv.submit(robot, q), wait_us=-1)
+    assert rc == sdf.SDF_OK and lat >= 5000.0
+    assert np.array_equal(d.view(np.uint32), _alone(sdf, ctx, robot, q, pts)[0].view(np.uint32))
+    # four requests fill max_batch and launch without waiting out the window
+    qs = [sg.spline_trajectory(rng, sc.dh, 3, 50).astype(np.float32) for _ in range(4)]
+    ts = [srv.submit(robot, x) for x in qs]
+    lats = [srv.poll(t, wait_us=-1)[4] for t in ts]
+    assert max(lats) < 5000.0
+    with pytest.raises(sdf.SdfError):
+        sdf.Server(0, batch_window_us=-1)
+    srv.close()
+
+
+def test_admission_by_memory_budget(sdf, world):
+    ctx, arms = world
+    sc, robot = arms[0]
+    rng = np.random.default_rng(42)
+    pts = sg.cloud_uniform(rng, 2000).astype(np.float32)
+    # the budget admits the sort scratch plus roughly one 300-waypoint request at a time
+    scratch = 5000 * 16 + (5000 // 32 + 2) * 32 + 64
+    budget = scratch + 300 * (6 * 4 + 12) + 100
+    srv = sdf.Server(0, memory_budget_bytes=budget, slots=4, max_batch=8, max_waypoints=2048, max_points=5000,
+                     max_dof=7)
+    srv.set_cloud(pts)
+    with pytest.raises(sdf.SdfError) as e:
+        srv.submit(robot, np.zeros((1000, 6), np.float32))      # alone exceeds the budget
+    assert e.value.code == sdf.SDF_ERR_OOM
+    qs = [sg.spline_trajectory(rng, sc.dh, 3, 300).astype(np.float32) for _ in range(6)]
+    tickets = [srv.submit(robot, q) for q in qs]
+    for q, t in zip(qs, tickets):
+        rc, d, l, p, _ = srv.poll(t, wait_us=-1)
+        assert rc == sdf.SDF_OK
+        d0, _, _ = _alone(sdf, ctx, robot, q, pts)
+        assert np.array_equal(d.view(np.uint32), d0.view(np.uint32))
+    st = srv.stats()
+    assert st["peak_in_flight"] == 1 and st["rejected"] == 1 and st["batches"] == 6
+    srv.close()
+
+
+def test_requests_use_the_current_cloud(sdf, world):
+    ctx, arms = world
+    sc, robot = arms[1]
+    rng = np.random.default_rng(43)
+    a = sg.cloud_uniform(rng, 2500).astype(np.float32)
+    b = (sg.cloud_uniform(rng, 1800) * 0.5).astype(np.float32)
+    srv = sdf.Server(0, slots=2, max_batch=4, max_waypoints=2048, max_points=5000, max_dof=7)
+    q = sg.spline_trajectory(rng, sc.dh, 3, 64).astype(np.float32)
+    srv.set_cloud(a)
+    rc, da, _, _, _ = srv.poll(srv.submit(robot, q), wait_us=-1)
+    srv.set_cloud(b)
+    rc2, db, _, _, _ = srv.poll(srv.submit(robot, q), wait_us=-1)
+    assert rc == rc2 == sdf.SDF_OK
+    assert np.array_equal(da.view(np.uint32), _alone(sdf, ctx, robot, q, a)[0].view(np.uint32))
+    assert np.array_equal(db.view(np.uint32), _alone(sdf, ctx, robot, q, b)[0].view(np.uint32))
+    srv.close()
