@@ -34,13 +34,17 @@ UNIT = "µs per check"
 # one cull test per (waypoint, link, point) pair: 3 sub, 1 mul, 2 fma, 1 compare
 CULL_OPS_PER_PAIR = 7
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one check_kernel launch on the 500 x 20k workload,
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
+# launch); profiles/check_kernel_paper_500x20k.md holds the capture and its command.
+CHECK_KERNEL_DRAM_BYTES = 11_810_816
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="paper", choices=["paper", "tiny", "batched", "serve"])
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of 125 Hz cycles")
@@ -327,6 +331,15 @@ def run_ours(args):
             e2e.append(dt * 1e6)
     assert np.array_equal(dh_.view(np.uint32), dist_o.cpu().numpy().view(np.uint32))
 
+    # gather roofline: lookups one check performs (statistics pass, untimed) against
+    # the measured rate of random 8-corner cell reads on the same grids
+    ctx.set_option(sdf.SDF_OPT_STATS, 1)
+    ctx.stats(reset=True)
+    step()
+    st = ctx.stats(reset=True)
+    ctx.set_option(sdf.SDF_OPT_STATS, 0)
+    gathers_ps, cells_ps = sdf.sdf_measure_gather(ctx, grids)
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -350,11 +363,20 @@ def run_ours(args):
         "grid_build_s": grid_build_s,
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved_ops / peak_ops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved_ops / peak_ops,
+                     "traffic": CHECK_KERNEL_DRAM_BYTES if scene.name == "paper" else None,
                      "kernel": "check_kernel", "kernel_us": kern_us,
                      "prep_kernel_us": statistics.mean(prep_ms) * 1e3,
                      "algorithmic": f"{CULL_OPS_PER_PAIR} FP32 ops x {pairs} (waypoint, link, point) pairs",
                      "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz"},
+        "gather": {"lookups_per_check": st["seed_lookups"] + st["lookups"],
+                   "achieved_lookups_per_s": (st["seed_lookups"] + st["lookups"]) / (kern_us * 1e-6),
+                   "peak_cell_reads_per_s": cells_ps, "peak_gathers_per_s": gathers_ps,
+                   "frac": (st["seed_lookups"] + st["lookups"]) / (kern_us * 1e-6) / cells_ps,
+                   "effective_pairs_per_s": pairs / (kern_us * 1e-6),
+                   "effective_frac": pairs / (kern_us * 1e-6) / cells_ps,
+                   "point_tests_per_check": st["point_tests"],
+                   "peak_source": "sdf_measure_gather on the check's grids (random cells, 2-8 blocks/SM, best)"},
         "e2e": {"value": statistics.median(e2e), "unit": UNIT, "p99": percentile(e2e, 99),
                 "h2d_bytes_per_step": int(qh.nbytes + ph.nbytes),
                 "d2h_bytes_per_step": int(dh_.nbytes + lh.nbytes + ph_.nbytes)},

@@ -154,6 +154,16 @@ int sdf_ctx_last_kernel_ms(sdf_ctx* ctx, int32_t kernel, float* ms);
 #define SDF_STAT_COUNT 32
 int sdf_ctx_stats(sdf_ctx* ctx, int64_t* out, int32_t n, int32_t reset);
 
+/* Gather roofline (measurement only).  A grid lookup (Sec. III-B, trilinear
+ * interpolation) reads the 8 corner values of one cell of one link grid at a
+ * data-dependent place, so the ceiling of the lookup rate is the rate of such reads.
+ * Times, with CUDA events on the context stream, kernels that read `grids`' values
+ * at pseudo-random places over 2, 4 and 8 blocks of 256 threads per SM and keeps the
+ * best:  gathers_per_s = independent random 4-byte loads per second;
+ * cells_per_s = random 8-corner cell reads per second.  Either output may be NULL.
+ * Allocates 4 bytes; synchronises.  Errors: INVALID_ARG, CUDA. */
+int sdf_measure_gather(sdf_ctx* ctx, const sdf_grids* grids, double* gathers_per_s, double* cells_per_s);
+
 /* --------------------------------------------------------------------- grids */
 
 /* Pre-processing (Sec. III-A, "Link SDFs"): build one signed distance grid per link

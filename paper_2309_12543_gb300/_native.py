@@ -89,6 +89,7 @@ def _load():
         "sdf_ctx_get_option": (ctypes.c_int, [P, i32, ctypes.POINTER(i64)]),
         "sdf_ctx_synchronize": (ctypes.c_int, [P]),
         "sdf_ctx_stats": (ctypes.c_int, [P, P, i32, i32]),
+        "sdf_measure_gather": (ctypes.c_int, [P, P, P, P]),
         "sdf_ctx_last_kernel_ms": (ctypes.c_int, [P, i32, ctypes.POINTER(ctypes.c_float)]),
         "sdf_build_grids": (ctypes.c_int, [P, P, i32, i32, ctypes.c_float, ctypes.POINTER(P)]),
         "sdf_grids_upload": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(P)]),
@@ -128,7 +129,7 @@ EXPORTED = ("sdf_ctx_create", "sdf_ctx_destroy", "sdf_ctx_set_stream", "sdf_last
             "sdf_forward_kinematics", "check_trajectory", "check_trajectory_host",
             "check_trajectory_noalloc", "check_batch", "sdf_ctx_reserve", "sdf_autotune",
             "sdf_server_create", "sdf_server_destroy", "sdf_server_set_cloud", "sdf_server_submit",
-            "sdf_server_poll", "sdf_server_stats")
+            "sdf_server_poll", "sdf_server_stats", "sdf_measure_gather")
 
 
 def _ptr(x) -> int:
@@ -352,6 +353,14 @@ def sdf_autotune(ctx: Context, requests, repeats: int = 5):
     ctx._check(lib.sdf_autotune(ctx.handle, ctypes.addressof(arr), len(requests), int(repeats), ctypes.byref(tw),
                                 ctypes.byref(tb), ctypes.byref(us)), "sdf_autotune")
     return int(tw.value), int(tb.value), float(us.value)
+
+
+def sdf_measure_gather(ctx: Context, grids: "Grids"):
+    """(random 4-byte gathers/s, random 8-corner cell reads/s) on these grids' values."""
+    g, c = ctypes.c_double(), ctypes.c_double()
+    ctx._check(lib.sdf_measure_gather(ctx.handle, grids.handle, ctypes.byref(g), ctypes.byref(c)),
+               "sdf_measure_gather")
+    return float(g.value), float(c.value)
 
 
 def sdf_ctx_reserve(ctx: Context, max_points: int, max_waypoints: int, max_pairs: int,

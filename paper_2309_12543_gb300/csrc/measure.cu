@@ -1,0 +1,141 @@
+// Gather-roofline calibration: how fast this GPU serves random reads from a
+// resident grid buffer.  The check kernel's grid lookups (trilinear interpolation,
+// Sec. III-B) read the 8 corner values of one cell of one link grid at a
+// data-dependent place; their ceiling is the rate of such random cell reads, which
+// this file measures on the grids the checks use.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChains = 8;     // independent random streams per thread
+
+__device__ __forceinline__ uint32_t lcg(uint32_t s) { return s * 1664525u + 1013904223u; }
+
+__device__ __forceinline__ uint32_t mix(uint32_t x) {   // integer hash for per-thread seeds
+    x ^= x >> 16; x *= 0x7feb352du;
+    x ^= x >> 15; x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Every accumulated value is a sum of grid values; the store only happens for one
+// bit pattern no sum produces in practice, so the loads cannot be removed.
+__device__ __forceinline__ void keep(float acc, float* sink) {
+    if (__float_as_uint(acc) == 0x7fc0beefu) *sink = acc;
+}
+
+// Independent random 4-byte loads, kChains in flight per thread.
+__global__ void __launch_bounds__(kThreads) gather_kernel(const float* __restrict__ buf, uint32_t n, int iters,
+                                                         float* sink) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t s[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s[j] = mix(tid * kChains + j + 1);
+    float acc = 0.f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) {
+            s[j] = lcg(s[j]);
+            acc += __ldg(buf + __umulhi(s[j], n));
+        }
+    }
+    keep(acc, sink);
+}
+
+// Random trilinear cell reads: a random link grid and cell, its 8 corners, two
+// cells in flight per thread.
+__global__ void __launch_bounds__(kThreads) cell_kernel(const float* __restrict__ buf, int links, int n, int iters,
+                                                       float* sink) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t s0 = mix(2 * tid + 1), s1 = mix(2 * tid + 2);
+    const uint32_t cells = (uint32_t)(n - 1);
+    const size_t nn = (size_t)n * n, n3 = nn * n;
+    float acc = 0.f;
+    for (int it = 0; it < iters; ++it) {
+        size_t base[2];
+        uint32_t* st[2] = {&s0, &s1};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            uint32_t& s = *st[c];
+            s = lcg(s); const uint32_t l = __umulhi(s, (uint32_t)links);
+            s = lcg(s); const uint32_t i = __umulhi(s, cells);
+            s = lcg(s); const uint32_t j = __umulhi(s, cells);
+            s = lcg(s); const uint32_t k = __umulhi(s, cells);
+            base[c] = l * n3 + k * nn + (size_t)j * n + i;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float* p = buf + base[c];
+            const float v000 = __ldg(p), v100 = __ldg(p + 1), v010 = __ldg(p + n), v110 = __ldg(p + n + 1);
+            const float v001 = __ldg(p + nn), v101 = __ldg(p + nn + 1), v011 = __ldg(p + nn + n),
+                        v111 = __ldg(p + nn + n + 1);
+            acc += 0.25f * ((v000 + v100) + (v010 + v110)) + 0.125f * ((v001 + v101) + (v011 + v111));
+        }
+    }
+    keep(acc, sink);
+}
+
+int set_err(sdf_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+}  // namespace
+
+extern "C" int sdf_measure_gather(sdf_ctx* ctx, const sdf_grids* grids, double* gathers_per_s,
+                                  double* cells_per_s) {
+    if (!ctx || !grids || !grids->values || grids->n < 2 || grids->n_links < 1)
+        return set_err(ctx, SDF_ERR_INVALID_ARG, "sdf_measure_gather: invalid argument");
+    if (grids->device != ctx->device)
+        return set_err(ctx, SDF_ERR_INVALID_ARG, "sdf_measure_gather: grids on another device");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    const size_t total = (size_t)grids->n_links * grids->n * grids->n * grids->n;
+    const uint32_t n_gather = (uint32_t)std::min<size_t>(total, 0xffffffffu);
+    float* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(float));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best_g = 0.0, best_c = 0.0;
+    constexpr int kIters = 64;
+    for (int bps = 2; bps <= 8 && e == cudaSuccess; bps *= 2) {
+        const int blocks = ctx->num_sms * bps;
+        const double threads = (double)blocks * kThreads;
+        for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // rep 0 warms up
+                e = cudaEventRecord(e0, ctx->stream);
+                if (kind == 0)
+                    gather_kernel<<<blocks, kThreads, 0, ctx->stream>>>(grids->values, n_gather, kIters, sink);
+                else
+                    cell_kernel<<<blocks, kThreads, 0, ctx->stream>>>(grids->values, grids->n_links, grids->n,
+                                                                     kIters, sink);
+                if (e == cudaSuccess) e = cudaGetLastError();
+                if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess || rep == 0 || ms <= 0.f) continue;
+                if (kind == 0)
+                    best_g = std::max(best_g, threads * kIters * kChains / (ms * 1e-3));
+                else
+                    best_c = std::max(best_c, threads * kIters * 2 / (ms * 1e-3));
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return set_err(ctx, SDF_ERR_CUDA, std::string("sdf_measure_gather: ") + cudaGetErrorString(e));
+    if (gathers_per_s) *gathers_per_s = best_g;
+    if (cells_per_s) *cells_per_s = best_c;
+    return SDF_OK;
+}
