@@ -468,3 +468,25 @@ def drifting_clouds(seed: int = 5, cycles: int = 250, N_range=(5000, 80000), sig
         N = min(int(rng.integers(N_range[0], N_range[1] + 1)), cells.shape[0])
         out.append(sample_voxels(rng, cells, N, voxel, order).astype(np.float32))
     return out
+
+
+# ------------------------------------------------------------ surrogate weights
+
+MLP_HIDDEN = 128
+MLP_PARAMS = MLP_HIDDEN * 3 + MLP_HIDDEN + 2 * (MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN) + MLP_HIDDEN + 1
+
+
+def mlp_init(seed: int, links: int) -> np.ndarray:
+    """Initial parameters of the per-link surrogate networks, [links, MLP_PARAMS] FP32:
+    every weight and bias of a layer uniform in +-1/sqrt(fan_in), in the parameter
+    order W1[128][3], b1, W2[128][128], b2, W3[128][128], b3, w4[128], b4."""
+    rng = np.random.default_rng(seed)
+    H = MLP_HIDDEN
+    out = np.empty((links, MLP_PARAMS), dtype=np.float32)
+    for l in range(links):
+        parts = []
+        for n, fan in ((H * 3, 3), (H, 3), (H * H, H), (H, H), (H * H, H), (H, H), (H, H), (1, H)):
+            b = 1.0 / math.sqrt(fan)
+            parts.append(rng.uniform(-b, b, n))
+        out[l] = np.concatenate(parts)
+    return out
