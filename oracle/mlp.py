@@ -23,9 +23,11 @@ precision, matrix products by numpy:
 * loss: mean absolute error over a batch, L = (1/B) sum_b |f(x_b) - y_b|, with
   d|r|/dr = sign(r) (0 at 0); the backward pass is the chain rule, with the
   quantised operands used where the forward used them (the rounding itself is
-  treated as the identity, a straight-through gradient) and the two products'
-  output gradients rounded to bfloat16 before they enter the transposed products
-  and the weight-gradient products;
+  treated as the identity, a straight-through gradient).  In the quantised form
+  every product of the backward pass also takes bfloat16 operands, as the GPU
+  runs each of them on the tensor cores: the pre-activation gradients dz1, dz2,
+  dz3, the inputs x and the last hidden layer s(z3) are rounded before they
+  enter a product, and each bias gradient is the batch sum of its rounded dz;
 * optimiser: Adam (Kingma & Ba, 2015, Algorithm 1): m <- b1 m + (1-b1) g,
   v <- b2 v + (1-b2) g^2, p <- p - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps);
 * training batches: step t (from 0) takes samples (t B + j) mod n, j < B;
@@ -127,21 +129,22 @@ def loss_and_grad(params, x, y, quantize: bool = False):
     gf = np.sign(r) / B                                  # dL/df
     P = c["P"]
     g = {}
-    g["w4"] = c["h3"].T @ gf
+    g["w4"] = _q(c["h3"], quantize).T @ gf
     g["b4"] = np.sum(gf)
     dz3 = np.outer(gf, P["w4"]) * silu_grad(c["z3"])     # [B, H]
-    g["b3"] = dz3.sum(axis=0)
     dz3q = _q(dz3, quantize)
+    g["b3"] = dz3q.sum(axis=0)
     g["W3"] = dz3q.T @ c["h2"]
     dh2 = dz3q @ c["W3"]
     dz2 = dh2 * silu_grad(c["z2"])
-    g["b2"] = dz2.sum(axis=0)
     dz2q = _q(dz2, quantize)
+    g["b2"] = dz2q.sum(axis=0)
     g["W2"] = dz2q.T @ c["h1"]
     dh1 = dz2q @ c["W2"]
     dz1 = dh1 * silu_grad(c["z1"])
-    g["b1"] = dz1.sum(axis=0)
-    g["W1"] = dz1.T @ c["x"]
+    dz1q = _q(dz1, quantize)
+    g["b1"] = dz1q.sum(axis=0)
+    g["W1"] = dz1q.T @ _q(c["x"], quantize)
     return loss, pack(g)
 
 
