@@ -336,6 +336,77 @@ int sdf_server_poll(sdf_server* server, uint64_t ticket, int64_t wait_us, float*
 #define SDF_SERVER_STAT_COUNT 10
 int sdf_server_stats(sdf_server* server, double* out, int32_t n, int32_t reset);
 
+/* ------------------------------------------------------------ learned surrogate
+ *
+ * No counterpart in the paper (its only network, Eq. (5), approximates its grid
+ * transform).  One network per link stands in for the link's grid lookup
+ * (Sec. III-A): f(x) = w4 . s(W3 s(W2 s(W1 x + b1) + b2) + b3) + b4 with
+ * s(z) = z / (1 + exp(-z)), hidden width SDF_MLP_HIDDEN, on the point normalised to
+ * the link's grid box, x = (p_loc - m) / a (m the box centre, a its half-span);
+ * the distance is a f(x), and outside the box the grid path's rule applies
+ * (distance to the box + the value at the nearest box point).  The two 128 x 128
+ * layers run on the tensor cores with bfloat16 operands and FP32 accumulation;
+ * training and its gradients do too.
+ *
+ * Parameter vector of one link (SDF_MLP_PARAMS FP32, row-major, output index
+ * first): W1[128][3], b1[128], W2[128][128], b2[128], W3[128][128], b3[128],
+ * w4[128], b4.  Host arrays of several links are [links][SDF_MLP_PARAMS]. */
+#define SDF_MLP_HIDDEN 128
+#define SDF_MLP_PARAMS 33665
+#define SDF_MLP_BATCH 128
+typedef struct sdf_surrogate sdf_surrogate;
+
+/* One network per link of `grids` (which must outlive it), initial parameters
+ * copied from params_host [n_links][SDF_MLP_PARAMS]; Adam state zeroed.
+ * Errors: INVALID_ARG, OOM, CUDA.  Synchronous. */
+int sdf_surrogate_create(sdf_ctx* ctx, const sdf_grids* grids, const float* params_host, sdf_surrogate** out);
+void sdf_surrogate_destroy(sdf_surrogate* surrogate);
+/* Current parameters of every link to params_host [n_links][SDF_MLP_PARAMS].
+ * Synchronises the context stream. */
+int sdf_surrogate_params(sdf_ctx* ctx, const sdf_surrogate* surrogate, float* params_host);
+
+/* Training samples of one link, labelled by its grid.  Sample j (0 <= j < n) is a
+ * "near" sample if j % 10 < near_per_10, else a uniform one.  Uniform sample u is
+ * candidate u of stream 1; near sample k is the k-th candidate of stream 0 (in
+ * counter order) whose grid value g satisfies |g| <= band (metres).  Candidate i of
+ * stream s is lo + U (hi - lo) componentwise over the grid box [lo, hi], with U
+ * the first three words of Philox4x32-10(counter (i, s, 0, 0), key (seed low,
+ * seed high)) as (word >> 8) 2^-24.  Outputs (device, caller-owned): x_dev n x 3
+ * normalised points, y_dev n normalised labels g / a, source_dev (optional) n
+ * int64 = stream << 40 | counter.  Synchronises (the number of candidates to draw
+ * is found on the way).  Errors: INVALID_ARG (also when 2^32 candidates give too
+ * few within the band), OOM, CUDA. */
+int sdf_surrogate_sample(sdf_ctx* ctx, const sdf_grids* grids, int32_t link, int64_t n, int32_t near_per_10,
+                         float band, uint64_t seed, float* x_dev, float* y_dev, int64_t* source_dev);
+
+/* Gradient of the mean absolute error over one batch of SDF_MLP_BATCH samples of
+ * link `link` (x_dev 128 x 3 normalised, y_dev 128 normalised labels) with respect
+ * to that link's parameters: grad_dev SDF_MLP_PARAMS FP32 in the parameter layout;
+ * loss_dev (optional) one FP32, the batch's mean absolute error.  The parameters
+ * are not changed.  Asynchronous. */
+int sdf_surrogate_grad(sdf_ctx* ctx, const sdf_surrogate* surrogate, int32_t link, const float* x_dev,
+                       const float* y_dev, float* grad_dev, float* loss_dev);
+
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, rate lr) on every link at
+ * once, one CTA per link.  Step s uses the batch of samples
+ * ((first_batch + s) * SDF_MLP_BATCH + j) mod n, j < SDF_MLP_BATCH, of x_dev
+ * [n_links][n][3] / y_dev [n_links][n] (as sdf_surrogate_sample writes them).
+ * loss_dev (optional, n_links FP32): the sum over the steps of each batch's mean
+ * absolute error.  Asynchronous. */
+int sdf_surrogate_train(sdf_ctx* ctx, sdf_surrogate* surrogate, const float* x_dev, const float* y_dev, int64_t n,
+                        int64_t first_batch, int32_t steps, float lr, float* loss_dev);
+
+/* f(x) of link `link` at n normalised points x_dev (n x 3) into f_dev (n FP32, in
+ * units of the half-span a).  Asynchronous. */
+int sdf_surrogate_eval(sdf_ctx* ctx, const sdf_surrogate* surrogate, int32_t link, const float* x_dev, int32_t n,
+                       float* f_dev);
+
+/* Error of link `link`'s network against its grid, in metres: n fresh samples
+ * drawn as by sdf_surrogate_sample (near_per_10, band, seed), *max_abs and
+ * *mean_abs of |a f(x) - g|.  Synchronises. */
+int sdf_surrogate_error(sdf_ctx* ctx, const sdf_surrogate* surrogate, int32_t link, int64_t n, int32_t near_per_10,
+                        float band, uint64_t seed, float* max_abs, float* mean_abs);
+
 /* ----------------------------------------------------------- allocation-free check */
 
 /* The paper has no counterpart to this entry point; it serves deployment.

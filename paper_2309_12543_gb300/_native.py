@@ -27,6 +27,9 @@ SDF_MAX_LINKS = 16
 SDF_MAX_POINTS = 16777215
 SDF_NOALLOC_MAX_POINTS = 32768
 SDF_MAX_BATCH = 128
+SDF_MLP_HIDDEN = 128
+SDF_MLP_PARAMS = 33665
+SDF_MLP_BATCH = 128
 
 SDF_OPT_CULL = 1
 SDF_OPT_POINT_STRIDE = 2
@@ -90,6 +93,14 @@ def _load():
         "sdf_ctx_synchronize": (ctypes.c_int, [P]),
         "sdf_ctx_stats": (ctypes.c_int, [P, P, i32, i32]),
         "sdf_measure_gather": (ctypes.c_int, [P, P, P, P]),
+        "sdf_surrogate_create": (ctypes.c_int, [P, P, P, P]),
+        "sdf_surrogate_destroy": (None, [P]),
+        "sdf_surrogate_params": (ctypes.c_int, [P, P, P]),
+        "sdf_surrogate_sample": (ctypes.c_int, [P, P, i32, i64, i32, ctypes.c_float, ctypes.c_uint64, P, P, P]),
+        "sdf_surrogate_grad": (ctypes.c_int, [P, P, i32, P, P, P, P]),
+        "sdf_surrogate_train": (ctypes.c_int, [P, P, P, P, i64, i64, i32, ctypes.c_float, P]),
+        "sdf_surrogate_eval": (ctypes.c_int, [P, P, i32, P, i32, P]),
+        "sdf_surrogate_error": (ctypes.c_int, [P, P, i32, i64, i32, ctypes.c_float, ctypes.c_uint64, P, P]),
         "sdf_ctx_last_kernel_ms": (ctypes.c_int, [P, i32, ctypes.POINTER(ctypes.c_float)]),
         "sdf_build_grids": (ctypes.c_int, [P, P, i32, i32, ctypes.c_float, ctypes.POINTER(P)]),
         "sdf_grids_upload": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(P)]),
@@ -129,7 +140,9 @@ EXPORTED = ("sdf_ctx_create", "sdf_ctx_destroy", "sdf_ctx_set_stream", "sdf_last
             "sdf_forward_kinematics", "check_trajectory", "check_trajectory_host",
             "check_trajectory_noalloc", "check_batch", "sdf_ctx_reserve", "sdf_autotune",
             "sdf_server_create", "sdf_server_destroy", "sdf_server_set_cloud", "sdf_server_submit",
-            "sdf_server_poll", "sdf_server_stats", "sdf_measure_gather")
+            "sdf_server_poll", "sdf_server_stats", "sdf_measure_gather", "sdf_surrogate_create",
+            "sdf_surrogate_destroy", "sdf_surrogate_params", "sdf_surrogate_sample", "sdf_surrogate_grad",
+            "sdf_surrogate_train", "sdf_surrogate_eval", "sdf_surrogate_error")
 
 
 def _ptr(x) -> int:
@@ -452,3 +465,57 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class Surrogate:
+    """Per-link MLP SDF surrogates (sdf_surrogate handle) on one context's device."""
+
+    def __init__(self, ctx: Context, grids: "Grids", params):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(grids.n_links, SDF_MLP_PARAMS)
+        h = ctypes.c_void_p()
+        ctx._check(lib.sdf_surrogate_create(ctx.handle, grids.handle, _ptr(p), ctypes.byref(h)),
+                   "sdf_surrogate_create")
+        self.ctx, self.grids, self.handle, self.n_links = ctx, grids, h, grids.n_links
+
+    def params(self) -> np.ndarray:
+        out = np.empty((self.n_links, SDF_MLP_PARAMS), dtype=np.float32)
+        self.ctx._check(lib.sdf_surrogate_params(self.ctx.handle, self.handle, _ptr(out)), "sdf_surrogate_params")
+        return out
+
+    def grad(self, link: int, x, y, grad, loss=None):
+        self.ctx._check(lib.sdf_surrogate_grad(self.ctx.handle, self.handle, int(link), _ptr(x), _ptr(y), _ptr(grad),
+                                               _ptr(loss)), "sdf_surrogate_grad")
+
+    def train(self, x, y, n: int, first_batch: int, steps: int, lr: float, loss=None):
+        self.ctx._check(lib.sdf_surrogate_train(self.ctx.handle, self.handle, _ptr(x), _ptr(y), int(n),
+                                                int(first_batch), int(steps), float(lr), _ptr(loss)),
+                        "sdf_surrogate_train")
+
+    def eval(self, link: int, x, n: int, f):
+        self.ctx._check(lib.sdf_surrogate_eval(self.ctx.handle, self.handle, int(link), _ptr(x), int(n), _ptr(f)),
+                        "sdf_surrogate_eval")
+
+    def error(self, link: int, n: int, near_per_10: int = 0, band: float = 0.1, seed: int = 99):
+        mx, mean = ctypes.c_float(), ctypes.c_float()
+        self.ctx._check(lib.sdf_surrogate_error(self.ctx.handle, self.handle, int(link), int(n), int(near_per_10),
+                                                float(band), ctypes.c_uint64(seed), ctypes.byref(mx),
+                                                ctypes.byref(mean)), "sdf_surrogate_error")
+        return float(mx.value), float(mean.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.sdf_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sdf_surrogate_sample(ctx: Context, grids: "Grids", link: int, n: int, near_per_10: int, band: float, seed: int,
+                         x, y, source=None):
+    ctx._check(lib.sdf_surrogate_sample(ctx.handle, grids.handle, int(link), int(n), int(near_per_10), float(band),
+                                        ctypes.c_uint64(seed), _ptr(x), _ptr(y), _ptr(source)),
+               "sdf_surrogate_sample")

@@ -36,11 +36,14 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "lookup.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace sdf {
 namespace {
+
+using namespace dev;
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kOrderedInf = 0xff800000u;   // ordered_bits(+inf): "no value yet"
@@ -49,14 +52,6 @@ constexpr int kPrepThreads = 1024;
 constexpr int kPrepCtas = 8;                        // one portable-size cluster
 constexpr int kBinsPerCta = kCells / kPrepCtas;
 constexpr int kPrepCached = 4;                      // points per thread kept in registers
-
-__device__ __forceinline__ unsigned ordered_bits(float f) {
-    unsigned u = __float_as_uint(f + 0.0f);  // -0 -> +0
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float from_ordered(unsigned o) {
-    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
-}
 
 // Affine 3x4 composition C = X * Y (row-major, implicit last row 0 0 0 1).
 __device__ __forceinline__ void affine_mul(const float* X, const float* Y, float* C) {
@@ -123,34 +118,6 @@ __device__ __forceinline__ void fk_links(const LinkTable& T, const float* qw, in
     if (lane == 0) store_link(T.base, T.sph_local[0], xf[0], &sph[0]);
 }
 
-// Interpolated link SDF at a link-frame point (trilinear inside the grid box,
-// distance to the box + boundary value outside).  Branch-free: the point is
-// clamped in index space and the clamp distance is added.
-__device__ __forceinline__ float grid_lookup(const float* __restrict__ G, int n, float4 o_ih,
-                                             float h, float px, float py, float pz) {
-    const float top = (float)(n - 1);
-    const float ux = (px - o_ih.x) * o_ih.w;
-    const float uy = (py - o_ih.y) * o_ih.w;
-    const float uz = (pz - o_ih.z) * o_ih.w;
-    const float cx = fminf(fmaxf(ux, 0.f), top);
-    const float cy = fminf(fmaxf(uy, 0.f), top);
-    const float cz = fminf(fmaxf(uz, 0.f), top);
-    const float ex = ux - cx, ey = uy - cy, ez = uz - cz;
-    const float dout = h * sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-    const int ix = min((int)cx, n - 2), iy = min((int)cy, n - 2), iz = min((int)cz, n - 2);
-    const float fx = cx - (float)ix, fy = cy - (float)iy, fz = cz - (float)iz;
-    const size_t nn = (size_t)n * n;
-    const float* b = G + (size_t)ix + (size_t)n * iy + nn * iz;
-    const float v000 = __ldg(b), v100 = __ldg(b + 1);
-    const float v010 = __ldg(b + n), v110 = __ldg(b + n + 1);
-    const float v001 = __ldg(b + nn), v101 = __ldg(b + nn + 1);
-    const float v011 = __ldg(b + nn + n), v111 = __ldg(b + nn + n + 1);
-    const float c00 = fmaf(fx, v100 - v000, v000), c10 = fmaf(fx, v110 - v010, v010);
-    const float c01 = fmaf(fx, v101 - v001, v001), c11 = fmaf(fx, v111 - v011, v011);
-    const float c0 = fmaf(fy, c10 - c00, c00), c1 = fmaf(fy, c11 - c01, c01);
-    return dout + fmaf(fz, c1 - c0, c0);
-}
-
 __device__ __forceinline__ float3 load_point(const float* __restrict__ pts, int stride, int i) {
     if (stride == 4) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(pts) + i);
@@ -164,9 +131,6 @@ __device__ __forceinline__ bool finite3(float3 p) {
     return isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
 }
 
-__device__ __forceinline__ unsigned long long pack_key(float g, int point, int link) {
-    return ((unsigned long long)ordered_bits(g) << 32) | ((unsigned)point << 4) | (unsigned)link;
-}
 
 // (score, index) arg-min across the warp; ties go to the smaller index.
 __device__ __forceinline__ int warp_argmin(float s, int idx) {

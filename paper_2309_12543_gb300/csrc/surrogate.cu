@@ -1,0 +1,1117 @@
+// Learned link-SDF surrogate on the fifth-generation tensor cores (tcgen05).
+//
+// No counterpart in the paper, whose only network approximates its grid transform
+// (Eq. (5)).  Here one small network per link stands in for the link's grid lookup
+// (Sec. III-A): f(x) = w4 . s(W3 s(W2 s(W1 x + b1) + b2) + b3) + b4, s = SiLU,
+// hidden width 128, x = (p_loc - m) / a the link-frame point normalised to the
+// grid box (centre m, half-span a), distance = a f(x), and outside the box the
+// grid path's rule (distance to the box + value at the nearest box point).
+//
+// The two 128 x 128 layers run as tcgen05 MMAs (bf16 operands from shared memory,
+// f32 accumulators in tensor memory); the 3-wide input layer and the 1-wide output
+// layer run on the FP32 cores.  Training (mean absolute error, Adam) runs one CTA
+// per link, one 128-sample batch per step; every product of the backward pass is a
+// tcgen05 MMA as well:
+//   dH2 = dZ3 W3,  dW3 = dZ3^T H2,  db3 = dZ3^T 1,  dw4 = H3^T g
+//   dH1 = dZ2 W2,  dW2 = dZ2^T H1,  db2 = dZ2^T 1,  [dW1 db1] = dZ1^T [x 1]
+// with all operands bf16.  Tensor memory (512 columns of 128 lanes) holds
+//   [0,128)   Z2, then dH1           [128,256) Z3, then dH2, then dW2
+//   [256,384) dW3                     [384,448) four 16-column small products
+// Master weights, Adam moments and step counts stay in FP32 in device memory; the
+// 128 x 128 blocks are stored transposed there ([in][out]) so that the thread of
+// output unit o reads them coalesced.
+//
+// The training samples come from a counter-based generator (Philox4x32-10,
+// Salmon et al., SC'11) and are labelled by the link's grid.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "lookup.cuh"
+#include "tc.cuh"
+
+namespace sdf {
+namespace {
+
+using namespace dev;
+
+constexpr int kH = SDF_MLP_HIDDEN;
+constexpr int kPar = SDF_MLP_PARAMS;
+constexpr int kOW1 = 0, kOB1 = 384, kOW2 = 512, kOB2 = kOW2 + kH * kH, kOW3 = kOB2 + kH, kOB3 = kOW3 + kH * kH,
+              kOW4 = kOB3 + kH, kOB4 = kOW4 + kH;
+static_assert(kOB4 + 1 == kPar, "parameter layout");
+
+constexpr int kTileBytes = kH * kH * 2;        // one 128 x 128 bf16 operand tile
+constexpr int kAuxCols = 16;                    // [x0 x1 x2 1 g 0 ...] per sample
+constexpr int kAuxBytes = kH * kAuxCols * 2;
+constexpr uint32_t kWaitPolls = 1u << 22;
+
+// training kernel shared memory (dynamic part)
+constexpr int kSW2 = 0, kSW3 = kTileBytes, kSH1 = 2 * kTileBytes, kSH2 = 3 * kTileBytes, kSDZ = 4 * kTileBytes,
+              kSH3 = 5 * kTileBytes, kSAux = 6 * kTileBytes, kSSmall = kSAux + kAuxBytes;
+constexpr int kSmallFloats = 384 + 4 * kH + 4;  // W1, b1, b2, b3, w4, b4 (+pad)
+constexpr int kTrainSmem = kSSmall + kSmallFloats * 4;
+// evaluation kernel shared memory
+constexpr int kEW2 = 0, kEW3 = kTileBytes, kEH1 = 2 * kTileBytes, kEH2 = 3 * kTileBytes, kESmall = 4 * kTileBytes;
+constexpr int kEvalSmem = kESmall + kSmallFloats * 4;
+
+// tensor-memory columns
+constexpr uint32_t kTZ2 = 0, kTZ3 = 128, kTDW3 = 256, kTS3 = 384, kTS2 = 400, kTS1 = 416, kTS4 = 432;
+
+// K-major operand of a 128-column tile: K-direction stride 128 B, row groups 2048 B,
+// 16 K-elements per MMA = 256 B.  MN-major: K-direction stride = row groups.
+constexpr uint32_t kRowGroup = 2048, kAuxRowGroup = 256;
+
+__device__ __forceinline__ float silu_sigma(float z) { return 1.0f / (1.0f + __expf(-z)); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+// 8 consecutive columns (one 16-byte core-matrix row) of a tile row.
+__device__ __forceinline__ void store_bf16x8(uint8_t* tile, int row, int col0, int cols, const float* v) {
+    uint4 u;
+    u.x = pack_bf16x2(v[0], v[1]);
+    u.y = pack_bf16x2(v[2], v[3]);
+    u.z = pack_bf16x2(v[4], v[5]);
+    u.w = pack_bf16x2(v[6], v[7]);
+    *reinterpret_cast<uint4*>(tile + tc::tile_offset(row, col0, cols)) = u;
+}
+
+// All threads' shared-memory writes become visible to the tensor core, and the
+// tensor-memory reads before this point are ordered before the next MMA.
+__device__ __forceinline__ void sync_for_mma() {
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+// Wait for the MMA batch just committed; the block agrees on the outcome.
+__device__ __forceinline__ bool wait_mma(uint64_t* mbar, uint32_t& phase) {
+    const bool ok = tc::mbar_wait(mbar, phase, kWaitPolls);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    return __syncthreads_and(ok) != 0;
+}
+
+// One K=128 product: 8 MMAs of K = 16.
+__device__ __forceinline__ void mma_k128(uint32_t d, uint32_t a_addr, uint32_t a_lbo, uint32_t a_sbo, uint32_t a_step,
+                                         uint32_t b_addr, uint32_t b_lbo, uint32_t b_sbo, uint32_t b_step,
+                                         uint32_t idesc) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        tc::mma_bf16(d, tc::smem_desc(a_addr + k * a_step, a_lbo, a_sbo), tc::smem_desc(b_addr + k * b_step, b_lbo, b_sbo),
+                     idesc, k > 0);
+}
+
+// Operand roles of a 128-column tile T (rows r, 8-element chunks along columns):
+//   K-major, M/N = rows, K = columns:  lbo 128, sbo 2048, step 256
+//   MN-major, K = rows, M/N = columns: lbo 2048, sbo 128, step 4096
+#define KMAJ(addr) (addr), 128u, kRowGroup, 256u
+#define MNMAJ(addr) (addr), kRowGroup, 128u, 2u * kRowGroup
+#define AUXMN(addr) (addr), kAuxRowGroup, 128u, 2u * kAuxRowGroup
+
+// Load one link's weights: the W2/W3 blocks (stored [in][out]) into K-major bf16
+// tiles [out][in] (thread t = output unit), the small parameters into FP32.
+__device__ __forceinline__ void load_weights(const float* __restrict__ P, uint8_t* w2, uint8_t* w3, float* small,
+                                             int t) {
+    for (int blk = 0; blk < 2; ++blk) {
+        const float* src = P + (blk == 0 ? kOW2 : kOW3);
+        uint8_t* dst = blk == 0 ? w2 : w3;
+        for (int i0 = 0; i0 < kH; i0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = src[(i0 + k) * kH + t];
+            store_bf16x8(dst, t, i0, kH, v);
+        }
+    }
+    for (int i = t; i < 384; i += blockDim.x) small[i] = P[kOW1 + i];
+    if (t < kH) {
+        small[384 + t] = P[kOB1 + t];
+        small[384 + kH + t] = P[kOB2 + t];
+        small[384 + 2 * kH + t] = P[kOB3 + t];
+        small[384 + 3 * kH + t] = P[kOW4 + t];
+    }
+    if (t == 0) small[384 + 4 * kH] = P[kOB4];
+}
+
+// Layer 1 of one sample into row `row` of the H1 tile (bf16).
+__device__ __forceinline__ void layer1(const float* small, float x0, float x1, float x2, uint8_t* h1, int row) {
+    const float* W1 = small;
+    const float* b1 = small + 384;
+    for (int j0 = 0; j0 < kH; j0 += 8) {
+        float h[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int j = j0 + k;
+            const float z = fmaf(W1[3 * j], x0, fmaf(W1[3 * j + 1], x1, fmaf(W1[3 * j + 2], x2, b1[j])));
+            h[k] = z * silu_sigma(z);
+        }
+        store_bf16x8(h1, row, j0, kH, h);
+    }
+}
+
+// Hidden layer epilogue: s(D + b) of this thread's lane into row `row` of tile out.
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* b, uint8_t* out, int row) {
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(taddr + c0, v);
+#pragma unroll
+        for (int k = 0; k < 32; k += 8) {
+            float h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float z = v[k + e] + b[c0 + k + e];
+                h[e] = z * silu_sigma(z);
+            }
+            store_bf16x8(out, row, c0 + k, kH, h);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ training
+
+struct TrainArgs {
+    float* master;            // [L][kPar], W2/W3 blocks [in][out]
+    float* adam_m;
+    float* adam_v;
+    int* step;                // [L] Adam steps taken
+    const float* x;           // [L][n][3] normalised inputs
+    const float* y;           // [L][n] normalised labels
+    long long n;
+    long long batch0;         // step s uses samples ((batch0 + s) * 128 + j) mod n
+    int steps;
+    int link0;
+    float lr, beta1, beta2, eps;
+    float* grad_out;          // gradient mode: [kPar] in the public layout (no update)
+    float* loss_out;          // [L]: sum over the steps of the batch loss
+    int* status;
+};
+
+__global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant__ TrainArgs A) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ float red[2][4];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int link = A.link0 + blockIdx.x;
+    float* P = A.master + (size_t)link * kPar;
+    uint8_t* sW2 = sm + kSW2;
+    uint8_t* sW3 = sm + kSW3;
+    uint8_t* sH1 = sm + kSH1;
+    uint8_t* sH2 = sm + kSH2;
+    uint8_t* sDZ = sm + kSDZ;
+    uint8_t* sH3 = sm + kSH3;
+    uint8_t* sAux = sm + kSAux;
+    float* small = reinterpret_cast<float*>(sm + kSSmall);
+    const float* W1 = small;
+    const float* b1 = small + 384;
+    const float* b2 = small + 384 + kH;
+    const float* b3 = small + 384 + 2 * kH;
+    const float* w4 = small + 384 + 3 * kH;
+
+    load_weights(P, sW2, sW3, small, t);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (t == 0) tc::mbar_init(&mbar, 1);
+    sync_for_mma();
+    const uint32_t tm = tmem_slot;
+    const uint32_t lane_addr = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH1 = tc::smem_u32(sH1),
+                   aH2 = tc::smem_u32(sH2), aDZ = tc::smem_u32(sDZ), aH3 = tc::smem_u32(sH3),
+                   aAux = tc::smem_u32(sAux);
+    constexpr uint32_t kN128KK = tc::idesc_bf16(128, 128, 0, 0);   // A K-major, B K-major
+    constexpr uint32_t kN128KM = tc::idesc_bf16(128, 128, 0, 1);   // A K-major, B MN-major
+    constexpr uint32_t kN128MM = tc::idesc_bf16(128, 128, 1, 1);
+    constexpr uint32_t kN16MM = tc::idesc_bf16(128, 16, 1, 1);
+    uint32_t phase = 0;
+    bool ok = true;
+    float loss_sum = 0.f;
+
+    for (int s = 0; s < A.steps && ok; ++s) {
+        // ---- the batch: sample t of this step
+        const long long idx = ((A.batch0 + s) * 128 + t) % A.n;
+        const float* xs = A.x + ((size_t)link * A.n + idx) * 3;
+        const float x0 = xs[0], x1 = xs[1], x2 = xs[2];
+        const float yv = A.y[(size_t)link * A.n + idx];
+        {
+            const float aux[8] = {x0, x1, x2, 1.f, 0.f, 0.f, 0.f, 0.f};
+            const float zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            store_bf16x8(sAux, t, 0, kAuxCols, aux);
+            store_bf16x8(sAux, t, 8, kAuxCols, zero);
+        }
+        // ---- forward
+        layer1(small, x0, x1, x2, sH1, t);
+        sync_for_mma();
+        if (t == 0) {
+            mma_k128(tm + kTZ2, KMAJ(aH1), KMAJ(aW2), kN128KK);
+            tc::mma_commit(&mbar);
+        }
+        if (!(ok = wait_mma(&mbar, phase))) break;
+        hidden_epilogue(lane_addr + kTZ2, b2, sH2, t);
+        sync_for_mma();
+        if (t == 0) {
+            mma_k128(tm + kTZ3, KMAJ(aH2), KMAJ(aW3), kN128KK);
+            tc::mma_commit(&mbar);
+        }
+        if (!(ok = wait_mma(&mbar, phase))) break;
+        // output layer and the loss gradient g = sign(f - y) / 128
+        float f = small[384 + 4 * kH];
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(lane_addr + kTZ3 + c0, v);
+#pragma unroll
+            for (int k = 0; k < 32; k += 8) {
+                float h[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float z = v[k + e] + b3[c0 + k + e];
+                    h[e] = z * silu_sigma(z);
+                    f = fmaf(w4[c0 + k + e], h[e], f);
+                }
+                store_bf16x8(sH3, t, c0 + k, kH, h);
+            }
+        }
+        const float r = f - yv;
+        const float g = r > 0.f ? (1.f / 128.f) : (r < 0.f ? -(1.f / 128.f) : 0.f);
+        {
+            const float aux[8] = {x0, x1, x2, 1.f, g, 0.f, 0.f, 0.f};
+            store_bf16x8(sAux, t, 0, kAuxCols, aux);
+        }
+        // dz3 = g w4 s'(z3)
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(lane_addr + kTZ3 + c0, v);
+#pragma unroll
+            for (int k = 0; k < 32; k += 8) {
+                float d[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float z = v[k + e] + b3[c0 + k + e];
+                    const float sg = silu_sigma(z);
+                    d[e] = g * w4[c0 + k + e] * (sg * fmaf(z, 1.f - sg, 1.f));
+                }
+                store_bf16x8(sDZ, t, c0 + k, kH, d);
+            }
+        }
+        // batch loss and db4 = sum g
+        float la = fabsf(r), lg = g;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            la += __shfl_xor_sync(0xffffffffu, la, o);
+            lg += __shfl_xor_sync(0xffffffffu, lg, o);
+        }
+        if (lane == 0) {
+            red[0][warp] = la;
+            red[1][warp] = lg;
+        }
+        sync_for_mma();
+        if (t == 0) {
+            mma_k128(tm + kTZ3, KMAJ(aDZ), MNMAJ(aW3), kN128KM);     // dH2 = dZ3 W3
+            mma_k128(tm + kTDW3, MNMAJ(aDZ), MNMAJ(aH2), kN128MM);   // dW3 = dZ3^T H2
+            mma_k128(tm + kTS3, MNMAJ(aDZ), AUXMN(aAux), kN16MM);    // db3 (column 3)
+            mma_k128(tm + kTS4, MNMAJ(aH3), AUXMN(aAux), kN16MM);    // dw4 (column 4)
+            tc::mma_commit(&mbar);
+        }
+        if (!(ok = wait_mma(&mbar, phase))) break;
+        // dz2 = dH2 s'(z2)
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float dh[32], zz[32];
+            tc::tmem_ld32(lane_addr + kTZ3 + c0, dh);
+            tc::tmem_ld32(lane_addr + kTZ2 + c0, zz);
+#pragma unroll
+            for (int k = 0; k < 32; k += 8) {
+                float d[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float z = zz[k + e] + b2[c0 + k + e];
+                    const float sg = silu_sigma(z);
+                    d[e] = dh[k + e] * (sg * fmaf(z, 1.f - sg, 1.f));
+                }
+                store_bf16x8(sDZ, t, c0 + k, kH, d);
+            }
+        }
+        sync_for_mma();
+        if (t == 0) {
+            mma_k128(tm + kTZ2, KMAJ(aDZ), MNMAJ(aW2), kN128KM);     // dH1 = dZ2 W2
+            mma_k128(tm + kTZ3, MNMAJ(aDZ), MNMAJ(aH1), kN128MM);    // dW2 = dZ2^T H1
+            mma_k128(tm + kTS2, MNMAJ(aDZ), AUXMN(aAux), kN16MM);    // db2 (column 3)
+            tc::mma_commit(&mbar);
+        }
+        if (!(ok = wait_mma(&mbar, phase))) break;
+        // dz1 = dH1 s'(z1), z1 recomputed
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float dh[32];
+            tc::tmem_ld32(lane_addr + kTZ2 + c0, dh);
+#pragma unroll
+            for (int k = 0; k < 32; k += 8) {
+                float d[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int j = c0 + k + e;
+                    const float z = fmaf(W1[3 * j], x0, fmaf(W1[3 * j + 1], x1, fmaf(W1[3 * j + 2], x2, b1[j])));
+                    const float sg = silu_sigma(z);
+                    d[e] = dh[k + e] * (sg * fmaf(z, 1.f - sg, 1.f));
+                }
+                store_bf16x8(sDZ, t, c0 + k, kH, d);
+            }
+        }
+        sync_for_mma();
+        if (t == 0) {
+            mma_k128(tm + kTS1, MNMAJ(aDZ), AUXMN(aAux), kN16MM);    // [dW1 db1] (columns 0..3)
+            tc::mma_commit(&mbar);
+        }
+        if (!(ok = wait_mma(&mbar, phase))) break;
+        const float batch_loss = (red[0][0] + red[0][1] + red[0][2] + red[0][3]) * (1.f / 128.f);
+        const float db4 = red[1][0] + red[1][1] + red[1][2] + red[1][3];
+        loss_sum += batch_loss;
+
+        // ---- gradients of output unit o = t, then the update
+        const int o = t;
+        float s1[16], s2[16], s3[16], s4[16];
+        tc::tmem_ld16(lane_addr + kTS1, s1);
+        tc::tmem_ld16(lane_addr + kTS2, s2);
+        tc::tmem_ld16(lane_addr + kTS3, s3);
+        tc::tmem_ld16(lane_addr + kTS4, s4);
+        if (A.grad_out) {
+            float* G = A.grad_out;
+            for (int c0 = 0; c0 < kH; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(lane_addr + kTZ3 + c0, v);
+                for (int k = 0; k < 32; ++k) G[kOW2 + o * kH + c0 + k] = v[k];
+                tc::tmem_ld32(lane_addr + kTDW3 + c0, v);
+                for (int k = 0; k < 32; ++k) G[kOW3 + o * kH + c0 + k] = v[k];
+            }
+            G[kOW1 + 3 * o] = s1[0];
+            G[kOW1 + 3 * o + 1] = s1[1];
+            G[kOW1 + 3 * o + 2] = s1[2];
+            G[kOB1 + o] = s1[3];
+            G[kOB2 + o] = s2[3];
+            G[kOB3 + o] = s3[3];
+            G[kOW4 + o] = s4[4];
+            if (o == 0) G[kOB4] = db4;
+            break;   // gradient mode: one batch, no update
+        }
+        // Adam (Kingma & Ba, Algorithm 1) on the master weights
+        const int tstep = A.step[link] + s + 1;
+        const float bc1 = 1.f - powf(A.beta1, (float)tstep), bc2 = 1.f - powf(A.beta2, (float)tstep);
+        const float b1c = A.beta1, b2c = A.beta2, lr = A.lr, eps = A.eps;
+        float* M = A.adam_m + (size_t)link * kPar;
+        float* V = A.adam_v + (size_t)link * kPar;
+        auto adam = [&](int i, float gr) -> float {
+            const float m = fmaf(b1c, M[i], (1.f - b1c) * gr);
+            const float v = fmaf(b2c, V[i], (1.f - b2c) * gr * gr);
+            M[i] = m;
+            V[i] = v;
+            const float p = P[i] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+            P[i] = p;
+            return p;
+        };
+        for (int blk = 0; blk < 2; ++blk) {
+            const uint32_t col = blk == 0 ? kTZ3 : kTDW3;
+            const int base = blk == 0 ? kOW2 : kOW3;
+            uint8_t* tile = blk == 0 ? sW2 : sW3;
+            for (int c0 = 0; c0 < kH; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(lane_addr + col + c0, v);
+#pragma unroll
+                for (int k = 0; k < 32; k += 8) {
+                    float w[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) w[e] = adam(base + (c0 + k + e) * kH + o, v[k + e]);
+                    store_bf16x8(tile, o, c0 + k, kH, w);
+                }
+            }
+        }
+        float nw[7];
+        nw[0] = adam(kOW1 + 3 * o, s1[0]);
+        nw[1] = adam(kOW1 + 3 * o + 1, s1[1]);
+        nw[2] = adam(kOW1 + 3 * o + 2, s1[2]);
+        nw[3] = adam(kOB1 + o, s1[3]);
+        nw[4] = adam(kOB2 + o, s2[3]);
+        nw[5] = adam(kOB3 + o, s3[3]);
+        nw[6] = adam(kOW4 + o, s4[4]);
+        float nb4 = 0.f;
+        if (o == 0) nb4 = adam(kOB4, db4);
+        __syncthreads();   // every thread is done reading the small parameters of this step
+        small[3 * o] = nw[0];
+        small[3 * o + 1] = nw[1];
+        small[3 * o + 2] = nw[2];
+        small[384 + o] = nw[3];
+        small[384 + kH + o] = nw[4];
+        small[384 + 2 * kH + o] = nw[5];
+        small[384 + 3 * kH + o] = nw[6];
+        if (o == 0) small[384 + 4 * kH] = nb4;
+        // the next step reads the new small parameters; its first MMA is preceded by
+        // sync_for_mma, which publishes the rewritten weight tiles to the tensor core
+        __syncthreads();
+    }
+    if (!ok) {
+        if (t == 0) atomicOr(A.status, kStatusTimeout);
+        tc::mbar_wait(&mbar, phase ^ 1u, kWaitPolls);   // give an MMA still in flight time to end
+    }
+    if (t == 0) {
+        if (A.loss_out) A.loss_out[link] = (A.grad_out ? 0.f : A.loss_out[link]) + loss_sum;
+        if (!A.grad_out && ok) A.step[link] += A.steps;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tm, 512);
+}
+
+// ------------------------------------------------------------------ evaluation
+
+struct EvalArgs {
+    const float* master;               // [L][kPar]
+    const float* x3;                   // plain mode: n x 3 normalised points
+    const float4* xq;                  // check mode: normalised point (xyz), added distance (w, metres)
+    const uint2* tag;                  // check mode: (waypoint, point << 4 | link)
+    const int* seg_count;              // check mode: queries per link segment
+    int seg_cap;                       // check mode: queries per segment slot
+    int L;
+    int n;                             // plain mode: queries of link `link0`
+    int link0;
+    float* f_out;                      // plain mode: f(x) (normalised)
+    unsigned long long* keys;          // check mode: per-waypoint packed keys
+    float scale[kMaxLinks];            // half-span a of each link's box
+    int* status;
+};
+
+__global__ void __launch_bounds__(128, 1) mlp_eval_kernel(const __grid_constant__ EvalArgs A) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int t = threadIdx.x, warp = t >> 5;
+    uint8_t* sW2 = sm + kEW2;
+    uint8_t* sW3 = sm + kEW3;
+    uint8_t* sH1 = sm + kEH1;
+    uint8_t* sH2 = sm + kEH2;
+    float* small = reinterpret_cast<float*>(sm + kESmall);
+    const float* b2 = small + 384 + kH;
+    const float* b3 = small + 384 + 2 * kH;
+    const float* w4 = small + 384 + 3 * kH;
+
+    // this CTA's range of 128-query tiles over the link segments
+    const bool check_mode = A.keys != nullptr;
+    int counts[kMaxLinks];
+    int total = 0;
+    for (int l = 0; l < kMaxLinks; ++l) {
+        counts[l] = 0;
+        if (l < A.L) counts[l] = check_mode ? min(A.seg_count[l], A.seg_cap) : (l == A.link0 ? A.n : 0);
+        total += (counts[l] + 127) / 128;
+    }
+    const int first = (int)((long long)total * blockIdx.x / gridDim.x);
+    const int last = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
+    if (first >= last) return;
+
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 256);
+    if (t == 0) tc::mbar_init(&mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = tmem_slot;
+    const uint32_t lane_addr = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH1 = tc::smem_u32(sH1), aH2 = tc::smem_u32(sH2);
+    constexpr uint32_t kN128KK = tc::idesc_bf16(128, 128, 0, 0);
+    uint32_t phase = 0;
+    bool ok = true;
+    int loaded = -1;
+    int tile = 0, l = 0, tile_in_l = 0;
+    // locate the first tile
+    {
+        int acc = 0;
+        for (l = 0; l < A.L; ++l) {
+            const int nt = (counts[l] + 127) / 128;
+            if (first < acc + nt) break;
+            acc += nt;
+        }
+        tile_in_l = first - acc;
+    }
+    for (tile = first; tile < last && ok; ++tile) {
+        while (tile_in_l * 128 >= counts[l]) {   // next non-empty segment
+            ++l;
+            tile_in_l = 0;
+        }
+        if (l != loaded) {
+            __syncthreads();   // previous tile's readers of the weights are done
+            load_weights(A.master + (size_t)l * kPar, sW2, sW3, small, t);
+            loaded = l;
+            __syncthreads();
+        }
+        const int k = tile_in_l * 128 + t;
+        const bool valid = k < counts[l];
+        const size_t qi = check_mode ? (size_t)l * A.seg_cap + k : (size_t)k;
+        float4 xq = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
+            if (check_mode)
+                xq = A.xq[qi];
+            else
+                xq = make_float4(A.x3[3 * qi], A.x3[3 * qi + 1], A.x3[3 * qi + 2], 0.f);
+        }
+        layer1(small, xq.x, xq.y, xq.z, sH1, t);
+        sync_for_mma();
+        if (t == 0) {
+            mma_k128(tm + 0, KMAJ(aH1), KMAJ(aW2), kN128KK);
+            tc::mma_commit(&mbar);
+        }
+        if (!(ok = wait_mma(&mbar, phase))) break;
+        hidden_epilogue(lane_addr + 0, b2, sH2, t);
+        sync_for_mma();
+        if (t == 0) {
+            mma_k128(tm + 128, KMAJ(aH2), KMAJ(aW3), kN128KK);
+            tc::mma_commit(&mbar);
+        }
+        if (!(ok = wait_mma(&mbar, phase))) break;
+        float f = small[384 + 4 * kH];
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(lane_addr + 128 + c0, v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const float z = v[e] + b3[c0 + e];
+                f = fmaf(w4[c0 + e], z * silu_sigma(z), f);
+            }
+        }
+        if (valid) {
+            if (check_mode) {
+                const uint2 tg = A.tag[qi];
+                const float d = fmaf(A.scale[l], f, xq.w);
+                if (!isnan(d)) {
+                    const unsigned long long key = ((unsigned long long)ordered_bits(d) << 32) | tg.y;
+                    atomicMin(&A.keys[tg.x], key);
+                }
+            } else {
+                A.f_out[k] = f;
+            }
+        }
+        ++tile_in_l;
+        tc::fence_before_sync();
+        __syncthreads();   // H1/H2 and tensor memory are rewritten by the next tile
+        tc::fence_after_sync();
+    }
+    if (!ok) {
+        if (t == 0) atomicOr(A.status, kStatusTimeout);
+        tc::mbar_wait(&mbar, phase ^ 1u, kWaitPolls);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tm, 256);
+}
+
+// ------------------------------------------------------------------ sampler
+
+// Philox4x32-10: 10 rounds of the multiply-xor round function with a Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+struct SampleArgs {
+    const float* grid;        // the link's n^3 values
+    int n;
+    float4 o_ih;              // grid origin, 1/h
+    float h;
+    float lo[3], span[3];     // box
+    float m[3], inv_a;        // centre, 1/half-span
+    uint2 key;                // seed
+    float band;               // near: |value| <= band (metres)
+    int near10;               // samples j with j % 10 < near10 are near samples
+    long long n_samples;
+    long long n_near;
+    float* x;                 // [n_samples][3]
+    float* y;                 // [n_samples]
+    long long* source;        // [n_samples] (stream << 40 | counter), may be null
+    long long start;          // near stream: first candidate of this chunk
+    int count;                // near stream: candidates in this chunk
+    int* block_count;         // per-block accepted counts
+    long long* found;         // near samples found before this chunk (device)
+};
+
+__device__ __forceinline__ void candidate(const SampleArgs& A, uint32_t stream, unsigned long long i, float* p) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, stream, 0u, 0u), A.key);
+    const float u0 = (float)(r.x >> 8) * (1.0f / 16777216.0f);
+    const float u1 = (float)(r.y >> 8) * (1.0f / 16777216.0f);
+    const float u2 = (float)(r.z >> 8) * (1.0f / 16777216.0f);
+    p[0] = fmaf(u0, A.span[0], A.lo[0]);
+    p[1] = fmaf(u1, A.span[1], A.lo[1]);
+    p[2] = fmaf(u2, A.span[2], A.lo[2]);
+}
+
+__device__ __forceinline__ void emit(const SampleArgs& A, long long j, const float* p, float g, long long src) {
+    A.x[3 * j] = (p[0] - A.m[0]) * A.inv_a;
+    A.x[3 * j + 1] = (p[1] - A.m[1]) * A.inv_a;
+    A.x[3 * j + 2] = (p[2] - A.m[2]) * A.inv_a;
+    A.y[j] = g * A.inv_a;
+    if (A.source) A.source[j] = src;
+}
+
+// Uniform samples: sample j with j % 10 >= near10 is uniform candidate u of stream 1.
+__global__ void sample_uniform_kernel(const __grid_constant__ SampleArgs A) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= A.n_samples || (int)(j % 10) < A.near10) return;
+    const long long u = (j / 10) * (10 - A.near10) + (j % 10 - A.near10);
+    float p[3];
+    candidate(A, 1u, (unsigned long long)u, p);
+    const float g = grid_lookup(A.grid, A.n, A.o_ih, A.h, p[0], p[1], p[2]);
+    emit(A, j, p, g, (1ll << 40) | u);
+}
+
+__device__ __forceinline__ bool near_ok(const SampleArgs& A, long long i, float* p, float* g) {
+    candidate(A, 0u, (unsigned long long)i, p);
+    *g = grid_lookup(A.grid, A.n, A.o_ih, A.h, p[0], p[1], p[2]);
+    return fabsf(*g) <= A.band;
+}
+
+// Near candidates: per-block counts of accepted candidates of this chunk.
+__global__ void __launch_bounds__(1024) sample_count_kernel(const __grid_constant__ SampleArgs A) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    float p[3], g;
+    const bool acc = i < A.count && near_ok(A, A.start + i, p, &g);
+    const unsigned b = __ballot_sync(0xffffffffu, acc);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&cnt, __popc(b));
+    __syncthreads();
+    if (threadIdx.x == 0) A.block_count[blockIdx.x] = cnt;
+}
+
+// Exclusive scan of the block counts (one block); the chunk's total is added to *found
+// after the scatter has used the old value (scatter reads found_before).
+__global__ void __launch_bounds__(1024) sample_scan_kernel(int* counts, int nb, long long* found,
+                                                           long long* found_before) {
+    __shared__ int part[1024];
+    const int t = threadIdx.x;
+    const int per = (nb + 1023) / 1024;
+    int s = 0;
+    for (int k = 0; k < per; ++k) {
+        const int i = t * per + k;
+        if (i < nb) s += counts[i];
+    }
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - s;   // exclusive prefix of this thread's range
+    for (int k = 0; k < per; ++k) {
+        const int i = t * per + k;
+        if (i < nb) {
+            const int c = counts[i];
+            counts[i] = run;
+            run += c;
+        }
+    }
+    if (t == 1023) {
+        *found_before = *found;
+        *found += part[1023];
+    }
+}
+
+// Scatter accepted candidates in counter order: near sample k goes to position
+// j = (k / near10) * 10 + k % near10.
+__global__ void __launch_bounds__(1024) sample_scatter_kernel(const __grid_constant__ SampleArgs A,
+                                                              const long long* found_before) {
+    __shared__ int warp_off[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float p[3], g = 0.f;
+    const bool acc = i < A.count && near_ok(A, A.start + i, p, &g);
+    const unsigned b = __ballot_sync(0xffffffffu, acc);
+    if (lane == 0) warp_off[warp] = __popc(b);
+    __syncthreads();
+    if (warp == 0) {
+        const int v = warp_off[lane];
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        warp_off[lane] = incl - v;
+    }
+    __syncthreads();
+    if (!acc) return;
+    const long long k = *found_before + A.block_count[blockIdx.x] + warp_off[warp] + __popc(b & ((1u << lane) - 1u));
+    if (k >= A.n_near) return;
+    const long long j = (k / A.near10) * 10 + k % A.near10;
+    if (j < A.n_samples) emit(A, j, p, g, A.start + i);
+}
+
+// ------------------------------------------------------------------ error measurement
+
+__global__ void error_reduce_kernel(const float* f, const float* y, int n, float a, unsigned* max_bits,
+                                    double* sum) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float e = 0.f;
+    if (i < n) e = fabsf(f[i] - y[i]) * a;
+    float m = e, s = e;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(max_bits, __float_as_uint(m));   // non-negative floats order as their bits
+        atomicAdd(sum, (double)s);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+
+cudaError_t configure_surrogate_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mlp_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kEvalSmem);
+    return e;
+}
+
+}  // namespace sdf
+
+// ====================================================================== C ABI
+
+struct sdf_surrogate {
+    int device = 0;
+    int L = 0;
+    const sdf_grids* grids = nullptr;
+    float* master = nullptr;   // [L][PARAMS], W2/W3 blocks [in][out]
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    int* step = nullptr;
+    float* loss = nullptr;     // [L]
+    float box_m[SDF_MAX_LINKS][3];
+    float box_a[SDF_MAX_LINKS];
+};
+
+namespace {
+
+using sdf::kH;
+using sdf::kPar;
+
+int sfail(sdf_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+int scuda(sdf_ctx* ctx, cudaError_t e, const char* what) {
+    return sfail(ctx, SDF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct Dev {
+    int prev = -1;
+    explicit Dev(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~Dev() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// public layout (W2, W3 [out][in]) <-> device layout ([in][out])
+void to_device_layout(const float* in, float* out) {
+    std::memcpy(out, in, sizeof(float) * kPar);
+    for (int blk = 0; blk < 2; ++blk) {
+        const int base = blk == 0 ? sdf::kOW2 : sdf::kOW3;
+        for (int o = 0; o < kH; ++o)
+            for (int i = 0; i < kH; ++i) out[base + i * kH + o] = in[base + o * kH + i];
+    }
+}
+void to_public_layout(const float* in, float* out) {
+    std::memcpy(out, in, sizeof(float) * kPar);
+    for (int blk = 0; blk < 2; ++blk) {
+        const int base = blk == 0 ? sdf::kOW2 : sdf::kOW3;
+        for (int o = 0; o < kH; ++o)
+            for (int i = 0; i < kH; ++i) out[base + o * kH + i] = in[base + i * kH + o];
+    }
+}
+
+bool surrogate_configured(int device) {
+    static bool done[64] = {};
+    if (device < 0 || device >= 64) return false;
+    if (!done[device]) done[device] = sdf::configure_surrogate_kernels() == cudaSuccess;
+    return done[device];
+}
+
+sdf::SampleArgs sample_args(const sdf_grids* G, int link) {
+    sdf::SampleArgs A{};
+    const sdf_grid_meta& m = G->meta[link];
+    const int n = G->n;
+    A.grid = G->values + (size_t)link * n * n * n;
+    A.n = n;
+    A.o_ih = make_float4(m.origin[0], m.origin[1], m.origin[2], 1.0f / m.h);
+    A.h = m.h;
+    const double a = 0.5 * (n - 1) * (double)m.h;
+    for (int k = 0; k < 3; ++k) {
+        A.lo[k] = m.origin[k];
+        A.span[k] = (float)(2.0 * a);
+        A.m[k] = (float)(m.origin[k] + a);
+    }
+    A.inv_a = (float)(1.0 / a);
+    return A;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdf_surrogate_create(sdf_ctx* ctx, const sdf_grids* grids, const float* params_host, sdf_surrogate** out) {
+    if (!ctx || !grids || !params_host || !out) return sfail(ctx, SDF_ERR_INVALID_ARG, "sdf_surrogate_create: null");
+    *out = nullptr;
+    if (grids->device != ctx->device) return sfail(ctx, SDF_ERR_INVALID_ARG, "sdf_surrogate_create: other device");
+    Dev guard(ctx->device);
+    if (!surrogate_configured(ctx->device)) return sfail(ctx, SDF_ERR_CUDA, "surrogate kernels: attributes");
+    sdf_surrogate* S = new (std::nothrow) sdf_surrogate();
+    if (!S) return sfail(ctx, SDF_ERR_OOM, "sdf_surrogate_create");
+    S->device = ctx->device;
+    S->L = grids->n_links;
+    S->grids = grids;
+    const size_t bytes = sizeof(float) * (size_t)kPar * S->L;
+    cudaError_t e = cudaMalloc(&S->master, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&S->adam_m, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&S->adam_v, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&S->step, sizeof(int) * S->L);
+    if (e == cudaSuccess) e = cudaMalloc(&S->loss, sizeof(float) * S->L);
+    std::vector<float> dev((size_t)kPar * S->L);
+    for (int l = 0; l < S->L; ++l) to_device_layout(params_host + (size_t)l * kPar, dev.data() + (size_t)l * kPar);
+    if (e == cudaSuccess) e = cudaMemcpy(S->master, dev.data(), bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(S->adam_m, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(S->adam_v, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(S->step, 0, sizeof(int) * S->L);
+    if (e == cudaSuccess) e = cudaMemset(S->loss, 0, sizeof(float) * S->L);
+    if (e != cudaSuccess) {
+        sdf_surrogate_destroy(S);
+        return scuda(ctx, e, "sdf_surrogate_create");
+    }
+    for (int l = 0; l < S->L; ++l) {
+        const sdf_grid_meta& m = grids->meta[l];
+        const double a = 0.5 * (grids->n - 1) * (double)m.h;
+        for (int k = 0; k < 3; ++k) S->box_m[l][k] = (float)(m.origin[k] + a);
+        S->box_a[l] = (float)a;
+    }
+    *out = S;
+    return SDF_OK;
+}
+
+void sdf_surrogate_destroy(sdf_surrogate* S) {
+    if (!S) return;
+    Dev guard(S->device);
+    cudaFree(S->master);
+    cudaFree(S->adam_m);
+    cudaFree(S->adam_v);
+    cudaFree(S->step);
+    cudaFree(S->loss);
+    delete S;
+}
+
+int sdf_surrogate_params(sdf_ctx* ctx, const sdf_surrogate* S, float* params_host) {
+    if (!ctx || !S || !params_host) return sfail(ctx, SDF_ERR_INVALID_ARG, "sdf_surrogate_params: null");
+    Dev guard(S->device);
+    std::vector<float> dev((size_t)kPar * S->L);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(dev.data(), S->master, dev.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return scuda(ctx, e, "sdf_surrogate_params");
+    for (int l = 0; l < S->L; ++l) to_public_layout(dev.data() + (size_t)l * kPar, params_host + (size_t)l * kPar);
+    return SDF_OK;
+}
+
+int sdf_surrogate_sample(sdf_ctx* ctx, const sdf_grids* G, int32_t link, int64_t n, int32_t near_per_10, float band,
+                         uint64_t seed, float* x_dev, float* y_dev, int64_t* source_dev) {
+    if (!ctx || !G || !x_dev || !y_dev || link < 0 || link >= G->n_links || n < 0 || near_per_10 < 0 ||
+        near_per_10 > 10 || !(band > 0.f))
+        return sfail(ctx, SDF_ERR_INVALID_ARG, "sdf_surrogate_sample: invalid argument");
+    if (n == 0) return SDF_OK;
+    Dev guard(ctx->device);
+    sdf::SampleArgs A = sample_args(G, link);
+    A.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    A.band = band;
+    A.near10 = near_per_10;
+    A.n_samples = n;
+    A.n_near = (n / 10) * near_per_10 + std::min<int64_t>(n % 10, near_per_10);
+    A.x = x_dev;
+    A.y = y_dev;
+    A.source = reinterpret_cast<long long*>(source_dev);
+    cudaStream_t st = ctx->stream;
+    sdf::sample_uniform_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return scuda(ctx, e, "sample_uniform_kernel");
+    if (A.n_near == 0) return SDF_OK;
+    // near samples: chunks of candidates until enough are accepted
+    const int chunk = (int)std::min<int64_t>(std::max<int64_t>(4 * A.n_near, 1 << 20), 1 << 26);
+    const int nb = (chunk + 1023) / 1024;
+    int* counts = nullptr;
+    long long* found = nullptr;   // [0] found, [1] found before this chunk
+    e = cudaMalloc(&counts, sizeof(int) * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&found, 2 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(found, 0, 2 * sizeof(long long), st);
+    long long have = 0;
+    long long start = 0;
+    const long long max_candidates = 1ll << 32;   // the counter is 32 bits wide
+    while (e == cudaSuccess && have < A.n_near) {
+        if (start >= max_candidates) {
+            cudaFree(counts);
+            cudaFree(found);
+            return sfail(ctx, SDF_ERR_INVALID_ARG, "sdf_surrogate_sample: too few candidates within the band");
+        }
+        A.start = start;
+        A.count = chunk;
+        A.block_count = counts;
+        A.found = found;
+        sdf::sample_count_kernel<<<nb, 1024, 0, st>>>(A);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) sdf::sample_scan_kernel<<<1, 1024, 0, st>>>(counts, nb, found, found + 1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) sdf::sample_scatter_kernel<<<nb, 1024, 0, st>>>(A, found + 1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&have, found, sizeof(long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        start += chunk;
+    }
+    cudaFree(counts);
+    cudaFree(found);
+    if (e != cudaSuccess) return scuda(ctx, e, "sdf_surrogate_sample");
+    return SDF_OK;
+}
+
+namespace {
+int launch_train(sdf_ctx* ctx, sdf_surrogate* S, int link0, int links, const float* x, const float* y, long long n,
+                 long long batch0, int steps, float lr, float* grad_out, float* loss_out) {
+    if (!surrogate_configured(ctx->device)) return sfail(ctx, SDF_ERR_CUDA, "surrogate kernels: attributes");
+    sdf::TrainArgs A{};
+    A.master = S->master;
+    A.adam_m = S->adam_m;
+    A.adam_v = S->adam_v;
+    A.step = S->step;
+    A.x = x;
+    A.y = y;
+    A.n = n;
+    A.batch0 = batch0;
+    A.steps = steps;
+    A.link0 = link0;
+    A.lr = lr;
+    A.beta1 = 0.9f;
+    A.beta2 = 0.999f;
+    A.eps = 1e-8f;
+    A.grad_out = grad_out;
+    A.loss_out = loss_out;
+    A.status = ctx->status;
+    sdf::mlp_train_kernel<<<links, 128, sdf::kTrainSmem, ctx->stream>>>(A);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SDF_OK : scuda(ctx, e, "mlp_train_kernel");
+}
+}  // namespace
+
+int sdf_surrogate_grad(sdf_ctx* ctx, const sdf_surrogate* S, int32_t link, const float* x_dev, const float* y_dev,
+                       float* grad_dev, float* loss_dev) {
+    if (!ctx || !S || !x_dev || !y_dev || !grad_dev || link < 0 || link >= S->L)
+        return sfail(ctx, SDF_ERR_INVALID_ARG, "sdf_surrogate_grad: invalid argument");
+    Dev guard(ctx->device);
+    // one batch of SDF_MLP_BATCH samples, read as link `link`'s samples: the kernel
+    // indexes x[link][n][3] with n = SDF_MLP_BATCH, so shift the base pointers back
+    const float* xb = x_dev - (size_t)link * SDF_MLP_BATCH * 3;
+    const float* yb = y_dev - (size_t)link * SDF_MLP_BATCH;
+    float* lb = loss_dev ? loss_dev - link : nullptr;
+    return launch_train(ctx, const_cast<sdf_surrogate*>(S), link, 1, xb, yb, SDF_MLP_BATCH, 0, 1, 0.f, grad_dev,
+                        lb);
+}
+
+int sdf_surrogate_train(sdf_ctx* ctx, sdf_surrogate* S, const float* x_dev, const float* y_dev, int64_t n,
+                        int64_t first_batch, int32_t steps, float lr, float* loss_dev) {
+    if (!ctx || !S || !x_dev || !y_dev || n < 1 || first_batch < 0 || steps < 0 || !(lr >= 0.f))
+        return sfail(ctx, SDF_ERR_INVALID_ARG, "sdf_surrogate_train: invalid argument");
+    if (steps == 0) return SDF_OK;
+    Dev guard(ctx->device);
+    float* loss = loss_dev ? loss_dev : S->loss;
+    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float) * S->L, ctx->stream);
+    if (e != cudaSuccess) return scuda(ctx, e, "sdf_surrogate_train");
+    return launch_train(ctx, S, 0, S->L, x_dev, y_dev, n, first_batch, steps, lr, nullptr, loss);
+}
+
+int sdf_surrogate_eval(sdf_ctx* ctx, const sdf_surrogate* S, int32_t link, const float* x_dev, int32_t n,
+                       float* f_dev) {
+    if (!ctx || !S || link < 0 || link >= S->L || n < 0 || (n > 0 && (!x_dev || !f_dev)))
+        return sfail(ctx, SDF_ERR_INVALID_ARG, "sdf_surrogate_eval: invalid argument");
+    if (n == 0) return SDF_OK;
+    Dev guard(ctx->device);
+    if (!surrogate_configured(ctx->device)) return sfail(ctx, SDF_ERR_CUDA, "surrogate kernels: attributes");
+    sdf::EvalArgs A{};
+    A.master = S->master;
+    A.x3 = x_dev;
+    A.L = S->L;
+    A.n = n;
+    A.link0 = link;
+    A.f_out = f_dev;
+    A.status = ctx->status;
+    const int tiles = (n + 127) / 128;
+    const int grid = std::min(tiles, ctx->num_sms);
+    sdf::mlp_eval_kernel<<<grid, 128, sdf::kEvalSmem, ctx->stream>>>(A);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SDF_OK : scuda(ctx, e, "mlp_eval_kernel");
+}
+
+int sdf_surrogate_error(sdf_ctx* ctx, const sdf_surrogate* S, int32_t link, int64_t n, int32_t near_per_10,
+                        float band, uint64_t seed, float* max_abs, float* mean_abs) {
+    if (!ctx || !S || link < 0 || link >= S->L || n < 1 || n > (1 << 30))
+        return sfail(ctx, SDF_ERR_INVALID_ARG, "sdf_surrogate_error: invalid argument");
+    Dev guard(ctx->device);
+    float *x = nullptr, *y = nullptr, *f = nullptr;
+    unsigned* mx = nullptr;
+    double* sum = nullptr;
+    cudaError_t e = cudaMalloc(&x, sizeof(float) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&f, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&mx, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&sum, sizeof(double));
+    int rc = e == cudaSuccess ? SDF_OK : scuda(ctx, e, "sdf_surrogate_error");
+    if (rc == SDF_OK) rc = sdf_surrogate_sample(ctx, S->grids, link, n, near_per_10, band, seed, x, y, nullptr);
+    if (rc == SDF_OK) rc = sdf_surrogate_eval(ctx, S, link, x, (int32_t)n, f);
+    unsigned hm = 0;
+    double hs = 0.0;
+    if (rc == SDF_OK) {
+        e = cudaMemsetAsync(mx, 0, sizeof(unsigned), ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sum, 0, sizeof(double), ctx->stream);
+        if (e == cudaSuccess)
+            sdf::error_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(f, y, (int)n,
+                                                                                       S->box_a[link], mx, sum);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, mx, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, sum, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = scuda(ctx, e, "sdf_surrogate_error");
+    }
+    cudaFree(x);
+    cudaFree(y);
+    cudaFree(f);
+    cudaFree(mx);
+    cudaFree(sum);
+    if (rc == SDF_OK) {
+        float m;
+        std::memcpy(&m, &hm, sizeof(float));
+        if (max_abs) *max_abs = m;
+        if (mean_abs) *mean_abs = (float)(hs / (double)n);
+    }
+    return rc;
+}
+
+}  // extern "C"

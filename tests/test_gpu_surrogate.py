@@ -1,0 +1,171 @@
+"""Learned surrogate on the GPU against the FP64 oracle (oracle/mlp.py): the
+sampler's candidates and labels, the forward pass, the gradient of one batch,
+Adam steps, and training that lowers the error against the grid.
+
+Tolerances.  The GPU rounds the products' operands to bfloat16 exactly where the
+oracle does, but it computes the values being rounded in FP32 (with a fast
+exponential in SiLU), so a value within ~1e-7 relative of a bfloat16 rounding
+boundary can round the other way: one bfloat16 ulp (2^-8 relative) on that
+operand.  Such flips are rare (about 1e-5 of the operands) and each moves a
+product by at most one term's ulp, so results agree to ~1e-3 of their scale,
+which is what the assertions allow; everything in FP32 alone agrees to ~1e-5."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sdf():
+    from paper_2309_12543_gb300 import build
+    build.build()
+    import paper_2309_12543_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def env(sdf):
+    sc = sg.make_scene("tiny")
+    vals, metas = oracle.build_grids_cached(sc.meshes, sc.resolution, sc.margin)
+    ctx = sdf.Context(0, torch.cuda.current_stream())
+    grids = sdf.sdf_grids_upload(ctx, vals, metas)
+    return sc, ctx, grids, np.asarray(vals), [np.asarray(m) for m in metas]
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def test_sampler_candidates_and_labels(sdf, env):
+    sc, ctx, grids, vals, metas = env
+    link, n, near10, band, seed = 2, 20000, 7, 0.10, 0x1234_5678_9abc
+    x = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    src = torch.empty(n, dtype=torch.int64, device="cuda")
+    sdf.sdf_surrogate_sample(ctx, grids, link, n, near10, band, seed, x, y, src)
+    assert ctx.synchronize() == 0
+    x, y, src = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64), src.cpu().numpy()
+    m, a, lo, hi = mlp.box_of(metas[link])
+    j = np.arange(n)
+    near = (j % 10) < near10
+    stream, counter = src >> 40, src & ((1 << 40) - 1)
+    assert np.array_equal(stream, np.where(near, 0, 1))
+    # uniform samples are the uniform stream in order
+    u = (j // 10) * (10 - near10) + (j % 10 - near10)
+    assert np.array_equal(counter[~near], u[~near])
+    # every sample is its candidate, normalised, and labelled by the grid
+    for s_id in (0, 1):
+        sel = stream == s_id
+        c = np.concatenate([mlp.sample_candidates(metas[link], seed, s_id, int(i), 1) for i in counter[sel][:500]])
+        assert np.allclose(x[sel][:500], (c - m) / a, atol=1e-6)
+    p = x * a + m
+    g = oracle.lookup(vals[link], metas[link], p)
+    assert np.max(np.abs(y * a - g)) < 1e-5
+    # near samples: the accepted candidates of stream 0 in counter order
+    k_counter = counter[near]
+    assert np.all(np.diff(k_counter) > 0)
+    assert np.all(np.abs(g[near]) <= band + 1e-5)
+    skipped = np.setdiff1d(np.arange(k_counter[-1] + 1), k_counter)
+    cs = mlp.sample_candidates(metas[link], seed, 0, 0, int(k_counter[-1]) + 1)[skipped]
+    assert np.all(np.abs(oracle.lookup(vals[link], metas[link], cs)) > band - 1e-5)
+
+
+def test_forward_matches_oracle(sdf, env):
+    sc, ctx, grids, vals, metas = env
+    params = sg.mlp_init(11, len(metas))
+    sur = sdf.Surrogate(ctx, grids, params)
+    assert np.array_equal(sur.params(), params)          # the layout round-trips
+    rng = np.random.default_rng(12)
+    for link, n in ((0, 1000), (5, 129), (6, 1)):
+        xs = rng.uniform(-1.2, 1.2, (n, 3)).astype(np.float32)
+        f = torch.empty(n, dtype=torch.float32, device="cuda")
+        sur.eval(link, _dev(xs), n, f)
+        assert ctx.synchronize() == 0
+        ref = mlp.forward(params[link].astype(np.float64), xs.astype(np.float64), quantize=True)
+        err = np.abs(f.cpu().numpy() - ref)
+        scale = np.max(np.abs(ref))
+        assert err.max() <= 2e-3 * scale + 1e-5, (link, err.max(), scale)
+        assert np.median(err) <= 1e-4 * scale + 1e-6
+
+
+def test_gradient_matches_oracle(sdf, env):
+    sc, ctx, grids, vals, metas = env
+    params = sg.mlp_init(13, len(metas))
+    sur = sdf.Surrogate(ctx, grids, params)
+    rng = np.random.default_rng(14)
+    for link in (1, 4):
+        xs = rng.uniform(-1, 1, (128, 3)).astype(np.float32)
+        f0 = mlp.forward(params[link].astype(np.float64), xs.astype(np.float64), quantize=True)
+        # labels away from the prediction, so sign(f - y) is the same on both sides
+        ys = (f0 + np.where(rng.random(128) < 0.5, -1, 1) * rng.uniform(0.05, 0.5, 128)).astype(np.float32)
+        g = torch.empty(sdf.SDF_MLP_PARAMS, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        sur.grad(link, _dev(xs), _dev(ys), g, loss)
+        assert ctx.synchronize() == 0
+        l_ref, g_ref = mlp.loss_and_grad(params[link].astype(np.float64), xs, ys, quantize=True)
+        assert abs(loss.item() - l_ref) <= 1e-4 * l_ref
+        G, R = mlp.unpack(g.cpu().numpy().astype(np.float64)), mlp.unpack(g_ref)
+        for k in R:
+            d = np.abs(np.asarray(G[k]) - np.asarray(R[k]))
+            scale = np.max(np.abs(R[k]))
+            assert d.max() <= 5e-3 * scale + 1e-7, (link, k, d.max(), scale)
+            assert np.linalg.norm(np.asarray(G[k]) - np.asarray(R[k])) <= 2e-3 * np.linalg.norm(R[k]) + 1e-7, k
+    assert np.array_equal(sur.params(), params)          # gradient mode changes nothing
+
+
+def test_adam_steps_match_oracle(sdf, env):
+    sc, ctx, grids, vals, metas = env
+    L = len(metas)
+    params = sg.mlp_init(15, L)
+    sur = sdf.Surrogate(ctx, grids, params)
+    rng = np.random.default_rng(16)
+    n, steps, lr = 384, 3, 1e-3
+    X = rng.uniform(-1, 1, (L, n, 3)).astype(np.float32)
+    Y = rng.uniform(-0.6, 0.6, (L, n)).astype(np.float32)
+    loss = torch.zeros(L, dtype=torch.float32, device="cuda")
+    sur.train(_dev(X), _dev(Y), n, 1, steps, lr, loss)
+    assert ctx.synchronize() == 0
+    got = sur.params().astype(np.float64)
+    for link in (0, 3):
+        # batches start at index 1 (first_batch = 1); Adam's step counter starts at 1
+        p_ref = params[link].astype(np.float64).copy()
+        m = np.zeros(mlp.PARAMS)
+        v = np.zeros(mlp.PARAMS)
+        ls = []
+        for s in range(steps):
+            idx = ((1 + s) * 128 + np.arange(128)) % n
+            lv, gr = mlp.loss_and_grad(p_ref, X[link][idx], Y[link][idx], quantize=True)
+            p_ref, m, v = mlp.adam_step(p_ref, gr, m, v, s + 1, lr)
+            ls.append(lv)
+        assert abs(loss.cpu().numpy()[link] - sum(ls)) <= 1e-3 * sum(ls)
+        step_gpu = got[link] - params[link]
+        step_ref = p_ref - params[link]
+        # each Adam step moves a parameter by about lr; where the gradient is tiny its
+        # sign (and so the step) is decided by rounding: compare all but a few
+        bad = np.abs(step_gpu - step_ref) > 0.2 * lr
+        assert bad.mean() < 0.01, (link, bad.mean())
+        assert np.max(np.abs(step_gpu - step_ref)) <= 2 * steps * lr * 1.01
+
+
+def test_training_lowers_the_error(sdf, env):
+    sc, ctx, grids, vals, metas = env
+    L = len(metas)
+    sur = sdf.Surrogate(ctx, grids, sg.mlp_init(17, L))
+    n = 65536
+    X = torch.empty((L, n, 3), dtype=torch.float32, device="cuda")
+    Y = torch.empty((L, n), dtype=torch.float32, device="cuda")
+    for l in range(L):
+        sdf.sdf_surrogate_sample(ctx, grids, l, n, 7, 0.10, 1000 + l, X[l], Y[l])
+    before = [sur.error(l, 20000, seed=5)[1] for l in range(L)]
+    loss = torch.zeros(L, dtype=torch.float32, device="cuda")
+    sur.train(X, Y, n, 0, 3000, 1e-3, loss)
+    assert ctx.synchronize() == 0
+    after = [sur.error(l, 20000, seed=5) for l in range(L)]
+    print("mean error before", before, "after", after)
+    for l in range(L):
+        assert after[l][1] < 0.2 * before[l], (l, before[l], after[l])
