@@ -231,7 +231,9 @@ int check_trajectory(sdf_ctx* ctx, const sdf_robot* robot, const float* q_dev, i
                      const float* points_dev, int32_t N, float* dist_dev,
                      int32_t* argmin_link_dev, int32_t* argmin_point_dev);
 
-/* One trajectory of a batch: the arguments of check_trajectory. */
+/* One trajectory of a batch: the arguments of check_trajectory, and an optional
+ * per-waypoint mask (device, W bytes): when set, only waypoints whose byte is
+ * non-zero are checked and written; the other outputs are left as they are. */
 typedef struct {
     const sdf_robot* robot;
     const float* q_dev;
@@ -241,6 +243,7 @@ typedef struct {
     float* dist_dev;
     int32_t* argmin_link_dev;
     int32_t* argmin_point_dev;
+    const uint8_t* mask_dev;
 } sdf_check_request;
 
 /* Batching (the paper batches all configurations of a trajectory, Sec. III-A;
@@ -406,6 +409,26 @@ int sdf_surrogate_eval(sdf_ctx* ctx, const sdf_surrogate* surrogate, int32_t lin
  * *mean_abs of |a f(x) - g|.  Synchronises. */
 int sdf_surrogate_error(sdf_ctx* ctx, const sdf_surrogate* surrogate, int32_t link, int64_t n, int32_t near_per_10,
                         float band, uint64_t seed, float* max_abs, float* mean_abs);
+
+/* The check with the surrogate in place of the grid lookup, and the grid path as
+ * fallback.  For each waypoint: forward kinematics, then every (link, point) pair
+ * whose sphere bound ||p - c_link|| - R_link is within the surrogate minimum found
+ * so far plus `eps` (seeded by the 32 points of the nearest tile per link) is
+ * evaluated by the link's network, with the out-of-box rule; the minimum and its
+ * arg-min are the surrogate result.  Waypoints whose surrogate minimum is below
+ * margin + eps -- eps being the caller's bound on the surrogate's error, e.g. from
+ * sdf_surrogate_error -- are checked again by the grid path, whose result replaces
+ * the surrogate's (exactly what check_trajectory returns for them).  Outputs as
+ * check_trajectory; rechecked_dev (optional, W bytes) is 1 where the grid path
+ * decided, surrogate_dist_dev (optional, W FP32) the surrogate minimum before the
+ * re-check.  Uses workspace owned by the surrogate (grown on demand, which
+ * synchronises): calls with the same surrogate must not overlap.  Asynchronous.
+ * Errors: INVALID_ARG (robot and surrogate built on different grids, bad sizes),
+ * OOM, CUDA. */
+int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* robot, const sdf_surrogate* surrogate,
+                               const float* q_dev, int32_t W, const float* points_dev, int32_t N, float margin,
+                               float eps, float* dist_dev, int32_t* argmin_link_dev, int32_t* argmin_point_dev,
+                               uint8_t* rechecked_dev, float* surrogate_dist_dev);
 
 /* ----------------------------------------------------------- allocation-free check */
 

@@ -63,7 +63,8 @@ class sdf_dh(ctypes.Structure):
 class sdf_check_request(ctypes.Structure):
     _fields_ = [("robot", ctypes.c_void_p), ("q_dev", ctypes.c_void_p), ("W", ctypes.c_int32),
                 ("points_dev", ctypes.c_void_p), ("N", ctypes.c_int32), ("dist_dev", ctypes.c_void_p),
-                ("argmin_link_dev", ctypes.c_void_p), ("argmin_point_dev", ctypes.c_void_p)]
+                ("argmin_link_dev", ctypes.c_void_p), ("argmin_point_dev", ctypes.c_void_p),
+                ("mask_dev", ctypes.c_void_p)]
 
 
 class sdf_server_config(ctypes.Structure):
@@ -101,6 +102,8 @@ def _load():
         "sdf_surrogate_train": (ctypes.c_int, [P, P, P, P, i64, i64, i32, ctypes.c_float, P]),
         "sdf_surrogate_eval": (ctypes.c_int, [P, P, i32, P, i32, P]),
         "sdf_surrogate_error": (ctypes.c_int, [P, P, i32, i64, i32, ctypes.c_float, ctypes.c_uint64, P, P]),
+        "check_trajectory_surrogate": (ctypes.c_int, [P, P, P, P, i32, P, i32, ctypes.c_float, ctypes.c_float,
+                                                      P, P, P, P, P]),
         "sdf_ctx_last_kernel_ms": (ctypes.c_int, [P, i32, ctypes.POINTER(ctypes.c_float)]),
         "sdf_build_grids": (ctypes.c_int, [P, P, i32, i32, ctypes.c_float, ctypes.POINTER(P)]),
         "sdf_grids_upload": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(P)]),
@@ -142,7 +145,7 @@ EXPORTED = ("sdf_ctx_create", "sdf_ctx_destroy", "sdf_ctx_set_stream", "sdf_last
             "sdf_server_create", "sdf_server_destroy", "sdf_server_set_cloud", "sdf_server_submit",
             "sdf_server_poll", "sdf_server_stats", "sdf_measure_gather", "sdf_surrogate_create",
             "sdf_surrogate_destroy", "sdf_surrogate_params", "sdf_surrogate_sample", "sdf_surrogate_grad",
-            "sdf_surrogate_train", "sdf_surrogate_eval", "sdf_surrogate_error")
+            "sdf_surrogate_train", "sdf_surrogate_eval", "sdf_surrogate_error", "check_trajectory_surrogate")
 
 
 def _ptr(x) -> int:
@@ -346,14 +349,16 @@ def check_trajectory(ctx: Context, robot: Robot, q_dev, W: int, points_dev, N: i
 
 def _requests(requests):
     arr = (sdf_check_request * max(len(requests), 1))()
-    for i, (robot, q, W, pts, N, d, al, ap) in enumerate(requests):
+    for i, r in enumerate(requests):
+        robot, q, W, pts, N, d, al, ap = r[:8]
+        mask = r[8] if len(r) > 8 else None
         arr[i] = sdf_check_request(robot.handle.value if hasattr(robot.handle, "value") else robot.handle,
-                                   _ptr(q), int(W), _ptr(pts), int(N), _ptr(d), _ptr(al), _ptr(ap))
+                                   _ptr(q), int(W), _ptr(pts), int(N), _ptr(d), _ptr(al), _ptr(ap), _ptr(mask))
     return arr
 
 
 def check_batch(ctx: Context, requests) -> None:
-    """requests: sequence of (robot, q_dev, W, points_dev, N, dist_dev, link_dev, point_dev)."""
+    """requests: sequence of (robot, q_dev, W, points_dev, N, dist_dev, link_dev, point_dev[, mask_dev])."""
     arr = _requests(requests)
     ctx._check(lib.check_batch(ctx.handle, ctypes.addressof(arr), len(requests)), "check_batch")
 
@@ -519,3 +524,12 @@ def sdf_surrogate_sample(ctx: Context, grids: "Grids", link: int, n: int, near_p
     ctx._check(lib.sdf_surrogate_sample(ctx.handle, grids.handle, int(link), int(n), int(near_per_10), float(band),
                                         ctypes.c_uint64(seed), _ptr(x), _ptr(y), _ptr(source)),
                "sdf_surrogate_sample")
+
+
+def check_trajectory_surrogate(ctx: Context, robot: "Robot", surrogate: Surrogate, q, W: int, points, N: int,
+                               margin: float, eps: float, dist, link, point, rechecked=None, surrogate_dist=None):
+    """The check with the surrogate in place of the grid lookup; waypoints below
+    margin + eps are re-checked by the grid path (device buffers, asynchronous)."""
+    ctx._check(lib.check_trajectory_surrogate(ctx.handle, robot.handle, surrogate.handle, _ptr(q), int(W), _ptr(points),
+                                              int(N), float(margin), float(eps), _ptr(dist), _ptr(link), _ptr(point),
+                                              _ptr(rechecked), _ptr(surrogate_dist)), "check_trajectory_surrogate")

@@ -503,6 +503,41 @@ static int reserve_scratch(sdf_ctx* ctx, size_t points, size_t tiles, size_t sup
     return rc;
 }
 
+}  // extern "C"
+
+namespace sdf {
+
+// Sort one cloud into the context's scratch (the layout check_batch uses for a
+// single request) and fill p for kernels that read it.  Asynchronous.
+int sort_cloud(sdf_ctx* ctx, const float* points_dev, int N, BatchParams* p) {
+    const uintptr_t pa = reinterpret_cast<uintptr_t>(points_dev);
+    if (N < 0 || N > SDF_MAX_POINTS || (N > 0 && !points_dev) || (pa & 3u) != 0 ||
+        (ctx->point_stride == 4 && (pa & 15u) != 0))
+        return fail(ctx, SDF_ERR_INVALID_ARG, "cloud: invalid points");
+    const size_t tiles = ((size_t)N + 31) / 32;
+    int rc = reserve_scratch(ctx, (size_t)N, tiles, (tiles + 31) / 32, 1);
+    if (rc != SDF_OK) return rc;
+    CloudDesc& C = p->cloud[0];
+    C.points = points_dev;
+    C.N = N;
+    C.point_base = C.tile_base = C.super_base = 0;
+    p->n_cloud = 1;
+    p->stride = ctx->point_stride;
+    p->cull = ctx->cull;
+    p->sorted = ctx->sorted;
+    p->tiles = ctx->tiles;
+    p->supers = ctx->supers;
+    p->n_valid = ctx->n_valid;
+    p->status = ctx->status;
+    p->stats = nullptr;
+    const cudaError_t e = launch_prep(*p, ctx->stream);
+    return e == cudaSuccess ? SDF_OK : cuda_fail(ctx, e, "cloud sort");
+}
+
+}  // namespace sdf
+
+extern "C" {
+
 int sdf_ctx_reserve(sdf_ctx* ctx, int64_t max_points, int64_t max_waypoints, int64_t max_pairs, int32_t max_requests) {
     if (!ctx || max_points < 0 || max_waypoints < 0 || max_pairs < 0 || max_requests < 0 || max_requests > SDF_MAX_BATCH)
         return SDF_ERR_INVALID_ARG;
@@ -585,6 +620,7 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
         I.L = r.robot->table.L;
         I.dof = r.robot->dof;
         I.cloud = c;
+        I.mask = r.mask_dev;
         launch_shape(ctx, key, I.L, &I.tw, &tile_batch);
         I.block_base = (int)blocks;
         blocks += ((size_t)r.W + I.tw - 1) / I.tw;
@@ -605,6 +641,7 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     p->stride = ctx->point_stride;
     p->cull = ctx->cull;
     p->stage_tiles = (int)std::min<size_t>(max_tiles, (size_t)sdf::kMaxStagedTiles);
+    p->skip_prep = ctx->reuse_sort;
     p->sorted = ctx->sorted;
     p->tiles = ctx->tiles;
     p->supers = ctx->supers;
@@ -685,7 +722,7 @@ int sdf_autotune(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n, int32_t
 int check_trajectory(sdf_ctx* ctx, const sdf_robot* R, const float* q_dev, int32_t W, const float* points_dev,
                      int32_t N, float* dist_dev, int32_t* argmin_link_dev, int32_t* argmin_point_dev) {
     if (!ctx || !R) return SDF_ERR_INVALID_ARG;
-    sdf_check_request r;
+    sdf_check_request r{};
     r.robot = R;
     r.q_dev = q_dev;
     r.W = W;

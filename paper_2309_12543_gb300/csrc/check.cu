@@ -573,6 +573,10 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
     const int w0 = ((int)blockIdx.x - I.block_base) * I.tw;
     const int nw = min(I.tw, I.W - w0);
     const int n_pair = nw * L;
+    if (I.mask) {   // a masked re-check: blocks without a selected waypoint leave at once
+        const bool any = tid < nw && I.mask[w0 + tid] != 0;
+        if (!__syncthreads_or(any)) return;
+    }
     if (tid < kCheckWarps) {
         s_best[tid] = kOrderedInf;
         s_key[tid] = ~0ull;
@@ -792,7 +796,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
     }
 
     // results of the block's waypoints
-    if (tid < nw) {
+    if (tid < nw && (!I.mask || I.mask[w0 + tid] != 0)) {
         const int w = w0 + tid;
         const unsigned long long key = s_key[tid];
         if (key == ~0ull) {
@@ -844,9 +848,12 @@ cudaError_t configure_kernels() {
 
 cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, cudaEvent_t ev_mid) {
     if (p.n_inst <= 0 || p.n_blocks <= 0) return cudaSuccess;
-    prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, 0, s>>>(p);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!p.skip_prep) {
+        prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, 0, s>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (ev_mid) {   // a timing event between the kernels; the check then starts after the sort ends
         e = cudaEventRecord(ev_mid, s);
         if (e != cudaSuccess) return e;
@@ -862,13 +869,19 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = ev_mid ? 0 : 1;
+    cfg.numAttrs = (ev_mid || p.skip_prep) ? 0 : 1;
     switch (tile_batch) {
         case 2: return cudaLaunchKernelEx(&cfg, check_kernel<2>, p);
         case 4: return cudaLaunchKernelEx(&cfg, check_kernel<4>, p);
         case 8: return cudaLaunchKernelEx(&cfg, check_kernel<8>, p);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_prep(const BatchParams& p, cudaStream_t s) {
+    if (p.n_cloud <= 0) return cudaSuccess;
+    prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, 0, s>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status, cudaStream_t s) {

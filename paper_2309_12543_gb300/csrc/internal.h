@@ -57,6 +57,7 @@ struct InstDesc {
     int cloud;                // index into BatchParams::cloud
     int tw;                   // waypoints per check block (tw * L <= kCheckWarps)
     int block_base;           // first check block of this trajectory
+    const uint8_t* mask;      // optional: only waypoints with a non-zero byte are checked
 };
 
 struct BatchParams {
@@ -66,6 +67,7 @@ struct BatchParams {
     int stride;               // floats per point: 3 or 4
     int cull;                 // 0: evaluate every pair
     int stage_tiles;          // tile spheres the dynamic shared memory holds (0: no staging)
+    int skip_prep;            // the clouds are already sorted in the scratch: launch the check only
     float4* sorted;           // finite points, spatially sorted: x, y, z, original index bits
     float4* tiles;            // sphere of each 32-point tile
     float4* supers;           // sphere of each 32-tile super-tile
@@ -87,9 +89,17 @@ cudaError_t configure_kernels();           // once per device, that device curre
 // is recorded between them.
 cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, cudaEvent_t ev_mid);
 cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status, cudaStream_t s);
+// Sorts one cloud into the scratch of p (prep kernel only).
+cudaError_t launch_prep(const BatchParams& p, cudaStream_t s);
 cudaError_t launch_grid_build(const float* tris9, const int* comp_off, int n_comp, int n_tris, float ox,
                               float oy, float oz, float h, int n, float* out, cudaStream_t s);
 
+}  // namespace sdf
+
+struct sdf_ctx;
+namespace sdf {
+// api.cu: sort one cloud into ctx's scratch and fill p's cloud/scratch fields.
+int sort_cloud(sdf_ctx* ctx, const float* points_dev, int N, BatchParams* p);
 }  // namespace sdf
 
 struct sdf_grids {
@@ -121,6 +131,7 @@ struct sdf_ctx {
     unsigned long long* d_stats = nullptr;  // kStatCount counters on the device
     int tw = 0;                            // waypoints per check block (0: tuned or as many as fit)
     int tile_batch = 0;                    // list entries per warp step (0: tuned or 4)
+    int reuse_sort = 0;                    // internal: the next check reuses the scratch's sorted cloud
     std::map<uint64_t, std::pair<int, int>> tuned;   // launch shape key -> (tw, tile batch)
     // scratch owned by the context (grown on demand, or up front by sdf_ctx_reserve)
     float4* sorted = nullptr;

@@ -99,6 +99,7 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         I.cloud = 0;
         I.tw = sdf::kCheckWarps / I.L > 0 ? sdf::kCheckWarps / I.L : 1;
         I.block_base = 0;
+        I.mask = nullptr;
         const int n_tiles = (N + 31) / 32;
         p.n_inst = 1;
         p.n_cloud = 1;
@@ -106,6 +107,7 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         p.stride = 3;
         p.cull = 1;
         p.stage_tiles = n_tiles < sdf::kMaxStagedTiles ? n_tiles : sdf::kMaxStagedTiles;
+        p.skip_prep = 0;
         p.sorted = reinterpret_cast<float4*>(base + kSortedOff);
         p.tiles = reinterpret_cast<float4*>(base + kTilesOff);
         p.supers = reinterpret_cast<float4*>(base + kSupersOff);

@@ -776,6 +776,148 @@ __global__ void error_reduce_kernel(const float* f, const float* y, int n, float
     }
 }
 
+
+// ------------------------------------------------------------------ surrogate check
+
+struct SurCheckArgs {
+    const float* poses;               // [W][L][16]: link-from-world 3x4, sphere centre (world), radius
+    int W, L;
+    const float4* sorted;             // the sorted cloud (x, y, z, original index bits)
+    const float4* tiles;              // sphere per 32 sorted points
+    const float4* supers;             // sphere per 32 tiles
+    const int* n_valid;
+    float lo[kMaxLinks][3], hi[kMaxLinks][3], m[kMaxLinks][3], inv_a[kMaxLinks];
+    float4* xq;                       // queries per link segment
+    uint2* tag;
+    int* seg_count;
+    int seg_cap;
+    const unsigned long long* keys;   // cull: the seeded per-waypoint minimum
+    float slack;                      // cull: error bound of the surrogate + rounding slack
+};
+
+// Warp-cooperative: lanes with `take` append the query of sorted point p for pair
+// (w, l) to link l's segment.
+__device__ __forceinline__ void emit_query(const SurCheckArgs& A, int w, int l, const float4* M, float4 p,
+                                           bool take, int lane) {
+    const unsigned b = __ballot_sync(0xffffffffu, take);
+    if (!b) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&A.seg_count[l], __popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (!take) return;
+    const int slot = base + __popc(b & ((1u << lane) - 1u));
+    if (slot >= A.seg_cap) return;   // overflow: the finish kernel sends every waypoint to the grid
+    const float lx = fmaf(M[0].x, p.x, fmaf(M[0].y, p.y, fmaf(M[0].z, p.z, M[0].w)));
+    const float ly = fmaf(M[1].x, p.x, fmaf(M[1].y, p.y, fmaf(M[1].z, p.z, M[1].w)));
+    const float lz = fmaf(M[2].x, p.x, fmaf(M[2].y, p.y, fmaf(M[2].z, p.z, M[2].w)));
+    const float cx = fminf(fmaxf(lx, A.lo[l][0]), A.hi[l][0]);
+    const float cy = fminf(fmaxf(ly, A.lo[l][1]), A.hi[l][1]);
+    const float cz = fminf(fmaxf(lz, A.lo[l][2]), A.hi[l][2]);
+    const float ex = lx - cx, ey = ly - cy, ez = lz - cz;
+    const float extra = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+    const float ia = A.inv_a[l];
+    const size_t q = (size_t)l * A.seg_cap + slot;
+    A.xq[q] = make_float4((cx - A.m[l][0]) * ia, (cy - A.m[l][1]) * ia, (cz - A.m[l][2]) * ia, extra);
+    A.tag[q] = make_uint2((unsigned)w, ((unsigned)__float_as_int(p.w) << 4) | (unsigned)l);
+}
+
+__device__ __forceinline__ float sphere_gap(float4 s, float cx, float cy, float cz) {
+    const float dx = s.x - cx, dy = s.y - cy, dz = s.z - cz;
+    return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - s.w;
+}
+
+// One warp per (waypoint, link) pair.  Seed mode: the 32 points of the tile nearest
+// to the link's sphere (nearest super-tile first).  Cull mode: every point whose
+// sphere bound ||p - c|| - R does not exceed the seeded minimum + slack.
+template <bool kSeed>
+__global__ void __launch_bounds__(256) sur_pairs_kernel(const __grid_constant__ SurCheckArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int pair = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (pair >= A.W * A.L) return;
+    const int w = pair / A.L, l = pair % A.L;
+    const float4* P = reinterpret_cast<const float4*>(A.poses + (size_t)pair * 16);
+    const float4 M[3] = {P[0], P[1], P[2]};
+    const float4 sph = P[3];
+    const int nv = *A.n_valid;
+    const int n_tiles = (nv + 31) >> 5, n_sup = (n_tiles + 31) >> 5;
+    if (nv == 0) return;
+    if (kSeed) {
+        float best = INFINITY;
+        int bi = 0x7fffffff;
+        for (int s = lane; s < n_sup; s += 32) {
+            const float g = sphere_gap(A.supers[s], sph.x, sph.y, sph.z);
+            if (g < best) { best = g; bi = s; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        const int t = bi * 32 + lane;
+        float tb = INFINITY;
+        int ti = 0x7fffffff;
+        if (t < n_tiles) { tb = sphere_gap(A.tiles[t], sph.x, sph.y, sph.z); ti = t; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, tb, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, ti, o);
+            if (ob < tb || (ob == tb && oi < ti)) { tb = ob; ti = oi; }
+        }
+        const int k = ti * 32 + lane;
+        const bool take = k < nv;
+        emit_query(A, w, l, M, take ? A.sorted[k] : make_float4(0.f, 0.f, 0.f, 0.f), take, lane);
+        return;
+    }
+    const unsigned long long key = A.keys[w];
+    const float T = key == ~0ull ? INFINITY : from_ordered((unsigned)(key >> 32));
+    const float thr = T + A.slack + sph.w;       // keep s when ||c_s - c|| - r_s <= thr
+    for (int s0 = 0; s0 < n_sup; s0 += 32) {
+        const int s = s0 + lane;
+        unsigned bs = __ballot_sync(0xffffffffu, s < n_sup && sphere_gap(A.supers[s], sph.x, sph.y, sph.z) <= thr);
+        while (bs) {
+            const int sv = s0 + __ffs(bs) - 1;
+            bs &= bs - 1;
+            const int t = sv * 32 + lane;
+            unsigned bt = __ballot_sync(0xffffffffu,
+                                        t < n_tiles && sphere_gap(A.tiles[t], sph.x, sph.y, sph.z) <= thr);
+            while (bt) {
+                const int tv = sv * 32 + __ffs(bt) - 1;
+                bt &= bt - 1;
+                const int k = tv * 32 + lane;
+                const float4 p = k < nv ? A.sorted[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool take = k < nv && sphere_gap(make_float4(p.x, p.y, p.z, 0.f), sph.x, sph.y, sph.z) <= thr;
+                emit_query(A, w, l, M, p, take, lane);
+            }
+        }
+    }
+}
+
+// Per waypoint: decode the surrogate minimum, write it as the result, and select the
+// waypoint for the grid re-check when it is below margin + error bound (or when a
+// query segment overflowed, every waypoint).
+__global__ void sur_finish_kernel(const unsigned long long* keys, const int* seg_count, int L, int seg_cap, int W,
+                                  float limit, float* dist, int32_t* arg_link, int32_t* arg_point, float* sur_dist,
+                                  uint8_t* mask) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    bool overflow = false;
+    for (int l = 0; l < L; ++l) overflow |= seg_count[l] > seg_cap;
+    const unsigned long long key = keys[w];
+    float d;
+    if (key == ~0ull) {
+        d = INFINITY;
+        arg_link[w] = -1;
+        arg_point[w] = -1;
+    } else {
+        d = from_ordered((unsigned)(key >> 32));
+        arg_link[w] = (int)(key & 15u);
+        arg_point[w] = (int)((key & 0xffffffffu) >> 4);
+    }
+    dist[w] = d;
+    if (sur_dist) sur_dist[w] = d;
+    mask[w] = (overflow || d < limit) ? 1 : 0;
+}
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -802,6 +944,15 @@ struct sdf_surrogate {
     float* loss = nullptr;     // [L]
     float box_m[SDF_MAX_LINKS][3];
     float box_a[SDF_MAX_LINKS];
+    // check workspace (grown on demand)
+    float* poses = nullptr;
+    unsigned long long* keys = nullptr;
+    uint8_t* mask = nullptr;
+    size_t w_cap = 0;
+    float4* xq = nullptr;
+    uint2* tag = nullptr;
+    int* seg_count = nullptr;
+    size_t seg_cap = 0;
 };
 
 namespace {
@@ -922,6 +1073,12 @@ void sdf_surrogate_destroy(sdf_surrogate* S) {
     cudaFree(S->adam_v);
     cudaFree(S->step);
     cudaFree(S->loss);
+    cudaFree(S->poses);
+    cudaFree(S->keys);
+    cudaFree(S->mask);
+    cudaFree(S->xq);
+    cudaFree(S->tag);
+    cudaFree(S->seg_count);
     delete S;
 }
 
@@ -1068,6 +1225,148 @@ int sdf_surrogate_eval(sdf_ctx* ctx, const sdf_surrogate* S, int32_t link, const
     sdf::mlp_eval_kernel<<<grid, 128, sdf::kEvalSmem, ctx->stream>>>(A);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SDF_OK : scuda(ctx, e, "mlp_eval_kernel");
+}
+
+
+int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surrogate* Sc, const float* q_dev,
+                               int32_t W, const float* points_dev, int32_t N, float margin, float eps,
+                               float* dist_dev, int32_t* argmin_link_dev, int32_t* argmin_point_dev,
+                               uint8_t* rechecked_dev, float* surrogate_dist_dev) {
+    sdf_surrogate* S = const_cast<sdf_surrogate*>(Sc);
+    if (!ctx || !R || !S) return sfail(ctx, SDF_ERR_INVALID_ARG, "check_trajectory_surrogate: null");
+    if (R->grids != S->grids || R->device != ctx->device)
+        return sfail(ctx, SDF_ERR_INVALID_ARG, "check_trajectory_surrogate: robot and surrogate use different grids");
+    if (W < 0 || N < 0 || N > SDF_MAX_POINTS || !(margin >= 0.f) || !(eps >= 0.f))
+        return sfail(ctx, SDF_ERR_INVALID_ARG, "check_trajectory_surrogate: invalid sizes or bounds");
+    if (W == 0) return SDF_OK;
+    if (!dist_dev || !argmin_link_dev || !argmin_point_dev || (R->dof > 0 && !q_dev) || (N > 0 && !points_dev))
+        return sfail(ctx, SDF_ERR_INVALID_ARG, "check_trajectory_surrogate: null buffer");
+    Dev guard(ctx->device);
+    if (!surrogate_configured(ctx->device)) return sfail(ctx, SDF_ERR_CUDA, "surrogate kernels: attributes");
+    const int L = S->L;
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    // workspace: poses, keys and mask per waypoint; query segments per link
+    if ((size_t)W > S->w_cap) {
+        const size_t cap = std::max<size_t>((size_t)W, 2 * S->w_cap);
+        cudaStreamSynchronize(st);
+        cudaFree(S->poses);
+        cudaFree(S->keys);
+        cudaFree(S->mask);
+        S->poses = nullptr;
+        S->keys = nullptr;
+        S->mask = nullptr;
+        S->w_cap = 0;
+        e = cudaMalloc(&S->poses, sizeof(float) * 16 * L * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&S->keys, sizeof(unsigned long long) * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&S->mask, cap);
+        if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate: workspace");
+        S->w_cap = cap;
+    }
+    const size_t want = std::min<size_t>((size_t)W * (size_t)std::max(N, 1),
+                                         std::max<size_t>((size_t)W * 256, (size_t)1 << 20));
+    if (want > S->seg_cap) {
+        cudaStreamSynchronize(st);
+        cudaFree(S->xq);
+        cudaFree(S->tag);
+        S->xq = nullptr;
+        S->tag = nullptr;
+        S->seg_cap = 0;
+        if (!S->seg_count) e = cudaMalloc(&S->seg_count, sizeof(int) * SDF_MAX_LINKS);
+        if (e == cudaSuccess) e = cudaMalloc(&S->xq, sizeof(float4) * L * want);
+        if (e == cudaSuccess) e = cudaMalloc(&S->tag, sizeof(uint2) * L * want);
+        if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate: query buffers");
+        S->seg_cap = want;
+    }
+    e = cudaMemsetAsync(S->keys, 0xff, sizeof(unsigned long long) * W, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->seg_count, 0, sizeof(int) * SDF_MAX_LINKS, st);
+    if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate");
+    sdf::BatchParams* bp = new (std::nothrow) sdf::BatchParams();
+    if (!bp) return sfail(ctx, SDF_ERR_OOM, "host allocation");
+    int rc = sdf::sort_cloud(ctx, points_dev, N, bp);
+    sdf::SurCheckArgs A{};
+    if (rc == SDF_OK) {
+        e = sdf::launch_fk(R->table, q_dev, W, S->poses, ctx->status, st);
+        A.poses = S->poses;
+        A.W = W;
+        A.L = L;
+        A.sorted = bp->sorted;
+        A.tiles = bp->tiles;
+        A.supers = bp->supers;
+        A.n_valid = bp->n_valid;
+        const sdf_grids* G = S->grids;
+        for (int l = 0; l < L; ++l) {
+            const double a = 0.5 * (G->n - 1) * (double)G->meta[l].h;
+            for (int k = 0; k < 3; ++k) {
+                A.lo[l][k] = G->meta[l].origin[k];
+                A.hi[l][k] = (float)(G->meta[l].origin[k] + 2.0 * a);
+                A.m[l][k] = S->box_m[l][k];
+            }
+            A.inv_a[l] = (float)(1.0 / a);
+        }
+        A.xq = S->xq;
+        A.tag = S->tag;
+        A.seg_count = S->seg_count;
+        A.seg_cap = (int)S->seg_cap;
+        A.keys = S->keys;
+        A.slack = eps + sdf::kCullSlack;
+    }
+    delete bp;
+    sdf::EvalArgs E{};
+    E.master = S->master;
+    E.xq = S->xq;
+    E.tag = S->tag;
+    E.seg_count = S->seg_count;
+    E.seg_cap = (int)S->seg_cap;
+    E.L = L;
+    E.keys = S->keys;
+    for (int l = 0; l < L; ++l) E.scale[l] = S->box_a[l];
+    E.status = ctx->status;
+    const unsigned pair_blocks = (unsigned)(((size_t)W * L * 32 + 255) / 256);
+    const int eval_grid = ctx->num_sms;
+    if (rc == SDF_OK && e == cudaSuccess) {
+        sdf::sur_pairs_kernel<true><<<pair_blocks, 256, 0, st>>>(A);
+        e = cudaGetLastError();
+    }
+    if (rc == SDF_OK && e == cudaSuccess) {
+        sdf::mlp_eval_kernel<<<eval_grid, 128, sdf::kEvalSmem, st>>>(E);
+        e = cudaGetLastError();
+    }
+    if (rc == SDF_OK && e == cudaSuccess) e = cudaMemsetAsync(S->seg_count, 0, sizeof(int) * SDF_MAX_LINKS, st);
+    if (rc == SDF_OK && e == cudaSuccess) {
+        sdf::sur_pairs_kernel<false><<<pair_blocks, 256, 0, st>>>(A);
+        e = cudaGetLastError();
+    }
+    if (rc == SDF_OK && e == cudaSuccess) {
+        sdf::mlp_eval_kernel<<<eval_grid, 128, sdf::kEvalSmem, st>>>(E);
+        e = cudaGetLastError();
+    }
+    if (rc == SDF_OK && e == cudaSuccess) {
+        sdf::sur_finish_kernel<<<(unsigned)((W + 255) / 256), 256, 0, st>>>(
+            S->keys, S->seg_count, L, (int)S->seg_cap, W, margin + eps, dist_dev, argmin_link_dev,
+            argmin_point_dev, surrogate_dist_dev, S->mask);
+        e = cudaGetLastError();
+    }
+    if (rc == SDF_OK && e == cudaSuccess && rechecked_dev)
+        e = cudaMemcpyAsync(rechecked_dev, S->mask, (size_t)W, cudaMemcpyDeviceToDevice, st);
+    if (rc == SDF_OK && e != cudaSuccess) rc = scuda(ctx, e, "check_trajectory_surrogate");
+    if (rc == SDF_OK) {
+        // the grid path re-checks the selected waypoints on the cloud sorted above
+        sdf_check_request r{};
+        r.robot = R;
+        r.q_dev = q_dev;
+        r.W = W;
+        r.points_dev = points_dev;
+        r.N = N;
+        r.dist_dev = dist_dev;
+        r.argmin_link_dev = argmin_link_dev;
+        r.argmin_point_dev = argmin_point_dev;
+        r.mask_dev = S->mask;
+        ctx->reuse_sort = 1;
+        rc = check_batch(ctx, &r, 1);
+        ctx->reuse_sort = 0;
+    }
+    return rc;
 }
 
 int sdf_surrogate_error(sdf_ctx* ctx, const sdf_surrogate* S, int32_t link, int64_t n, int32_t near_per_10,

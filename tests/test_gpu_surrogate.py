@@ -169,3 +169,112 @@ def test_training_lowers_the_error(sdf, env):
     print("mean error before", before, "after", after)
     for l in range(L):
         assert after[l][1] < 0.2 * before[l], (l, before[l], after[l])
+
+
+# ----------------------------------------------------------------- surrogate check
+
+def _sur_check(sdf, ctx, robot, sur, q, pts, margin, eps):
+    W, N = len(q), len(pts)
+    d = torch.full((W,), 7.0, dtype=torch.float32, device="cuda")
+    l = torch.full((W,), -7, dtype=torch.int32, device="cuda")
+    p = torch.full((W,), -7, dtype=torch.int32, device="cuda")
+    rech = torch.full((W,), 9, dtype=torch.uint8, device="cuda")
+    sd = torch.full((W,), 7.0, dtype=torch.float32, device="cuda")
+    pd = _dev(pts) if N else torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    sdf.check_trajectory_surrogate(ctx, robot, sur, _dev(q), W, pd, N, margin, eps, d, l, p, rech, sd)
+    assert ctx.synchronize() == 0
+    return [t.cpu().numpy() for t in (d, l, p, rech, sd)]
+
+
+def _grid_check(sdf, ctx, robot, q, pts):
+    W = len(q)
+    out = [torch.empty(W, dtype=dt, device="cuda") for dt in (torch.float32, torch.int32, torch.int32)]
+    sdf.check_trajectory(ctx, robot, _dev(q), W, _dev(pts), len(pts), *out)
+    assert ctx.synchronize() == 0
+    return [t.cpu().numpy() for t in out]
+
+
+def _trained(sdf, ctx, grids, L, steps=3000, seed=31):
+    sur = sdf.Surrogate(ctx, grids, sg.mlp_init(seed, L))
+    n = 65536
+    X = torch.empty((L, n, 3), dtype=torch.float32, device="cuda")
+    Y = torch.empty((L, n), dtype=torch.float32, device="cuda")
+    for l in range(L):
+        sdf.sdf_surrogate_sample(ctx, grids, l, n, 7, 0.10, 2000 + l, X[l], Y[l])
+    sur.train(X, Y, n, 0, steps, 1e-3)
+    assert ctx.synchronize() == 0
+    return sur
+
+
+def test_surrogate_check_without_culling_is_the_brute_force_minimum(sdf, env):
+    sc, ctx, grids, vals, metas = env
+    L = len(metas)
+    params = sg.mlp_init(21, L)
+    sur = sdf.Surrogate(ctx, grids, params)
+    robot = sdf.Robot(ctx, sc.dh, grids, sc.base)
+    q, pts = sc.q[:20].astype(np.float32), sc.points[:400].astype(np.float32)
+    d, l, p, rech, sd = _sur_check(sdf, ctx, robot, sur, q, pts, margin=0.0, eps=100.0)   # eps: no culling
+    ref_d, ref_l, ref_p = mlp.check(sc.dh, sc.base, params.astype(np.float64), metas, q, pts, quantize=True)
+    assert np.max(np.abs(sd - ref_d)) <= 2e-3, np.max(np.abs(sd - ref_d))
+    assert np.median(np.abs(sd - ref_d)) <= 2e-4
+    # everything is below margin + eps: the grid path decided every waypoint, exactly
+    assert np.all(rech == 1)
+    g = _grid_check(sdf, ctx, robot, q, pts)
+    assert np.array_equal(d.view(np.uint32), g[0].view(np.uint32))
+    assert np.array_equal(l, g[1]) and np.array_equal(p, g[2])
+
+
+def test_surrogate_check_with_trained_network_and_fallback(sdf, env):
+    sc, ctx, grids, vals, metas = env
+    L = len(metas)
+    sur = _trained(sdf, ctx, grids, L)
+    robot = sdf.Robot(ctx, sc.dh, grids, sc.base)
+    errs = [max(sur.error(k, 50000, 0, seed=77)[0], sur.error(k, 50000, 10, 0.1, seed=78)[0]) for k in range(L)]
+    eps = 2.0 * max(errs) + 0.01
+    margin = 0.05
+    # the cloud beyond 0.8 m from the base: some waypoints come within the margin, some
+    # stay far from every point (grid distances 2 cm to 46 cm)
+    q = sc.q.astype(np.float32)
+    pts = sc.points[np.linalg.norm(sc.points, axis=1) >= 0.8].astype(np.float32)
+    d, l, p, rech, sd = _sur_check(sdf, ctx, robot, sur, q, pts, margin, eps)
+    params = sur.params().astype(np.float64)
+    ref_d, _, _ = mlp.check(sc.dh, sc.base, params, metas, q[:25], pts, quantize=True)
+    assert np.max(np.abs(sd[:25] - ref_d)) <= 2e-3
+    assert np.array_equal(rech, (sd < np.float32(margin + eps)).astype(np.uint8))
+    g = _grid_check(sdf, ctx, robot, q, pts)
+    sel = rech == 1
+    assert np.array_equal(d[sel].view(np.uint32), g[0][sel].view(np.uint32))
+    assert np.array_equal(d[~sel].view(np.uint32), sd[~sel].view(np.uint32))
+    # the safety property: every waypoint truly within the margin went to the grid
+    assert np.all(rech[g[0] < margin] == 1)
+    # and where the surrogate decided, it is within its bound of the grid
+    assert 0 < sel.sum() < len(q)
+    assert np.all(np.abs(d[~sel] - g[0][~sel]) <= eps)
+    print("eps", eps, "rechecked", int(sel.sum()), "of", len(q))
+
+
+def test_surrogate_check_empty_cloud(sdf, env):
+    sc, ctx, grids, vals, metas = env
+    sur = sdf.Surrogate(ctx, grids, sg.mlp_init(23, len(metas)))
+    robot = sdf.Robot(ctx, sc.dh, grids, sc.base)
+    d, l, p, rech, sd = _sur_check(sdf, ctx, robot, sur, sc.q[:7].astype(np.float32), np.zeros((0, 3)), 0.05, 0.01)
+    assert np.all(np.isinf(d)) and np.all(l == -1) and np.all(p == -1) and np.all(rech == 0)
+
+
+def test_masked_grid_check_writes_only_selected_waypoints(sdf, env):
+    sc, ctx, grids, vals, metas = env
+    robot = sdf.Robot(ctx, sc.dh, grids, sc.base)
+    q, pts = sc.q.astype(np.float32), sc.points.astype(np.float32)
+    W = len(q)
+    mask = (np.arange(W) % 3 == 1).astype(np.uint8)
+    out = [torch.full((W,), 7.0, dtype=torch.float32, device="cuda"),
+           torch.full((W,), -7, dtype=torch.int32, device="cuda"), torch.full((W,), -7, dtype=torch.int32, device="cuda")]
+    qd, pd, md = _dev(q), _dev(pts), _dev(mask, torch.uint8)
+    sdf.check_batch(ctx, [(robot, qd, W, pd, len(pts), *out, md)])
+    assert ctx.synchronize() == 0
+    d, l, p = [t.cpu().numpy() for t in out]
+    g = _grid_check(sdf, ctx, robot, q, pts)
+    sel = mask == 1
+    assert np.array_equal(d[sel].view(np.uint32), g[0][sel].view(np.uint32))
+    assert np.array_equal(l[sel], g[1][sel]) and np.array_equal(p[sel], g[2][sel])
+    assert np.all(d[~sel] == 7.0) and np.all(l[~sel] == -7) and np.all(p[~sel] == -7)
