@@ -46,7 +46,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="paper", choices=["paper", "tiny", "batched", "serve"])
+    ap.add_argument("--config", default="paper", choices=["paper", "tiny", "batched", "serve", "surrogate"])
+    ap.add_argument("--sur-samples", type=int, default=2_000_000, help="surrogate: training samples per link")
+    ap.add_argument("--sur-steps", type=int, default=30000, help="surrogate: Adam steps (128 samples each)")
+    ap.add_argument("--margin", type=float, default=0.05, help="surrogate: safety margin (m) of the fallback")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of 125 Hz cycles")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: mean requests per cycle (Poisson)")
     ap.add_argument("--order", default="voxel", choices=["voxel", "random"])
@@ -566,12 +569,160 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------- surrogate
+
+# one network evaluation: 3x128 + 2 x 128x128 + 128x1 multiply-adds
+MLP_FLOPS_PER_QUERY = 2 * (3 * 128 + 2 * 128 * 128 + 128)
+SUR_METRIC = "µs per 500-waypoint×20k-point check, learned surrogate with grid fallback (p50/p99)"
+
+
+def run_surrogate(args):
+    """Train the per-link surrogates of the paper scene on the GPU, bound their error
+    against the grid, and time the surrogate form of the check (with its grid
+    fallback) beside the grid form on the same 500 x 20k workload."""
+    import torch
+    import paper_2309_12543_gb300 as sdf
+    import scenegen
+    from paper_2309_12543_gb300 import build as pkg_build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg_build.build()
+    scene = scenegen.make_scene("paper", order=args.order)
+    W, N, L = scene.q.shape[0], scene.points.shape[0], scene.n_links
+    stream = torch.cuda.current_stream(dev)
+    ctx = sdf.Context(local, stream)
+    grids = sdf.sdf_build_grids(ctx, scene.meshes, scene.resolution, scene.margin)
+    robot = sdf.Robot(ctx, scene.dh, grids, scene.base)
+
+    # training samples: 70% within 10 cm of the surface, 30% uniform in the box
+    n = args.sur_samples
+    X = torch.empty((L, n, 3), dtype=torch.float32, device=dev)
+    Y = torch.empty((L, n), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for l in range(L):
+        sdf.sdf_surrogate_sample(ctx, grids, l, n, 7, 0.10, 5000 + l, X[l], Y[l])
+    torch.cuda.synchronize(dev)
+    sample_s = time.perf_counter() - t0
+    sur = sdf.Surrogate(ctx, grids, scenegen.mlp_init(9, L))
+    # Adam: 2/3 of the steps at 1e-3, the rest at 2e-4 (batches continue in sequence)
+    s1 = (2 * args.sur_steps) // 3
+    loss = torch.zeros(L, dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    sur.train(X, Y, n, 0, s1, 1e-3, loss)
+    sur.train(X, Y, n, s1, args.sur_steps - s1, 2e-4, loss)
+    rc = ctx.synchronize()
+    train_s = time.perf_counter() - t0
+    if rc != 0:
+        raise RuntimeError(f"training failed: {ctx.last_error()}")
+    final_loss = (loss.cpu().numpy() / max(args.sur_steps - s1, 1)).tolist()
+    del X, Y
+    # error bound against the grid: fresh uniform and near-surface samples
+    errs = []
+    for l in range(L):
+        u = sur.error(l, 1 << 20, 0, 0.10, seed=7000 + l)
+        nr = sur.error(l, 1 << 20, 10, 0.10, seed=8000 + l)
+        errs.append({"link": l, "max_uniform": u[0], "mean_uniform": u[1], "max_near": nr[0], "mean_near": nr[1]})
+    eps = max(max(e["max_uniform"], e["max_near"]) for e in errs)
+    # the same memory as a grid: 32^3 FP32 values (131 KB) vs 33,665 FP32 parameters
+    coarse = sdf.sdf_build_grids(ctx, scene.meshes, 32, scene.margin)
+    m = 1 << 20
+    xf = torch.empty((m, 3), dtype=torch.float32, device=dev)
+    yf = torch.empty(m, dtype=torch.float32, device=dev)
+    xc = torch.empty_like(xf)
+    yc = torch.empty_like(yf)
+    coarse_err = []
+    fine_meta = grids.download()[1]
+    for l in range(L):
+        sdf.sdf_surrogate_sample(ctx, grids, l, m, 0, 0.10, 7000 + l, xf, yf)
+        sdf.sdf_surrogate_sample(ctx, coarse, l, m, 0, 0.10, 7000 + l, xc, yc)
+        a = 0.5 * (scene.resolution - 1) * fine_meta[l]["h"]
+        diff = (yf - yc).abs() * a
+        coarse_err.append({"link": l, "max": float(diff.max()), "mean": float(diff.mean())})
+
+    q = torch.tensor(scene.q, dtype=torch.float32, device=dev)
+    pts = torch.tensor(scene.points, dtype=torch.float32, device=dev)
+    out = [torch.empty(W, dtype=dt, device=dev) for dt in (torch.float32, torch.int32, torch.int32)]
+    g_out = [torch.empty(W, dtype=dt, device=dev) for dt in (torch.float32, torch.int32, torch.int32)]
+    rech = torch.empty(W, dtype=torch.uint8, device=dev)
+    sd = torch.empty(W, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def sur_step():
+        sdf.check_trajectory_surrogate(ctx, robot, sur, q, W, pts, N, args.margin, eps, *out, rech, sd)
+
+    def grid_step():
+        sdf.check_trajectory(ctx, robot, q, W, pts, N, *g_out)
+
+    def timed(fn, steps):
+        for _ in range(max(args.warmup, 3)):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return [a.elapsed_time(b) * 1e3 for a, b in ev]
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    sur_us = timed(sur_step, args.steps)
+    grid_us = timed(grid_step, args.steps)
+    clk = clocks.stop()
+    if ctx.synchronize() != 0:
+        raise RuntimeError(f"checks failed: {ctx.last_error()}")
+    ctx.set_option(sdf.SDF_OPT_STATS, 1)
+    ctx.stats(reset=True)
+    sur_step()
+    st = ctx.stats(reset=True)
+    ctx.set_option(sdf.SDF_OPT_STATS, 0)
+    queries = st["sur_seed_queries"] + st["sur_queries"]
+    d, r, s_d, gd = out[0].cpu().numpy(), rech.cpu().numpy().astype(bool), sd.cpu().numpy(), g_out[0].cpu().numpy()
+    exact = bool(np.array_equal(d[r].view(np.uint32), gd[r].view(np.uint32)))
+    within = float(np.max(np.abs(d[~r] - gd[~r]), initial=0.0))
+    if rank != 0:
+        return
+    res = {
+        "metric": SUR_METRIC, "value": percentile(sur_us, 50), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(sur_us) / 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (network products), f32 (rest)", "data": "synthetic",
+        "config": {"workload": "paper: 6-DoF arm, 7 links, 96^3 FP32 grids, W=500, N=20000; per-link MLP "
+                               "3-128-128-128-1 SiLU trained on the GPU", "samples_per_link": n,
+                   "train_steps": args.sur_steps, "batch": 128, "margin_m": args.margin,
+                   "l2": "flushed before every timed step (256 MiB write)"},
+        "p50_us": percentile(sur_us, 50), "p99_us": percentile(sur_us, 99),
+        "grid_form": {"p50_us": percentile(grid_us, 50), "p99_us": percentile(grid_us, 99)},
+        "network_queries": {"seed": st["sur_seed_queries"], "after_cull": st["sur_queries"],
+                            "flops_per_query": MLP_FLOPS_PER_QUERY,
+                            "tflops_over_the_check": queries * MLP_FLOPS_PER_QUERY / (percentile(sur_us, 50) * 1e-6) / 1e12},
+        "rechecked_waypoints": int(r.sum()), "fallback_exact": exact, "max_diff_where_surrogate_decided_m": within,
+        "eps_m": eps, "errors": errs, "equal_memory_grid_32": coarse_err,
+        "memory_bytes_per_link": {"surrogate_fp32_params": sdf.SDF_MLP_PARAMS * 4,
+                                  "grid_96": scene.resolution ** 3 * 4, "grid_32": 32 ** 3 * 4},
+        "sample_s": sample_s, "train_s": train_s, "final_loss_per_link": final_loss,
+        "clocks": clk,
+    }
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "serve":
         run_serve(args)
+    elif args.config == "surrogate":
+        run_surrogate(args)
     elif args.config == "batched":
         run_batched(args)
     else:

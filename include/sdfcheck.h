@@ -151,6 +151,8 @@ int sdf_ctx_last_kernel_ms(sdf_ctx* ctx, int32_t kernel, float* ms);
 #define SDF_STAT_NS_SORT_SCATTER 23 /* scatter                                      */
 #define SDF_STAT_NS_SORT_TILES 24 /* tile spheres                                   */
 #define SDF_STAT_NS_SORT_SUPERS 25 /* super-tile spheres                            */
+#define SDF_STAT_SUR_SEED_QUERIES 26 /* surrogate check: seed queries evaluated      */
+#define SDF_STAT_SUR_QUERIES 27   /* surrogate check: queries after the cull        */
 #define SDF_STAT_COUNT 32
 int sdf_ctx_stats(sdf_ctx* ctx, int64_t* out, int32_t n, int32_t reset);
 
@@ -421,8 +423,9 @@ int sdf_surrogate_error(sdf_ctx* ctx, const sdf_surrogate* surrogate, int32_t li
  * the surrogate's (exactly what check_trajectory returns for them).  Outputs as
  * check_trajectory; rechecked_dev (optional, W bytes) is 1 where the grid path
  * decided, surrogate_dist_dev (optional, W FP32) the surrogate minimum before the
- * re-check.  Uses workspace owned by the surrogate (grown on demand, which
- * synchronises): calls with the same surrogate must not overlap.  Asynchronous.
+ * re-check.  Uses workspace owned by the context (grown on demand, which
+ * synchronises); contexts on different streams may share one surrogate.
+ * Asynchronous.
  * Errors: INVALID_ARG (robot and surrogate built on different grids, bad sizes),
  * OOM, CUDA. */
 int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* robot, const sdf_surrogate* surrogate,

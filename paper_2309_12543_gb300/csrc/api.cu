@@ -117,6 +117,12 @@ void sdf_ctx_destroy(sdf_ctx* ctx) {
     cudaFree(ctx->st_dist);
     cudaFree(ctx->st_link);
     cudaFree(ctx->st_point);
+    cudaFree(ctx->sur_poses);
+    cudaFree(ctx->sur_keys);
+    cudaFree(ctx->sur_mask);
+    cudaFree(ctx->sur_xq);
+    cudaFree(ctx->sur_tag);
+    cudaFree(ctx->sur_count);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);
@@ -401,6 +407,118 @@ void sdf_grids_destroy(sdf_grids* G) {
 
 // -------------------------------------------------------------------- robot
 
+}  // extern "C"
+
+namespace {
+
+// A capsule (segment a-b, radius r) containing the link's surface, found from its
+// grid: every surface point lies within p = h sqrt(3)/2 of a node whose value has
+// magnitude <= p, so the capsule around those nodes, grown by p, contains the
+// surface and hence the (bounded) solid.  The signed distance to a convex superset
+// bounds the link SDF from below at every node, and so (convexity, 1-Lipschitz)
+// the interpolated value everywhere: the same exact cull as the bounding sphere,
+// tighter for elongated links.  The axis is the principal axis of those nodes; the
+// segment ends are pulled in as far as the radius allows.  When the sphere is the
+// smaller volume, the capsule degenerates to it (a = b = centre).
+void link_capsule(const float* v, int n, const sdf_grid_meta& m, float4* ca, float4* cb) {
+    const double h = m.h, pad = h * std::sqrt(3.0) * 0.5 * 1.0001 + 1e-7;
+    std::vector<double> P;
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                const float x = v[((size_t)k * n + j) * n + i];
+                if (std::fabs((double)x) <= pad) {
+                    P.push_back(m.origin[0] + i * h);
+                    P.push_back(m.origin[1] + j * h);
+                    P.push_back(m.origin[2] + k * h);
+                }
+            }
+    const double R = m.radius;
+    *ca = make_float4(m.center[0], m.center[1], m.center[2], m.radius);
+    *cb = make_float4(m.center[0], m.center[1], m.center[2], 0.f);
+    const size_t np = P.size() / 3;
+    if (np < 2) return;
+    double mu[3] = {0, 0, 0}, C[9] = {0};
+    for (size_t q = 0; q < np; ++q)
+        for (int a = 0; a < 3; ++a) mu[a] += P[3 * q + a] / (double)np;
+    for (size_t q = 0; q < np; ++q)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) C[3 * a + b] += (P[3 * q + a] - mu[a]) * (P[3 * q + b] - mu[b]);
+    double u[3] = {0.577, 0.578, 0.576};
+    for (int it = 0; it < 100; ++it) {   // power iteration: principal axis
+        double w[3];
+        for (int a = 0; a < 3; ++a) w[a] = C[3 * a] * u[0] + C[3 * a + 1] * u[1] + C[3 * a + 2] * u[2];
+        const double nw = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        if (!(nw > 0)) break;
+        for (int a = 0; a < 3; ++a) u[a] = w[a] / nw;
+    }
+    double rp2 = 0;
+    std::vector<double> s(np), rho2(np);
+    for (size_t q = 0; q < np; ++q) {
+        double d[3], t = 0;
+        for (int a = 0; a < 3; ++a) {
+            d[a] = P[3 * q + a] - mu[a];
+            t += d[a] * u[a];
+        }
+        double r2 = 0;
+        for (int a = 0; a < 3; ++a) r2 += (d[a] - t * u[a]) * (d[a] - t * u[a]);
+        s[q] = t;
+        rho2[q] = r2;
+        rp2 = std::max(rp2, r2);
+    }
+    double s_lo = INFINITY, s_hi = -INFINITY;
+    for (size_t q = 0; q < np; ++q) {
+        const double e = std::sqrt(std::max(rp2 - rho2[q], 0.0));
+        s_hi = std::max(s_hi, s[q] - e);
+        s_lo = std::min(s_lo, s[q] + e);
+    }
+    if (s_lo > s_hi) s_lo = s_hi = 0.5 * (s_lo + s_hi);
+    double A[3], B[3], D[3], dd = 0;
+    for (int a = 0; a < 3; ++a) {
+        A[a] = mu[a] + s_lo * u[a];
+        B[a] = mu[a] + s_hi * u[a];
+        D[a] = B[a] - A[a];
+        dd += D[a] * D[a];
+    }
+    double r = 0;
+    for (size_t q = 0; q < np; ++q) {
+        double x[3], t = 0;
+        for (int a = 0; a < 3; ++a) {
+            x[a] = P[3 * q + a] - A[a];
+            t += x[a] * D[a];
+        }
+        t = dd > 0 ? std::min(std::max(t / dd, 0.0), 1.0) : 0.0;
+        double r2 = 0;
+        for (int a = 0; a < 3; ++a) r2 += (x[a] - t * D[a]) * (x[a] - t * D[a]);
+        r = std::max(r, std::sqrt(r2));
+    }
+    r += pad;
+    const double pi = 3.14159265358979323846;
+    const double vol_c = pi * r * r * std::sqrt(dd) + 4.0 / 3.0 * pi * r * r * r;
+    const double vol_s = 4.0 / 3.0 * pi * R * R * R;
+    if (!(vol_c < vol_s)) return;
+    const float rf = std::nextafter((float)r, INFINITY);
+    *ca = make_float4((float)A[0], (float)A[1], (float)A[2], rf);
+    *cb = make_float4((float)B[0], (float)B[1], (float)B[2], 0.f);
+}
+
+int grid_capsules(sdf_ctx* ctx, sdf_grids* G) {
+    if (G->capsules) return SDF_OK;
+    const size_t n3 = (size_t)G->n * G->n * G->n;
+    std::vector<float> v(n3);
+    for (int l = 0; l < G->n_links; ++l) {
+        const cudaError_t e = cudaMemcpy(v.data(), G->values + l * n3, n3 * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "grid download (capsules)");
+        link_capsule(v.data(), G->n, G->meta[l], &G->cap_a[l], &G->cap_b[l]);
+    }
+    G->capsules = true;
+    return SDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int sdf_robot_create(sdf_ctx* ctx, const sdf_dh* dh, int32_t dof, const float* base_3x4,
                      const sdf_grids* grids, sdf_robot** out) {
     if (!ctx || !out) return SDF_ERR_INVALID_ARG;
@@ -436,9 +554,19 @@ int sdf_robot_create(sdf_ctx* ctx, const sdf_dh* dh, int32_t dof, const float* b
         T.dh_sa[j] = (float)std::sin((double)dh[j].alpha);
         T.dh_th[j] = dh[j].theta_offset;
     }
+    {
+        DeviceGuard g0(ctx->device);
+        const int rc = grid_capsules(ctx, const_cast<sdf_grids*>(grids));
+        if (rc != SDF_OK) {
+            delete R;
+            return rc;
+        }
+    }
     for (int l = 0; l < T.L; ++l) {
         const sdf_grid_meta& m = grids->meta[l];
         T.sph_local[l] = make_float4(m.center[0], m.center[1], m.center[2], m.radius);
+        T.cap_a[l] = grids->cap_a[l];
+        T.cap_b[l] = grids->cap_b[l];
         T.grid_o[l] = make_float4(m.origin[0], m.origin[1], m.origin[2], (float)(1.0 / (double)m.h));
         T.grid_h[l] = m.h;
     }

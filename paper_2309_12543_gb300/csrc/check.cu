@@ -437,7 +437,7 @@ struct BlockState {
     const float4* sorted;      // this trajectory's sorted points
     const float* values;       // this robot's grids
     int n, L, n_valid;
-    float4 (*pose)[4];         // per pair: rows[3], sphere
+    float4 (*pose)[6];         // per pair: rows[3], sphere, capsule start (+radius), capsule axis (+1/len^2)
     const float4* grid_o;      // per link (shared memory)
     const float* grid_h;
     unsigned* best;            // per waypoint of the block
@@ -452,14 +452,24 @@ __device__ __forceinline__ void stat_add(const BlockState& B, int idx, unsigned 
 
 __device__ __forceinline__ float pair_threshold(const BlockState& B, int pair) {
     if (!B.cull) return __int_as_float(0x7f800000);
-    const float t = from_ordered(B.best[pair / B.L]) + B.pose[pair][3].w + kCullSlack;
+    const float t = from_ordered(B.best[pair / B.L]) + B.pose[pair][4].w + kCullSlack;
     return (t == t) ? t : __int_as_float(0x7f800000);
 }
 
-__device__ __forceinline__ bool sphere_reaches(float4 c, float4 sph, float thr) {
-    const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
+// Squared distance from (x, y, z) to the segment A + t D, t in [0, 1] (D.w = 1/|D|^2,
+// 0 for a point).
+__device__ __forceinline__ float seg_dist2(float x, float y, float z, float4 A, float4 D) {
+    const float px = x - A.x, py = y - A.y, pz = z - A.z;
+    const float t = fminf(fmaxf(fmaf(px, D.x, fmaf(py, D.y, pz * D.z)) * D.w, 0.f), 1.f);
+    const float qx = fmaf(-t, D.x, px), qy = fmaf(-t, D.y, py), qz = fmaf(-t, D.z, pz);
+    return fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+}
+
+// Can a sphere c (centre, radius) hold a point within thr of the link's capsule
+// surface?  thr already includes the capsule radius.
+__device__ __forceinline__ bool capsule_reaches(float4 c, float4 A, float4 D, float thr) {
     const float base = thr + c.w;
-    return base >= 0.f && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= base * base;
+    return base >= 0.f && seg_dist2(c.x, c.y, c.z, A, D) <= base * base;
 }
 
 // Interpolated distance of sorted point `pos` for block pair `pair`, folded into
@@ -527,10 +537,9 @@ __device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, co
     for (int k = 0; k < TB; ++k) {
         if (k >= cnt) break;
         const int pair = (int)(ent[k] >> 28);
-        const float4 sph = B.pose[pair][3];
         const float thr = pair_threshold(B, pair);
-        const float dx = pt[k].x - sph.x, dy = pt[k].y - sph.y, dz = pt[k].z - sph.z;
-        const bool surv = pos[k] < B.n_valid && thr >= 0.f && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= thr * thr;
+        const bool surv = pos[k] < B.n_valid && thr >= 0.f &&
+                          seg_dist2(pt[k].x, pt[k].y, pt[k].z, B.pose[pair][4], B.pose[pair][5]) <= thr * thr;
         if (B.stat) stat_add(B, kWsPointT, (unsigned)__popc(__ballot_sync(kFull, pos[k] < B.n_valid)), lane);
         queue_push(B, Q, surv, pos[k], pair, lane);
     }
@@ -540,7 +549,7 @@ __device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, co
 template <int TB>
 __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid_constant__ BatchParams P) {
     extern __shared__ float4 s_spheres[];            // tiles [stage_tiles], then super-tiles
-    __shared__ float4 s_pose[kCheckWarps][4];
+    __shared__ float4 s_pose[kCheckWarps][6];
     __shared__ float4 s_grid_o[kMaxLinks];
     __shared__ float s_grid_h[kMaxLinks];
     __shared__ unsigned s_best[kCheckWarps];
@@ -611,6 +620,18 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
             dst[1] = rows[1];
             dst[2] = rows[2];
             dst[3] = sp;
+            // the link's bounding capsule in the world frame
+            const float4 a = T.cap_a[lane], b = T.cap_b[lane];
+            float A[3], Bw[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                A[r] = fmaf(Mj[4 * r], a.x, fmaf(Mj[4 * r + 1], a.y, fmaf(Mj[4 * r + 2], a.z, Mj[4 * r + 3])));
+                Bw[r] = fmaf(Mj[4 * r], b.x, fmaf(Mj[4 * r + 1], b.y, fmaf(Mj[4 * r + 2], b.z, Mj[4 * r + 3])));
+            }
+            const float dx = Bw[0] - A[0], dy = Bw[1] - A[1], dz = Bw[2] - A[2];
+            const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            dst[4] = make_float4(A[0], A[1], A[2], a.w);
+            dst[5] = make_float4(dx, dy, dz, dd > 0.f ? 1.f / dd : 0.f);
         }
     }
     const bool pair_warp = warp < n_pair;
@@ -646,7 +667,8 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
     const float4* tiles = staged ? s_spheres : P.tiles + C.tile_base;
     const float4* supers = staged ? s_spheres + P.stage_tiles : P.supers + C.super_base;
     const unsigned long long t_fk = (stats && tid == 0) ? global_ns() : 0ull;
-    const float4 sph = s_pose[pair_warp ? warp : 0][3];
+    const float4 capA = s_pose[pair_warp ? warp : 0][4];
+    const float4 capD = s_pose[pair_warp ? warp : 0][5];
 
     BlockState B;
     B.sorted = P.sorted + C.point_base;
@@ -674,8 +696,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
                 const int s = s0 + lane;
                 if (s < n_super) {
                     const float4 c = supers[s];
-                    const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
-                    const float sc = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + c.w;
+                    const float sc = sqrtf(seg_dist2(c.x, c.y, c.z, capA, capD)) + c.w;
                     if (sc < bs) { bs = sc; bi = s; }
                 }
             }
@@ -685,8 +706,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
                 float ts = kInf;
                 if (t < n_tiles) {
                     const float4 c = tiles[t];
-                    const float dx = c.x - sph.x, dy = c.y - sph.y, dz = c.z - sph.z;
-                    ts = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + c.w;
+                    ts = sqrtf(seg_dist2(c.x, c.y, c.z, capA, capD)) + c.w;
                 }
                 const int t_seed = warp_argmin(ts, t < n_tiles ? t : 0x7fffffff);
                 const bool ev = t_seed < n_tiles && t_seed * 32 + lane < n_valid;
@@ -706,7 +726,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
         for (int s0 = 0; s0 < n_super; s0 += 32) {
             const int s = s0 + lane;
             float thr = pair_threshold(B, warp);
-            unsigned ms = __ballot_sync(kFull, s < n_super && sphere_reaches(supers[min(s, n_super - 1)], sph, thr));
+            unsigned ms = __ballot_sync(kFull, s < n_super && capsule_reaches(supers[min(s, n_super - 1)], capA, capD, thr));
             if (stats) {
                 stat_add(B, kWsSuperT, (unsigned)min(32, n_super - s0), lane);
                 stat_add(B, kWsSuperP, (unsigned)__popc(ms), lane);
@@ -716,7 +736,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
                 ms &= ms - 1;
                 thr = pair_threshold(B, warp);
                 const int t = sidx * 32 + lane;
-                const unsigned mt = __ballot_sync(kFull, t < n_tiles && sphere_reaches(tiles[min(t, n_tiles - 1)], sph, thr));
+                const unsigned mt = __ballot_sync(kFull, t < n_tiles && capsule_reaches(tiles[min(t, n_tiles - 1)], capA, capD, thr));
                 if (stats) {
                     stat_add(B, kWsTileT, (unsigned)min(32, n_tiles - sidx * 32), lane);
                     stat_add(B, kWsTileP, (unsigned)__popc(mt), lane);

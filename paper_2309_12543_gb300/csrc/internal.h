@@ -32,6 +32,8 @@ struct LinkTable {
     float dh_a[kMaxLinks], dh_d[kMaxLinks], dh_ca[kMaxLinks], dh_sa[kMaxLinks],
         dh_th[kMaxLinks];     // per joint: a, d, cos(alpha), sin(alpha), theta offset
     float4 sph_local[kMaxLinks];   // bounding sphere centre (link frame) + radius
+    float4 cap_a[kMaxLinks];       // bounding capsule: segment start (link frame) + radius
+    float4 cap_b[kMaxLinks];       // segment end (w unused)
     float4 grid_o[kMaxLinks];      // grid origin (link frame) + 1/h
     float grid_h[kMaxLinks];
     const float* values;           // L grids of n^3 floats, x fastest
@@ -108,6 +110,8 @@ struct sdf_grids {
     int n = 0;
     float* values = nullptr;  // device, n_links * n^3
     sdf_grid_meta meta[SDF_MAX_LINKS];
+    bool capsules = false;    // cap_a / cap_b computed (on first use)
+    float4 cap_a[SDF_MAX_LINKS], cap_b[SDF_MAX_LINKS];
 };
 
 struct sdf_robot {
@@ -152,6 +156,16 @@ struct sdf_ctx {
     int32_t* st_link = nullptr;
     int32_t* st_point = nullptr;
     size_t st_out_cap = 0;
+    // surrogate check workspace (grown on demand)
+    float* sur_poses = nullptr;
+    unsigned long long* sur_keys = nullptr;
+    uint8_t* sur_mask = nullptr;
+    size_t sur_w_cap = 0;
+    size_t sur_links = 0;
+    float4* sur_xq = nullptr;
+    uint2* sur_tag = nullptr;
+    int* sur_count = nullptr;
+    size_t sur_cap = 0;
     // timing
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
     bool timed_valid = false;

@@ -69,7 +69,10 @@ constexpr uint32_t kTZ2 = 0, kTZ3 = 128, kTDW3 = 256, kTS3 = 384, kTS2 = 400, kT
 // 16 K-elements per MMA = 256 B.  MN-major: K-direction stride = row groups.
 constexpr uint32_t kRowGroup = 2048, kAuxRowGroup = 256;
 
-__device__ __forceinline__ float silu_sigma(float z) { return 1.0f / (1.0f + __expf(-z)); }
+// Logistic function with the fast exponential and division intrinsics (a few ulp;
+// the results are rounded to bfloat16 or compared at ~1e-3 anyway).  For z below
+// about -88 the exponential overflows and the quotient is 0.
+__device__ __forceinline__ float silu_sigma(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -120,25 +123,26 @@ __device__ __forceinline__ void mma_k128(uint32_t d, uint32_t a_addr, uint32_t a
 #define AUXMN(addr) (addr), kAuxRowGroup, 128u, 2u * kAuxRowGroup
 
 // Load one link's weights: the W2/W3 blocks (stored [in][out]) into K-major bf16
-// tiles [out][in] (thread t = output unit), the small parameters into FP32.
+// tiles [out][in], the small parameters into FP32.  All `nthreads` threads help;
+// consecutive threads read consecutive output units (coalesced).
 __device__ __forceinline__ void load_weights(const float* __restrict__ P, uint8_t* w2, uint8_t* w3, float* small,
-                                             int t) {
-    for (int blk = 0; blk < 2; ++blk) {
+                                             int t, int nthreads) {
+    constexpr int kChunks = kH * (kH / 8);   // 8-element row chunks per block
+    for (int idx = t; idx < 2 * kChunks; idx += nthreads) {
+        const int blk = idx / kChunks, rem = idx % kChunks;
+        const int o = rem % kH, i0 = (rem / kH) * 8;
         const float* src = P + (blk == 0 ? kOW2 : kOW3);
-        uint8_t* dst = blk == 0 ? w2 : w3;
-        for (int i0 = 0; i0 < kH; i0 += 8) {
-            float v[8];
+        float v[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = src[(i0 + k) * kH + t];
-            store_bf16x8(dst, t, i0, kH, v);
-        }
+        for (int k = 0; k < 8; ++k) v[k] = src[(i0 + k) * kH + o];
+        store_bf16x8(blk == 0 ? w2 : w3, o, i0, kH, v);
     }
-    for (int i = t; i < 384; i += blockDim.x) small[i] = P[kOW1 + i];
-    if (t < kH) {
-        small[384 + t] = P[kOB1 + t];
-        small[384 + kH + t] = P[kOB2 + t];
-        small[384 + 2 * kH + t] = P[kOB3 + t];
-        small[384 + 3 * kH + t] = P[kOW4 + t];
+    for (int i = t; i < 384; i += nthreads) small[i] = P[kOW1 + i];
+    for (int i = t; i < kH; i += nthreads) {
+        small[384 + i] = P[kOB1 + i];
+        small[384 + kH + i] = P[kOB2 + i];
+        small[384 + 2 * kH + i] = P[kOB3 + i];
+        small[384 + 3 * kH + i] = P[kOW4 + i];
     }
     if (t == 0) small[384 + 4 * kH] = P[kOB4];
 }
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
     const float* b3 = small + 384 + 2 * kH;
     const float* w4 = small + 384 + 3 * kH;
 
-    load_weights(P, sW2, sW3, small, t);
+    load_weights(P, sW2, sW3, small, t, 128);
     if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
     if (t == 0) tc::mbar_init(&mbar, 1);
     sync_for_mma();
@@ -414,20 +418,37 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
             P[i] = p;
             return p;
         };
+        // the 128 x 128 blocks: 32 columns at a time, their loads issued together
+        float* __restrict__ Pr = P;
+        float* __restrict__ Mr = M;
+        float* __restrict__ Vr = V;
         for (int blk = 0; blk < 2; ++blk) {
             const uint32_t col = blk == 0 ? kTZ3 : kTDW3;
             const int base = blk == 0 ? kOW2 : kOW3;
             uint8_t* tile = blk == 0 ? sW2 : sW3;
             for (int c0 = 0; c0 < kH; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(lane_addr + col + c0, v);
+                float gr[32], pm[32], pv[32], pp[32];
+                tc::tmem_ld32(lane_addr + col + c0, gr);
 #pragma unroll
-                for (int k = 0; k < 32; k += 8) {
-                    float w[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) w[e] = adam(base + (c0 + k + e) * kH + o, v[k + e]);
-                    store_bf16x8(tile, o, c0 + k, kH, w);
+                for (int e = 0; e < 32; ++e) {
+                    const int i = base + (c0 + e) * kH + o;
+                    pm[e] = Mr[i];
+                    pv[e] = Vr[i];
+                    pp[e] = Pr[i];
                 }
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    const int i = base + (c0 + e) * kH + o;
+                    const float m = fmaf(b1c, pm[e], (1.f - b1c) * gr[e]);
+                    const float v = fmaf(b2c, pv[e], (1.f - b2c) * gr[e] * gr[e]);
+                    const float p = pp[e] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+                    Mr[i] = m;
+                    Vr[i] = v;
+                    Pr[i] = p;
+                    pp[e] = p;
+                }
+#pragma unroll
+                for (int k = 0; k < 32; k += 8) store_bf16x8(tile, o, c0 + k, kH, pp + k);
             }
         }
         float nw[7];
@@ -484,16 +505,27 @@ struct EvalArgs {
     int* status;
 };
 
-__global__ void __launch_bounds__(128, 1) mlp_eval_kernel(const __grid_constant__ EvalArgs A) {
+constexpr int kEvalThreads = 512;   // 16 warps: 4 column groups x the 4 lane quarters
+
+// One 128-query tile at a time: warp w serves tensor-memory lanes 32 (w % 4) .. +31
+// (queries) and hidden units 32 (w / 4) .. +31 of every layer; the output layer's
+// four partial sums meet in shared memory.
+__global__ void __launch_bounds__(kEvalThreads, 1) mlp_eval_kernel(const __grid_constant__ EvalArgs A) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_slot;
-    const int t = threadIdx.x, warp = t >> 5;
+    __shared__ float partial[4][kH];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int row = ((warp & 3) << 5) | lane;
+    const int cg = warp >> 2;
+    const int c0 = cg * 32;
     uint8_t* sW2 = sm + kEW2;
     uint8_t* sW3 = sm + kEW3;
     uint8_t* sH1 = sm + kEH1;
     uint8_t* sH2 = sm + kEH2;
     float* small = reinterpret_cast<float*>(sm + kESmall);
+    const float* W1 = small;
+    const float* b1 = small + 384;
     const float* b2 = small + 384 + kH;
     const float* b3 = small + 384 + 2 * kH;
     const float* w4 = small + 384 + 3 * kH;
@@ -517,14 +549,13 @@ __global__ void __launch_bounds__(128, 1) mlp_eval_kernel(const __grid_constant_
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tm = tmem_slot;
-    const uint32_t lane_addr = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_addr = tm + ((uint32_t)((warp & 3) * 32) << 16);
     const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH1 = tc::smem_u32(sH1), aH2 = tc::smem_u32(sH2);
     constexpr uint32_t kN128KK = tc::idesc_bf16(128, 128, 0, 0);
     uint32_t phase = 0;
     bool ok = true;
     int loaded = -1;
-    int tile = 0, l = 0, tile_in_l = 0;
-    // locate the first tile
+    int l = 0, tile_in_l = 0;
     {
         int acc = 0;
         for (l = 0; l < A.L; ++l) {
@@ -534,18 +565,18 @@ __global__ void __launch_bounds__(128, 1) mlp_eval_kernel(const __grid_constant_
         }
         tile_in_l = first - acc;
     }
-    for (tile = first; tile < last && ok; ++tile) {
+    for (int tile = first; tile < last && ok; ++tile) {
         while (tile_in_l * 128 >= counts[l]) {   // next non-empty segment
             ++l;
             tile_in_l = 0;
         }
         if (l != loaded) {
-            __syncthreads();   // previous tile's readers of the weights are done
-            load_weights(A.master + (size_t)l * kPar, sW2, sW3, small, t);
+            __syncthreads();
+            load_weights(A.master + (size_t)l * kPar, sW2, sW3, small, t, kEvalThreads);
             loaded = l;
             __syncthreads();
         }
-        const int k = tile_in_l * 128 + t;
+        const int k = tile_in_l * 128 + row;
         const bool valid = k < counts[l];
         const size_t qi = check_mode ? (size_t)l * A.seg_cap + k : (size_t)k;
         float4 xq = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -555,45 +586,78 @@ __global__ void __launch_bounds__(128, 1) mlp_eval_kernel(const __grid_constant_
             else
                 xq = make_float4(A.x3[3 * qi], A.x3[3 * qi + 1], A.x3[3 * qi + 2], 0.f);
         }
-        layer1(small, xq.x, xq.y, xq.z, sH1, t);
+        // layer 1: this thread's 32 hidden units of its query
+#pragma unroll
+        for (int j0 = 0; j0 < 32; j0 += 8) {
+            float h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int j = c0 + j0 + e;
+                const float z = fmaf(W1[3 * j], xq.x, fmaf(W1[3 * j + 1], xq.y, fmaf(W1[3 * j + 2], xq.z, b1[j])));
+                h[e] = z * silu_sigma(z);
+            }
+            store_bf16x8(sH1, row, c0 + j0, kH, h);
+        }
         sync_for_mma();
         if (t == 0) {
             mma_k128(tm + 0, KMAJ(aH1), KMAJ(aW2), kN128KK);
             tc::mma_commit(&mbar);
         }
         if (!(ok = wait_mma(&mbar, phase))) break;
-        hidden_epilogue(lane_addr + 0, b2, sH2, t);
+        {
+            float v[32];
+            tc::tmem_ld32(lane_addr + c0, v);
+#pragma unroll
+            for (int j0 = 0; j0 < 32; j0 += 8) {
+                float h[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float z = v[j0 + e] + b2[c0 + j0 + e];
+                    h[e] = z * silu_sigma(z);
+                }
+                store_bf16x8(sH2, row, c0 + j0, kH, h);
+            }
+        }
         sync_for_mma();
         if (t == 0) {
             mma_k128(tm + 128, KMAJ(aH2), KMAJ(aW3), kN128KK);
             tc::mma_commit(&mbar);
         }
         if (!(ok = wait_mma(&mbar, phase))) break;
-        float f = small[384 + 4 * kH];
-        for (int c0 = 0; c0 < kH; c0 += 32) {
+        {
             float v[32];
             tc::tmem_ld32(lane_addr + 128 + c0, v);
+            float f = 0.f;
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
                 const float z = v[e] + b3[c0 + e];
                 f = fmaf(w4[c0 + e], z * silu_sigma(z), f);
             }
+            partial[cg][row] = f;
         }
-        if (valid) {
+        __syncthreads();
+        if (cg == 0) {   // warps 0..3: one query per lane
+            const float f = small[384 + 4 * kH] + ((partial[0][row] + partial[1][row]) +
+                                                   (partial[2][row] + partial[3][row]));
             if (check_mode) {
-                const uint2 tg = A.tag[qi];
+                // lanes of the same waypoint agree on their smallest key first, and one
+                // of them does the atomic
+                const uint2 tg = valid ? A.tag[qi] : make_uint2(0xffffffffu, 0xffffffffu);
                 const float d = fmaf(A.scale[l], f, xq.w);
-                if (!isnan(d)) {
-                    const unsigned long long key = ((unsigned long long)ordered_bits(d) << 32) | tg.y;
-                    atomicMin(&A.keys[tg.x], key);
-                }
-            } else {
+                const bool use = valid && !isnan(d);
+                const unsigned hi = use ? ordered_bits(d) : 0xffffffffu;
+                const unsigned peers = __match_any_sync(0xffffffffu, use ? tg.x : 0xffffffffu);
+                const unsigned hmin = __reduce_min_sync(peers, hi);
+                const unsigned lmin = __reduce_min_sync(peers, hi == hmin ? tg.y : 0xffffffffu);
+                if (use && lane == __ffs(peers) - 1)
+                    atomicMin(&A.keys[tg.x], ((unsigned long long)hmin << 32) | lmin);
+            } else if (valid) {
                 A.f_out[k] = f;
             }
         }
         ++tile_in_l;
         tc::fence_before_sync();
-        __syncthreads();   // H1/H2 and tensor memory are rewritten by the next tile
+        __syncthreads();   // H1/H2, the partial sums and tensor memory are rewritten by the next tile
         tc::fence_after_sync();
     }
     if (!ok) {
@@ -787,6 +851,7 @@ struct SurCheckArgs {
     const float4* supers;             // sphere per 32 tiles
     const int* n_valid;
     float lo[kMaxLinks][3], hi[kMaxLinks][3], m[kMaxLinks][3], inv_a[kMaxLinks];
+    float4 cap_a[kMaxLinks], cap_b[kMaxLinks];   // bounding capsules (link frame), radius in cap_a.w
     float4* xq;                       // queries per link segment
     uint2* tag;
     int* seg_count;
@@ -821,9 +886,13 @@ __device__ __forceinline__ void emit_query(const SurCheckArgs& A, int w, int l, 
     A.tag[q] = make_uint2((unsigned)w, ((unsigned)__float_as_int(p.w) << 4) | (unsigned)l);
 }
 
-__device__ __forceinline__ float sphere_gap(float4 s, float cx, float cy, float cz) {
-    const float dx = s.x - cx, dy = s.y - cy, dz = s.z - cz;
-    return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - s.w;
+// Distance from sphere s (centre, radius) to the segment A + t D (D.w = 1/|D|^2),
+// minus the sphere's radius.
+__device__ __forceinline__ float capsule_gap(float4 s, float4 A, float4 D) {
+    const float px = s.x - A.x, py = s.y - A.y, pz = s.z - A.z;
+    const float t = fminf(fmaxf(fmaf(px, D.x, fmaf(py, D.y, pz * D.z)) * D.w, 0.f), 1.f);
+    const float qx = fmaf(-t, D.x, px), qy = fmaf(-t, D.y, py), qz = fmaf(-t, D.z, pz);
+    return sqrtf(fmaf(qx, qx, fmaf(qy, qy, qz * qz))) - s.w;
 }
 
 // One warp per (waypoint, link) pair.  Seed mode: the 32 points of the tile nearest
@@ -837,7 +906,24 @@ __global__ void __launch_bounds__(256) sur_pairs_kernel(const __grid_constant__ 
     const int w = pair / A.L, l = pair % A.L;
     const float4* P = reinterpret_cast<const float4*>(A.poses + (size_t)pair * 16);
     const float4 M[3] = {P[0], P[1], P[2]};
-    const float4 sph = P[3];
+    // the link's bounding capsule in the world frame: x = R a + t with R the
+    // transpose of the link-from-world rotation and t = -R w (w its last column)
+    float4 cA, cD;
+    {
+        const float4 a = A.cap_a[l], b = A.cap_b[l];
+        const float ax = a.x - M[0].w, ay = a.y - M[1].w, az = a.z - M[2].w;
+        const float bx = b.x - M[0].w, by = b.y - M[1].w, bz = b.z - M[2].w;
+        const float Ax = fmaf(M[0].x, ax, fmaf(M[1].x, ay, M[2].x * az));
+        const float Ay = fmaf(M[0].y, ax, fmaf(M[1].y, ay, M[2].y * az));
+        const float Az = fmaf(M[0].z, ax, fmaf(M[1].z, ay, M[2].z * az));
+        const float Bx = fmaf(M[0].x, bx, fmaf(M[1].x, by, M[2].x * bz));
+        const float By = fmaf(M[0].y, bx, fmaf(M[1].y, by, M[2].y * bz));
+        const float Bz = fmaf(M[0].z, bx, fmaf(M[1].z, by, M[2].z * bz));
+        const float dx = Bx - Ax, dy = By - Ay, dz = Bz - Az;
+        const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        cA = make_float4(Ax, Ay, Az, a.w);
+        cD = make_float4(dx, dy, dz, dd > 0.f ? 1.f / dd : 0.f);
+    }
     const int nv = *A.n_valid;
     const int n_tiles = (nv + 31) >> 5, n_sup = (n_tiles + 31) >> 5;
     if (nv == 0) return;
@@ -845,7 +931,7 @@ __global__ void __launch_bounds__(256) sur_pairs_kernel(const __grid_constant__ 
         float best = INFINITY;
         int bi = 0x7fffffff;
         for (int s = lane; s < n_sup; s += 32) {
-            const float g = sphere_gap(A.supers[s], sph.x, sph.y, sph.z);
+            const float g = capsule_gap(A.supers[s], cA, cD);
             if (g < best) { best = g; bi = s; }
         }
 #pragma unroll
@@ -857,7 +943,7 @@ __global__ void __launch_bounds__(256) sur_pairs_kernel(const __grid_constant__ 
         const int t = bi * 32 + lane;
         float tb = INFINITY;
         int ti = 0x7fffffff;
-        if (t < n_tiles) { tb = sphere_gap(A.tiles[t], sph.x, sph.y, sph.z); ti = t; }
+        if (t < n_tiles) { tb = capsule_gap(A.tiles[t], cA, cD); ti = t; }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const float ob = __shfl_xor_sync(0xffffffffu, tb, o);
@@ -871,26 +957,33 @@ __global__ void __launch_bounds__(256) sur_pairs_kernel(const __grid_constant__ 
     }
     const unsigned long long key = A.keys[w];
     const float T = key == ~0ull ? INFINITY : from_ordered((unsigned)(key >> 32));
-    const float thr = T + A.slack + sph.w;       // keep s when ||c_s - c|| - r_s <= thr
+    const float thr = T + A.slack + cA.w;        // keep s when dist(c_s, segment) - r_s <= thr
     for (int s0 = 0; s0 < n_sup; s0 += 32) {
         const int s = s0 + lane;
-        unsigned bs = __ballot_sync(0xffffffffu, s < n_sup && sphere_gap(A.supers[s], sph.x, sph.y, sph.z) <= thr);
+        unsigned bs = __ballot_sync(0xffffffffu, s < n_sup && capsule_gap(A.supers[s], cA, cD) <= thr);
         while (bs) {
             const int sv = s0 + __ffs(bs) - 1;
             bs &= bs - 1;
             const int t = sv * 32 + lane;
             unsigned bt = __ballot_sync(0xffffffffu,
-                                        t < n_tiles && sphere_gap(A.tiles[t], sph.x, sph.y, sph.z) <= thr);
+                                        t < n_tiles && capsule_gap(A.tiles[t], cA, cD) <= thr);
             while (bt) {
                 const int tv = sv * 32 + __ffs(bt) - 1;
                 bt &= bt - 1;
                 const int k = tv * 32 + lane;
                 const float4 p = k < nv ? A.sorted[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const bool take = k < nv && sphere_gap(make_float4(p.x, p.y, p.z, 0.f), sph.x, sph.y, sph.z) <= thr;
+                const bool take = k < nv && capsule_gap(make_float4(p.x, p.y, p.z, 0.f), cA, cD) <= thr;
                 emit_query(A, w, l, M, p, take, lane);
             }
         }
     }
+}
+
+// Statistics: queries in the segments (capped at the segment size) added to *out.
+__global__ void count_queries_kernel(const int* seg_count, int L, int cap, unsigned long long* out) {
+    unsigned long long n = 0;
+    for (int l = 0; l < L; ++l) n += (unsigned long long)min(seg_count[l], cap);
+    *out += n;
 }
 
 // Per waypoint: decode the surrogate minimum, write it as the result, and select the
@@ -944,15 +1037,6 @@ struct sdf_surrogate {
     float* loss = nullptr;     // [L]
     float box_m[SDF_MAX_LINKS][3];
     float box_a[SDF_MAX_LINKS];
-    // check workspace (grown on demand)
-    float* poses = nullptr;
-    unsigned long long* keys = nullptr;
-    uint8_t* mask = nullptr;
-    size_t w_cap = 0;
-    float4* xq = nullptr;
-    uint2* tag = nullptr;
-    int* seg_count = nullptr;
-    size_t seg_cap = 0;
 };
 
 namespace {
@@ -1073,12 +1157,6 @@ void sdf_surrogate_destroy(sdf_surrogate* S) {
     cudaFree(S->adam_v);
     cudaFree(S->step);
     cudaFree(S->loss);
-    cudaFree(S->poses);
-    cudaFree(S->keys);
-    cudaFree(S->mask);
-    cudaFree(S->xq);
-    cudaFree(S->tag);
-    cudaFree(S->seg_count);
     delete S;
 }
 
@@ -1222,7 +1300,7 @@ int sdf_surrogate_eval(sdf_ctx* ctx, const sdf_surrogate* S, int32_t link, const
     A.status = ctx->status;
     const int tiles = (n + 127) / 128;
     const int grid = std::min(tiles, ctx->num_sms);
-    sdf::mlp_eval_kernel<<<grid, 128, sdf::kEvalSmem, ctx->stream>>>(A);
+    sdf::mlp_eval_kernel<<<grid, sdf::kEvalThreads, sdf::kEvalSmem, ctx->stream>>>(A);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SDF_OK : scuda(ctx, e, "mlp_eval_kernel");
 }
@@ -1246,48 +1324,51 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
     const int L = S->L;
     cudaStream_t st = ctx->stream;
     cudaError_t e = cudaSuccess;
-    // workspace: poses, keys and mask per waypoint; query segments per link
-    if ((size_t)W > S->w_cap) {
-        const size_t cap = std::max<size_t>((size_t)W, 2 * S->w_cap);
+    // workspace (the context's): poses, keys and mask per waypoint; query segments per link
+    if ((size_t)W > ctx->sur_w_cap || (size_t)L > ctx->sur_links) {
+        const size_t cap = std::max<size_t>((size_t)W, 2 * ctx->sur_w_cap);
         cudaStreamSynchronize(st);
-        cudaFree(S->poses);
-        cudaFree(S->keys);
-        cudaFree(S->mask);
-        S->poses = nullptr;
-        S->keys = nullptr;
-        S->mask = nullptr;
-        S->w_cap = 0;
-        e = cudaMalloc(&S->poses, sizeof(float) * 16 * L * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&S->keys, sizeof(unsigned long long) * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&S->mask, cap);
+        cudaFree(ctx->sur_poses);
+        cudaFree(ctx->sur_keys);
+        cudaFree(ctx->sur_mask);
+        ctx->sur_poses = nullptr;
+        ctx->sur_keys = nullptr;
+        ctx->sur_mask = nullptr;
+        ctx->sur_w_cap = 0;
+        e = cudaMalloc(&ctx->sur_poses, sizeof(float) * 16 * SDF_MAX_LINKS * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->sur_keys, sizeof(unsigned long long) * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->sur_mask, cap);
         if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate: workspace");
-        S->w_cap = cap;
+        ctx->sur_w_cap = cap;
     }
     const size_t want = std::min<size_t>((size_t)W * (size_t)std::max(N, 1),
                                          std::max<size_t>((size_t)W * 256, (size_t)1 << 20));
-    if (want > S->seg_cap) {
+    if (want > ctx->sur_cap || (size_t)L > ctx->sur_links) {
+        const size_t cap = std::max(want, ctx->sur_cap);
         cudaStreamSynchronize(st);
-        cudaFree(S->xq);
-        cudaFree(S->tag);
-        S->xq = nullptr;
-        S->tag = nullptr;
-        S->seg_cap = 0;
-        if (!S->seg_count) e = cudaMalloc(&S->seg_count, sizeof(int) * SDF_MAX_LINKS);
-        if (e == cudaSuccess) e = cudaMalloc(&S->xq, sizeof(float4) * L * want);
-        if (e == cudaSuccess) e = cudaMalloc(&S->tag, sizeof(uint2) * L * want);
+        cudaFree(ctx->sur_xq);
+        cudaFree(ctx->sur_tag);
+        ctx->sur_xq = nullptr;
+        ctx->sur_tag = nullptr;
+        ctx->sur_cap = 0;
+        ctx->sur_links = 0;
+        if (!ctx->sur_count) e = cudaMalloc(&ctx->sur_count, sizeof(int) * SDF_MAX_LINKS);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->sur_xq, sizeof(float4) * L * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->sur_tag, sizeof(uint2) * L * cap);
         if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate: query buffers");
-        S->seg_cap = want;
+        ctx->sur_cap = cap;
+        ctx->sur_links = (size_t)L;
     }
-    e = cudaMemsetAsync(S->keys, 0xff, sizeof(unsigned long long) * W, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S->seg_count, 0, sizeof(int) * SDF_MAX_LINKS, st);
+    e = cudaMemsetAsync(ctx->sur_keys, 0xff, sizeof(unsigned long long) * W, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_count, 0, sizeof(int) * SDF_MAX_LINKS, st);
     if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate");
     sdf::BatchParams* bp = new (std::nothrow) sdf::BatchParams();
     if (!bp) return sfail(ctx, SDF_ERR_OOM, "host allocation");
     int rc = sdf::sort_cloud(ctx, points_dev, N, bp);
     sdf::SurCheckArgs A{};
     if (rc == SDF_OK) {
-        e = sdf::launch_fk(R->table, q_dev, W, S->poses, ctx->status, st);
-        A.poses = S->poses;
+        e = sdf::launch_fk(R->table, q_dev, W, ctx->sur_poses, ctx->status, st);
+        A.poses = ctx->sur_poses;
         A.W = W;
         A.L = L;
         A.sorted = bp->sorted;
@@ -1304,22 +1385,26 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
             }
             A.inv_a[l] = (float)(1.0 / a);
         }
-        A.xq = S->xq;
-        A.tag = S->tag;
-        A.seg_count = S->seg_count;
-        A.seg_cap = (int)S->seg_cap;
-        A.keys = S->keys;
+        A.xq = ctx->sur_xq;
+        A.tag = ctx->sur_tag;
+        A.seg_count = ctx->sur_count;
+        A.seg_cap = (int)ctx->sur_cap;
+        A.keys = ctx->sur_keys;
         A.slack = eps + sdf::kCullSlack;
+        for (int l = 0; l < L; ++l) {
+            A.cap_a[l] = R->table.cap_a[l];
+            A.cap_b[l] = R->table.cap_b[l];
+        }
     }
     delete bp;
     sdf::EvalArgs E{};
     E.master = S->master;
-    E.xq = S->xq;
-    E.tag = S->tag;
-    E.seg_count = S->seg_count;
-    E.seg_cap = (int)S->seg_cap;
+    E.xq = ctx->sur_xq;
+    E.tag = ctx->sur_tag;
+    E.seg_count = ctx->sur_count;
+    E.seg_cap = (int)ctx->sur_cap;
     E.L = L;
-    E.keys = S->keys;
+    E.keys = ctx->sur_keys;
     for (int l = 0; l < L; ++l) E.scale[l] = S->box_a[l];
     E.status = ctx->status;
     const unsigned pair_blocks = (unsigned)(((size_t)W * L * 32 + 255) / 256);
@@ -1329,26 +1414,34 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
         e = cudaGetLastError();
     }
     if (rc == SDF_OK && e == cudaSuccess) {
-        sdf::mlp_eval_kernel<<<eval_grid, 128, sdf::kEvalSmem, st>>>(E);
+        sdf::mlp_eval_kernel<<<eval_grid, sdf::kEvalThreads, sdf::kEvalSmem, st>>>(E);
         e = cudaGetLastError();
     }
-    if (rc == SDF_OK && e == cudaSuccess) e = cudaMemsetAsync(S->seg_count, 0, sizeof(int) * SDF_MAX_LINKS, st);
+    if (rc == SDF_OK && e == cudaSuccess && ctx->stats && ctx->d_stats) {
+        sdf::count_queries_kernel<<<1, 1, 0, st>>>(ctx->sur_count, L, (int)ctx->sur_cap, ctx->d_stats + 26);
+        e = cudaGetLastError();
+    }
+    if (rc == SDF_OK && e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_count, 0, sizeof(int) * SDF_MAX_LINKS, st);
     if (rc == SDF_OK && e == cudaSuccess) {
         sdf::sur_pairs_kernel<false><<<pair_blocks, 256, 0, st>>>(A);
         e = cudaGetLastError();
     }
     if (rc == SDF_OK && e == cudaSuccess) {
-        sdf::mlp_eval_kernel<<<eval_grid, 128, sdf::kEvalSmem, st>>>(E);
+        sdf::mlp_eval_kernel<<<eval_grid, sdf::kEvalThreads, sdf::kEvalSmem, st>>>(E);
+        e = cudaGetLastError();
+    }
+    if (rc == SDF_OK && e == cudaSuccess && ctx->stats && ctx->d_stats) {
+        sdf::count_queries_kernel<<<1, 1, 0, st>>>(ctx->sur_count, L, (int)ctx->sur_cap, ctx->d_stats + 27);
         e = cudaGetLastError();
     }
     if (rc == SDF_OK && e == cudaSuccess) {
         sdf::sur_finish_kernel<<<(unsigned)((W + 255) / 256), 256, 0, st>>>(
-            S->keys, S->seg_count, L, (int)S->seg_cap, W, margin + eps, dist_dev, argmin_link_dev,
-            argmin_point_dev, surrogate_dist_dev, S->mask);
+            ctx->sur_keys, ctx->sur_count, L, (int)ctx->sur_cap, W, margin + eps, dist_dev, argmin_link_dev,
+            argmin_point_dev, surrogate_dist_dev, ctx->sur_mask);
         e = cudaGetLastError();
     }
     if (rc == SDF_OK && e == cudaSuccess && rechecked_dev)
-        e = cudaMemcpyAsync(rechecked_dev, S->mask, (size_t)W, cudaMemcpyDeviceToDevice, st);
+        e = cudaMemcpyAsync(rechecked_dev, ctx->sur_mask, (size_t)W, cudaMemcpyDeviceToDevice, st);
     if (rc == SDF_OK && e != cudaSuccess) rc = scuda(ctx, e, "check_trajectory_surrogate");
     if (rc == SDF_OK) {
         // the grid path re-checks the selected waypoints on the cloud sorted above
@@ -1361,7 +1454,7 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
         r.dist_dev = dist_dev;
         r.argmin_link_dev = argmin_link_dev;
         r.argmin_point_dev = argmin_point_dev;
-        r.mask_dev = S->mask;
+        r.mask_dev = ctx->sur_mask;
         ctx->reuse_sort = 1;
         rc = check_batch(ctx, &r, 1);
         ctx->reuse_sort = 0;
