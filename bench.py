@@ -37,7 +37,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one check_kernel launch on the 500 x 20k workload,
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # launch); profiles/check_kernel_paper_500x20k.md holds the capture and its command.
-CHECK_KERNEL_DRAM_BYTES = 11_810_816
+CHECK_KERNEL_DRAM_BYTES = 8_797_952
 
 
 def parse():
@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--margin", type=float, default=0.05, help="surrogate: safety margin (m) of the fallback")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of 125 Hz cycles")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: mean requests per cycle (Poisson)")
+    ap.add_argument("--forms", default="grid,surrogate", help="serve: forms to run (grid, surrogate)")
     ap.add_argument("--order", default="voxel", choices=["voxel", "random"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100)
@@ -544,13 +545,41 @@ def run_serve(args):
         for t in outstanding:
             srv.poll(t, wait_us=-1)
         return time.perf_counter() - t0, late
-    run_cycles(50, 0)
-    srv.stats(reset=True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    wall, late = run_cycles(cycles, 50)
-    clk = clocks.stop()
-    st = srv.stats()
+    def measure():
+        run_cycles(50, 0)
+        srv.stats(reset=True)
+        clocks = ClockSampler(local)
+        clocks.start()
+        wall, late = run_cycles(cycles, 50)
+        clk = clocks.stop()
+        return srv.stats(reset=True), wall, late, clk
+
+    forms = [f for f in args.forms.split(",") if f]
+    st, wall, late, clk = measure() if "grid" in forms else (None, None, None, None)
+    sur_form = None
+    if "surrogate" in forms:
+        # train the surrogates on the GPU, bound their error, then serve in that form
+        L = scene.n_links
+        n = 1_000_000
+        X = torch.empty((L, n, 3), dtype=torch.float32, device="cuda")
+        Y = torch.empty((L, n), dtype=torch.float32, device="cuda")
+        for l in range(L):
+            sdf.sdf_surrogate_sample(ctx, grids, l, n, 7, 0.10, 5000 + l, X[l], Y[l])
+        sur = sdf.Surrogate(ctx, grids, scenegen.mlp_init(9, L))
+        sur.train(X, Y, n, 0, 20000, 1e-3)
+        sur.train(X, Y, n, 20000, 10000, 2e-4)
+        del X, Y
+        eps = max(max(sur.error(l, 1 << 20, 0, 0.1, seed=7000 + l)[0], sur.error(l, 1 << 20, 10, 0.1, seed=8000 + l)[0])
+                  for l in range(L))
+        srv.set_surrogate(sur, 0.05, eps)
+        s2, w2, late2, clk2 = measure()
+        srv.set_surrogate(None)
+        sur_form = {"p50_us": s2["p50_us"], "p99_us": s2["p99_us"], "mean_us": s2["mean_us"], "max_us": s2["max_us"],
+                    "checks_per_s": s2["completed"] / w2, "completed": int(s2["completed"]),
+                    "mean_batch": s2["mean_batch"], "late_cycles": late2, "eps_m": eps, "margin_m": 0.05,
+                    "clocks": clk2}
+        if st is None:
+            st, wall, late, clk = s2, w2, late2, clk2
     srv.close()
     if rank != 0:
         return
@@ -564,6 +593,7 @@ def run_serve(args):
         "p50_us": st["p50_us"], "p99_us": st["p99_us"], "mean_us": st["mean_us"], "max_us": st["max_us"],
         "checks_per_s": st["completed"] / wall, "completed": int(st["completed"]), "batches": int(st["batches"]),
         "mean_batch": st["mean_batch"], "peak_in_flight": int(st["peak_in_flight"]), "late_cycles": late,
+        "form": "grid" if "grid" in forms else "surrogate", "surrogate_form": sur_form,
         "clocks": clk,
     }
     print(json.dumps(out), flush=True)

@@ -433,6 +433,12 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* robot, const sdf_s
                                float eps, float* dist_dev, int32_t* argmin_link_dev, int32_t* argmin_point_dev,
                                uint8_t* rechecked_dev, float* surrogate_dist_dev);
 
+/* Serving in the surrogate form: requests whose robot uses `surrogate`'s grids are
+ * checked by check_trajectory_surrogate (margin, eps as there) on their slot's
+ * stream, one after the other; other requests keep the batched grid path.  NULL
+ * returns to the grid form.  Applies to batches formed after the call. */
+int sdf_server_set_surrogate(sdf_server* server, const sdf_surrogate* surrogate, float margin, float eps);
+
 /* ----------------------------------------------------------- allocation-free check */
 
 /* The paper has no counterpart to this entry point; it serves deployment.

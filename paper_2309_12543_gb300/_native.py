@@ -104,6 +104,7 @@ def _load():
         "sdf_surrogate_error": (ctypes.c_int, [P, P, i32, i64, i32, ctypes.c_float, ctypes.c_uint64, P, P]),
         "check_trajectory_surrogate": (ctypes.c_int, [P, P, P, P, i32, P, i32, ctypes.c_float, ctypes.c_float,
                                                       P, P, P, P, P]),
+        "sdf_server_set_surrogate": (ctypes.c_int, [P, P, ctypes.c_float, ctypes.c_float]),
         "sdf_ctx_last_kernel_ms": (ctypes.c_int, [P, i32, ctypes.POINTER(ctypes.c_float)]),
         "sdf_build_grids": (ctypes.c_int, [P, P, i32, i32, ctypes.c_float, ctypes.POINTER(P)]),
         "sdf_grids_upload": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(P)]),
@@ -145,7 +146,8 @@ EXPORTED = ("sdf_ctx_create", "sdf_ctx_destroy", "sdf_ctx_set_stream", "sdf_last
             "sdf_server_create", "sdf_server_destroy", "sdf_server_set_cloud", "sdf_server_submit",
             "sdf_server_poll", "sdf_server_stats", "sdf_measure_gather", "sdf_surrogate_create",
             "sdf_surrogate_destroy", "sdf_surrogate_params", "sdf_surrogate_sample", "sdf_surrogate_grad",
-            "sdf_surrogate_train", "sdf_surrogate_eval", "sdf_surrogate_error", "check_trajectory_surrogate")
+            "sdf_surrogate_train", "sdf_surrogate_eval", "sdf_surrogate_error", "check_trajectory_surrogate",
+            "sdf_server_set_surrogate")
 
 
 def _ptr(x) -> int:
@@ -453,6 +455,13 @@ class Server:
         if rc != SDF_PENDING and rc != SDF_ERR_TIMEOUT:
             self._w.pop(ticket, None)
         return rc, d, l, p, float(lat.value)
+
+    def set_surrogate(self, surrogate, margin: float = 0.05, eps: float = 0.0):
+        """Serve requests on the surrogate's grids in the surrogate form (None: grid form)."""
+        rc = lib.sdf_server_set_surrogate(self.handle, surrogate.handle if surrogate is not None else None,
+                                          float(margin), float(eps))
+        if rc != SDF_OK:
+            raise SdfError(rc, "sdf_server_set_surrogate")
 
     def stats(self, reset: bool = False) -> dict:
         out = np.zeros(10, dtype=np.float64)

@@ -102,6 +102,8 @@ struct sdf_ctx;
 namespace sdf {
 // api.cu: sort one cloud into ctx's scratch and fill p's cloud/scratch fields.
 int sort_cloud(sdf_ctx* ctx, const float* points_dev, int N, BatchParams* p);
+// surrogate.cu: the grids a surrogate was built on.
+const sdf_grids* surrogate_grids(const sdf_surrogate* s);
 }  // namespace sdf
 
 struct sdf_grids {

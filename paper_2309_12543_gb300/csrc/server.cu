@@ -88,6 +88,10 @@ struct sdf_server {
     uint64_t completed = 0, rejected = 0, batches = 0, batched_requests = 0;
     int in_flight = 0, peak_in_flight = 0;
     std::string err;
+    // surrogate form (requests on the surrogate's grids), or none
+    const sdf_surrogate* surrogate = nullptr;
+    const sdf_grids* surrogate_grids = nullptr;
+    float margin = 0.f, eps = 0.f;
 };
 
 namespace {
@@ -192,7 +196,23 @@ void launch(sdf_server* S) {
         if (cudaMemcpyAsync(s.d_q, s.h_q, qoff * sizeof(float), cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
             cudaStreamWaitEvent(s.stream, cb.ready, 0) != cudaSuccess)
             rc = SDF_ERR_CUDA;
-        if (rc == SDF_OK) rc = check_batch(s.ctx, req.data(), n);
+        if (rc == SDF_OK && S->surrogate) {
+            // the surrogate form, one request after the other on the slot's stream;
+            // requests on other grids take the grid path together
+            std::vector<sdf_check_request> rest;
+            for (auto& q : req) {
+                if (rc != SDF_OK) break;
+                if (q.robot->grids == S->surrogate_grids)
+                    rc = check_trajectory_surrogate(s.ctx, q.robot, S->surrogate, q.q_dev, q.W, q.points_dev, q.N,
+                                                    S->margin, S->eps, q.dist_dev, q.argmin_link_dev,
+                                                    q.argmin_point_dev, nullptr, nullptr);
+                else
+                    rest.push_back(q);
+            }
+            if (rc == SDF_OK && !rest.empty()) rc = check_batch(s.ctx, rest.data(), (int)rest.size());
+        } else if (rc == SDF_OK) {
+            rc = check_batch(s.ctx, req.data(), n);
+        }
         for (int part = 0; part < 3 && rc == SDF_OK; ++part)
             if (cudaMemcpyAsync(s.h_out + part * maxw, s.d_out + part * maxw, (size_t)woff * sizeof(float),
                                 cudaMemcpyDeviceToHost, s.stream) != cudaSuccess)
@@ -314,6 +334,16 @@ void sdf_server_destroy(sdf_server* S) {
     if (S->engine.joinable()) S->engine.join();
     cudaSetDevice(S->cfg.device);
     free_server(S);
+}
+
+int sdf_server_set_surrogate(sdf_server* S, const sdf_surrogate* surrogate, float margin, float eps) {
+    if (!S || !(margin >= 0.f) || !(eps >= 0.f)) return SDF_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->surrogate = surrogate;
+    S->surrogate_grids = surrogate ? sdf::surrogate_grids(surrogate) : nullptr;
+    S->margin = margin;
+    S->eps = eps;
+    return SDF_OK;
 }
 
 int sdf_server_set_cloud(sdf_server* S, const float* points_host, int32_t N) {

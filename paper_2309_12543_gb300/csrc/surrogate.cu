@@ -1039,6 +1039,10 @@ struct sdf_surrogate {
     float box_a[SDF_MAX_LINKS];
 };
 
+namespace sdf {
+const sdf_grids* surrogate_grids(const sdf_surrogate* s) { return s ? s->grids : nullptr; }
+}  // namespace sdf
+
 namespace {
 
 using sdf::kH;

@@ -128,3 +128,32 @@ def test_requests_use_the_current_cloud(sdf, world):
     assert np.array_equal(da.view(np.uint32), _alone(sdf, ctx, robot, q, a)[0].view(np.uint32))
     assert np.array_equal(db.view(np.uint32), _alone(sdf, ctx, robot, q, b)[0].view(np.uint32))
     srv.close()
+
+
+def test_surrogate_form_results_equal_alone(sdf, world):
+    ctx, arms = world
+    sc, robot = arms[0]
+    grids = robot.grids
+    sur = sdf.Surrogate(ctx, grids, sg.mlp_init(51, sc.dof + 1))
+    rng = np.random.default_rng(45)
+    pts = sg.cloud_uniform(rng, 2000).astype(np.float32)
+    margin, eps = 0.05, 0.3
+    srv = sdf.Server(0, slots=2, max_batch=4, max_waypoints=4096, max_points=5000, max_dof=7)
+    srv.set_surrogate(sur, margin, eps)
+    srv.set_cloud(pts)
+    jobs = []
+    for i in range(12):
+        q = sg.spline_trajectory(rng, sc.dh, 3, int(rng.integers(1, 300))).astype(np.float32)
+        jobs.append((q, srv.submit(robot, q)))
+    for q, t in jobs:
+        rc, d, l, p, _ = srv.poll(t, wait_us=-1)
+        assert rc == sdf.SDF_OK
+        W = len(q)
+        out = [torch.empty(W, dtype=dt, device="cuda") for dt in (torch.float32, torch.int32, torch.int32)]
+        sdf.check_trajectory_surrogate(ctx, robot, sur, torch.tensor(q, device="cuda"), W,
+                                       torch.tensor(pts, device="cuda"), len(pts), margin, eps, *out)
+        assert ctx.synchronize() == 0
+        assert np.array_equal(d.view(np.uint32), out[0].cpu().numpy().view(np.uint32))
+        assert np.array_equal(l, out[1].cpu().numpy()) and np.array_equal(p, out[2].cpu().numpy())
+    srv.set_surrogate(None)
+    srv.close()
