@@ -37,6 +37,7 @@ SDF_OPT_WAYPOINTS_PER_BLOCK = 3
 SDF_OPT_TILE_BATCH = 4
 SDF_OPT_TIME_KERNELS = 6
 SDF_OPT_STATS = 7
+SDF_OPT_BLOCK_WARPS = 8
 SDF_KERNEL_PREP = 0
 SDF_KERNEL_CHECK = 1
 

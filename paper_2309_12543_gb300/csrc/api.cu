@@ -156,6 +156,10 @@ int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t v) {
             ctx->tile_batch = (int)v;
             return SDF_OK;
         case SDF_OPT_TIME_KERNELS: ctx->time_kernels = v ? 1 : 0; return SDF_OK;
+        case SDF_OPT_BLOCK_WARPS:
+            if (v != 0 && v != 8 && v != 16) return fail(ctx, SDF_ERR_INVALID_ARG, "block warps must be 0, 8 or 16");
+            ctx->block_warps = (int)v;
+            return SDF_OK;
         case SDF_OPT_STATS:
             if (v && !ctx->d_stats) {
                 DeviceGuard g(ctx->device);
@@ -179,6 +183,7 @@ int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* v) {
         case SDF_OPT_TILE_BATCH: *v = ctx->tile_batch; return SDF_OK;
         case SDF_OPT_TIME_KERNELS: *v = ctx->time_kernels; return SDF_OK;
         case SDF_OPT_STATS: *v = ctx->stats; return SDF_OK;
+        case SDF_OPT_BLOCK_WARPS: *v = ctx->block_warps; return SDF_OK;
         default: return SDF_ERR_INVALID_ARG;
     }
 }
@@ -690,16 +695,29 @@ static uint64_t shape_key(const sdf_check_request* reqs, int n) {
     return (k << 40) | (L << 32) | (lg(W) << 16) | lg(N);
 }
 
-// Waypoints per check block for a robot with L links (one warp per waypoint and
-// link) and list entries per warp step: explicit options first, then a tuned
-// configuration for this launch shape, then the defaults.
-static void launch_shape(const sdf_ctx* ctx, uint64_t key, int L, int* tw, int* tb) {
-    const int fit = std::max(1, sdf::kCheckWarps / L);
+// Warps per check block for a launch whose largest robot has Lmax links: the
+// option, else the tuned value for this shape, else 8 (smaller blocks balance
+// uneven waypoints better); 8 only when a waypoint's links fit (one warp per
+// waypoint and link).
+static int launch_warps(const sdf_ctx* ctx, uint64_t key, int Lmax) {
+    int nw = ctx->block_warps;
+    if (nw == 0) {
+        auto it = ctx->tuned.find(key);
+        nw = it != ctx->tuned.end() ? it->second.nw : 8;
+    }
+    return (nw == 8 && Lmax <= 8) ? 8 : 16;
+}
+
+// Waypoints per check block for a robot with L links in blocks of nw warps, and
+// list entries per warp step: explicit options first, then a tuned configuration
+// for this launch shape, then the defaults.
+static void launch_shape(const sdf_ctx* ctx, uint64_t key, int L, int nw, int* tw, int* tb) {
+    const int fit = std::max(1, nw / L);
     int t = ctx->tw, b = ctx->tile_batch;
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) {
-        if (t == 0) t = it->second.first;
-        if (b == 0) b = it->second.second;
+        if (t == 0) t = it->second.tw;
+        if (b == 0) b = it->second.tb;
     }
     *tw = t > 0 ? std::min(t, fit) : fit;
     *tb = b > 0 ? b : sdf::kDefaultTileBatch;
@@ -718,6 +736,10 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     const uint64_t key = shape_key(reqs, n);
     int tile_batch = sdf::kDefaultTileBatch;
     size_t points = 0, tiles = 0, supers = 0, blocks = 0, max_tiles = 0;
+    int Lmax = 1;
+    for (int i = 0; i < n; ++i)
+        if (reqs[i].W > 0) Lmax = std::max(Lmax, reqs[i].robot->table.L);
+    const int nw = launch_warps(ctx, key, Lmax);
     int k = 0, nc = 0;
     for (int i = 0; i < n; ++i) {
         const sdf_check_request& r = reqs[i];
@@ -749,7 +771,7 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
         I.dof = r.robot->dof;
         I.cloud = c;
         I.mask = r.mask_dev;
-        launch_shape(ctx, key, I.L, &I.tw, &tile_batch);
+        launch_shape(ctx, key, I.L, nw, &I.tw, &tile_batch);
         I.block_base = (int)blocks;
         blocks += ((size_t)r.W + I.tw - 1) / I.tw;
     }
@@ -770,6 +792,7 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     p->cull = ctx->cull;
     p->stage_tiles = (int)std::min<size_t>(max_tiles, (size_t)sdf::kMaxStagedTiles);
     p->skip_prep = ctx->reuse_sort;
+    p->warps = nw;
     p->sorted = ctx->sorted;
     p->tiles = ctx->tiles;
     p->supers = ctx->supers;
@@ -800,20 +823,27 @@ int sdf_autotune(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n, int32_t
     }
     DeviceGuard g(ctx->device);
     const uint64_t key = shape_key(reqs, n);
-    const int save_tw = ctx->tw, save_tb = ctx->tile_batch, save_time = ctx->time_kernels;
+    const int save_tw = ctx->tw, save_tb = ctx->tile_batch, save_time = ctx->time_kernels,
+              save_nw = ctx->block_warps;
     ctx->time_kernels = 0;
     ctx->tuned.erase(key);
     cudaEvent_t a = nullptr, b = nullptr;
     SDF_CUDA(ctx, cudaEventCreate(&a));
     SDF_CUDA(ctx, cudaEventCreate(&b));
     float best = INFINITY;
-    int btw = 0, btb = 0, rc = SDF_OK;
+    int btw = 0, btb = 0, bnw = 16, rc = SDF_OK;
     const int tbs[3] = {2, 4, 8};
-    const int fit = std::max(1, sdf::kCheckWarps / Lmin);
-    for (int tw = 1; tw <= fit && rc == SDF_OK; ++tw) {
+    int Lmax = 1;
+    for (int i = 0; i < n; ++i)
+        if (reqs[i].W > 0) Lmax = std::max(Lmax, reqs[i].robot->table.L);
+    for (int nw = 16; nw >= 8 && rc == SDF_OK; nw -= 8) {
+      if (nw == 8 && Lmax > 8) break;
+      const int fit = std::max(1, nw / Lmin);
+      for (int tw = 1; tw <= fit && rc == SDF_OK; ++tw) {
         for (int tb : tbs) {
             ctx->tw = tw;
             ctx->tile_batch = tb;
+            ctx->block_warps = nw;
             rc = check_batch(ctx, reqs, n);   // warm-up, grows scratch if needed
             std::vector<float> ms;
             for (int r = 0; r < repeats && rc == SDF_OK; ++r) {
@@ -831,16 +861,19 @@ int sdf_autotune(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n, int32_t
                 best = med;
                 btw = tw;
                 btb = tb;
+                bnw = nw;
             }
         }
+      }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     ctx->tw = save_tw;
     ctx->tile_batch = save_tb;
     ctx->time_kernels = save_time;
+    ctx->block_warps = save_nw;
     if (rc != SDF_OK) return rc;
-    ctx->tuned[key] = std::make_pair(btw, btb);
+    ctx->tuned[key] = sdf_ctx::Shape{btw, btb, bnw};
     if (best_tw) *best_tw = btw;
     if (best_tile_batch) *best_tile_batch = btb;
     if (best_us) *best_us = best * 1e3f;

@@ -1,9 +1,10 @@
 // Runtime distance check for sm_103a, for one trajectory or a batch of them.
 // Two kernels per launch:
 //
-// prep_kernel -- one thread-block cluster (8 CTAs x 1024 threads) per trajectory
-//   sorts its obstacle points in space: bounding box, 32^3-cell Morton key,
-//   counting sort in distributed shared memory, scatter into float4 (x, y, z,
+// prep_kernel -- one thread-block cluster (8 CTAs x 1024 threads) per cloud sorts
+//   its obstacle points in space: bounding box (shared through distributed shared
+//   memory), 16^3-cell Morton key, a full counting-sort histogram in every CTA's
+//   shared memory, each CTA scattering its own run of cells into float4 (x, y, z,
 //   original index); then a bounding sphere per tile of 32 sorted points and per
 //   super-tile of 32 tiles.  Non-finite points are dropped (and flagged).
 // check_kernel -- one block per (trajectory, group of waypoints); the trajectory's
@@ -47,11 +48,13 @@ using namespace dev;
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kOrderedInf = 0xff800000u;   // ordered_bits(+inf): "no value yet"
-constexpr int kCells = 32768;                       // 32^3 Morton cells for the cloud sort
+constexpr int kCellsPerAxis = 16;
+constexpr int kCells = kCellsPerAxis * kCellsPerAxis * kCellsPerAxis;   // Morton cells of the cloud sort
 constexpr int kPrepThreads = 1024;
 constexpr int kPrepCtas = 8;                        // one portable-size cluster
-constexpr int kBinsPerCta = kCells / kPrepCtas;
-constexpr int kPrepCached = 4;                      // points per thread kept in registers
+constexpr int kPrepKeyCache = 65536;                // points whose cell keys fit shared memory
+constexpr int kPrepChunk = 8;                       // points a thread loads before using them
+constexpr size_t kPrepSmem = kCells * sizeof(unsigned) + kPrepKeyCache * sizeof(unsigned short);
 
 // Affine 3x4 composition C = X * Y (row-major, implicit last row 0 0 0 1).
 __device__ __forceinline__ void affine_mul(const float* X, const float* Y, float* C) {
@@ -153,28 +156,12 @@ __device__ __forceinline__ unsigned spread5(unsigned v) {
 }
 
 __device__ __forceinline__ unsigned cell_key(float3 p, float3 lo, float3 inv) {
-    const int ix = min(max((int)((p.x - lo.x) * inv.x), 0), 31);
-    const int iy = min(max((int)((p.y - lo.y) * inv.y), 0), 31);
-    const int iz = min(max((int)((p.z - lo.z) * inv.z), 0), 31);
+    const int ix = min(max((int)((p.x - lo.x) * inv.x), 0), kCellsPerAxis - 1);
+    const int iy = min(max((int)((p.y - lo.y) * inv.y), 0), kCellsPerAxis - 1);
+    const int iz = min(max((int)((p.z - lo.z) * inv.z), 0), kCellsPerAxis - 1);
     return spread5((unsigned)ix) | (spread5((unsigned)iy) << 1) | (spread5((unsigned)iz) << 2);
 }
 
-template <typename Op>
-__device__ __forceinline__ float block_reduce(float v, float* s_tmp, Op op) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(kFull, v, o));
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) s_tmp[warp] = v;
-    __syncthreads();
-    v = s_tmp[lane];   // kPrepThreads / 32 == 32 partials
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-
-struct FMin { __device__ float operator()(float a, float b) const { return fminf(a, b); } };
-struct FMax { __device__ float operator()(float a, float b) const { return fmaxf(a, b); } };
 
 
 // ------------------------------------------------------------------ prep kernel
@@ -185,11 +172,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-
-// One cluster per cloud sorts it: 32^3 cell counters spread over the
-// CTAs' shared memory, every phase one pass over the points with cluster barriers
-// in between; up to kPrepCached points per thread stay in registers between the
-// passes.
+// One cluster of kPrepCtas CTAs per cloud sorts it by 16^3-cell Morton key.  The
+// CTAs share the bounding box through distributed shared memory; then each builds
+// the full histogram of the cloud in its own shared memory (no remote atomics),
+// scans it, and scatters the cells that start in its eighth of the sorted order.
+// Three cluster barriers in all.
 __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads, 1)
     prep_kernel(const __grid_constant__ BatchParams P) {
     cg::cluster_group cluster = cg::this_cluster();
@@ -198,19 +185,24 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     const CloudDesc& C = P.cloud[cidx];
     // the check grid may start now: its set-up reads nothing this kernel writes
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    __shared__ unsigned s_bins[kBinsPerCta];     // counters, then cursors, of this CTA's cells
-    __shared__ float s_tmp[32];
+    // dynamic shared memory: the histogram of all kCells cells (then their offsets,
+    // then their cursors), followed by the points' cell keys when they fit
+    extern __shared__ unsigned s_prep[];
+    unsigned* bins = s_prep;
+    unsigned short* keys = reinterpret_cast<unsigned short*>(s_prep + kCells);
+    __shared__ float s_box6[32][6];
     __shared__ float s_box[6];
     __shared__ unsigned s_tot[32];
-    __shared__ unsigned s_cta_total;
+    __shared__ unsigned s_range[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gtid = (int)rank * kPrepThreads + tid;
     constexpr int kStride = kPrepCtas * kPrepThreads;
     constexpr int kClusterWarps = kPrepCtas * (kPrepThreads / 32);
+    constexpr unsigned short kNoKey = 0xffffu;   // cell keys are 12 bits
     const float kInf = __int_as_float(0x7f800000);
     const int N = C.N;
     const float* pts = C.points;
-    const bool cached = N <= kStride * kPrepCached;
+    const bool key_cache = N <= kPrepKeyCache;
     // phase timestamps of the first CTA (SDF_OPT_STATS)
     const bool clock = P.stats != nullptr && rank == 0 && tid == 0;
     unsigned long long t_mark = clock ? global_ns() : 0ull;
@@ -222,44 +214,38 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         }
     };
 
-    float3 pc[kPrepCached];
-#pragma unroll
-    for (int k = 0; k < kPrepCached; ++k) {
-        const int i = gtid + k * kStride;
-        pc[k] = (cached && i < N) ? load_point(pts, P.stride, i) : make_float3(0.f, 0.f, 0.f);
-    }
-
-    auto for_each_point = [&](auto&& f) {
-        if (cached) {
-#pragma unroll
-            for (int k = 0; k < kPrepCached; ++k) {
-                const int i = gtid + k * kStride;
-                if (i < N) f(pc[k], i);
-            }
-        } else {
-            for (int i = gtid; i < N; i += kStride) f(load_point(pts, P.stride, i), i);
-        }
-    };
-
-    // 1. bounding box of the finite points (per CTA, then across the cluster)
+    // 1. bounding box of the finite points: this CTA's share, then across the cluster
     float lo[3] = {kInf, kInf, kInf}, hi[3] = {-kInf, -kInf, -kInf};
     bool bad = false;
-    for_each_point([&](float3 p, int) {
+    for (int i = gtid; i < N; i += kStride) {
+        const float3 p = load_point(pts, P.stride, i);
         if (finite3(p)) {
             lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
             hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
         } else {
             bad = true;
         }
-    });
-    if (__syncthreads_or(bad) && tid == 0) atomicOr(P.status, kStatusNonFinite);
-    const float r0 = block_reduce(lo[0], s_tmp, FMin()), r1 = block_reduce(lo[1], s_tmp, FMin());
-    const float r2 = block_reduce(lo[2], s_tmp, FMin()), r3 = block_reduce(hi[0], s_tmp, FMax());
-    const float r4 = block_reduce(hi[1], s_tmp, FMax()), r5 = block_reduce(hi[2], s_tmp, FMax());
-    if (tid == 0) {
-        s_box[0] = r0; s_box[1] = r1; s_box[2] = r2; s_box[3] = r3; s_box[4] = r4; s_box[5] = r5;
     }
-    for (int b = tid; b < kBinsPerCta; b += kPrepThreads) s_bins[b] = 0u;
+    // the six extremes at once: maxima as negated minima, warp then CTA
+    float e6[6] = {lo[0], lo[1], lo[2], -hi[0], -hi[1], -hi[2]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) e6[a] = fminf(e6[a], __shfl_xor_sync(kFull, e6[a], o));
+    if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) s_box6[warp][a] = e6[a];
+    for (int b = tid; b < kCells; b += kPrepThreads) bins[b] = 0u;
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(P.status, kStatusNonFinite);
+    if (warp == 0) {
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            float v = s_box6[lane][a];   // kPrepThreads / 32 == 32 partials
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+            if (lane == 0) s_box[a] = a < 3 ? v : -v;
+        }
+    }
     cluster.sync();
     float3 blo = make_float3(kInf, kInf, kInf), bhi = make_float3(-kInf, -kInf, -kInf);
 #pragma unroll
@@ -268,34 +254,49 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         blo.x = fminf(blo.x, b[0]); blo.y = fminf(blo.y, b[1]); blo.z = fminf(blo.z, b[2]);
         bhi.x = fmaxf(bhi.x, b[3]); bhi.y = fmaxf(bhi.y, b[4]); bhi.z = fmaxf(bhi.z, b[5]);
     }
-    const float3 inv = make_float3(32.f / fmaxf(bhi.x - blo.x, 1e-6f), 32.f / fmaxf(bhi.y - blo.y, 1e-6f),
-                                   32.f / fmaxf(bhi.z - blo.z, 1e-6f));
+    constexpr float kAxis = (float)kCellsPerAxis;
+    const float3 inv = make_float3(kAxis / fmaxf(bhi.x - blo.x, 1e-6f), kAxis / fmaxf(bhi.y - blo.y, 1e-6f),
+                                   kAxis / fmaxf(bhi.z - blo.z, 1e-6f));
     mark(20);
 
-    // 2. histogram: cell c is counted in CTA c / kBinsPerCta
-    for_each_point([&](float3 p, int) {
-        if (finite3(p)) {
-            const unsigned c = cell_key(p, blo, inv);
-            atomicAdd(cluster.map_shared_rank(&s_bins[c % kBinsPerCta], (int)(c / kBinsPerCta)), 1u);
+    // 2. every CTA counts every point into its own full histogram (shared-memory
+    //    atomics only; the CTAs compute identical histograms)
+    for (int i0 = tid; i0 < N; i0 += kPrepThreads * kPrepChunk) {
+        float3 pv[kPrepChunk];   // all loads of the chunk in flight before the first use
+#pragma unroll
+        for (int k = 0; k < kPrepChunk; ++k) {
+            const int i = i0 + k * kPrepThreads;
+            pv[k] = i < N ? load_point(pts, P.stride, i) : make_float3(0.f, 0.f, 0.f);
         }
-    });
-    cluster.sync();
+#pragma unroll
+        for (int k = 0; k < kPrepChunk; ++k) {
+            const int i = i0 + k * kPrepThreads;
+            if (i >= N) break;
+            unsigned short kk = kNoKey;
+            if (finite3(pv[k])) {
+                const unsigned c = cell_key(pv[k], blo, inv);
+                atomicAdd(&bins[c], 1u);
+                kk = (unsigned short)c;
+            }
+            if (key_cache) keys[i] = kk;
+        }
+    }
+    __syncthreads();
     mark(21);
 
-    // 3. exclusive scan of this CTA's cells (warp w owns a contiguous run), then
-    //    the CTA totals of lower ranks give the CTA's offset
-    constexpr int kPerWarp = kBinsPerCta / (kPrepThreads / 32);
+    // 3. exclusive scan of the cells (warp w owns a contiguous run of them)
+    constexpr int kPerWarp = kCells / (kPrepThreads / 32);
     unsigned running = 0;
     for (int k = 0; k < kPerWarp; k += 32) {
         const int idx = warp * kPerWarp + k + lane;
-        const unsigned c = s_bins[idx];
+        const unsigned c = bins[idx];
         unsigned incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned v = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += v;
         }
-        s_bins[idx] = running + incl - c;
+        bins[idx] = running + incl - c;
         running += __shfl_sync(kFull, incl, 31);
     }
     if (lane == 0) s_tot[warp] = running;
@@ -309,32 +310,69 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
             if (lane >= o) ti += v;
         }
         s_tot[lane] = ti - t;
-        if (lane == 31) s_cta_total = ti;
+        if (lane == 31) s_tot[0] = ti;   // lane 0's exclusive prefix is 0: keep the total there
     }
-    cluster.sync();
-    unsigned prefix = 0, total = 0;
-#pragma unroll
-    for (int r = 0; r < kPrepCtas; ++r) {
-        const unsigned t = *cluster.map_shared_rank(&s_cta_total, r);
-        prefix += (r < (int)rank) ? t : 0u;
-        total += t;
-    }
-    const unsigned off = prefix + s_tot[warp];
-    for (int k = 0; k < kPerWarp; k += 32) s_bins[warp * kPerWarp + k + lane] += off;
+    __syncthreads();
+    const unsigned total = s_tot[0];
+    const unsigned off = warp == 0 ? 0u : s_tot[warp];
+    __syncthreads();
+    for (int k = 0; k < kPerWarp; k += 32) bins[warp * kPerWarp + k + lane] += off;
+    __syncthreads();
     const int n_valid = (int)total;
-    cluster.sync();
+    // this CTA scatters the cells whose first position lies in its eighth of the
+    // sorted order: cells [c_lo, c_hi), found by binary search on the offsets
+    if (tid < 2) {
+        const unsigned target = (unsigned)(((unsigned long long)total * (rank + tid)) / kPrepCtas);
+        unsigned a = 0, b = kCells;   // first cell whose offset >= target
+        if (rank + tid >= kPrepCtas) a = kCells;
+        while (a < b) {
+            const unsigned m = (a + b) >> 1;
+            if (bins[m] < target) a = m + 1; else b = m;
+        }
+        s_range[tid] = a;
+    }
+    __syncthreads();
+    const unsigned c_lo = s_range[0], c_hi = s_range[1];
     mark(22);
 
-    // 4. scatter (order inside a cell is arbitrary; keys carry the original index)
+    // 4. scatter this CTA's cells (order inside a cell is arbitrary; the w
+    //    component carries the original index)
     float4* sorted = P.sorted + C.point_base;
-    for_each_point([&](float3 p, int i) {
-        if (finite3(p)) {
-            const unsigned c = cell_key(p, blo, inv);
-            const unsigned pos = atomicAdd(cluster.map_shared_rank(&s_bins[c % kBinsPerCta], (int)(c / kBinsPerCta)), 1u);
-            sorted[pos] = make_float4(p.x, p.y, p.z, __int_as_float(i));
+    for (int i0 = tid; i0 < N; i0 += kPrepThreads * kPrepChunk) {
+        unsigned cv[kPrepChunk];
+        float3 pv[kPrepChunk];
+#pragma unroll
+        for (int k = 0; k < kPrepChunk; ++k) {   // this CTA's points of the chunk, loads in flight
+            const int i = i0 + k * kPrepThreads;
+            cv[k] = 0xffffffffu;
+            pv[k] = make_float3(0.f, 0.f, 0.f);
+            if (i < N) {
+                if (key_cache) {
+                    const unsigned kk = keys[i];
+                    if (kk != kNoKey && kk >= c_lo && kk < c_hi) {
+                        cv[k] = kk;
+                        pv[k] = load_point(pts, P.stride, i);
+                    }
+                } else {
+                    pv[k] = load_point(pts, P.stride, i);
+                }
+            }
         }
-    });
-    cluster.sync();   // orders the scatter before the reads below (cluster scope)
+#pragma unroll
+        for (int k = 0; k < kPrepChunk; ++k) {
+            const int i = i0 + k * kPrepThreads;
+            if (i >= N) break;
+            unsigned c = cv[k];
+            if (!key_cache && finite3(pv[k])) {
+                const unsigned kk = cell_key(pv[k], blo, inv);
+                if (kk >= c_lo && kk < c_hi) c = kk;
+            }
+            if (c == 0xffffffffu) continue;
+            const unsigned pos = atomicAdd(&bins[c], 1u);
+            sorted[pos] = make_float4(pv[k].x, pv[k].y, pv[k].z, __int_as_float(i));
+        }
+    }
+    cluster.sync();   // orders every CTA's scatter before the reads below (cluster scope)
     mark(23);
 
     // 5. tile spheres: centre of the tile's box, radius to its farthest point
@@ -546,20 +584,21 @@ __device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, co
 }
 
 // TB: list entries a warp takes per step in phase B (their point loads go out together).
-template <int TB>
-__global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid_constant__ BatchParams P) {
+// NW: warps per block (8 or 16); at 64 registers a thread, 32 / NW blocks fit an SM.
+template <int TB, int NW>
+__global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_constant__ BatchParams P) {
     extern __shared__ float4 s_spheres[];            // tiles [stage_tiles], then super-tiles
-    __shared__ float4 s_pose[kCheckWarps][6];
+    __shared__ float4 s_pose[NW][6];
     __shared__ float4 s_grid_o[kMaxLinks];
     __shared__ float s_grid_h[kMaxLinks];
-    __shared__ unsigned s_best[kCheckWarps];
-    __shared__ unsigned long long s_key[kCheckWarps];
+    __shared__ unsigned s_best[NW];
+    __shared__ unsigned long long s_key[NW];
     __shared__ unsigned s_list[kBlockList];
     __shared__ unsigned s_list_n, s_list_next;
-    __shared__ uint2 s_queue[kCheckWarps][64];
+    __shared__ uint2 s_queue[NW][64];
     __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ unsigned s_stat[kCheckWarps][kWsCount];
-    __shared__ unsigned long long s_stat_ns[kCheckWarps][kWnCount];
+    __shared__ unsigned s_stat[NW][kWsCount];
+    __shared__ unsigned long long s_stat_ns[NW][kWnCount];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool stats = P.stats != nullptr;
@@ -586,7 +625,7 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
         const bool any = tid < nw && I.mask[w0 + tid] != 0;
         if (!__syncthreads_or(any)) return;
     }
-    if (tid < kCheckWarps) {
+    if (tid < NW) {
         s_best[tid] = kOrderedInf;
         s_key[tid] = ~0ull;
     }
@@ -793,12 +832,12 @@ __global__ void __launch_bounds__(kCheckWarps * 32, 2) check_kernel(const __grid
         // block sums of the warp rows, one global atomic per counter
         if (tid < kWsCount) {
             unsigned long long v = 0;
-            for (int k = 0; k < kCheckWarps; ++k) v += s_stat[k][tid];
+            for (int k = 0; k < NW; ++k) v += s_stat[k][tid];
             const int dst[kWsCount] = {1, 2, 3, 4, 5, 6, 7, 8};
             atomicAdd(&P.stats[dst[tid]], v);
         } else if (tid >= 32 && tid < 32 + kWnCount) {
             unsigned long long v = 0;
-            for (int k = 0; k < kCheckWarps; ++k) v += s_stat_ns[k][tid - 32];
+            for (int k = 0; k < NW; ++k) v += s_stat_ns[k][tid - 32];
             atomicAdd(&P.stats[11 + (tid - 32)], v);
         } else if (tid == 64) {
             const unsigned long long t_end = global_ns();
@@ -860,9 +899,12 @@ size_t staged_bytes(int stage_tiles) {
 
 cudaError_t configure_kernels() {
     const int smem = (int)staged_bytes(kMaxStagedTiles);
-    cudaError_t e = cudaFuncSetAttribute(check_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(check_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(check_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const void* fns[6] = {(const void*)check_kernel<2, 16>, (const void*)check_kernel<4, 16>,
+                          (const void*)check_kernel<8, 16>, (const void*)check_kernel<2, 8>,
+                          (const void*)check_kernel<4, 8>,  (const void*)check_kernel<8, 8>};
+    cudaError_t e = cudaFuncSetAttribute(prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmem);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+        e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
@@ -870,7 +912,7 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
     if (p.n_inst <= 0 || p.n_blocks <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     if (!p.skip_prep) {
-        prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, 0, s>>>(p);
+        prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, kPrepSmem, s>>>(p);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -882,7 +924,8 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
     // runs its forward kinematics, then waits (griddepcontrol.wait) for the sort
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)p.n_blocks);
-    cfg.blockDim = dim3(kCheckWarps * 32);
+    const int nw = p.warps == 8 ? 8 : 16;
+    cfg.blockDim = dim3(nw * 32);
     cfg.dynamicSmemBytes = staged_bytes(p.stage_tiles);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -890,17 +933,20 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = (ev_mid || p.skip_prep) ? 0 : 1;
-    switch (tile_batch) {
-        case 2: return cudaLaunchKernelEx(&cfg, check_kernel<2>, p);
-        case 4: return cudaLaunchKernelEx(&cfg, check_kernel<4>, p);
-        case 8: return cudaLaunchKernelEx(&cfg, check_kernel<8>, p);
+    switch (tile_batch * 100 + nw) {
+        case 216: return cudaLaunchKernelEx(&cfg, check_kernel<2, 16>, p);
+        case 416: return cudaLaunchKernelEx(&cfg, check_kernel<4, 16>, p);
+        case 816: return cudaLaunchKernelEx(&cfg, check_kernel<8, 16>, p);
+        case 208: return cudaLaunchKernelEx(&cfg, check_kernel<2, 8>, p);
+        case 408: return cudaLaunchKernelEx(&cfg, check_kernel<4, 8>, p);
+        case 808: return cudaLaunchKernelEx(&cfg, check_kernel<8, 8>, p);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_prep(const BatchParams& p, cudaStream_t s) {
     if (p.n_cloud <= 0) return cudaSuccess;
-    prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, 0, s>>>(p);
+    prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, kPrepSmem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ constexpr int kMaxLinks = SDF_MAX_LINKS;
 // the transform, the sphere centre and the interpolation (~1e-6 m).
 constexpr float kCullSlack = 1e-4f;
 constexpr int kMaxBatch = 128;            // trajectories per launch (kernel-parameter table)
-constexpr int kCheckWarps = 16;           // warps per check block
+constexpr int kCheckWarps = 16;           // warps per check block (the larger of the two shapes)
 constexpr int kDefaultTileBatch = 4;      // (pair, tile) entries per warp step (2, 4 or 8)
 constexpr int kBlockList = 2048;          // (pair, tile) entries a block can queue in shared memory
 constexpr int kMaxStagedTiles = 4096;     // tile spheres a block can stage in shared memory
@@ -70,6 +70,7 @@ struct BatchParams {
     int cull;                 // 0: evaluate every pair
     int stage_tiles;          // tile spheres the dynamic shared memory holds (0: no staging)
     int skip_prep;            // the clouds are already sorted in the scratch: launch the check only
+    int warps;                // warps per check block: 8 or 16
     float4* sorted;           // finite points, spatially sorted: x, y, z, original index bits
     float4* tiles;            // sphere of each 32-point tile
     float4* supers;           // sphere of each 32-tile super-tile
@@ -138,7 +139,9 @@ struct sdf_ctx {
     int tw = 0;                            // waypoints per check block (0: tuned or as many as fit)
     int tile_batch = 0;                    // list entries per warp step (0: tuned or 4)
     int reuse_sort = 0;                    // internal: the next check reuses the scratch's sorted cloud
-    std::map<uint64_t, std::pair<int, int>> tuned;   // launch shape key -> (tw, tile batch)
+    int block_warps = 0;                   // warps per check block (0: tuned or 16)
+    struct Shape { int tw, tb, nw; };
+    std::map<uint64_t, Shape> tuned;       // launch shape key -> (waypoints per block, tile batch, warps)
     // scratch owned by the context (grown on demand, or up front by sdf_ctx_reserve)
     float4* sorted = nullptr;
     size_t sorted_cap = 0;

@@ -108,6 +108,7 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         p.cull = 1;
         p.stage_tiles = n_tiles < sdf::kMaxStagedTiles ? n_tiles : sdf::kMaxStagedTiles;
         p.skip_prep = 0;
+        p.warps = 16;
         p.sorted = reinterpret_cast<float4*>(base + kSortedOff);
         p.tiles = reinterpret_cast<float4*>(base + kTilesOff);
         p.supers = reinterpret_cast<float4*>(base + kSupersOff);
