@@ -3,9 +3,9 @@
 //
 // prep_kernel -- one thread-block cluster (8 CTAs x 1024 threads) per cloud sorts
 //   its obstacle points in space: bounding box (shared through distributed shared
-//   memory), 16^3-cell Morton key, a full counting-sort histogram in every CTA's
-//   shared memory, each CTA scattering its own run of cells into float4 (x, y, z,
-//   original index); then a bounding sphere per tile of 32 sorted points and per
+//   memory), 16^3-cell Morton key, a counting sort whose partial histograms meet
+//   through distributed shared memory, each CTA scattering its own points into
+//   float4 (x, y, z, original index); then a bounding sphere per tile of 32 sorted points and per
 //   super-tile of 32 tiles.  Non-finite points are dropped (and flagged).
 // check_kernel -- one block per (trajectory, group of waypoints); the trajectory's
 //   tile and super-tile spheres reach shared memory by one TMA bulk copy that
@@ -52,9 +52,7 @@ constexpr int kCellsPerAxis = 16;
 constexpr int kCells = kCellsPerAxis * kCellsPerAxis * kCellsPerAxis;   // Morton cells of the cloud sort
 constexpr int kPrepThreads = 1024;
 constexpr int kPrepCtas = 8;                        // one portable-size cluster
-constexpr int kPrepKeyCache = 65536;                // points whose cell keys fit shared memory
-constexpr int kPrepChunk = 8;                       // points a thread loads before using them
-constexpr size_t kPrepSmem = kCells * sizeof(unsigned) + kPrepKeyCache * sizeof(unsigned short);
+constexpr int kPrepChunk = 4;                       // points a thread loads before using them
 
 // Affine 3x4 composition C = X * Y (row-major, implicit last row 0 0 0 1).
 __device__ __forceinline__ void affine_mul(const float* X, const float* Y, float* C) {
@@ -172,11 +170,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// One cluster of kPrepCtas CTAs per cloud sorts it by 16^3-cell Morton key.  The
-// CTAs share the bounding box through distributed shared memory; then each builds
-// the full histogram of the cloud in its own shared memory (no remote atomics),
-// scans it, and scatters the cells that start in its eighth of the sorted order.
-// Three cluster barriers in all.
+// One cluster of kPrepCtas CTAs per cloud sorts it by 16^3-cell Morton key, a
+// counting sort without remote atomics: each CTA histograms its share of the points
+// in its own shared memory; every CTA then reads the eight partial histograms
+// through distributed shared memory, which gives each cell's start and this CTA's
+// first slot in it; each CTA scatters its own points with local atomics.
 __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads, 1)
     prep_kernel(const __grid_constant__ BatchParams P) {
     cg::cluster_group cluster = cg::this_cluster();
@@ -185,24 +183,20 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     const CloudDesc& C = P.cloud[cidx];
     // the check grid may start now: its set-up reads nothing this kernel writes
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    // dynamic shared memory: the histogram of all kCells cells (then their offsets,
-    // then their cursors), followed by the points' cell keys when they fit
-    extern __shared__ unsigned s_prep[];
-    unsigned* bins = s_prep;
-    unsigned short* keys = reinterpret_cast<unsigned short*>(s_prep + kCells);
+    // this CTA's histogram of its share of the points, then its scatter cursors
+    __shared__ __align__(16) unsigned bins[kCells];
     __shared__ float s_box6[32][6];
-    __shared__ float s_box[6];
-    __shared__ unsigned s_tot[32];
-    __shared__ unsigned s_range[2];
+    __shared__ __align__(16) float s_box[8];
+    __shared__ float s_gbox[6];
+    __shared__ unsigned s_warp_total[32];
+    __shared__ unsigned s_cloud_total;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gtid = (int)rank * kPrepThreads + tid;
     constexpr int kStride = kPrepCtas * kPrepThreads;
     constexpr int kClusterWarps = kPrepCtas * (kPrepThreads / 32);
-    constexpr unsigned short kNoKey = 0xffffu;   // cell keys are 12 bits
     const float kInf = __int_as_float(0x7f800000);
     const int N = C.N;
     const float* pts = C.points;
-    const bool key_cache = N <= kPrepKeyCache;
     // phase timestamps of the first CTA (SDF_OPT_STATS)
     const bool clock = P.stats != nullptr && rank == 0 && tid == 0;
     unsigned long long t_mark = clock ? global_ns() : 0ull;
@@ -247,155 +241,159 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         }
     }
     cluster.sync();
-    float3 blo = make_float3(kInf, kInf, kInf), bhi = make_float3(-kInf, -kInf, -kInf);
+    // lane r < kPrepCtas of warp 0 reads rank r's box; the cluster's box goes to all
+    // threads through this CTA's shared memory
+    if (warp == 0) {
+        float g[6] = {kInf, kInf, kInf, kInf, kInf, kInf};   // minima and negated maxima
+        if (lane < kPrepCtas) {
+            const float4* b = reinterpret_cast<const float4*>(cluster.map_shared_rank(s_box, lane));
+            const float4 b0 = b[0], b1 = b[1];
+            g[0] = b0.x; g[1] = b0.y; g[2] = b0.z; g[3] = -b0.w; g[4] = -b1.x; g[5] = -b1.y;
+        }
 #pragma unroll
-    for (int r = 0; r < kPrepCtas; ++r) {
-        const float* b = cluster.map_shared_rank(s_box, r);
-        blo.x = fminf(blo.x, b[0]); blo.y = fminf(blo.y, b[1]); blo.z = fminf(blo.z, b[2]);
-        bhi.x = fmaxf(bhi.x, b[3]); bhi.y = fmaxf(bhi.y, b[4]); bhi.z = fmaxf(bhi.z, b[5]);
+        for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+            for (int a = 0; a < 6; ++a) g[a] = fminf(g[a], __shfl_xor_sync(kFull, g[a], o));
+        if (lane == 0)
+#pragma unroll
+            for (int a = 0; a < 6; ++a) s_gbox[a] = a < 3 ? g[a] : -g[a];
     }
+    __syncthreads();
+    const float3 blo = make_float3(s_gbox[0], s_gbox[1], s_gbox[2]);
+    const float3 bhi = make_float3(s_gbox[3], s_gbox[4], s_gbox[5]);
     constexpr float kAxis = (float)kCellsPerAxis;
     const float3 inv = make_float3(kAxis / fmaxf(bhi.x - blo.x, 1e-6f), kAxis / fmaxf(bhi.y - blo.y, 1e-6f),
                                    kAxis / fmaxf(bhi.z - blo.z, 1e-6f));
     mark(20);
 
-    // 2. every CTA counts every point into its own full histogram (shared-memory
-    //    atomics only; the CTAs compute identical histograms)
-    for (int i0 = tid; i0 < N; i0 += kPrepThreads * kPrepChunk) {
-        float3 pv[kPrepChunk];   // all loads of the chunk in flight before the first use
+    // 2. each CTA counts its own share of the points (shared-memory atomics); the
+    //    share's cell keys stay in registers for the scatter
+    unsigned kc[kPrepChunk];
+    float3 pv[kPrepChunk];
+    const bool in_regs = N <= kStride * kPrepChunk;
+    auto count_chunk = [&](int i0) {
 #pragma unroll
-        for (int k = 0; k < kPrepChunk; ++k) {
-            const int i = i0 + k * kPrepThreads;
+        for (int k = 0; k < kPrepChunk; ++k) {   // all loads of the chunk in flight before the first use
+            const int i = i0 + k * kStride;
             pv[k] = i < N ? load_point(pts, P.stride, i) : make_float3(0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int k = 0; k < kPrepChunk; ++k) {
-            const int i = i0 + k * kPrepThreads;
-            if (i >= N) break;
-            unsigned short kk = kNoKey;
-            if (finite3(pv[k])) {
-                const unsigned c = cell_key(pv[k], blo, inv);
-                atomicAdd(&bins[c], 1u);
-                kk = (unsigned short)c;
+            const int i = i0 + k * kStride;
+            kc[k] = 0xffffffffu;
+            if (i < N && finite3(pv[k])) {
+                kc[k] = cell_key(pv[k], blo, inv);
+                atomicAdd(&bins[kc[k]], 1u);
             }
-            if (key_cache) keys[i] = kk;
         }
+    };
+    if (in_regs) {
+        count_chunk(gtid);
+    } else {
+        for (int i0 = gtid; i0 < N; i0 += kStride * kPrepChunk) count_chunk(i0);
     }
-    __syncthreads();
+    cluster.sync();
     mark(21);
 
-    // 3. exclusive scan of the cells (warp w owns a contiguous run of them)
-    constexpr int kPerWarp = kCells / (kPrepThreads / 32);
-    unsigned running = 0;
-    for (int k = 0; k < kPerWarp; k += 32) {
-        const int idx = warp * kPerWarp + k + lane;
-        const unsigned c = bins[idx];
-        unsigned incl = c;
+    // 3. every CTA reads the eight partial histograms: the cell totals give each
+    //    cell's start in the sorted order (an exclusive scan), and the lower ranks'
+    //    counts of the same cell give this CTA's first slot in it.  Thread t owns
+    //    cells 4t .. 4t+3 and reads them as one 16-byte word per rank.
+    static_assert(kCells == 4 * kPrepThreads, "four cells per thread");
+    uint4 tot = make_uint4(0u, 0u, 0u, 0u), mine = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned v = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += v;
+    for (int r = 0; r < kPrepCtas; ++r) {
+        const uint4 v = reinterpret_cast<const uint4*>(cluster.map_shared_rank(bins, r))[tid];
+        tot.x += v.x; tot.y += v.y; tot.z += v.z; tot.w += v.w;
+        if (r < (int)rank) {
+            mine.x += v.x; mine.y += v.y; mine.z += v.z; mine.w += v.w;
         }
-        bins[idx] = running + incl - c;
-        running += __shfl_sync(kFull, incl, 31);
     }
-    if (lane == 0) s_tot[warp] = running;
+    cluster.sync();   // every CTA has read every partial histogram before any is rewritten
+    const unsigned own = tot.x + tot.y + tot.z + tot.w;
+    unsigned incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_warp_total[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        const unsigned t = s_tot[lane];
+        const unsigned t = s_warp_total[lane];
         unsigned ti = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned v = __shfl_up_sync(kFull, ti, o);
             if (lane >= o) ti += v;
         }
-        s_tot[lane] = ti - t;
-        if (lane == 31) s_tot[0] = ti;   // lane 0's exclusive prefix is 0: keep the total there
+        s_warp_total[lane] = ti - t;
+        if (lane == 31) s_cloud_total = ti;
     }
     __syncthreads();
-    const unsigned total = s_tot[0];
-    const unsigned off = warp == 0 ? 0u : s_tot[warp];
-    __syncthreads();
-    for (int k = 0; k < kPerWarp; k += 32) bins[warp * kPerWarp + k + lane] += off;
-    __syncthreads();
-    const int n_valid = (int)total;
-    // this CTA scatters the cells whose first position lies in its eighth of the
-    // sorted order: cells [c_lo, c_hi), found by binary search on the offsets
-    if (tid < 2) {
-        const unsigned target = (unsigned)(((unsigned long long)total * (rank + tid)) / kPrepCtas);
-        unsigned a = 0, b = kCells;   // first cell whose offset >= target
-        if (rank + tid >= kPrepCtas) a = kCells;
-        while (a < b) {
-            const unsigned m = (a + b) >> 1;
-            if (bins[m] < target) a = m + 1; else b = m;
-        }
-        s_range[tid] = a;
-    }
-    __syncthreads();
-    const unsigned c_lo = s_range[0], c_hi = s_range[1];
+    const unsigned c0 = s_warp_total[warp] + incl - own;   // start of cell 4t
+    const unsigned c1 = c0 + tot.x, c2 = c1 + tot.y, c3 = c2 + tot.z;
+    reinterpret_cast<uint4*>(bins)[tid] = make_uint4(c0 + mine.x, c1 + mine.y, c2 + mine.z, c3 + mine.w);
+    const unsigned running = s_cloud_total;
+    __syncthreads();   // the cursors are complete before any CTA thread scatters
+    const int n_valid = (int)running;
     mark(22);
 
-    // 4. scatter this CTA's cells (order inside a cell is arbitrary; the w
+    // 4. scatter this CTA's points (order inside a cell is arbitrary; the w
     //    component carries the original index)
     float4* sorted = P.sorted + C.point_base;
-    for (int i0 = tid; i0 < N; i0 += kPrepThreads * kPrepChunk) {
-        unsigned cv[kPrepChunk];
-        float3 pv[kPrepChunk];
+    if (in_regs) {
+        unsigned pos[kPrepChunk];
 #pragma unroll
-        for (int k = 0; k < kPrepChunk; ++k) {   // this CTA's points of the chunk, loads in flight
-            const int i = i0 + k * kPrepThreads;
-            cv[k] = 0xffffffffu;
-            pv[k] = make_float3(0.f, 0.f, 0.f);
-            if (i < N) {
-                if (key_cache) {
-                    const unsigned kk = keys[i];
-                    if (kk != kNoKey && kk >= c_lo && kk < c_hi) {
-                        cv[k] = kk;
-                        pv[k] = load_point(pts, P.stride, i);
-                    }
-                } else {
-                    pv[k] = load_point(pts, P.stride, i);
-                }
-            }
-        }
+        for (int k = 0; k < kPrepChunk; ++k) pos[k] = kc[k] != 0xffffffffu ? atomicAdd(&bins[kc[k]], 1u) : 0u;
 #pragma unroll
-        for (int k = 0; k < kPrepChunk; ++k) {
-            const int i = i0 + k * kPrepThreads;
-            if (i >= N) break;
-            unsigned c = cv[k];
-            if (!key_cache && finite3(pv[k])) {
-                const unsigned kk = cell_key(pv[k], blo, inv);
-                if (kk >= c_lo && kk < c_hi) c = kk;
-            }
-            if (c == 0xffffffffu) continue;
-            const unsigned pos = atomicAdd(&bins[c], 1u);
-            sorted[pos] = make_float4(pv[k].x, pv[k].y, pv[k].z, __int_as_float(i));
+        for (int k = 0; k < kPrepChunk; ++k)
+            if (kc[k] != 0xffffffffu)
+                sorted[pos[k]] = make_float4(pv[k].x, pv[k].y, pv[k].z, __int_as_float(gtid + k * kStride));
+    } else {
+        for (int i = gtid; i < N; i += kStride) {
+            const float3 p = load_point(pts, P.stride, i);
+            if (!finite3(p)) continue;
+            const unsigned pos = atomicAdd(&bins[cell_key(p, blo, inv)], 1u);
+            sorted[pos] = make_float4(p.x, p.y, p.z, __int_as_float(i));
         }
     }
     cluster.sync();   // orders every CTA's scatter before the reads below (cluster scope)
     mark(23);
 
-    // 5. tile spheres: centre of the tile's box, radius to its farthest point
+    // 5. tile spheres: centre of the tile's box, radius to its farthest point; a warp
+    //    loads up to kTileLoads of its tiles before it uses any
     const int n_tiles = (n_valid + 31) >> 5;
     float4* tiles = P.tiles + C.tile_base;
-    for (int t = (int)rank * (kPrepThreads / 32) + warp; t < n_tiles; t += kClusterWarps) {
-        const int i = t * 32 + lane;
-        const bool v = i < n_valid;
-        const float4 p = v ? __ldcg(&sorted[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float mn[3] = {v ? p.x : kInf, v ? p.y : kInf, v ? p.z : kInf};
-        float mx[3] = {v ? p.x : -kInf, v ? p.y : -kInf, v ? p.z : -kInf};
+    constexpr int kTileLoads = 4;
+    for (int t0 = (int)rank * (kPrepThreads / 32) + warp; t0 < n_tiles; t0 += kClusterWarps * kTileLoads) {
+        float4 pt[kTileLoads];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
+        for (int j = 0; j < kTileLoads; ++j) {
+            const int i = (t0 + j * kClusterWarps) * 32 + lane;
+            pt[j] = i < n_valid ? __ldcg(&sorted[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                mn[a] = fminf(mn[a], __shfl_xor_sync(kFull, mn[a], o));
-                mx[a] = fmaxf(mx[a], __shfl_xor_sync(kFull, mx[a], o));
-            }
-        const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]), cz = 0.5f * (mn[2] + mx[2]);
-        float r2 = v ? (p.x - cx) * (p.x - cx) + (p.y - cy) * (p.y - cy) + (p.z - cz) * (p.z - cz) : 0.f;
+        for (int j = 0; j < kTileLoads; ++j) {
+            const int t = t0 + j * kClusterWarps;
+            if (t >= n_tiles) break;
+            const bool v = t * 32 + lane < n_valid;
+            const float4 p = pt[j];
+            float mn[3] = {v ? p.x : kInf, v ? p.y : kInf, v ? p.z : kInf};
+            float mx[3] = {v ? p.x : -kInf, v ? p.y : -kInf, v ? p.z : -kInf};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(kFull, r2, o));
-        if (lane == 0) tiles[t] = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-6f) + 1e-7f);
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    mn[a] = fminf(mn[a], __shfl_xor_sync(kFull, mn[a], o));
+                    mx[a] = fmaxf(mx[a], __shfl_xor_sync(kFull, mx[a], o));
+                }
+            const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]), cz = 0.5f * (mn[2] + mx[2]);
+            float r2 = v ? (p.x - cx) * (p.x - cx) + (p.y - cy) * (p.y - cy) + (p.z - cz) * (p.z - cz) : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(kFull, r2, o));
+            if (lane == 0) tiles[t] = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-6f) + 1e-7f);
+        }
     }
     cluster.sync();
     mark(24);
@@ -902,7 +900,7 @@ cudaError_t configure_kernels() {
     const void* fns[6] = {(const void*)check_kernel<2, 16>, (const void*)check_kernel<4, 16>,
                           (const void*)check_kernel<8, 16>, (const void*)check_kernel<2, 8>,
                           (const void*)check_kernel<4, 8>,  (const void*)check_kernel<8, 8>};
-    cudaError_t e = cudaFuncSetAttribute(prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmem);
+    cudaError_t e = cudaSuccess;
     for (int k = 0; k < 6 && e == cudaSuccess; ++k)
         e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
@@ -912,7 +910,7 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
     if (p.n_inst <= 0 || p.n_blocks <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     if (!p.skip_prep) {
-        prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, kPrepSmem, s>>>(p);
+        prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, 0, s>>>(p);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -946,7 +944,7 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
 
 cudaError_t launch_prep(const BatchParams& p, cudaStream_t s) {
     if (p.n_cloud <= 0) return cudaSuccess;
-    prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, kPrepSmem, s>>>(p);
+    prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 
