@@ -229,3 +229,28 @@ def test_gpu_pipeline_end_to_end(sdf, ctx, tiny):
     rc, d, al, ap = device_check(sdf, torch, ctx, robot, sc.q, sc.points)
     assert rc == 0
     assert_parity(sc.dh, sc.base, vals, metas, sc.q, sc.points, d, al, ap, ref=ref)
+
+
+def test_maximum_cloud_size(sdf, ctx, tiny):
+    """N = SDF_MAX_POINTS (2^24 - 1, the largest index the packed key holds):
+    the sort's loop paths and the top of the index range, against the oracle on a
+    few waypoints; the arg-min may point anywhere in the cloud."""
+    sc, vals, metas, ref = tiny
+    robot = _robot(sdf, ctx, sc, vals, metas)
+    N = sdf.SDF_MAX_POINTS
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(77)
+    pts = (torch.rand((N, 3), generator=gen, device="cuda") * 2.4 - 1.2).contiguous()
+    # the last point sits on the robot's base, so the last index wins for most waypoints
+    pts[N - 1] = torch.tensor(sc.base[:, 3], dtype=torch.float32, device="cuda")
+    q = sc.q[:3]
+    W = len(q)
+    out = [torch.full((W,), 7.0, dtype=torch.float32, device="cuda"),
+           torch.full((W,), -7, dtype=torch.int32, device="cuda"), torch.full((W,), -7, dtype=torch.int32, device="cuda")]
+    sdf.check_trajectory(ctx, robot, torch.tensor(q, dtype=torch.float32, device="cuda"), W, pts, N, *out)
+    assert ctx.synchronize() == 0
+    d, al, ap = [t.cpu().numpy() for t in out]
+    host = pts.cpu().numpy()
+    del pts
+    assert_parity(sc.dh, sc.base, vals, metas, q, host, d, al, ap)
+    assert np.all(ap >= 0) and np.all(ap < N)
