@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of 125 Hz cycles")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: mean requests per cycle (Poisson)")
     ap.add_argument("--forms", default="grid,surrogate", help="serve: forms to run (grid, surrogate)")
+    ap.add_argument("--rates", default="", help="serve: extra arrival rates (per cycle) to sweep, grid form")
     ap.add_argument("--order", default="voxel", choices=["voxel", "random"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100)
@@ -522,7 +523,8 @@ def run_serve(args):
     period = 1.0 / 125.0
     cycles = int(round(args.duration * 125))
     # warm-up: a few cycles, then reset the statistics
-    def run_cycles(n, start_idx):
+    def run_cycles(n, start_idx, rate=None):
+        rate = args.rate if rate is None else rate
         outstanding = []
         t0 = time.perf_counter()
         late = 0
@@ -530,7 +532,7 @@ def run_serve(args):
             target = t0 + k * period
             while srv.set_cloud(clouds[(start_idx + k) % len(clouds)]) != 0:
                 time.sleep(50e-6)
-            for _ in range(rng.poisson(args.rate)):
+            for _ in range(rng.poisson(rate)):
                 outstanding.append(srv.submit(robot, trajs[int(rng.integers(0, len(trajs)))]))
             still = []
             for t in outstanding:
@@ -545,17 +547,23 @@ def run_serve(args):
         for t in outstanding:
             srv.poll(t, wait_us=-1)
         return time.perf_counter() - t0, late
-    def measure():
-        run_cycles(50, 0)
+    def measure(rate=None):
+        run_cycles(50, 0, rate)
         srv.stats(reset=True)
         clocks = ClockSampler(local)
         clocks.start()
-        wall, late = run_cycles(cycles, 50)
+        wall, late = run_cycles(cycles, 50, rate)
         clk = clocks.stop()
         return srv.stats(reset=True), wall, late, clk
 
     forms = [f for f in args.forms.split(",") if f]
     st, wall, late, clk = measure() if "grid" in forms else (None, None, None, None)
+    sweep = []
+    for r in [float(x) for x in args.rates.split(",") if x]:
+        s_r, w_r, l_r, _ = measure(r)
+        sweep.append({"rate_per_cycle": r, "p50_us": s_r["p50_us"], "p99_us": s_r["p99_us"],
+                      "checks_per_s": s_r["completed"] / w_r, "mean_batch": s_r["mean_batch"],
+                      "peak_in_flight": int(s_r["peak_in_flight"]), "late_cycles": l_r})
     sur_form = None
     if "surrogate" in forms:
         # train the surrogates on the GPU, bound their error, then serve in that form
@@ -593,7 +601,7 @@ def run_serve(args):
         "p50_us": st["p50_us"], "p99_us": st["p99_us"], "mean_us": st["mean_us"], "max_us": st["max_us"],
         "checks_per_s": st["completed"] / wall, "completed": int(st["completed"]), "batches": int(st["batches"]),
         "mean_batch": st["mean_batch"], "peak_in_flight": int(st["peak_in_flight"]), "late_cycles": late,
-        "form": "grid" if "grid" in forms else "surrogate", "surrogate_form": sur_form,
+        "form": "grid" if "grid" in forms else "surrogate", "surrogate_form": sur_form, "rate_sweep": sweep,
         "clocks": clk,
     }
     print(json.dumps(out), flush=True)
