@@ -344,6 +344,21 @@ def run_ours(args):
     st = ctx.stats(reset=True)
     ctx.set_option(sdf.SDF_OPT_STATS, 0)
     gathers_ps, cells_ps = sdf.sdf_measure_gather(ctx, grids)
+    # the lookup machinery in the dense regime: the same check with culling off
+    # (every pair looked up), check kernel timed alone
+    ctx.set_option(sdf.SDF_OPT_CULL, 0)
+    ctx.set_option(sdf.SDF_OPT_TIME_KERNELS, 1)
+    dense_ms = []
+    for i in range(6):
+        flush.zero_()
+        step()
+        if i:
+            dense_ms.append(ctx.last_kernel_ms(sdf.SDF_KERNEL_CHECK))
+    ctx.set_option(sdf.SDF_OPT_TIME_KERNELS, 0)
+    ctx.set_option(sdf.SDF_OPT_CULL, 1)
+    if ctx.synchronize() != 0:
+        raise RuntimeError(f"dense check failed: {ctx.last_error()}")
+    dense_us = statistics.median(dense_ms) * 1e3
 
     if rank != 0:
         if ws > 1:
@@ -381,7 +396,11 @@ def run_ours(args):
                    "effective_pairs_per_s": pairs / (kern_us * 1e-6),
                    "effective_frac": pairs / (kern_us * 1e-6) / cells_ps,
                    "point_tests_per_check": st["point_tests"],
-                   "peak_source": "sdf_measure_gather on the check's grids (random cells, 2-8 blocks/SM, best)"},
+                   "dense_lookups_per_s": W * L * N / (dense_us * 1e-6),
+                   "dense_frac": W * L * N / (dense_us * 1e-6) / cells_ps,
+                   "dense_kernel_us": dense_us,
+                   "peak_source": "sdf_measure_gather on the check's grids (random cells, 2-8 blocks/SM, best)",
+                   "dense": "culling off: every (waypoint, link, point) pair looked up, check kernel alone"},
         "e2e": {"value": statistics.median(e2e), "unit": UNIT, "p99": percentile(e2e, 99),
                 "h2d_bytes_per_step": int(qh.nbytes + ph.nbytes),
                 "d2h_bytes_per_step": int(dh_.nbytes + lh.nbytes + ph_.nbytes)},
