@@ -275,9 +275,14 @@ int sdf_autotune(sdf_ctx* ctx, const sdf_check_request* requests, int32_t n, int
 int sdf_ctx_reserve(sdf_ctx* ctx, int64_t max_points, int64_t max_waypoints, int64_t max_pairs,
                     int32_t max_requests);
 
-/* The same check on HOST buffers: copies q and points to context-owned device
- * staging buffers, runs check_trajectory, copies the three outputs back and
- * synchronises.  Host buffers may be pageable; page-locked buffers copy faster.
+/* The same check on HOST buffers, synchronising.  When all five buffers are
+ * page-locked (cudaHostAlloc / cudaHostRegister) the kernels read q and the points
+ * and write the outputs over the CPU-GPU link directly; otherwise q and the
+ * points are copied to context-owned device staging and the outputs copied back.
+ * The first call with a given set of buffers and sizes captures the whole call
+ * (copies, kernels, copies back) in a CUDA graph that later identical calls replay
+ * (where the capture is refused the call runs directly); the graphs are dropped
+ * when the context's scratch grows or an option changes.
  * Returns the check's status (including NONFINITE). */
 int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* robot, const float* q_host, int32_t W,
                           const float* points_host, int32_t N, float* dist_host,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -51,9 +52,17 @@ struct DeviceGuard {
     }
 };
 
+// Cached host-call graphs capture device addresses of the scratch: drop them
+// before any of it moves.
+void drop_host_graphs(sdf_ctx* ctx) {
+    for (auto& g : ctx->host_graphs) cudaGraphExecDestroy(g.exec);
+    ctx->host_graphs.clear();
+}
+
 template <typename T>
 int grow(sdf_ctx* ctx, T** buf, size_t* cap, size_t need, bool fill_ff) {
     if (need <= *cap) return SDF_OK;
+    drop_host_graphs(ctx);
     size_t n = std::max(need, *cap * 2);
     if (*buf) cudaFree(*buf);
     *buf = nullptr;
@@ -89,6 +98,7 @@ int sdf_ctx_create(sdf_ctx** out, int device, void* cuda_stream) {
     DeviceGuard g(device);
     if (cudaMalloc((void**)&ctx->status, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaHostAlloc((void**)&ctx->h_status, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
         cudaEventCreate(&ctx->ev2) != cudaSuccess) {
         sdf_ctx_destroy(ctx);
@@ -106,12 +116,15 @@ void sdf_ctx_destroy(sdf_ctx* ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    drop_host_graphs(ctx);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     cudaFree(ctx->sorted);
     cudaFree(ctx->tiles);
     cudaFree(ctx->supers);
     cudaFree(ctx->n_valid);
     cudaFree(ctx->d_stats);
     cudaFree(ctx->status);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
     cudaFree(ctx->st_q);
     cudaFree(ctx->st_pts);
     cudaFree(ctx->st_dist);
@@ -139,6 +152,10 @@ const char* sdf_last_error(const sdf_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t v) {
     if (!ctx) return SDF_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(ctx->device);
+        drop_host_graphs(ctx);   // captured launches follow the options
+    }
     switch (key) {
         case SDF_OPT_CULL: ctx->cull = v ? 1 : 0; return SDF_OK;
         case SDF_OPT_POINT_STRIDE:
@@ -188,20 +205,33 @@ int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* v) {
     }
 }
 
+}  // extern "C"
+
+namespace {
+// Enqueue: the status word to page-locked host memory, then cleared on the device.
+cudaError_t enqueue_status_readback(sdf_ctx* ctx, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(int), st);
+    return e;
+}
+// The status word read back by enqueue_status_readback, as a return code.
+int status_code(sdf_ctx* ctx) {
+    const int st = *ctx->h_status;
+    if (st & sdf::kStatusTimeout)
+        return fail(ctx, SDF_ERR_TIMEOUT, "a bounded device wait gave up; results of that call are invalid");
+    if (st & sdf::kStatusNonFinite) return fail(ctx, SDF_ERR_NONFINITE, "non-finite joint value or point in a check");
+    return SDF_OK;
+}
+}  // namespace
+
+extern "C" {
+
 int sdf_ctx_synchronize(sdf_ctx* ctx) {
     if (!ctx) return SDF_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
+    SDF_CUDA(ctx, enqueue_status_readback(ctx, ctx->stream));
     SDF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    int st = 0;
-    SDF_CUDA(ctx, cudaMemcpy(&st, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (st) {
-        SDF_CUDA(ctx, cudaMemset(ctx->status, 0, sizeof(int)));
-        if (st & sdf::kStatusTimeout)
-            return fail(ctx, SDF_ERR_TIMEOUT, "a bounded device wait gave up; results of that call are invalid");
-        if (st & sdf::kStatusNonFinite)
-            return fail(ctx, SDF_ERR_NONFINITE, "non-finite joint value or point in a check");
-    }
-    return SDF_OK;
+    return status_code(ctx);
 }
 
 int sdf_ctx_stats(sdf_ctx* ctx, int64_t* out, int32_t n, int32_t reset) {
@@ -542,9 +572,11 @@ int sdf_robot_create(sdf_ctx* ctx, const sdf_dh* dh, int32_t dof, const float* b
             if (!std::isfinite(base_3x4[k])) return fail(ctx, SDF_ERR_INVALID_ARG, "non-finite base transform");
     sdf_robot* R = new (std::nothrow) sdf_robot();
     if (!R) return fail(ctx, SDF_ERR_OOM, "host allocation");
+    static std::atomic<uint64_t> next_robot_id{1};
     R->device = ctx->device;
     R->dof = dof;
     R->grids = grids;
+    R->id = next_robot_id.fetch_add(1);
     sdf::LinkTable& T = R->table;
     memset(&T, 0, sizeof T);
     T.L = dof + 1;
@@ -874,6 +906,7 @@ int sdf_autotune(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n, int32_t
     ctx->block_warps = save_nw;
     if (rc != SDF_OK) return rc;
     ctx->tuned[key] = sdf_ctx::Shape{btw, btb, bnw};
+    drop_host_graphs(ctx);
     if (best_tw) *best_tw = btw;
     if (best_tile_batch) *best_tile_batch = btb;
     if (best_us) *best_us = best * 1e3f;
@@ -910,6 +943,7 @@ int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* R, const float* q_host,
     int rc = grow(ctx, &ctx->st_q, &ctx->st_q_cap, nq, false);
     if (rc == SDF_OK) rc = grow(ctx, &ctx->st_pts, &ctx->st_pts_cap, np, false);
     if (rc == SDF_OK && (size_t)W > ctx->st_out_cap) {
+        drop_host_graphs(ctx);
         cudaFree(ctx->st_dist);
         cudaFree(ctx->st_link);
         cudaFree(ctx->st_point);
@@ -925,21 +959,101 @@ int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* R, const float* q_host,
             ctx->st_out_cap = cap;
     }
     if (rc != SDF_OK) return rc;
-    if (R->dof > 0)
-        SDF_CUDA(ctx, cudaMemcpyAsync(ctx->st_q, q_host, (size_t)W * R->dof * sizeof(float), cudaMemcpyHostToDevice,
-                                      ctx->stream));
-    if (N > 0)
-        SDF_CUDA(ctx, cudaMemcpyAsync(ctx->st_pts, points_host, (size_t)N * ctx->point_stride * sizeof(float),
-                                      cudaMemcpyHostToDevice, ctx->stream));
-    rc = check_trajectory(ctx, R, ctx->st_q, W, ctx->st_pts, N, ctx->st_dist, ctx->st_link, ctx->st_point);
-    if (rc != SDF_OK) return rc;
-    SDF_CUDA(ctx, cudaMemcpyAsync(dist_host, ctx->st_dist, (size_t)W * sizeof(float), cudaMemcpyDeviceToHost,
-                                  ctx->stream));
-    SDF_CUDA(ctx, cudaMemcpyAsync(argmin_link_host, ctx->st_link, (size_t)W * sizeof(int32_t),
-                                  cudaMemcpyDeviceToHost, ctx->stream));
-    SDF_CUDA(ctx, cudaMemcpyAsync(argmin_point_host, ctx->st_point, (size_t)W * sizeof(int32_t),
-                                  cudaMemcpyDeviceToHost, ctx->stream));
-    return sdf_ctx_synchronize(ctx);
+    // scratch for this cloud before any capture (growing it synchronises)
+    {
+        const size_t tiles = ((size_t)N + 31) / 32;
+        rc = reserve_scratch(ctx, (size_t)N, tiles, (tiles + 31) / 32, 1);
+        if (rc != SDF_OK) return rc;
+    }
+    // Page-locked host buffers are read and written by the kernels themselves over
+    // the CPU-GPU link (no copies); other host memory goes through device staging.
+    bool zero_copy = true;
+    const void* hp[5] = {q_host, points_host, dist_host, argmin_link_host, argmin_point_host};
+    void* dp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 5 && zero_copy; ++k) {
+        if ((k == 0 && R->dof == 0) || (k == 1 && N == 0)) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, hp[k]) != cudaSuccess || a.type != cudaMemoryTypeHost || !a.devicePointer)
+            zero_copy = false;
+        else
+            dp[k] = a.devicePointer;
+    }
+    cudaGetLastError();   // a pointer unknown to CUDA is not an error here
+    // copies in, the check, copies out
+    auto enqueue = [&](cudaStream_t st) -> int {
+        if (zero_copy) {
+            cudaStream_t saved = ctx->stream;
+            ctx->stream = st;
+            int r = check_trajectory(ctx, R, static_cast<const float*>(dp[0]), W, static_cast<const float*>(dp[1]),
+                                     N, static_cast<float*>(dp[2]), static_cast<int32_t*>(dp[3]),
+                                     static_cast<int32_t*>(dp[4]));
+            if (r == SDF_OK && enqueue_status_readback(ctx, st) != cudaSuccess) r = SDF_ERR_CUDA;
+            ctx->stream = saved;
+            return r;
+        }
+        cudaStream_t saved = ctx->stream;
+        ctx->stream = st;
+        int r = SDF_OK;
+        if (R->dof > 0 && cudaMemcpyAsync(ctx->st_q, q_host, (size_t)W * R->dof * sizeof(float),
+                                          cudaMemcpyHostToDevice, st) != cudaSuccess)
+            r = SDF_ERR_CUDA;
+        if (r == SDF_OK && N > 0 &&
+            cudaMemcpyAsync(ctx->st_pts, points_host, (size_t)N * ctx->point_stride * sizeof(float),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess)
+            r = SDF_ERR_CUDA;
+        if (r == SDF_OK) r = check_trajectory(ctx, R, ctx->st_q, W, ctx->st_pts, N, ctx->st_dist, ctx->st_link,
+                                              ctx->st_point);
+        if (r == SDF_OK && (cudaMemcpyAsync(dist_host, ctx->st_dist, (size_t)W * sizeof(float),
+                                            cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                            cudaMemcpyAsync(argmin_link_host, ctx->st_link, (size_t)W * sizeof(int32_t),
+                                            cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                            cudaMemcpyAsync(argmin_point_host, ctx->st_point, (size_t)W * sizeof(int32_t),
+                                            cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                            enqueue_status_readback(ctx, st) != cudaSuccess))
+            r = SDF_ERR_CUDA;
+        ctx->stream = saved;
+        return r;
+    };
+    if (ctx->time_kernels || ctx->stats) {   // per-kernel events and counters: no graph
+        rc = enqueue(ctx->stream);
+        if (rc != SDF_OK) return rc == SDF_ERR_CUDA ? cuda_fail(ctx, cudaGetLastError(), "host check") : rc;
+        SDF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        return status_code(ctx);
+    }
+    const void* ptr[5] = {q_host, points_host, dist_host, argmin_link_host, argmin_point_host};
+    cudaGraphExec_t exec = nullptr;
+    for (auto& hg : ctx->host_graphs)
+        if (hg.robot == R->id && hg.W == W && hg.N == N && hg.zero_copy == zero_copy &&
+            std::equal(ptr, ptr + 5, hg.ptr))
+            exec = hg.exec;
+    if (!exec) {
+        // capture the call once on the context's own stream, then replay it; when the
+        // capture is refused (some host memory cannot be captured), run it directly
+        if (!ctx->capture_stream)
+            SDF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        int r = SDF_ERR_CUDA;
+        if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            r = enqueue(ctx->capture_stream);
+            if (cudaStreamEndCapture(ctx->capture_stream, &graph) != cudaSuccess) r = SDF_ERR_CUDA;
+        }
+        if (r == SDF_OK && graph && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+        if (graph) cudaGraphDestroy(graph);
+        if (!exec) {
+            cudaGetLastError();   // clear the refused capture's error
+            rc = enqueue(ctx->stream);
+            if (rc != SDF_OK) return rc == SDF_ERR_CUDA ? cuda_fail(ctx, cudaGetLastError(), "host check") : rc;
+            SDF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            return status_code(ctx);
+        }
+        if (ctx->host_graphs.size() >= 8) drop_host_graphs(ctx);
+        sdf_ctx::HostGraph hg{R->id, {}, W, N, zero_copy, exec};
+        std::copy(ptr, ptr + 5, hg.ptr);
+        ctx->host_graphs.push_back(hg);
+    }
+    SDF_CUDA(ctx, cudaGraphLaunch(exec, ctx->stream));
+    SDF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return status_code(ctx);
 }
 
 }  // extern "C"

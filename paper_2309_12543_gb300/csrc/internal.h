@@ -7,6 +7,7 @@
 #include <map>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "sdfcheck.h"
 
@@ -120,6 +121,7 @@ struct sdf_grids {
 struct sdf_robot {
     int device = 0;
     int dof = 0;
+    uint64_t id = 0;                       // unique per created robot (cache keys)
     const sdf_grids* grids = nullptr;
     sdf::LinkTable table;                  // host copy
     sdf::LinkTable* d_table = nullptr;     // device copy read by the kernels
@@ -152,6 +154,7 @@ struct sdf_ctx {
     int* n_valid = nullptr;
     size_t n_valid_cap = 0;
     int* status = nullptr;
+    int* h_status = nullptr;               // page-locked copy of the status word
     // staging for check_trajectory_host
     float* st_q = nullptr;
     size_t st_q_cap = 0;
@@ -174,4 +177,15 @@ struct sdf_ctx {
     // timing
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
     bool timed_valid = false;
+    // check_trajectory_host: one CUDA graph per argument set (copies in, sort, check,
+    // copies out), dropped whenever scratch or staging moves or an option changes
+    struct HostGraph {
+        uint64_t robot;
+        const void* ptr[5];
+        int W, N;
+        bool zero_copy;
+        cudaGraphExec_t exec;
+    };
+    std::vector<HostGraph> host_graphs;
+    cudaStream_t capture_stream = nullptr;
 };

@@ -254,3 +254,29 @@ def test_maximum_cloud_size(sdf, ctx, tiny):
     del pts
     assert_parity(sc.dh, sc.base, vals, metas, q, host, d, al, ap)
     assert np.all(ap >= 0) and np.all(ap < N)
+
+
+def test_host_calls_replay_with_new_contents(sdf, ctx, tiny):
+    """Repeated host-buffer calls (replayed as one captured graph when the buffers are
+    page-locked) read the buffers' current contents and follow option changes."""
+    sc, vals, metas, ref = tiny
+    robot = _robot(sdf, ctx, sc, vals, metas)
+    W, N = len(sc.q), len(sc.points)
+    q = torch.tensor(sc.q, dtype=torch.float32).pin_memory()
+    p = torch.tensor(sc.points, dtype=torch.float32).pin_memory()
+    outs = [torch.empty(W, dtype=dt).pin_memory() for dt in (torch.float32, torch.int32, torch.int32)]
+    rng = np.random.default_rng(21)
+    for it in range(4):
+        if it == 2:
+            ctx.set_option(sdf.SDF_OPT_CULL, 0)   # drops the captured graph
+        qq = sc.q + rng.normal(0, 0.05, sc.q.shape) * (it > 0)
+        pp = sc.points + rng.normal(0, 0.02, sc.points.shape) * (it > 0)
+        q.copy_(torch.tensor(qq, dtype=torch.float32))
+        p.copy_(torch.tensor(pp, dtype=torch.float32))
+        rc = sdf.check_trajectory_host(ctx, robot, q.numpy(), W, p.numpy(), N, *[o.numpy() for o in outs])
+        assert rc == 0
+        rc2, d, al, ap = device_check(sdf, torch, ctx, robot, q.numpy(), p.numpy())
+        assert rc2 == 0
+        assert np.array_equal(outs[0].numpy().view(np.uint32), d.view(np.uint32))
+        assert np.array_equal(outs[1].numpy(), al) and np.array_equal(outs[2].numpy(), ap)
+    ctx.set_option(sdf.SDF_OPT_CULL, 1)
