@@ -446,6 +446,35 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* robot, const sdf_s
  * returns to the grid form.  Applies to batches formed after the call. */
 int sdf_server_set_surrogate(sdf_server* server, const sdf_surrogate* surrogate, float margin, float eps);
 
+/* --------------------------------------------------- the paper's Robot-SDF form
+ *
+ * The paper's own formulation of the check (Sec. III-A), for comparison with the
+ * per-point form above: for every configuration, each Link SDF is transformed into
+ * an environment voxel grid (Eq. (1)-(4): the samples land on voxel centres) over
+ * the voxels of its block -- the "grids in sphere" of Sec. III-B, radius
+ * R_link + reach + sqrt(3) voxel / 2 around the link's bounding-sphere centre --
+ * and the Robot SDF of the configuration is the minimum over links per voxel.  The
+ * cloud is voxelised (a point occupies voxel floor((p - origin) * fl32(1/voxel))
+ * per axis, in single precision; points outside the grid occupy none) and the
+ * distance of a configuration is the minimum of its Robot SDF over the occupied
+ * voxels (+inf when none lies in a block).
+ *
+ * Memory: W x dims[0] x dims[1] x dims[2] x 4 bytes of context workspace (grown on
+ * demand, which synchronises), the cost that formulation carries. */
+typedef struct {
+    float origin[3];   /* lower corner of the grid (world frame, metres)          */
+    float voxel;       /* voxel edge (metres)                                     */
+    int32_t dims[3];   /* voxels per axis; their product at most 2^31 - 1          */
+    float reach;       /* distance range covered beyond a link's bounding sphere  */
+} sdf_env_grid;
+
+/* dist_dev: W FP32 distances; argmin_voxel_dev: W int32 linear voxel indices
+ * (i + dims[0] (j + dims[1] k); smallest index on ties; -1 with +inf).
+ * Asynchronous.  Errors: INVALID_ARG (null, sizes, grid), OOM, CUDA. */
+int check_trajectory_robot_sdf(sdf_ctx* ctx, const sdf_robot* robot, const sdf_env_grid* env,
+                               const float* q_dev, int32_t W, const float* points_dev, int32_t N,
+                               float* dist_dev, int32_t* argmin_voxel_dev);
+
 /* ----------------------------------------------------------- allocation-free check */
 
 /* The paper has no counterpart to this entry point; it serves deployment.

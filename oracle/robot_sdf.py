@@ -18,8 +18,9 @@ is the distance range the caller wants covered.  A voxel that no block covers
 holds +inf.
 
 Environment grid: origin o (lower corner), voxel edge r_e, dims (nx, ny, nz);
-voxel (i, j, k) covers o + [i, i+1) r_e etc., its centre o + (i + 1/2) r_e, and
-its linear index is i + nx (j + ny k).  A point outside the grid occupies no voxel.
+voxel (i, j, k) covers o + [i, i+1) r_e etc. (the index taken in single precision,
+see voxel_of), its centre o + (i + 1/2) r_e, and its linear index is
+i + nx (j + ny k).  A point outside the grid occupies no voxel.
 
 Parity status: pinned by reduction to the per-point check (every voxel in every
 block gives oracle.check at the occupied voxel centres) and by hand-computed
@@ -33,10 +34,16 @@ import oracle
 
 
 def voxel_of(points, origin, voxel, dims):
-    """Linear voxel index of each point, -1 outside the grid or non-finite."""
-    p = (np.asarray(points, dtype=np.float64).reshape(-1, 3) - np.asarray(origin, dtype=np.float64)) / voxel
-    with np.errstate(invalid="ignore"):
-        ijk = np.floor(p)
+    """Linear voxel index of each point, -1 outside the grid or non-finite.  The
+    index is an integer decided by floating point, so it is taken in single
+    precision as the GPU takes it: floor((p - o) * fl32(1 / r)), each operation
+    rounded to float32, no fused multiply-add."""
+    p32 = np.asarray(points, dtype=np.float32).reshape(-1, 3)
+    o32 = np.asarray(origin, dtype=np.float32)
+    inv = np.float32(1.0 / float(voxel))
+    with np.errstate(invalid="ignore", over="ignore"):
+        p = ((p32 - o32).astype(np.float32) * inv).astype(np.float32)
+        ijk = np.floor(p.astype(np.float64))
     ok = np.all(np.isfinite(ijk), axis=1)
     d = np.asarray(dims)
     ok &= np.all((ijk >= 0) & (ijk < d), axis=1)

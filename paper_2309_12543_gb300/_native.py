@@ -74,6 +74,11 @@ class sdf_server_config(ctypes.Structure):
                 ("max_dof", ctypes.c_int32), ("batch_window_us", ctypes.c_int32)]
 
 
+class sdf_env_grid(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("voxel", ctypes.c_float), ("dims", ctypes.c_int32 * 3),
+                ("reach", ctypes.c_float)]
+
+
 class sdf_grid_meta(ctypes.Structure):
     _fields_ = [("origin", ctypes.c_float * 3), ("h", ctypes.c_float), ("n", ctypes.c_int32),
                 ("center", ctypes.c_float * 3), ("radius", ctypes.c_float), ("margin", ctypes.c_float)]
@@ -106,6 +111,7 @@ def _load():
         "check_trajectory_surrogate": (ctypes.c_int, [P, P, P, P, i32, P, i32, ctypes.c_float, ctypes.c_float,
                                                       P, P, P, P, P]),
         "sdf_server_set_surrogate": (ctypes.c_int, [P, P, ctypes.c_float, ctypes.c_float]),
+        "check_trajectory_robot_sdf": (ctypes.c_int, [P, P, P, P, i32, P, i32, P, P]),
         "sdf_ctx_last_kernel_ms": (ctypes.c_int, [P, i32, ctypes.POINTER(ctypes.c_float)]),
         "sdf_build_grids": (ctypes.c_int, [P, P, i32, i32, ctypes.c_float, ctypes.POINTER(P)]),
         "sdf_grids_upload": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(P)]),
@@ -148,7 +154,7 @@ EXPORTED = ("sdf_ctx_create", "sdf_ctx_destroy", "sdf_ctx_set_stream", "sdf_last
             "sdf_server_poll", "sdf_server_stats", "sdf_measure_gather", "sdf_surrogate_create",
             "sdf_surrogate_destroy", "sdf_surrogate_params", "sdf_surrogate_sample", "sdf_surrogate_grad",
             "sdf_surrogate_train", "sdf_surrogate_eval", "sdf_surrogate_error", "check_trajectory_surrogate",
-            "sdf_server_set_surrogate")
+            "sdf_server_set_surrogate", "check_trajectory_robot_sdf")
 
 
 def _ptr(x) -> int:
@@ -544,3 +550,14 @@ def check_trajectory_surrogate(ctx: Context, robot: "Robot", surrogate: Surrogat
     ctx._check(lib.check_trajectory_surrogate(ctx.handle, robot.handle, surrogate.handle, _ptr(q), int(W), _ptr(points),
                                               int(N), float(margin), float(eps), _ptr(dist), _ptr(link), _ptr(point),
                                               _ptr(rechecked), _ptr(surrogate_dist)), "check_trajectory_surrogate")
+
+
+def check_trajectory_robot_sdf(ctx: Context, robot: "Robot", origin, voxel: float, dims, reach: float, q, W: int,
+                               points, N: int, dist, argmin_voxel) -> None:
+    """The paper's Robot-SDF form of the check on an environment voxel grid
+    (device buffers, asynchronous)."""
+    env = sdf_env_grid((ctypes.c_float * 3)(*[float(x) for x in origin]), float(voxel),
+                       (ctypes.c_int32 * 3)(*[int(x) for x in dims]), float(reach))
+    ctx._check(lib.check_trajectory_robot_sdf(ctx.handle, robot.handle, ctypes.byref(env), _ptr(q), int(W),
+                                              _ptr(points), int(N), _ptr(dist), _ptr(argmin_voxel)),
+               "check_trajectory_robot_sdf")

@@ -130,6 +130,10 @@ void sdf_ctx_destroy(sdf_ctx* ctx) {
     cudaFree(ctx->st_dist);
     cudaFree(ctx->st_link);
     cudaFree(ctx->st_point);
+    cudaFree(ctx->rs_sdf);
+    cudaFree(ctx->rs_bits);
+    cudaFree(ctx->rs_list);
+    cudaFree(ctx->rs_poses);
     cudaFree(ctx->sur_poses);
     cudaFree(ctx->sur_keys);
     cudaFree(ctx->sur_mask);

@@ -164,6 +164,15 @@ struct sdf_ctx {
     int32_t* st_link = nullptr;
     int32_t* st_point = nullptr;
     size_t st_out_cap = 0;
+    // Robot-SDF workspace (grown on demand)
+    unsigned* rs_sdf = nullptr;
+    size_t rs_sdf_cap = 0;
+    unsigned* rs_bits = nullptr;
+    size_t rs_bits_cap = 0;
+    int* rs_list = nullptr;
+    size_t rs_list_cap = 0;
+    float* rs_poses = nullptr;
+    size_t rs_poses_cap = 0;
     // surrogate check workspace (grown on demand)
     float* sur_poses = nullptr;
     unsigned long long* sur_keys = nullptr;
