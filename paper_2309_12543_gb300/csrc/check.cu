@@ -474,6 +474,7 @@ struct BlockState {
     const float* values;       // this robot's grids
     int n, L, n_valid;
     float4 (*pose)[6];         // per pair: rows[3], sphere, capsule start (+radius), capsule axis (+1/len^2)
+    const uchar2* pair_wl;     // per pair: (waypoint of the block, link), no division in the hot loops
     const float4* grid_o;      // per link (shared memory)
     const float* grid_h;
     unsigned* best;            // per waypoint of the block
@@ -488,7 +489,7 @@ __device__ __forceinline__ void stat_add(const BlockState& B, int idx, unsigned 
 
 __device__ __forceinline__ float pair_threshold(const BlockState& B, int pair) {
     if (!B.cull) return __int_as_float(0x7f800000);
-    const float t = from_ordered(B.best[pair / B.L]) + B.pose[pair][4].w + kCullSlack;
+    const float t = from_ordered(B.best[B.pair_wl[pair].x]) + B.pose[pair][4].w + kCullSlack;
     return (t == t) ? t : __int_as_float(0x7f800000);
 }
 
@@ -513,7 +514,8 @@ __device__ __forceinline__ bool capsule_reaches(float4 c, float4 A, float4 D, fl
 __device__ __forceinline__ void evaluate(const BlockState& B, int pos, int pair) {
     const float4 p = __ldg(&B.sorted[pos]);
     const float4 r0 = B.pose[pair][0], r1 = B.pose[pair][1], r2 = B.pose[pair][2];
-    const int wl = pair / B.L, l = pair - wl * B.L;
+    const uchar2 pw = B.pair_wl[pair];
+    const int wl = pw.x, l = pw.y;
     const float lx = fmaf(r0.x, p.x, fmaf(r0.y, p.y, fmaf(r0.z, p.z, r0.w)));
     const float ly = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
     const float lz = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
@@ -587,6 +589,7 @@ template <int TB, int NW>
 __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_constant__ BatchParams P) {
     extern __shared__ float4 s_spheres[];            // tiles [stage_tiles], then super-tiles
     __shared__ float4 s_pose[NW][6];
+    __shared__ uchar2 s_pair_wl[NW];
     __shared__ float4 s_grid_o[kMaxLinks];
     __shared__ float s_grid_h[kMaxLinks];
     __shared__ unsigned s_best[NW];
@@ -631,6 +634,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
         s_grid_o[tid] = T.grid_o[tid];
         s_grid_h[tid] = T.grid_h[tid];
     }
+    if (tid < n_pair) s_pair_wl[tid] = make_uchar2((unsigned char)(tid / L), (unsigned char)(tid % L));
     if (tid == 0) {
         s_list_n = 0u;
         s_list_next = 0u;
@@ -712,6 +716,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     B.values = T.values;
     B.n = T.n;
     B.L = L;
+    B.pair_wl = s_pair_wl;
     B.n_valid = n_valid;
     B.pose = s_pose;
     B.grid_o = s_grid_o;
