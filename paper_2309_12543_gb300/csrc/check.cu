@@ -472,7 +472,7 @@ constexpr unsigned kTileMask = (1u << 28) - 1u;     // tile index of a list entr
 struct BlockState {
     const float4* sorted;      // this trajectory's sorted points
     const float* values;       // this robot's grids
-    int n, L, n_valid;
+    int n, n3, L, n_valid;
     float4 (*pose)[6];         // per pair: rows[3], sphere, capsule start (+radius), capsule axis (+1/len^2)
     const uchar2* pair_wl;     // per pair: (waypoint of the block, link), no division in the hot loops
     const float4* grid_o;      // per link (shared memory)
@@ -519,7 +519,7 @@ __device__ __forceinline__ void evaluate(const BlockState& B, int pos, int pair)
     const float lx = fmaf(r0.x, p.x, fmaf(r0.y, p.y, fmaf(r0.z, p.z, r0.w)));
     const float ly = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
     const float lz = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
-    const float g = grid_lookup(B.values + (size_t)l * B.n * B.n * B.n, B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz);
+    const float g = grid_lookup(B.values + (size_t)(l * B.n3), B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz);
     const unsigned long long key = pack_key(g, __float_as_int(p.w), l);
     const unsigned ob = (unsigned)(key >> 32);
     if (ob <= B.best[wl]) {
@@ -715,6 +715,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     B.sorted = P.sorted + C.point_base;
     B.values = T.values;
     B.n = T.n;
+    B.n3 = T.n * T.n * T.n;
     B.L = L;
     B.pair_wl = s_pair_wl;
     B.n_valid = n_valid;

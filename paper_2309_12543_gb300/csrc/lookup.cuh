@@ -41,8 +41,8 @@ __device__ __forceinline__ float grid_lookup(const float* __restrict__ G, int n,
     const float dout = h * sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
     const int ix = min((int)cx, n - 2), iy = min((int)cy, n - 2), iz = min((int)cz, n - 2);
     const float fx = cx - (float)ix, fy = cy - (float)iy, fz = cz - (float)iz;
-    const size_t nn = (size_t)n * n;
-    const float* b = G + (size_t)ix + (size_t)n * iy + nn * iz;
+    const int nn = n * n;   // grids hold at most 512^3 < 2^31 values: 32-bit offsets
+    const float* b = G + (ix + n * iy + nn * iz);
     const float v000 = __ldg(b), v100 = __ldg(b + 1);
     const float v010 = __ldg(b + n), v110 = __ldg(b + n + 1);
     const float v001 = __ldg(b + nn), v101 = __ldg(b + nn + 1);
