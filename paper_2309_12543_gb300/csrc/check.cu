@@ -208,17 +208,32 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         }
     };
 
-    // 1. bounding box of the finite points: this CTA's share, then across the cluster
+    // 1. bounding box of the finite points: this CTA's share, then across the cluster.
+    //    A share of at most kPrepChunk points a thread is loaded once and kept in
+    //    registers for the histogram and the scatter.
     float lo[3] = {kInf, kInf, kInf}, hi[3] = {-kInf, -kInf, -kInf};
     bool bad = false;
-    for (int i = gtid; i < N; i += kStride) {
-        const float3 p = load_point(pts, P.stride, i);
+    const bool in_regs = N <= kStride * kPrepChunk;
+    float3 pv[kPrepChunk];
+    auto extend_box = [&](float3 p) {
         if (finite3(p)) {
             lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
             hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
         } else {
             bad = true;
         }
+    };
+    if (in_regs) {
+#pragma unroll
+        for (int k = 0; k < kPrepChunk; ++k) {   // all loads in flight before the first use
+            const int i = gtid + k * kStride;
+            pv[k] = i < N ? load_point(pts, P.stride, i) : make_float3(0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < kPrepChunk; ++k)
+            if (gtid + k * kStride < N) extend_box(pv[k]);
+    } else {
+        for (int i = gtid; i < N; i += kStride) extend_box(load_point(pts, P.stride, i));
     }
     // the six extremes at once: maxima as negated minima, warp then CTA
     float e6[6] = {lo[0], lo[1], lo[2], -hi[0], -hi[1], -hi[2]};
@@ -269,13 +284,13 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     // 2. each CTA counts its own share of the points (shared-memory atomics); the
     //    share's cell keys stay in registers for the scatter
     unsigned kc[kPrepChunk];
-    float3 pv[kPrepChunk];
-    const bool in_regs = N <= kStride * kPrepChunk;
-    auto count_chunk = [&](int i0) {
+    auto count_chunk = [&](int i0, bool load) {
+        if (load) {
 #pragma unroll
-        for (int k = 0; k < kPrepChunk; ++k) {   // all loads of the chunk in flight before the first use
-            const int i = i0 + k * kStride;
-            pv[k] = i < N ? load_point(pts, P.stride, i) : make_float3(0.f, 0.f, 0.f);
+            for (int k = 0; k < kPrepChunk; ++k) {   // all loads of the chunk in flight before the first use
+                const int i = i0 + k * kStride;
+                pv[k] = i < N ? load_point(pts, P.stride, i) : make_float3(0.f, 0.f, 0.f);
+            }
         }
 #pragma unroll
         for (int k = 0; k < kPrepChunk; ++k) {
@@ -288,9 +303,9 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         }
     };
     if (in_regs) {
-        count_chunk(gtid);
+        count_chunk(gtid, false);   // the points loaded for the box
     } else {
-        for (int i0 = gtid; i0 < N; i0 += kStride * kPrepChunk) count_chunk(i0);
+        for (int i0 = gtid; i0 < N; i0 += kStride * kPrepChunk) count_chunk(i0, true);
     }
     cluster.sync();
     mark(21);
