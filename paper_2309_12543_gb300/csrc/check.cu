@@ -189,7 +189,8 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     __shared__ __align__(16) float s_box[8];
     __shared__ float s_gbox[6];
     __shared__ unsigned s_warp_total[32];
-    __shared__ unsigned s_cloud_total;
+    __shared__ unsigned s_cloud_total, s_slice_total, s_slice_off;
+    __shared__ unsigned s_cnt[kPrepCtas][kCells / kPrepCtas];   // the slice's counts, by rank
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gtid = (int)rank * kPrepThreads + tid;
     constexpr int kStride = kPrepCtas * kPrepThreads;
@@ -310,32 +311,32 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     cluster.sync();
     mark(21);
 
-    // 3. every CTA reads the eight partial histograms: the cell totals give each
-    //    cell's start in the sorted order (an exclusive scan), and the lower ranks'
-    //    counts of the same cell give this CTA's first slot in it.  Thread t owns
-    //    cells 4t .. 4t+3 and reads them as one 16-byte word per rank.
-    static_assert(kCells == 4 * kPrepThreads, "four cells per thread");
-    uint4 tot = make_uint4(0u, 0u, 0u, 0u), mine = make_uint4(0u, 0u, 0u, 0u);
+    // 3. merge of the partial histograms, one slice of kSlice cells per CTA: CTA r
+    //    reads the counts of its slice from every rank, scans the slice, learns the
+    //    lower slices' totals, and writes into every rank's histogram that rank's
+    //    first slot in each cell of the slice (the histogram becomes its cursors).
+    //    Thread t serves cell t mod kSlice of the slice and ranks 4 (t / kSlice) + 0..3.
+    constexpr int kSlice = kCells / kPrepCtas;
+    static_assert(2 * kSlice == kPrepThreads && kPrepCtas == 8, "two threads per slice cell");
+    const int cl = tid & (kSlice - 1), half = tid / kSlice;
+    const int cell = (int)rank * kSlice + cl;
 #pragma unroll
-    for (int r = 0; r < kPrepCtas; ++r) {
-        const uint4 v = reinterpret_cast<const uint4*>(cluster.map_shared_rank(bins, r))[tid];
-        tot.x += v.x; tot.y += v.y; tot.z += v.z; tot.w += v.w;
-        if (r < (int)rank) {
-            mine.x += v.x; mine.y += v.y; mine.z += v.z; mine.w += v.w;
-        }
-    }
-    cluster.sync();   // every CTA has read every partial histogram before any is rewritten
-    const unsigned own = tot.x + tot.y + tot.z + tot.w;
-    unsigned incl = own;
+    for (int k = 0; k < 4; ++k) s_cnt[4 * half + k][cl] = cluster.map_shared_rank(bins, 4 * half + k)[cell];
+    __syncthreads();
+    unsigned total_c = 0;
+#pragma unroll
+    for (int r = 0; r < kPrepCtas; ++r) total_c += s_cnt[r][cl];
+    unsigned incl = total_c;   // exclusive scan over the slice's cells (threads 0 .. kSlice-1)
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned v = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += v;
     }
-    if (lane == 31) s_warp_total[warp] = incl;
+    if (lane == 31 && half == 0) s_warp_total[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        const unsigned t = s_warp_total[lane];
+        constexpr int kSliceWarps = kSlice / 32;
+        const unsigned t = lane < kSliceWarps ? s_warp_total[lane] : 0u;
         unsigned ti = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -343,14 +344,37 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
             if (lane >= o) ti += v;
         }
         s_warp_total[lane] = ti - t;
-        if (lane == 31) s_cloud_total = ti;
+        if (lane == kSliceWarps - 1) s_slice_total = ti;
     }
     __syncthreads();
-    const unsigned c0 = s_warp_total[warp] + incl - own;   // start of cell 4t
-    const unsigned c1 = c0 + tot.x, c2 = c1 + tot.y, c3 = c2 + tot.z;
-    reinterpret_cast<uint4*>(bins)[tid] = make_uint4(c0 + mine.x, c1 + mine.y, c2 + mine.z, c3 + mine.w);
+    const unsigned start_local = s_warp_total[warp % (kSlice / 32)] + incl - total_c;
+    cluster.sync();   // slice totals published; every read of a partial histogram is done
+    if (warp == 0) {
+        const unsigned t = lane < kPrepCtas ? *cluster.map_shared_rank(&s_slice_total, lane) : 0u;
+        unsigned ti = t;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const unsigned v = __shfl_up_sync(kFull, ti, o);
+            if (lane >= o) ti += v;
+        }
+        if (lane == (int)rank) s_slice_off = ti - t;
+        if (lane == kPrepCtas - 1) s_cloud_total = ti;
+    }
+    __syncthreads();
+    {
+        const unsigned start = s_slice_off + start_local;   // threads of both halves agree
+        unsigned pre = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) pre += half ? s_cnt[r][cl] : 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int r = 4 * half + k;
+            cluster.map_shared_rank(bins, r)[cell] = start + pre;
+            pre += s_cnt[r][cl];
+        }
+    }
     const unsigned running = s_cloud_total;
-    __syncthreads();   // the cursors are complete before any CTA thread scatters
+    cluster.sync();   // every rank's cursors are written before any scatter
     const int n_valid = (int)running;
     mark(22);
 
