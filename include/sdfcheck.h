@@ -151,8 +151,8 @@ int sdf_ctx_last_kernel_ms(sdf_ctx* ctx, int32_t kernel, float* ms);
 #define SDF_STAT_NS_SORT_HIST 21  /* histogram                                      */
 #define SDF_STAT_NS_SORT_SCAN 22  /* scan                                           */
 #define SDF_STAT_NS_SORT_SCATTER 23 /* scatter                                      */
-#define SDF_STAT_NS_SORT_TILES 24 /* tile spheres                                   */
-#define SDF_STAT_NS_SORT_SUPERS 25 /* super-tile spheres                            */
+#define SDF_STAT_NS_SORT_TILES 24 /* tile and super-tile spheres                   */
+#define SDF_STAT_NS_SORT_SUPERS 25 /* 0: counted with the tile spheres             */
 #define SDF_STAT_SUR_SEED_QUERIES 26 /* surrogate check: seed queries evaluated      */
 #define SDF_STAT_SUR_QUERIES 27   /* surrogate check: queries after the cull        */
 #define SDF_STAT_COUNT 32

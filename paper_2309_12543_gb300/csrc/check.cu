@@ -191,10 +191,10 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     __shared__ unsigned s_warp_total[32];
     __shared__ unsigned s_cloud_total, s_slice_total, s_slice_off;
     __shared__ unsigned s_cnt[kPrepCtas][kCells / kPrepCtas];   // the slice's counts, by rank
+    __shared__ float4 s_tile[32];                                // tile spheres of a super-tile
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gtid = (int)rank * kPrepThreads + tid;
     constexpr int kStride = kPrepCtas * kPrepThreads;
-    constexpr int kClusterWarps = kPrepCtas * (kPrepThreads / 32);
     const float kInf = __int_as_float(0x7f800000);
     const int N = C.N;
     const float* pts = C.points;
@@ -400,24 +400,20 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     cluster.sync();   // orders every CTA's scatter before the reads below (cluster scope)
     mark(23);
 
-    // 5. tile spheres: centre of the tile's box, radius to its farthest point; a warp
-    //    loads up to kTileLoads of its tiles before it uses any
+    // 5. tile and super-tile spheres.  CTA r builds super-tiles r, r + kPrepCtas, ...:
+    //    warp w computes tile 32 s + w (centre of the tile's box, radius to its
+    //    farthest point), then warp 0 the super-tile (box of the tile spheres, radius
+    //    to the farthest one) from shared memory -- no cluster barrier needed
     const int n_tiles = (n_valid + 31) >> 5;
+    const int n_super = (n_tiles + 31) >> 5;
     float4* tiles = P.tiles + C.tile_base;
-    constexpr int kTileLoads = 4;
-    for (int t0 = (int)rank * (kPrepThreads / 32) + warp; t0 < n_tiles; t0 += kClusterWarps * kTileLoads) {
-        float4 pt[kTileLoads];
-#pragma unroll
-        for (int j = 0; j < kTileLoads; ++j) {
-            const int i = (t0 + j * kClusterWarps) * 32 + lane;
-            pt[j] = i < n_valid ? __ldcg(&sorted[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int j = 0; j < kTileLoads; ++j) {
-            const int t = t0 + j * kClusterWarps;
-            if (t >= n_tiles) break;
+    float4* supers = P.supers + C.super_base;
+    static_assert(kPrepThreads / 32 == 32, "one warp per tile of a super-tile");
+    for (int s = (int)rank; s < n_super; s += kPrepCtas) {
+        const int t = s * 32 + warp;
+        if (t < n_tiles) {
             const bool v = t * 32 + lane < n_valid;
-            const float4 p = pt[j];
+            const float4 p = v ? __ldcg(&sorted[t * 32 + lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
             float mn[3] = {v ? p.x : kInf, v ? p.y : kInf, v ? p.z : kInf};
             float mx[3] = {v ? p.x : -kInf, v ? p.y : -kInf, v ? p.z : -kInf};
 #pragma unroll
@@ -431,35 +427,35 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
             float r2 = v ? (p.x - cx) * (p.x - cx) + (p.y - cy) * (p.y - cy) + (p.z - cz) * (p.z - cz) : 0.f;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(kFull, r2, o));
-            if (lane == 0) tiles[t] = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-6f) + 1e-7f);
-        }
-    }
-    cluster.sync();
-    mark(24);
-
-    // 6. super-tile spheres over 32 consecutive tiles: box of the tile spheres,
-    //    radius to the farthest tile sphere
-    const int n_super = (n_tiles + 31) >> 5;
-    float4* supers = P.supers + C.super_base;
-    for (int s = (int)rank * (kPrepThreads / 32) + warp; s < n_super; s += kClusterWarps) {
-        const int t = s * 32 + lane;
-        const bool v = t < n_tiles;
-        const float4 c = v ? __ldcg(&tiles[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float mn[3] = {v ? c.x - c.w : kInf, v ? c.y - c.w : kInf, v ? c.z - c.w : kInf};
-        float mx[3] = {v ? c.x + c.w : -kInf, v ? c.y + c.w : -kInf, v ? c.z + c.w : -kInf};
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                mn[a] = fminf(mn[a], __shfl_xor_sync(kFull, mn[a], o));
-                mx[a] = fmaxf(mx[a], __shfl_xor_sync(kFull, mx[a], o));
+            if (lane == 0) {
+                const float4 sph = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-6f) + 1e-7f);
+                tiles[t] = sph;
+                s_tile[warp] = sph;
             }
-        const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]), cz = 0.5f * (mn[2] + mx[2]);
-        float r = v ? sqrtf((c.x - cx) * (c.x - cx) + (c.y - cy) * (c.y - cy) + (c.z - cz) * (c.z - cz)) + c.w : 0.f;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const bool v = s * 32 + lane < n_tiles;
+            const float4 c = v ? s_tile[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float mn[3] = {v ? c.x - c.w : kInf, v ? c.y - c.w : kInf, v ? c.z - c.w : kInf};
+            float mx[3] = {v ? c.x + c.w : -kInf, v ? c.y + c.w : -kInf, v ? c.z + c.w : -kInf};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(kFull, r, o));
-        if (lane == 0) supers[s] = make_float4(cx, cy, cz, r * (1.f + 1e-6f) + 1e-7f);
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    mn[a] = fminf(mn[a], __shfl_xor_sync(kFull, mn[a], o));
+                    mx[a] = fmaxf(mx[a], __shfl_xor_sync(kFull, mx[a], o));
+                }
+            const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]), cz = 0.5f * (mn[2] + mx[2]);
+            float r = v ? sqrtf((c.x - cx) * (c.x - cx) + (c.y - cy) * (c.y - cy) + (c.z - cz) * (c.z - cz)) + c.w
+                        : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(kFull, r, o));
+            if (lane == 0) supers[s] = make_float4(cx, cy, cz, r * (1.f + 1e-6f) + 1e-7f);
+        }
+        __syncthreads();   // s_tile is rewritten by the next round
     }
+    mark(24);
     if (rank == 0 && tid == 0) P.n_valid[cidx] = n_valid;
     mark(25);
 }
