@@ -191,7 +191,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     __shared__ unsigned s_warp_total[32];
     __shared__ unsigned s_cloud_total, s_slice_total, s_slice_off;
     __shared__ unsigned s_cnt[kPrepCtas][kCells / kPrepCtas];   // the slice's counts, by rank
-    __shared__ float4 s_tile[32];                                // tile spheres of a super-tile
+    __shared__ float4 s_tile[4][32];                             // tile spheres of four super-tiles
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gtid = (int)rank * kPrepThreads + tid;
     constexpr int kStride = kPrepCtas * kPrepThreads;
@@ -400,45 +400,60 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     cluster.sync();   // orders every CTA's scatter before the reads below (cluster scope)
     mark(23);
 
-    // 5. tile and super-tile spheres.  CTA r builds super-tiles r, r + kPrepCtas, ...:
-    //    warp w computes tile 32 s + w (centre of the tile's box, radius to its
-    //    farthest point), then warp 0 the super-tile (box of the tile spheres, radius
-    //    to the farthest one) from shared memory -- no cluster barrier needed
+    // 5. tile and super-tile spheres.  CTA r builds super-tiles r, r + kPrepCtas, ...,
+    //    kRounds of them at a time: warp w loads tile 32 s + w of each (all loads in
+    //    flight before the first use) and computes its sphere (centre of the tile's
+    //    box, radius to its farthest point); warp k then forms super-tile k of the
+    //    group (box of the tile spheres, radius to the farthest one) from shared
+    //    memory -- no cluster barrier needed
     const int n_tiles = (n_valid + 31) >> 5;
     const int n_super = (n_tiles + 31) >> 5;
     float4* tiles = P.tiles + C.tile_base;
     float4* supers = P.supers + C.super_base;
     static_assert(kPrepThreads / 32 == 32, "one warp per tile of a super-tile");
-    for (int s = (int)rank; s < n_super; s += kPrepCtas) {
-        const int t = s * 32 + warp;
-        if (t < n_tiles) {
-            const bool v = t * 32 + lane < n_valid;
-            const float4 p = v ? __ldcg(&sorted[t * 32 + lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
-            float mn[3] = {v ? p.x : kInf, v ? p.y : kInf, v ? p.z : kInf};
-            float mx[3] = {v ? p.x : -kInf, v ? p.y : -kInf, v ? p.z : -kInf};
+    constexpr int kRounds = 4;
+    for (int s0 = (int)rank; s0 < n_super; s0 += kRounds * kPrepCtas) {
+        float4 p[kRounds];
+        bool v[kRounds];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < kRounds; ++k) {
+            const int t = (s0 + k * kPrepCtas) * 32 + warp;
+            v[k] = t * 32 + lane < n_valid;
+            p[k] = v[k] ? __ldcg(&sorted[t * 32 + lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    mn[a] = fminf(mn[a], __shfl_xor_sync(kFull, mn[a], o));
-                    mx[a] = fmaxf(mx[a], __shfl_xor_sync(kFull, mx[a], o));
+        for (int k = 0; k < kRounds; ++k) {
+            const int t = (s0 + k * kPrepCtas) * 32 + warp;
+            if (t < n_tiles) {   // uniform across the warp
+                float mn[3] = {v[k] ? p[k].x : kInf, v[k] ? p[k].y : kInf, v[k] ? p[k].z : kInf};
+                float mx[3] = {v[k] ? p[k].x : -kInf, v[k] ? p[k].y : -kInf, v[k] ? p[k].z : -kInf};
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        mn[a] = fminf(mn[a], __shfl_xor_sync(kFull, mn[a], o));
+                        mx[a] = fmaxf(mx[a], __shfl_xor_sync(kFull, mx[a], o));
+                    }
+                const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]), cz = 0.5f * (mn[2] + mx[2]);
+                float r2 = v[k] ? (p[k].x - cx) * (p[k].x - cx) + (p[k].y - cy) * (p[k].y - cy) +
+                                      (p[k].z - cz) * (p[k].z - cz)
+                                : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(kFull, r2, o));
+                if (lane == 0) {
+                    const float4 sph = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-6f) + 1e-7f);
+                    tiles[t] = sph;
+                    s_tile[k][warp] = sph;
                 }
-            const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]), cz = 0.5f * (mn[2] + mx[2]);
-            float r2 = v ? (p.x - cx) * (p.x - cx) + (p.y - cy) * (p.y - cy) + (p.z - cz) * (p.z - cz) : 0.f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(kFull, r2, o));
-            if (lane == 0) {
-                const float4 sph = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-6f) + 1e-7f);
-                tiles[t] = sph;
-                s_tile[warp] = sph;
             }
         }
         __syncthreads();
-        if (warp == 0) {
-            const bool v = s * 32 + lane < n_tiles;
-            const float4 c = v ? s_tile[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float mn[3] = {v ? c.x - c.w : kInf, v ? c.y - c.w : kInf, v ? c.z - c.w : kInf};
-            float mx[3] = {v ? c.x + c.w : -kInf, v ? c.y + c.w : -kInf, v ? c.z + c.w : -kInf};
+        const int s = s0 + warp * kPrepCtas;
+        if (warp < kRounds && s < n_super) {
+            const bool vt = s * 32 + lane < n_tiles;
+            const float4 c = vt ? s_tile[warp][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float mn[3] = {vt ? c.x - c.w : kInf, vt ? c.y - c.w : kInf, vt ? c.z - c.w : kInf};
+            float mx[3] = {vt ? c.x + c.w : -kInf, vt ? c.y + c.w : -kInf, vt ? c.z + c.w : -kInf};
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -447,13 +462,13 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
                     mx[a] = fmaxf(mx[a], __shfl_xor_sync(kFull, mx[a], o));
                 }
             const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]), cz = 0.5f * (mn[2] + mx[2]);
-            float r = v ? sqrtf((c.x - cx) * (c.x - cx) + (c.y - cy) * (c.y - cy) + (c.z - cz) * (c.z - cz)) + c.w
-                        : 0.f;
+            float r = vt ? sqrtf((c.x - cx) * (c.x - cx) + (c.y - cy) * (c.y - cy) + (c.z - cz) * (c.z - cz)) + c.w
+                         : 0.f;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(kFull, r, o));
             if (lane == 0) supers[s] = make_float4(cx, cy, cz, r * (1.f + 1e-6f) + 1e-7f);
         }
-        __syncthreads();   // s_tile is rewritten by the next round
+        __syncthreads();   // s_tile is rewritten by the next group
     }
     mark(24);
     if (rank == 0 && tid == 0) P.n_valid[cidx] = n_valid;
