@@ -164,6 +164,19 @@ __device__ __forceinline__ unsigned cell_key(float3 p, float3 lo, float3 inv) {
 
 // ------------------------------------------------------------------ prep kernel
 
+// Warp-wide minimum / maximum of a float in one redux.sync on its order-preserving
+// unsigned encoding (exact; -0 and +0 compare equal).
+__device__ __forceinline__ float warp_min(float x) {
+    return from_ordered(__reduce_min_sync(kFull, ordered_bits(x)));
+}
+__device__ __forceinline__ float warp_max(float x) {
+    return from_ordered(__reduce_max_sync(kFull, ordered_bits(x)));
+}
+// ... of a float known to be >= 0 (its bits already order as unsigned)
+__device__ __forceinline__ float warp_max_nonneg(float x) {
+    return __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(x)));
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -189,7 +202,8 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     __shared__ __align__(16) float s_box[8];
     __shared__ float s_gbox[6];
     __shared__ unsigned s_warp_total[32];
-    __shared__ unsigned s_cloud_total, s_slice_total, s_slice_off;
+    __shared__ unsigned s_cloud_total, s_slice_off;
+    __shared__ __align__(16) unsigned s_slice_cnt[kPrepCtas];   // this CTA's points in each slice
     __shared__ unsigned s_cnt[kPrepCtas][kCells / kPrepCtas];   // the slice's counts, by rank
     __shared__ float4 s_tile[4][32];                             // tile spheres of four super-tiles
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -239,20 +253,17 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     // the six extremes at once: maxima as negated minima, warp then CTA
     float e6[6] = {lo[0], lo[1], lo[2], -hi[0], -hi[1], -hi[2]};
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int a = 0; a < 6; ++a) e6[a] = fminf(e6[a], __shfl_xor_sync(kFull, e6[a], o));
+    for (int a = 0; a < 6; ++a) e6[a] = warp_min(e6[a]);
     if (lane == 0)
 #pragma unroll
         for (int a = 0; a < 6; ++a) s_box6[warp][a] = e6[a];
     for (int b = tid; b < kCells; b += kPrepThreads) bins[b] = 0u;
+    if (tid < kPrepCtas) s_slice_cnt[tid] = 0u;
     if (__syncthreads_or(bad) && tid == 0) atomicOr(P.status, kStatusNonFinite);
     if (warp == 0) {
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
-            float v = s_box6[lane][a];   // kPrepThreads / 32 == 32 partials
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+            const float v = warp_min(s_box6[lane][a]);   // kPrepThreads / 32 == 32 partials
             if (lane == 0) s_box[a] = a < 3 ? v : -v;
         }
     }
@@ -267,9 +278,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
             g[0] = b0.x; g[1] = b0.y; g[2] = b0.z; g[3] = -b0.w; g[4] = -b1.x; g[5] = -b1.y;
         }
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1)
-#pragma unroll
-            for (int a = 0; a < 6; ++a) g[a] = fminf(g[a], __shfl_xor_sync(kFull, g[a], o));
+        for (int a = 0; a < 6; ++a) g[a] = warp_min(g[a]);
         if (lane == 0)
 #pragma unroll
             for (int a = 0; a < 6; ++a) s_gbox[a] = a < 3 ? g[a] : -g[a];
@@ -308,25 +317,54 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     } else {
         for (int i0 = gtid; i0 < N; i0 += kStride * kPrepChunk) count_chunk(i0, true);
     }
+    // this CTA's count in each slice of kSlice cells: warp w sums cells 128 w .. 128 w + 127
+    constexpr int kSlice = kCells / kPrepCtas;
+    static_assert(kCells == 4 * kPrepThreads && kSlice % 128 == 0, "four cells a thread, whole warps a slice");
+    __syncthreads();
+    {
+        const uint4 c = reinterpret_cast<const uint4*>(bins)[tid];
+        const unsigned sum = __reduce_add_sync(kFull, c.x + c.y + c.z + c.w);
+        if (lane == 0 && sum) atomicAdd(&s_slice_cnt[(warp * 128) / kSlice], sum);
+    }
     cluster.sync();
     mark(21);
 
     // 3. merge of the partial histograms, one slice of kSlice cells per CTA: CTA r
-    //    reads the counts of its slice from every rank, scans the slice, learns the
-    //    lower slices' totals, and writes into every rank's histogram that rank's
-    //    first slot in each cell of the slice (the histogram becomes its cursors).
-    //    Thread t serves cell t mod kSlice of the slice and ranks 4 (t / kSlice) + 0..3.
-    constexpr int kSlice = kCells / kPrepCtas;
+    //    reads the counts of its slice from every rank and scans the slice; warp 1
+    //    reads every rank's slice totals, which give the lower slices' total; CTA r
+    //    then writes into every rank's histogram that rank's first slot in each cell
+    //    of the slice (the histogram becomes its cursors).  The cells of slice r are
+    //    read and written by CTA r alone, so no barrier separates the reads from the
+    //    writes.  Thread t serves cell t mod kSlice and ranks 4 (t / kSlice) + 0..3.
     static_assert(2 * kSlice == kPrepThreads && kPrepCtas == 8, "two threads per slice cell");
     const int cl = tid & (kSlice - 1), half = tid / kSlice;
     const int cell = (int)rank * kSlice + cl;
+    if (warp == 1) {
+        unsigned below = 0, total = 0;
+        if (lane < kPrepCtas) {
+            const uint4* c = reinterpret_cast<const uint4*>(cluster.map_shared_rank(s_slice_cnt, lane));
+            const uint4 c0 = c[0], c1 = c[1];
+            const unsigned v[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+            for (int j = 0; j < kPrepCtas; ++j) {
+                total += v[j];
+                below += j < (int)rank ? v[j] : 0u;
+            }
+        }
+        below = __reduce_add_sync(kFull, below);
+        total = __reduce_add_sync(kFull, total);
+        if (lane == 0) {
+            s_slice_off = below;
+            s_cloud_total = total;
+        }
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) s_cnt[4 * half + k][cl] = cluster.map_shared_rank(bins, 4 * half + k)[cell];
     __syncthreads();
     unsigned total_c = 0;
 #pragma unroll
     for (int r = 0; r < kPrepCtas; ++r) total_c += s_cnt[r][cl];
-    unsigned incl = total_c;   // exclusive scan over the slice's cells (threads 0 .. kSlice-1)
+    unsigned incl = total_c;   // inclusive scan over the slice's cells (threads 0 .. kSlice-1)
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned v = __shfl_up_sync(kFull, incl, o);
@@ -344,25 +382,10 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
             if (lane >= o) ti += v;
         }
         s_warp_total[lane] = ti - t;
-        if (lane == kSliceWarps - 1) s_slice_total = ti;
-    }
-    __syncthreads();
-    const unsigned start_local = s_warp_total[warp % (kSlice / 32)] + incl - total_c;
-    cluster.sync();   // slice totals published; every read of a partial histogram is done
-    if (warp == 0) {
-        const unsigned t = lane < kPrepCtas ? *cluster.map_shared_rank(&s_slice_total, lane) : 0u;
-        unsigned ti = t;
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            const unsigned v = __shfl_up_sync(kFull, ti, o);
-            if (lane >= o) ti += v;
-        }
-        if (lane == (int)rank) s_slice_off = ti - t;
-        if (lane == kPrepCtas - 1) s_cloud_total = ti;
     }
     __syncthreads();
     {
-        const unsigned start = s_slice_off + start_local;   // threads of both halves agree
+        const unsigned start = s_slice_off + s_warp_total[warp % (kSlice / 32)] + incl - total_c;
         unsigned pre = 0;
 #pragma unroll
         for (int r = 0; r < 4; ++r) pre += half ? s_cnt[r][cl] : 0u;
@@ -425,21 +448,15 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         for (int k = 0; k < kRounds; ++k) {
             const int t = (s0 + k * kPrepCtas) * 32 + warp;
             if (t < n_tiles) {   // uniform across the warp
-                float mn[3] = {v[k] ? p[k].x : kInf, v[k] ? p[k].y : kInf, v[k] ? p[k].z : kInf};
-                float mx[3] = {v[k] ? p[k].x : -kInf, v[k] ? p[k].y : -kInf, v[k] ? p[k].z : -kInf};
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        mn[a] = fminf(mn[a], __shfl_xor_sync(kFull, mn[a], o));
-                        mx[a] = fmaxf(mx[a], __shfl_xor_sync(kFull, mx[a], o));
-                    }
+                const float mn[3] = {warp_min(v[k] ? p[k].x : kInf), warp_min(v[k] ? p[k].y : kInf),
+                                     warp_min(v[k] ? p[k].z : kInf)};
+                const float mx[3] = {warp_max(v[k] ? p[k].x : -kInf), warp_max(v[k] ? p[k].y : -kInf),
+                                     warp_max(v[k] ? p[k].z : -kInf)};
                 const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]), cz = 0.5f * (mn[2] + mx[2]);
                 float r2 = v[k] ? (p[k].x - cx) * (p[k].x - cx) + (p[k].y - cy) * (p[k].y - cy) +
                                       (p[k].z - cz) * (p[k].z - cz)
                                 : 0.f;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(kFull, r2, o));
+                r2 = warp_max_nonneg(r2);
                 if (lane == 0) {
                     const float4 sph = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-6f) + 1e-7f);
                     tiles[t] = sph;
@@ -452,20 +469,14 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         if (warp < kRounds && s < n_super) {
             const bool vt = s * 32 + lane < n_tiles;
             const float4 c = vt ? s_tile[warp][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float mn[3] = {vt ? c.x - c.w : kInf, vt ? c.y - c.w : kInf, vt ? c.z - c.w : kInf};
-            float mx[3] = {vt ? c.x + c.w : -kInf, vt ? c.y + c.w : -kInf, vt ? c.z + c.w : -kInf};
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    mn[a] = fminf(mn[a], __shfl_xor_sync(kFull, mn[a], o));
-                    mx[a] = fmaxf(mx[a], __shfl_xor_sync(kFull, mx[a], o));
-                }
+            const float mn[3] = {warp_min(vt ? c.x - c.w : kInf), warp_min(vt ? c.y - c.w : kInf),
+                                 warp_min(vt ? c.z - c.w : kInf)};
+            const float mx[3] = {warp_max(vt ? c.x + c.w : -kInf), warp_max(vt ? c.y + c.w : -kInf),
+                                 warp_max(vt ? c.z + c.w : -kInf)};
             const float cx = 0.5f * (mn[0] + mx[0]), cy = 0.5f * (mn[1] + mx[1]), cz = 0.5f * (mn[2] + mx[2]);
             float r = vt ? sqrtf((c.x - cx) * (c.x - cx) + (c.y - cy) * (c.y - cy) + (c.z - cz) * (c.z - cz)) + c.w
                          : 0.f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(kFull, r, o));
+            r = warp_max_nonneg(r);
             if (lane == 0) supers[s] = make_float4(cx, cy, cz, r * (1.f + 1e-6f) + 1e-7f);
         }
         __syncthreads();   // s_tile is rewritten by the next group
