@@ -807,6 +807,10 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
         I.dof = r.robot->dof;
         I.cloud = c;
         I.mask = r.mask_dev;
+        I.warm = r.robot->table.values;
+        I.warm_bytes = (unsigned long long)I.L * r.robot->table.n * r.robot->table.n * r.robot->table.n * sizeof(float);
+        for (int j = 0; j < k - 1; ++j)
+            if (p->inst[j].warm == I.warm) I.warm = nullptr;   // warmed by an earlier trajectory
         launch_shape(ctx, key, I.L, nw, &I.tw, &tile_batch);
         I.block_base = (int)blocks;
         blocks += ((size_t)r.W + I.tw - 1) / I.tw;
@@ -828,6 +832,7 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     p->cull = ctx->cull;
     p->stage_tiles = (int)std::min<size_t>(max_tiles, (size_t)sdf::kMaxStagedTiles);
     p->skip_prep = ctx->reuse_sort;
+    p->warm_l2 = !ctx->reuse_sort && !ctx->time_kernels;   // the launches that overlap check and sort
     p->warps = nw;
     p->sorted = ctx->sorted;
     p->tiles = ctx->tiles;

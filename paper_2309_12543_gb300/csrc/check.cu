@@ -522,6 +522,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
+// L2 prefetch of a global range (bulk, no completion to wait for).  The start must
+// be 16-byte aligned; the size is a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // ------------------------------------------------------------------ check kernel
 
 // per-warp statistics rows (SDF_OPT_STATS), written by lane 0 of their warp
@@ -737,6 +743,19 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
         }
     }
     const bool pair_warp = warp < n_pair;
+    // the trajectory's blocks split the robot's grids and prefetch them into L2
+    // while the sort runs (the lookups then miss only to L2); not when nothing
+    // overlaps the prefetch
+    if (P.warm_l2 && I.warm && warp == NW - 1 && lane == 0) {
+        const unsigned long long chunks = I.warm_bytes >> 4;   // whole 16-byte units
+        const unsigned long long nb = (unsigned long long)((I.W + I.tw - 1) / I.tw);
+        const unsigned long long per = (chunks + nb - 1) / nb;
+        unsigned long long c = (unsigned long long)((int)blockIdx.x - I.block_base) * per;
+        const unsigned long long end = min(c + per, chunks);
+        constexpr unsigned long long kPiece = 1u << 12;        // 64 KB per prefetch
+        for (; c < end; c += kPiece)
+            prefetch_l2(reinterpret_cast<const char*>(I.warm) + (c << 4), (unsigned)(min(kPiece, end - c) << 4));
+    }
 
     // wait for the sort (a no-op without programmatic dependent launch), then stage
     // this trajectory's tile and super-tile spheres

@@ -61,6 +61,10 @@ struct InstDesc {
     int tw;                   // waypoints per check block (tw * L <= kCheckWarps)
     int block_base;           // first check block of this trajectory
     const uint8_t* mask;      // optional: only waypoints with a non-zero byte are checked
+    const float* warm;        // the robot's grids, for the first trajectory of each robot
+                              // in the launch (null otherwise): its blocks prefetch them
+                              // into L2 while the sort runs
+    unsigned long long warm_bytes;
 };
 
 struct BatchParams {
@@ -72,6 +76,8 @@ struct BatchParams {
     int stage_tiles;          // tile spheres the dynamic shared memory holds (0: no staging)
     int skip_prep;            // the clouds are already sorted in the scratch: launch the check only
     int warps;                // warps per check block: 8 or 16
+    int warm_l2;              // the check overlaps the sort (programmatic dependent launch):
+                              // its blocks prefetch the grids meanwhile (InstDesc::warm)
     float4* sorted;           // finite points, spatially sorted: x, y, z, original index bits
     float4* tiles;            // sphere of each 32-point tile
     float4* supers;           // sphere of each 32-tile super-tile

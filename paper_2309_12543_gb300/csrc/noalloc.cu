@@ -100,6 +100,8 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         I.tw = sdf::kCheckWarps / I.L > 0 ? sdf::kCheckWarps / I.L : 1;
         I.block_base = 0;
         I.mask = nullptr;
+        I.warm = R->table.values;
+        I.warm_bytes = (unsigned long long)I.L * R->table.n * R->table.n * R->table.n * sizeof(float);
         const int n_tiles = (N + 31) / 32;
         p.n_inst = 1;
         p.n_cloud = 1;
@@ -108,6 +110,7 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         p.cull = 1;
         p.stage_tiles = n_tiles < sdf::kMaxStagedTiles ? n_tiles : sdf::kMaxStagedTiles;
         p.skip_prep = 0;
+        p.warm_l2 = 1;
         p.warps = 16;
         p.sorted = reinterpret_cast<float4*>(base + kSortedOff);
         p.tiles = reinterpret_cast<float4*>(base + kTilesOff);
