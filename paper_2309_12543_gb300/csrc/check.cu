@@ -638,15 +638,21 @@ __device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, co
         pos[k] = (int)(ent[k] & kTileMask) * 32 + lane;
         pt[k] = (k < cnt && pos[k] < B.n_valid) ? __ldg(&B.sorted[pos[k]]) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    // every entry's test first (independent shared-memory reads), then the pushes
+    // (whose evaluations may lower the thresholds of later groups)
+    bool surv[TB];
+#pragma unroll
+    for (int k = 0; k < TB; ++k) {
+        const int pair = (int)(ent[k] >> 28);
+        const float thr = pair_threshold(B, pair);
+        surv[k] = k < cnt && pos[k] < B.n_valid && thr >= 0.f &&
+                  seg_dist2(pt[k].x, pt[k].y, pt[k].z, B.pose[pair][4], B.pose[pair][5]) <= thr * thr;
+    }
 #pragma unroll
     for (int k = 0; k < TB; ++k) {
         if (k >= cnt) break;
-        const int pair = (int)(ent[k] >> 28);
-        const float thr = pair_threshold(B, pair);
-        const bool surv = pos[k] < B.n_valid && thr >= 0.f &&
-                          seg_dist2(pt[k].x, pt[k].y, pt[k].z, B.pose[pair][4], B.pose[pair][5]) <= thr * thr;
         if (B.stat) stat_add(B, kWsPointT, (unsigned)__popc(__ballot_sync(kFull, pos[k] < B.n_valid)), lane);
-        queue_push(B, Q, surv, pos[k], pair, lane);
+        queue_push(B, Q, surv[k], pos[k], (int)(ent[k] >> 28), lane);
     }
 }
 
