@@ -731,15 +731,16 @@ static uint64_t shape_key(const sdf_check_request* reqs, int n) {
     return (k << 40) | (L << 32) | (lg(W) << 16) | lg(N);
 }
 
-// Warps per check block for a launch whose largest robot has Lmax links: the
-// option, else the tuned value for this shape, else 8 (smaller blocks balance
-// uneven waypoints better); 8 only when a waypoint's links fit (one warp per
-// waypoint and link).
-static int launch_warps(const sdf_ctx* ctx, uint64_t key, int Lmax) {
+// Warps per check block for a launch whose largest robot has Lmax links and that
+// checks W_total waypoints: the option, else the tuned value for this shape, else
+// 8 when one-waypoint blocks would leave SMs idle (W_total <= SMs), 16 otherwise
+// (two interleaved waypoints a block even out uneven waypoints); 8 only when a
+// waypoint's links fit (one warp per waypoint and link).
+static int launch_warps(const sdf_ctx* ctx, uint64_t key, int Lmax, size_t W_total) {
     int nw = ctx->block_warps;
     if (nw == 0) {
         auto it = ctx->tuned.find(key);
-        nw = it != ctx->tuned.end() ? it->second.nw : 8;
+        nw = it != ctx->tuned.end() ? it->second.nw : (W_total <= (size_t)ctx->num_sms ? 8 : 16);
     }
     return (nw == 8 && Lmax <= 8) ? 8 : 16;
 }
@@ -773,9 +774,13 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     int tile_batch = sdf::kDefaultTileBatch;
     size_t points = 0, tiles = 0, supers = 0, blocks = 0, max_tiles = 0;
     int Lmax = 1;
+    size_t W_total = 0;
     for (int i = 0; i < n; ++i)
-        if (reqs[i].W > 0) Lmax = std::max(Lmax, reqs[i].robot->table.L);
-    const int nw = launch_warps(ctx, key, Lmax);
+        if (reqs[i].W > 0) {
+            Lmax = std::max(Lmax, reqs[i].robot->table.L);
+            W_total += (size_t)reqs[i].W;
+        }
+    const int nw = launch_warps(ctx, key, Lmax, W_total);
     int k = 0, nc = 0;
     for (int i = 0; i < n; ++i) {
         const sdf_check_request& r = reqs[i];
@@ -828,6 +833,8 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     p->n_inst = k;
     p->n_cloud = nc;
     p->n_blocks = (int)blocks;
+    for (int i = 0; i < k; ++i)
+        p->inst[i].interleave = sdf::interleave_waypoints((long long)blocks, p->inst[i].tw, nw, ctx->num_sms);
     p->stride = ctx->point_stride;
     p->cull = ctx->cull;
     p->stage_tiles = (int)std::min<size_t>(max_tiles, (size_t)sdf::kMaxStagedTiles);

@@ -692,11 +692,16 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     const CloudDesc& C = P.cloud[I.cloud];
     const LinkTable& T = *I.robot;
     const int L = I.L;
-    const int w0 = ((int)blockIdx.x - I.block_base) * I.tw;
-    const int nw = min(I.tw, I.W - w0);
+    // waypoint j of this block: b + j * n_blk (interleaved: a block's waypoints come
+    // from distant parts of the trajectory, which evens out the blocks' work), else b * tw + j
+    const int b_loc = (int)blockIdx.x - I.block_base;
+    const int n_blk = (I.W + I.tw - 1) / I.tw;
+    const int w0 = I.interleave ? b_loc : b_loc * I.tw;
+    const int w_step = I.interleave ? n_blk : 1;
+    const int nw = I.interleave ? min(I.tw, (I.W - b_loc + n_blk - 1) / n_blk) : min(I.tw, I.W - w0);
     const int n_pair = nw * L;
     if (I.mask) {   // a masked re-check: blocks without a selected waypoint leave at once
-        const bool any = tid < nw && I.mask[w0 + tid] != 0;
+        const bool any = tid < nw && I.mask[w0 + tid * w_step] != 0;
         if (!__syncthreads_or(any)) return;
     }
     if (tid < NW) {
@@ -716,7 +721,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     // phase A.1: forward kinematics, one warp per waypoint (before the sort is
     // waited for); lane j writes link j's pose
     if (warp < nw) {
-        const float* qw = I.q + (size_t)(w0 + warp) * I.dof;
+        const float* qw = I.q + (size_t)(w0 + warp * w_step) * I.dof;
         if (lane < I.dof && !isfinite(qw[lane])) atomicOr(P.status, kStatusNonFinite);
         float M[12];
         fk_warp(T, qw, lane, M);
@@ -945,8 +950,8 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     }
 
     // results of the block's waypoints
-    if (tid < nw && (!I.mask || I.mask[w0 + tid] != 0)) {
-        const int w = w0 + tid;
+    if (tid < nw && (!I.mask || I.mask[w0 + tid * w_step] != 0)) {
+        const int w = w0 + tid * w_step;
         const unsigned long long key = s_key[tid];
         if (key == ~0ull) {
             I.dist[w] = kInf;

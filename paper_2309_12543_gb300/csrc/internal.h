@@ -65,6 +65,7 @@ struct InstDesc {
                               // in the launch (null otherwise): its blocks prefetch them
                               // into L2 while the sort runs
     unsigned long long warm_bytes;
+    int interleave;           // block b takes waypoints b, b + ceil(W / tw), ... instead of b * tw + j
 };
 
 struct BatchParams {
@@ -95,6 +96,15 @@ constexpr int kStatCount = 32;
 
 // Launchers (check.cu / grid_build.cu).  Each returns the launch's cudaError_t.
 cudaError_t configure_kernels();           // once per device, that device current
+
+// Whether a launch's blocks take interleaved waypoints (InstDesc::interleave): when
+// a block holds several waypoints and every block is resident at once (one wave of
+// 32 / nw blocks an SM at 64 registers a thread), the kernel ends with its slowest
+// block, and pairing waypoints from distant parts of a trajectory evens the blocks
+// out.  With more blocks than fit at once the block scheduler balances them.
+inline int interleave_waypoints(long long n_blocks, int tw, int nw, int num_sms) {
+    return tw > 1 && n_blocks <= (long long)num_sms * (32 / nw) ? 1 : 0;
+}
 // Enqueues the two kernels of one batch (spatial sort, check); ev_mid (may be null)
 // is recorded between them.
 cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, cudaEvent_t ev_mid);

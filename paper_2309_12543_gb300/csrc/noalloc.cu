@@ -38,6 +38,7 @@ struct PerDevice {
     std::once_flag once;
     cudaError_t err = cudaSuccess;
     unsigned char* base = nullptr;   // device address of g_noalloc_scratch on this device
+    int num_sms = 0;
 };
 constexpr int kMaxDevices = 64;
 PerDevice g_per_device[kMaxDevices];
@@ -47,6 +48,9 @@ PerDevice g_per_device[kMaxDevices];
 void setup_device(PerDevice* pd) {
     pd->err = cudaGetSymbolAddress((void**)&pd->base, g_noalloc_scratch);
     if (pd->err == cudaSuccess) pd->err = sdf::configure_kernels();
+    int dev = 0;
+    if (pd->err == cudaSuccess) pd->err = cudaGetDevice(&dev);
+    if (pd->err == cudaSuccess) pd->err = cudaDeviceGetAttribute(&pd->num_sms, cudaDevAttrMultiProcessorCount, dev);
 }
 
 // The launch parameters are large (one kernel-parameter table); keep one per
@@ -106,6 +110,7 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         p.n_inst = 1;
         p.n_cloud = 1;
         p.n_blocks = (W + I.tw - 1) / I.tw;
+        I.interleave = sdf::interleave_waypoints(p.n_blocks, I.tw, 16, pd->num_sms);
         p.stride = 3;
         p.cull = 1;
         p.stage_tiles = n_tiles < sdf::kMaxStagedTiles ? n_tiles : sdf::kMaxStagedTiles;

@@ -88,11 +88,15 @@ def test_fk_matches_oracle(sdf, ctx):
         np.testing.assert_allclose(o[..., 12:15], c, atol=5e-6)
 
 
+@pytest.mark.parametrize("warps", [8, 16])
 @pytest.mark.parametrize("tw", [0, 1, 2, 3])
 @pytest.mark.parametrize("cull", [1, 0])
-def test_check_tiny_all_launch_shapes(sdf, ctx, tiny, tw, cull):
+def test_check_tiny_all_launch_shapes(sdf, ctx, tiny, tw, cull, warps):
+    # 16-warp blocks hold two waypoints of the 7-link arm; the 19 blocks of W = 37
+    # are one wave, so they take interleaved waypoints (b and b + 19)
     sc, vals, metas, ref = tiny
     robot = _robot(sdf, ctx, sc, vals, metas)
+    ctx.set_option(sdf.SDF_OPT_BLOCK_WARPS, warps)
     ctx.set_option(sdf.SDF_OPT_WAYPOINTS_PER_BLOCK, tw)
     ctx.set_option(sdf.SDF_OPT_CULL, cull)
     rc, d, al, ap = device_check(sdf, torch, ctx, robot, sc.q, sc.points)

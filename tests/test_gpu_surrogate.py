@@ -261,8 +261,11 @@ def test_surrogate_check_empty_cloud(sdf, env):
     assert np.all(np.isinf(d)) and np.all(l == -1) and np.all(p == -1) and np.all(rech == 0)
 
 
-def test_masked_grid_check_writes_only_selected_waypoints(sdf, env):
+@pytest.mark.parametrize("warps", [8, 16])
+def test_masked_grid_check_writes_only_selected_waypoints(sdf, env, warps):
+    # with 16 warps a block holds two interleaved waypoints, the mask read at both
     sc, ctx, grids, vals, metas = env
+    ctx.set_option(sdf.SDF_OPT_BLOCK_WARPS, warps)
     robot = sdf.Robot(ctx, sc.dh, grids, sc.base)
     q, pts = sc.q.astype(np.float32), sc.points.astype(np.float32)
     W = len(q)
@@ -278,3 +281,4 @@ def test_masked_grid_check_writes_only_selected_waypoints(sdf, env):
     assert np.array_equal(d[sel].view(np.uint32), g[0][sel].view(np.uint32))
     assert np.array_equal(l[sel], g[1][sel]) and np.array_equal(p[sel], g[2][sel])
     assert np.all(d[~sel] == 7.0) and np.all(l[~sel] == -7) and np.all(p[~sel] == -7)
+    ctx.set_option(sdf.SDF_OPT_BLOCK_WARPS, 0)
