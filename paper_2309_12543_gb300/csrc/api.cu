@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -99,6 +100,9 @@ int sdf_ctx_create(sdf_ctx** out, int device, void* cuda_stream) {
     if (cudaMalloc((void**)&ctx->status, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess ||
         cudaHostAlloc((void**)&ctx->h_status, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_seq, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(ctx->d_seq, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaHostAlloc((void**)&ctx->h_done, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
         cudaEventCreate(&ctx->ev2) != cudaSuccess) {
         sdf_ctx_destroy(ctx);
@@ -125,6 +129,8 @@ void sdf_ctx_destroy(sdf_ctx* ctx) {
     cudaFree(ctx->d_stats);
     cudaFree(ctx->status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    cudaFree(ctx->d_seq);
+    if (ctx->h_done) cudaFreeHost(ctx->h_done);
     cudaFree(ctx->st_q);
     cudaFree(ctx->st_pts);
     cudaFree(ctx->st_dist);
@@ -218,6 +224,17 @@ cudaError_t enqueue_status_readback(sdf_ctx* ctx, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(int), st);
     return e;
 }
+// Polls the host-buffer path's completion word for the value `want` (written by
+// finish_kernel after the status); gives up after 2 s, after which the caller
+// synchronises the stream.  The acquire load orders the later reads of the results.
+bool wait_done(sdf_ctx* ctx, unsigned want) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (unsigned i = 0;; ++i) {
+        if (__atomic_load_n(ctx->h_done, __ATOMIC_ACQUIRE) == want) return true;
+        if ((i & 1023u) == 1023u && std::chrono::steady_clock::now() - t0 > std::chrono::seconds(2)) return false;
+    }
+}
+
 // The status word read back by enqueue_status_readback, as a return code.
 int status_code(sdf_ctx* ctx) {
     const int st = *ctx->h_status;
@@ -1003,7 +1020,9 @@ int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* R, const float* q_host,
             int r = check_trajectory(ctx, R, static_cast<const float*>(dp[0]), W, static_cast<const float*>(dp[1]),
                                      N, static_cast<float*>(dp[2]), static_cast<int32_t*>(dp[3]),
                                      static_cast<int32_t*>(dp[4]));
-            if (r == SDF_OK && enqueue_status_readback(ctx, st) != cudaSuccess) r = SDF_ERR_CUDA;
+            if (r == SDF_OK && sdf::launch_finish(ctx->status, ctx->h_status, ctx->d_seq, ctx->h_done, st) !=
+                                   cudaSuccess)
+                r = SDF_ERR_CUDA;
             ctx->stream = saved;
             return r;
         }
@@ -1034,6 +1053,7 @@ int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* R, const float* q_host,
         rc = enqueue(ctx->stream);
         if (rc != SDF_OK) return rc == SDF_ERR_CUDA ? cuda_fail(ctx, cudaGetLastError(), "host check") : rc;
         SDF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        ctx->seq = *ctx->h_done;
         return status_code(ctx);
     }
     const void* ptr[5] = {q_host, points_host, dist_host, argmin_link_host, argmin_point_host};
@@ -1060,6 +1080,7 @@ int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* R, const float* q_host,
             rc = enqueue(ctx->stream);
             if (rc != SDF_OK) return rc == SDF_ERR_CUDA ? cuda_fail(ctx, cudaGetLastError(), "host check") : rc;
             SDF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            ctx->seq = *ctx->h_done;
             return status_code(ctx);
         }
         if (ctx->host_graphs.size() >= 8) drop_host_graphs(ctx);
@@ -1068,7 +1089,9 @@ int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* R, const float* q_host,
         ctx->host_graphs.push_back(hg);
     }
     SDF_CUDA(ctx, cudaGraphLaunch(exec, ctx->stream));
+    if (zero_copy && wait_done(ctx, ++ctx->seq)) return status_code(ctx);
     SDF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->seq = *ctx->h_done;   // back in step after a synchronisation
     return status_code(ctx);
 }
 

@@ -965,6 +965,19 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     }
 }
 
+// End of a host-buffer check: the status word reaches host memory, then the
+// completion count (the results were written to host memory by the check kernel,
+// which precedes this kernel in stream order).
+__global__ void finish_kernel(int* status, int* h_status, unsigned* d_seq, unsigned* h_done) {
+    const int st = *status;
+    *status = 0;
+    *reinterpret_cast<volatile int*>(h_status) = st;
+    const unsigned s = *d_seq + 1u;
+    *d_seq = s;
+    __threadfence_system();
+    *reinterpret_cast<volatile unsigned*>(h_done) = s;
+}
+
 __global__ void __launch_bounds__(128) fk_kernel(const __grid_constant__ LinkTable T,
                                                  const float* __restrict__ q, int W,
                                                  float* __restrict__ out, int* status) {
@@ -1042,6 +1055,11 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
 cudaError_t launch_prep(const BatchParams& p, cudaStream_t s) {
     if (p.n_cloud <= 0) return cudaSuccess;
     prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(int* status, int* h_status, unsigned* d_seq, unsigned* h_done, cudaStream_t s) {
+    finish_kernel<<<1, 1, 0, s>>>(status, h_status, d_seq, h_done);
     return cudaGetLastError();
 }
 

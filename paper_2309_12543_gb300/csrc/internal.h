@@ -96,6 +96,9 @@ constexpr int kStatCount = 32;
 
 // Launchers (check.cu / grid_build.cu).  Each returns the launch's cudaError_t.
 cudaError_t configure_kernels();           // once per device, that device current
+// One thread: moves the device status word to page-locked host memory (and clears
+// it), then publishes ++(*d_seq) in *h_done behind a system-scope fence.
+cudaError_t launch_finish(int* status, int* h_status, unsigned* d_seq, unsigned* h_done, cudaStream_t s);
 
 // Whether a launch's blocks take interleaved waypoints (InstDesc::interleave): when
 // a block holds several waypoints and every block is resident at once (one wave of
@@ -171,6 +174,12 @@ struct sdf_ctx {
     size_t n_valid_cap = 0;
     int* status = nullptr;
     int* h_status = nullptr;               // page-locked copy of the status word
+    // completion word of the host-buffer path: finish_kernel bumps d_seq and writes it
+    // to page-locked h_done after the status, and the host waits for the value it
+    // expects (seq) by polling instead of a stream synchronisation
+    unsigned* d_seq = nullptr;
+    unsigned* h_done = nullptr;
+    unsigned seq = 0;
     // staging for check_trajectory_host
     float* st_q = nullptr;
     size_t st_q_cap = 0;
