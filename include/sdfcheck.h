@@ -282,7 +282,12 @@ int sdf_ctx_reserve(sdf_ctx* ctx, int64_t max_points, int64_t max_waypoints, int
  * The first call with a given set of buffers and sizes captures the whole call
  * (copies, kernels, copies back) in a CUDA graph that later identical calls replay
  * (where the capture is refused the call runs directly); the graphs are dropped
- * when the context's scratch grows or an option changes.
+ * when the context's scratch grows or an option changes.  In the page-locked case
+ * the call returns as soon as the graph's last kernel has published the status
+ * and a completion count to page-locked memory (polled, at most 2 s before it
+ * falls back to synchronising the stream), so the results are in the caller's
+ * buffers but the stream may not yet be idle; later work on the context's stream
+ * is ordered after it as usual.
  * Returns the check's status (including NONFINITE). */
 int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* robot, const float* q_host, int32_t W,
                           const float* points_host, int32_t N, float* dist_host,
