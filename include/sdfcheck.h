@@ -109,8 +109,11 @@ const char* sdf_last_error(const sdf_ctx* ctx);
 #define SDF_OPT_TILE_BATCH 4      /* list entries per warp step: 2, 4 or 8; 0 (default) = tuned or 4  */
 #define SDF_OPT_TIME_KERNELS 6    /* 1: record CUDA events around the two kernels of a check      */
 #define SDF_OPT_STATS 7           /* 1: count culls/lookups and time kernel phases (adds atomics)  */
-#define SDF_OPT_BLOCK_WARPS 8     /* warps per check block, 8 or 16 (0 = tuned, else 8 when every
-                                     robot of the launch has at most 8 links, else 16)       */
+#define SDF_OPT_BLOCK_WARPS 8     /* warps per check block, 8 or 16 (0 = tuned, else 8 when the
+                                     launch has no more waypoints than SMs, else 16; always
+                                     16 when a robot has more than 8 links).  Blocks of
+                                     several waypoints take interleaved ones (b, b + blocks,
+                                     ...) when the whole launch is resident at once. */
 int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t value);
 int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* value);
 
