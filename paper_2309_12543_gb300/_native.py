@@ -409,6 +409,28 @@ def check_trajectory_host(ctx: Context, robot: Robot, q_host, W: int, points_hos
     return int(rc)
 
 
+class HostCheck:
+    """check_trajectory_host bound to fixed host buffers: the buffer addresses are
+    taken once, and each call re-reads the buffers' current contents.  The object
+    keeps the five arrays alive (so they cannot be freed or resized under it); a
+    call costs one C call.  Returns the status code like check_trajectory_host."""
+
+    def __init__(self, ctx: Context, robot: Robot, q_host, W: int, points_host, N: int, dist_host,
+                 argmin_link_host, argmin_point_host):
+        self._keep = (ctx, robot, q_host, points_host, dist_host, argmin_link_host, argmin_point_host)
+        P, i32 = ctypes.c_void_p, ctypes.c_int32
+        self._args = (ctx.handle, robot.handle, P(_ptr(q_host)), i32(int(W)), P(_ptr(points_host)),
+                      i32(int(N)), P(_ptr(dist_host)), P(_ptr(argmin_link_host)), P(_ptr(argmin_point_host)))
+        self._fn = lib.check_trajectory_host
+        self._ctx = ctx
+
+    def __call__(self) -> int:
+        rc = self._fn(*self._args)
+        if rc != SDF_OK and rc != SDF_ERR_NONFINITE:
+            self._ctx._check(rc, "check_trajectory_host")
+        return rc
+
+
 def check_trajectory_noalloc(robot: Robot, stream, q_dev, W: int, points_dev, N: int, dist_dev,
                              argmin_link_dev, argmin_point_dev, status_dev=None) -> int:
     """The allocation-free check (no context, fixed-size device scratch); returns

@@ -284,3 +284,35 @@ def test_host_calls_replay_with_new_contents(sdf, ctx, tiny):
         assert np.array_equal(outs[0].numpy().view(np.uint32), d.view(np.uint32))
         assert np.array_equal(outs[1].numpy(), al) and np.array_equal(outs[2].numpy(), ap)
     ctx.set_option(sdf.SDF_OPT_CULL, 1)
+
+
+def test_prepared_host_check_reads_current_contents(sdf, ctx, tiny):
+    """sdf.HostCheck binds the five page-locked buffers once; every call re-reads their
+    contents, returns promptly with the results in place, and agrees bitwise with the
+    device path; a non-finite point still comes back as SDF_ERR_NONFINITE."""
+    sc, vals, metas, ref = tiny
+    robot = _robot(sdf, ctx, sc, vals, metas)
+    W, N = len(sc.q), len(sc.points)
+    q = torch.tensor(sc.q, dtype=torch.float32).pin_memory()
+    p = torch.tensor(sc.points, dtype=torch.float32).pin_memory()
+    outs = [torch.empty(W, dtype=dt).pin_memory() for dt in (torch.float32, torch.int32, torch.int32)]
+    call = sdf.HostCheck(ctx, robot, q.numpy(), W, p.numpy(), N, *[o.numpy() for o in outs])
+    rng = np.random.default_rng(22)
+    for it in range(6):
+        qq = sc.q + rng.normal(0, 0.05, sc.q.shape) * (it > 0)
+        pp = sc.points + rng.normal(0, 0.02, sc.points.shape) * (it > 0)
+        q.copy_(torch.tensor(qq, dtype=torch.float32))
+        p.copy_(torch.tensor(pp, dtype=torch.float32))
+        outs[0].fill_(float("nan"))
+        assert call() == 0
+        rc2, d, al, ap = device_check(sdf, torch, ctx, robot, q.numpy(), p.numpy())
+        assert rc2 == 0
+        assert np.array_equal(outs[0].numpy().view(np.uint32), d.view(np.uint32))
+        assert np.array_equal(outs[1].numpy(), al) and np.array_equal(outs[2].numpy(), ap)
+        if it == 0:
+            assert_parity(sc.dh, sc.base, vals, metas, sc.q, sc.points, outs[0].numpy(), outs[1].numpy(),
+                          outs[2].numpy(), ref=ref)
+    p[3, 1] = float("nan")
+    assert call() == sdf.SDF_ERR_NONFINITE
+    p[3, 1] = 0.0
+    assert call() == 0
