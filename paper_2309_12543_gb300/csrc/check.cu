@@ -3,26 +3,30 @@
 //
 // prep_kernel -- one thread-block cluster (8 CTAs x 1024 threads) per cloud sorts
 //   its obstacle points in space: bounding box (shared through distributed shared
-//   memory), 16^3-cell Morton key, a counting sort whose partial histograms meet
-//   through distributed shared memory, each CTA scattering its own points into
-//   float4 (x, y, z, original index); then a bounding sphere per tile of 32 sorted points and per
-//   super-tile of 32 tiles.  Non-finite points are dropped (and flagged).
-// check_kernel -- one block per (trajectory, group of waypoints); the trajectory's
-//   tile and super-tile spheres reach shared memory by one TMA bulk copy that
-//   completes on an mbarrier (bounded wait).
+//   memory), 16^3-cell Morton key, a counting sort whose partial histograms are
+//   merged slice by slice through distributed shared memory, each CTA scattering
+//   its own points into float4 (x, y, z, original index); then a bounding sphere
+//   per tile of 32 sorted points and per super-tile of 32 tiles.  Non-finite
+//   points are dropped (and flagged).
+// check_kernel -- one block per (trajectory, group of waypoints), started while
+//   the sort runs (programmatic dependent launch).  Before it waits for the sort,
+//   the block runs forward kinematics (Sec. III-A "parallel forward kinematics":
+//   lanes build the DH joint transforms and a warp scan composes them; each pair's
+//   link-from-world transform and world bounding capsule go to shared memory) and
+//   prefetches its share of the robot's grids into L2.  A block of two waypoints
+//   takes two from distant parts of the trajectory when the launch is one wave.
+//   The trajectory's tile and super-tile spheres then reach shared memory by one
+//   TMA bulk copy that completes on an mbarrier (bounded wait).
 //   Phase A, one warp per (waypoint, link) pair:
-//   * forward kinematics (Sec. III-A "parallel forward kinematics"): lanes build
-//     the DH joint transforms and a warp scan composes them; the pair's
-//     link-from-world transform and world bounding sphere go to shared memory;
-//   * seed: the tile whose farthest point is nearest to the link's sphere centre
-//     is evaluated in full, which makes the waypoint's best value (a shared-memory
-//     atomic shared by the waypoint's warps) a tight upper bound early;
-//   * culls super-tiles, then tiles, with ||c - c_link|| - r - R_link > best + slack
-//     (the analogue of the paper's "grids in sphere", Sec. III-B); every surviving
+//   * seed: the tile nearest to the link's capsule is evaluated in full, which
+//     makes the waypoint's best value (a shared-memory atomic shared by the
+//     waypoint's warps) a tight upper bound early;
+//   * culls super-tiles, then tiles, against the capsule with best + slack (the
+//     analogue of the paper's "grids in sphere", Sec. III-B); every surviving
 //     (pair, tile) goes to a block-wide list in shared memory.
 //   Phase B, all warps of the block: entries are taken from the list a few at a time
 //   (loads issued together), the tile's points are tested against the pair's
-//   sphere, survivors are compacted into a per-warp queue and evaluated 32 at a
+//   capsule, survivors are compacted into a per-warp queue and evaluated 32 at a
 //   time: transform into the link frame (the per-point form of Sec. II-B / Fig.
 //   2), trilinear lookup in the FP32 link grid (the grid-sample interpolation of
 //   Sec. III-A), distance to the grid box outside it.  Each value is folded into
