@@ -6,8 +6,11 @@
 // trajectories from any thread; one engine thread forms batches whenever one of
 // `slots` in-flight slots is free and the device-memory budget admits the batch,
 // launches it with check_batch on the slot's own stream (so batches overlap on the
-// device), and a host callback marks its requests done when the results are back
-// in host memory.  Grids, robots and the latest cloud stay resident on the device.
+// device).  The kernels read the joint values from, and write the results to, the
+// slot's page-locked buffers (over the CPU-GPU link, no copies); a one-thread
+// finish kernel then publishes the status and a completion count in page-locked
+// memory, which the engine polls while batches are in flight.  Grids, robots and
+// the latest cloud stay resident on the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,14 +58,14 @@ struct Slot {
     sdf_server* srv = nullptr;
     sdf_ctx* ctx = nullptr;
     cudaStream_t stream = nullptr;
-    float* d_q = nullptr;            // max_waypoints x max_dof
-    float* h_q = nullptr;            // pinned
-    float* d_out = nullptr;          // dist | link | point, max_waypoints each
-    float* h_out = nullptr;          // pinned
+    float* h_q = nullptr;            // page-locked, max_waypoints x max_dof: read by the kernels
+    float* h_out = nullptr;          // page-locked, dist | link | point, max_waypoints each:
+                                     // written by the kernels
     std::vector<std::shared_ptr<Request>> reqs;
     int cloud = -1;
     size_t bytes = 0;
-    std::atomic<bool> finished{false};
+    std::atomic<bool> finished{false};   // set only when the launch itself failed
+    unsigned seq = 0;                    // completion count the batch's finish kernel publishes
     bool busy = false;
 };
 
@@ -82,6 +85,7 @@ struct sdf_server {
     size_t in_flight_bytes = 0;
     size_t scratch_bytes = 0;        // per batch: sorted cloud and spheres
     bool stop = false;
+    std::atomic<uint64_t> submits{0};   // bumped by every submission (wakes a polling engine)
     std::thread engine;
     // statistics
     std::vector<double> latencies;
@@ -96,13 +100,19 @@ struct sdf_server {
 
 namespace {
 
-// Runs on a CUDA-internal thread once the batch's results are in host memory.  It
-// makes no CUDA call and takes no lock (the engine may hold the lock while it
-// synchronises this stream); the engine also wakes on its own every 200 us.
-void CUDART_CB on_batch_done(void* arg) {
-    Slot* s = static_cast<Slot*>(arg);
-    s->finished.store(true, std::memory_order_release);
-    s->srv->cv.notify_all();
+// Whether a slot's batch has completed: its finish kernel has published the
+// expected count (the acquire load orders the reads of the results after it), or
+// its launch failed.
+bool slot_done(const Slot& s) {
+    return s.finished.load(std::memory_order_acquire) || __atomic_load_n(s.ctx->h_done, __ATOMIC_ACQUIRE) == s.seq;
+}
+
+// The status word the finish kernel published, as a return code.
+int published_status(const Slot& s) {
+    const int st = __atomic_load_n(s.ctx->h_status, __ATOMIC_ACQUIRE);
+    if (st & sdf::kStatusTimeout) return SDF_ERR_TIMEOUT;
+    if (st & sdf::kStatusNonFinite) return SDF_ERR_NONFINITE;
+    return SDF_OK;
 }
 
 size_t request_bytes(const sdf_server* S, int W, int dof) {
@@ -115,8 +125,8 @@ void retire(sdf_server* S, std::unique_lock<std::mutex>& lk) {
     (void)lk;
     for (auto& sp : S->slots) {
         Slot& s = *sp;
-        if (!s.busy || !s.finished.load(std::memory_order_acquire)) continue;
-        const int rc = sdf_ctx_synchronize(s.ctx);
+        if (!s.busy || !slot_done(s)) continue;
+        const int rc = s.finished.load(std::memory_order_relaxed) ? SDF_OK : published_status(s);
         const auto now = Clock::now();
         const int maxw = S->cfg.max_waypoints;
         int off = 0;
@@ -172,7 +182,8 @@ void launch(sdf_server* S) {
         CloudBuf& cb = S->clouds[S->current_cloud];
         s.cloud = S->current_cloud;
         cb.refs++;
-        // pack joint values, enqueue copy, check, copy back, completion callback
+        // pack joint values; the check reads them and writes its results in the
+        // slot's page-locked buffers; then the finish kernel
         const int maxw = S->cfg.max_waypoints;
         std::vector<sdf_check_request> req(n);
         size_t qoff = 0;
@@ -181,21 +192,19 @@ void launch(sdf_server* S) {
             Request& r = *s.reqs[i];
             std::memcpy(s.h_q + qoff, r.q.data(), r.q.size() * sizeof(float));
             req[i].robot = r.robot;
-            req[i].q_dev = s.d_q + qoff;
+            req[i].q_dev = s.h_q + qoff;
             req[i].W = r.W;
             req[i].points_dev = cb.d;
             req[i].N = cb.N;
-            req[i].dist_dev = s.d_out + woff;
-            req[i].argmin_link_dev = reinterpret_cast<int32_t*>(s.d_out + maxw) + woff;
-            req[i].argmin_point_dev = reinterpret_cast<int32_t*>(s.d_out + 2 * maxw) + woff;
+            req[i].dist_dev = s.h_out + woff;
+            req[i].argmin_link_dev = reinterpret_cast<int32_t*>(s.h_out + maxw) + woff;
+            req[i].argmin_point_dev = reinterpret_cast<int32_t*>(s.h_out + 2 * maxw) + woff;
             qoff += r.q.size();
             woff += r.W;
             r.state = 1;
         }
         int rc = SDF_OK;
-        if (cudaMemcpyAsync(s.d_q, s.h_q, qoff * sizeof(float), cudaMemcpyHostToDevice, s.stream) != cudaSuccess ||
-            cudaStreamWaitEvent(s.stream, cb.ready, 0) != cudaSuccess)
-            rc = SDF_ERR_CUDA;
+        if (cudaStreamWaitEvent(s.stream, cb.ready, 0) != cudaSuccess) rc = SDF_ERR_CUDA;
         if (rc == SDF_OK && S->surrogate) {
             // the surrogate form, one request after the other on the slot's stream;
             // requests on other grids take the grid path together
@@ -213,10 +222,14 @@ void launch(sdf_server* S) {
         } else if (rc == SDF_OK) {
             rc = check_batch(s.ctx, req.data(), n);
         }
-        for (int part = 0; part < 3 && rc == SDF_OK; ++part)
-            if (cudaMemcpyAsync(s.h_out + part * maxw, s.d_out + part * maxw, (size_t)woff * sizeof(float),
-                                cudaMemcpyDeviceToHost, s.stream) != cudaSuccess)
+        if (rc == SDF_OK) {
+            s.seq = s.ctx->seq + 1u;
+            if (sdf::launch_finish(s.ctx->status, s.ctx->h_status, s.ctx->d_seq, s.ctx->h_done, s.stream) ==
+                cudaSuccess)
+                s.ctx->seq = s.seq;
+            else
                 rc = SDF_ERR_CUDA;
+        }
         s.bytes = bytes;
         s.busy = true;
         S->in_flight_bytes += bytes;
@@ -224,7 +237,6 @@ void launch(sdf_server* S) {
         S->peak_in_flight = std::max(S->peak_in_flight, S->in_flight);
         S->batches++;
         S->batched_requests += (uint64_t)n;
-        if (rc == SDF_OK && cudaLaunchHostFunc(s.stream, on_batch_done, &s) != cudaSuccess) rc = SDF_ERR_CUDA;
         if (rc != SDF_OK) {
             // report the failure on these requests; the slot is released at once
             for (auto& r : s.reqs) r->status = rc;
@@ -240,7 +252,23 @@ void engine_loop(sdf_server* S) {
         retire(S, lk);
         launch(S);
         S->cv.notify_all();   // clients waiting on results
-        S->cv.wait_for(lk, std::chrono::microseconds(200));
+        if (S->in_flight > 0) {
+            // batches in flight: poll their completion words, without the lock, until
+            // one completes, a request arrives, or 100 us pass (the batch window)
+            const uint64_t sub0 = S->submits.load(std::memory_order_relaxed);
+            lk.unlock();
+            const auto t0 = Clock::now();
+            for (unsigned i = 0;; ++i) {
+                bool any = false;
+                for (auto& sp : S->slots)   // only this thread changes the slots
+                    if (sp->busy && slot_done(*sp)) any = true;
+                if (any || S->submits.load(std::memory_order_relaxed) != sub0) break;
+                if ((i & 63u) == 63u && Clock::now() - t0 > std::chrono::microseconds(100)) break;
+            }
+            lk.lock();
+        } else {
+            S->cv.wait_for(lk, std::chrono::microseconds(200));
+        }
     }
 }
 
@@ -248,8 +276,6 @@ void free_server(sdf_server* S) {
     for (auto& sp : S->slots) {
         Slot& s = *sp;
         if (s.stream) cudaStreamSynchronize(s.stream);
-        cudaFree(s.d_q);
-        cudaFree(s.d_out);
         cudaFreeHost(s.h_q);
         cudaFreeHost(s.h_out);
         if (s.ctx) sdf_ctx_destroy(s.ctx);
@@ -309,9 +335,7 @@ int sdf_server_create(const sdf_server_config* cfg, sdf_server** out) {
         rc = sdf_ctx_reserve(s.ctx, c.max_points, c.max_waypoints, (int64_t)c.max_waypoints * (c.max_dof + 1),
                              c.max_batch);
         if (rc != SDF_OK) break;
-        if (cudaMalloc((void**)&s.d_q, qn * sizeof(float)) != cudaSuccess ||
-            cudaMallocHost((void**)&s.h_q, qn * sizeof(float)) != cudaSuccess ||
-            cudaMalloc((void**)&s.d_out, 3 * (size_t)c.max_waypoints * sizeof(float)) != cudaSuccess ||
+        if (cudaMallocHost((void**)&s.h_q, qn * sizeof(float)) != cudaSuccess ||
             cudaMallocHost((void**)&s.h_out, 3 * (size_t)c.max_waypoints * sizeof(float)) != cudaSuccess)
             rc = SDF_ERR_OOM;
     }
@@ -386,6 +410,7 @@ int sdf_server_submit(sdf_server* S, const sdf_robot* robot, const float* q_host
     r->ticket = S->next_ticket++;
     r->submitted = Clock::now();
     S->pending.push_back(r);
+    S->submits.fetch_add(1, std::memory_order_relaxed);
     S->by_ticket[r->ticket] = r;
     *ticket = r->ticket;
     S->cv.notify_all();
