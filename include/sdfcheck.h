@@ -307,9 +307,12 @@ int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* robot, const float* q_h
  * (max_batch requests, max_waypoints in total) and the device-memory budget
  * (the request buffers and sort scratch of every in-flight batch count against
  * it), and launches it with check_batch on the slot's own stream, so batches
- * overlap on the device.  Every request of a batch is checked against the cloud
- * current when the batch forms.  Robots (grids) stay resident; the server owns
- * its streams, buffers and contexts. */
+ * overlap on the device.  The kernels read the joint values from and write the
+ * results to the slot's page-locked buffers; the engine learns of completion by
+ * polling a count published in page-locked memory (it spins while batches are in
+ * flight).  Every request of a batch is checked against the cloud current when
+ * the batch forms.  Robots (grids) stay resident; the server owns its streams,
+ * buffers and contexts. */
 typedef struct sdf_server sdf_server;
 typedef struct {
     int32_t device;
