@@ -869,32 +869,48 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
                 stat_add(B, kWsSuperT, (unsigned)min(32, n_super - s0), lane);
                 stat_add(B, kWsSuperP, (unsigned)__popc(ms), lane);
             }
+            // two surviving super-tiles per round: their tile tests and ballots are
+            // independent, and one list reservation covers both
             while (ms) {
-                const int sidx = s0 + __ffs(ms) - 1;
+                const int sa = s0 + __ffs(ms) - 1;
                 ms &= ms - 1;
+                const int sb = ms ? s0 + __ffs(ms) - 1 : -1;
+                if (ms) ms &= ms - 1;
                 thr = pair_threshold(B, warp);
-                const int t = sidx * 32 + lane;
-                const unsigned mt = __ballot_sync(kFull, t < n_tiles && capsule_reaches(tiles[min(t, n_tiles - 1)], capA, capD, thr));
+                const int ta = sa * 32 + lane, tb = sb * 32 + lane;
+                const bool ra = ta < n_tiles && capsule_reaches(tiles[min(ta, n_tiles - 1)], capA, capD, thr);
+                const bool rb = sb >= 0 && tb < n_tiles && capsule_reaches(tiles[min(tb, n_tiles - 1)], capA, capD, thr);
+                const unsigned mta = __ballot_sync(kFull, ra), mtb = __ballot_sync(kFull, rb);
                 if (stats) {
-                    stat_add(B, kWsTileT, (unsigned)min(32, n_tiles - sidx * 32), lane);
-                    stat_add(B, kWsTileP, (unsigned)__popc(mt), lane);
+                    stat_add(B, kWsTileT, (unsigned)min(32, n_tiles - sa * 32), lane);
+                    stat_add(B, kWsTileP, (unsigned)__popc(mta), lane);
+                    if (sb >= 0) {
+                        stat_add(B, kWsTileT, (unsigned)min(32, n_tiles - sb * 32), lane);
+                        stat_add(B, kWsTileP, (unsigned)__popc(mtb), lane);
+                    }
                 }
-                if (!mt) continue;
+                const unsigned na = (unsigned)__popc(mta);
+                if (!(mta | mtb)) continue;
                 unsigned base = 0;
-                if (lane == 0) base = atomicAdd(&s_list_n, (unsigned)__popc(mt));
+                if (lane == 0) base = atomicAdd(&s_list_n, na + (unsigned)__popc(mtb));
                 base = __shfl_sync(kFull, base, 0);
-                const bool mine = (mt >> lane) & 1u;
-                const unsigned slot = base + __popc(mt & ((1u << lane) - 1u));
-                const unsigned ent = ((unsigned)warp << 28) | (unsigned)t;
-                if (mine && slot < (unsigned)kBlockList) s_list[slot] = ent;
-                unsigned over = __ballot_sync(kFull, mine && slot >= (unsigned)kBlockList);
-                if (stats) stat_add(B, kWsOver, (unsigned)__popc(over), lane);
-                while (over) {   // the list is full: test these tiles here
-                    over_ent[over_n] = ((unsigned)warp << 28) | (unsigned)(sidx * 32 + __ffs(over) - 1);
-                    over &= over - 1;
-                    if (++over_n == TB) {
-                        test_tiles<TB>(B, Q, over_ent, over_n, lane);
-                        over_n = 0;
+                const unsigned lt = (1u << lane) - 1u;
+                const unsigned slot_a = base + __popc(mta & lt), slot_b = base + na + __popc(mtb & lt);
+                if (ra && slot_a < (unsigned)kBlockList) s_list[slot_a] = ((unsigned)warp << 28) | (unsigned)ta;
+                if (rb && slot_b < (unsigned)kBlockList) s_list[slot_b] = ((unsigned)warp << 28) | (unsigned)tb;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {   // the list is full: test the rest here
+                    const int sidx = h ? sb : sa;
+                    unsigned over = __ballot_sync(kFull, h ? (rb && slot_b >= (unsigned)kBlockList)
+                                                           : (ra && slot_a >= (unsigned)kBlockList));
+                    if (stats) stat_add(B, kWsOver, (unsigned)__popc(over), lane);
+                    while (over) {
+                        over_ent[over_n] = ((unsigned)warp << 28) | (unsigned)(sidx * 32 + __ffs(over) - 1);
+                        over &= over - 1;
+                        if (++over_n == TB) {
+                            test_tiles<TB>(B, Q, over_ent, over_n, lane);
+                            over_n = 0;
+                        }
                     }
                 }
             }
