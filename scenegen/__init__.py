@@ -454,8 +454,8 @@ def make_batched(seed: int = 3, n: int = 64, W_range=(50, 1000), N_range=(1000, 
 def drifting_clouds(seed: int = 5, cycles: int = 250, N_range=(5000, 80000), sigma: float = 0.005,
                     voxel: float = 0.02, order: str = "voxel"):
     """Clouds for a control-cycle stream: three human clusters whose positions take
-    a Gaussian random walk (``sigma`` metres per axis per cycle, so about 0.9 cm
-    per cycle on average), voxelised at ``voxel`` and sampled to N ~ U(N_range)
+    a Gaussian random walk (``sigma`` metres per axis per cycle, so a mean step of
+    sigma * sqrt(8 / pi), about 0.8 cm), voxelised at ``voxel`` and sampled to N ~ U(N_range)
     points each cycle."""
     rng = np.random.default_rng(seed)
     clusters = [human_voxels(rng, 1, voxel) for _ in range(3)]
