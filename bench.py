@@ -37,7 +37,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one check_kernel launch on the 500 x 20k workload,
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # launch), taken on a launch with per-kernel events like the ones kernel_us times;
-# profiles/check_kernel_paper_500x20k.md holds the capture and its command.
+# the check kernel's ncu summary under profiles/ gives the capture and its command.
 CHECK_KERNEL_DRAM_BYTES = 8_632_832
 
 

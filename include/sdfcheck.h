@@ -114,6 +114,15 @@ const char* sdf_last_error(const sdf_ctx* ctx);
                                      16 when a robot has more than 8 links).  Blocks of
                                      several waypoints take interleaved ones (b, b + blocks,
                                      ...) when the whole launch is resident at once. */
+#define SDF_OPT_WAIT_POLLS 9      /* polls a bounded device wait makes before it gives up (the
+                                     staging copy of the check kernel, the tensor-core MMA
+                                     completions of the surrogate kernels), 0..2^32-1; default
+                                     2^22.  A wait that gives up sets SDF_ERR_TIMEOUT (reported
+                                     by sdf_ctx_synchronize and the synchronising calls) and
+                                     every output of that launch is invalid; the block first
+                                     drains its own copies or MMAs with a wait of the default
+                                     length, then leaves.  Small values exist for tests of the
+                                     timeout path. */
 int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t value);
 int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* value);
 
@@ -185,8 +194,17 @@ int sdf_measure_gather(sdf_ctx* ctx, const sdf_grids* grids, double* gathers_per
 int sdf_build_grids(sdf_ctx* ctx, const sdf_mesh* links, int32_t n_links, int32_t resolution,
                     float margin, sdf_grids** out);
 
-/* Use grids computed elsewhere: host_values holds n_links grids of n^3 FP32
- * values each (same n for all links, layout as sdf_grid_meta).  Synchronises. */
+/* Link SDFs built elsewhere (Sec. III-A, "Link SDFs": one signed distance grid per
+ * link in the link's own frame), e.g. by an offline tool: host_values holds n_links
+ * grids of n^3 FP32 values each, x fastest (value index i + n (j + n k) at
+ * origin + (i,j,k) h), the same n for every link; meta[l] gives link l's origin,
+ * h, n, bounding-sphere centre and radius.  The radius is rounded up by one FP32
+ * ulp on the way in, so a radius that is the nearest-FP32 rounding of an exact
+ * bound (which may lie below it) still bounds every vertex; the culls rely on it.
+ * Values and metadata are copied (the caller keeps its arrays).  Synchronises.
+ * Errors: INVALID_ARG (NULL arrays, n_links outside 1..SDF_MAX_LINKS, n outside
+ * 2..SDF_MAX_RESOLUTION or different between links, h <= 0, non-finite origin or
+ * centre, negative radius), OOM, CUDA. */
 int sdf_grids_upload(sdf_ctx* ctx, const float* host_values, const sdf_grid_meta* meta,
                      int32_t n_links, sdf_grids** out);
 
@@ -199,9 +217,16 @@ void sdf_grids_destroy(sdf_grids* grids);
 
 /* --------------------------------------------------------------------- robot */
 
-/* A serial arm of `dof` revolute joints (standard DH rows) with world-from-base
- * transform base_3x4 (NULL = identity) whose L = dof + 1 links use `grids`
- * (which must hold exactly L grids and outlive the robot).  Errors: INVALID_ARG. */
+/* The robot whose links the check poses by forward kinematics (Sec. III-A, the
+ * kinematic chain behind "parallel forward kinematics"; the paper's arm, a DENSO
+ * VS-060 in Sec. IV-C, is not given, so joints are standard DH rows): a serial
+ * arm of `dof` revolute joints dh[0..dof-1] (host, copied) with world-from-base
+ * transform base_3x4 (host, 3x4 row-major, copied; NULL = identity) whose
+ * L = dof + 1 links use `grids` (which must hold exactly L grids and outlive the
+ * robot; link 0 is the static base).  Derives each link's bounding capsule for the
+ * culls from its grid (downloads the grids once per sdf_grids object, which
+ * synchronises).  Errors: INVALID_ARG (dof outside 0..SDF_MAX_LINKS-1, DH table
+ * missing, non-finite DH row or base, grid count != dof + 1), OOM, CUDA. */
 int sdf_robot_create(sdf_ctx* ctx, const sdf_dh* dh, int32_t dof, const float* base_3x4,
                      const sdf_grids* grids, sdf_robot** out);
 void sdf_robot_destroy(sdf_robot* robot);
@@ -486,6 +511,19 @@ int check_trajectory_robot_sdf(sdf_ctx* ctx, const sdf_robot* robot, const sdf_e
                                const float* q_dev, int32_t W, const float* points_dev, int32_t N,
                                float* dist_dev, int32_t* argmin_voxel_dev);
 
+/* ------------------------------------------------------------ fault injection
+ *
+ * The paper has no counterpart: these serve tests of the library's error paths.
+ * Every device or page-locked host allocation the library makes is counted.
+ * sdf_debug_fail_alloc(k), k >= 1: the k-th allocation from now (in any thread,
+ * on any device) fails as if the memory were exhausted, so the call making it
+ * returns SDF_ERR_OOM (and must free what it had allocated); 0 disarms.  Nothing
+ * happens on the GPU.  sdf_debug_alloc_live: the library's live allocations, their
+ * total bytes and the remaining countdown (0 = disarmed); any output may be NULL.
+ * Errors: INVALID_ARG (k < 0). */
+int sdf_debug_fail_alloc(int64_t k);
+int sdf_debug_alloc_live(int64_t* count, int64_t* bytes, int64_t* countdown);
+
 /* ----------------------------------------------------------- allocation-free check */
 
 /* The paper has no counterpart to this entry point; it serves deployment.
@@ -500,7 +538,7 @@ int check_trajectory_robot_sdf(sdf_ctx* ctx, const sdf_robot* robot, const sdf_e
  * library holds until the process exits.
  *
  * Limits: N <= SDF_NOALLOC_MAX_POINTS, else SDF_ERR_INVALID_ARG (nothing is
- * enqueued); W is not limited.  Points are N x 3 FP32; culling is on.
+ * enqueued); W up to 2^31 - 1 (any int32).  Points are N x 3 FP32; culling is on.
  *
  * robot: as for check_trajectory (its device is made current for the call).
  * cuda_stream: the cudaStream_t to enqueue on (NULL = legacy default stream).
@@ -510,7 +548,8 @@ int check_trajectory_robot_sdf(sdf_ctx* ctx, const sdf_robot* robot, const sdf_e
  * SDF_ERR_CUDA (launch or set-up failure).
  *
  * The first call on each device looks up the array's device address; make that
- * first call before any stream capture.  Every call shares the one array and it
+ * first call before any stream capture.  A set-up that failed (SDF_ERR_CUDA) is
+ * tried again by the next call.  Every call shares the one array and it
  * keeps the previous call's contents (the call resets what must start cleared),
  * so calls whose work overlaps on the GPU -- on different streams, or from
  * different host threads -- race and must be serialised by the caller. */

@@ -64,7 +64,6 @@ def _load():
         "oracle_mesh_sdf_many": (None, [P, P, P, i32, P, i64, P]),
         "oracle_grid_meta": (None, [P, i32, i32, f64, P]),
         "oracle_build_grid": (None, [P, i32, P, P, i32, i32, f64, P, P]),
-        "oracle_grid_nodes": (None, [P, P, P, i32, P, P, i64, P]),
         "oracle_fk": (None, [P, i32, P, P, i64, P]),
         "oracle_lookup": (f64, [P, P, P]),
         "oracle_lookup_many": (None, [P, P, P, i64, P]),
@@ -146,18 +145,6 @@ def build_grid(mesh, n: int, margin: float):
     _load().oracle_build_grid(_p(v), int(v.shape[0]), _p(t), _p(off), int(off.shape[0] - 1),
                               int(n), float(margin), _p(vals), _p(meta))
     return vals, meta
-
-
-def grid_nodes(mesh, meta, node_idx) -> np.ndarray:
-    """Values of selected grid nodes (flat x-fastest indices) of a mesh's grid."""
-    v, t = _d(mesh.verts), np.ascontiguousarray(mesh.tris, np.int32)
-    off = np.ascontiguousarray(mesh.comp_offsets, np.int32)
-    idx = np.ascontiguousarray(node_idx, np.int64)
-    out = np.empty(idx.shape[0])
-    meta = _d(meta)
-    _load().oracle_grid_nodes(_p(v), _p(t), _p(off), int(off.shape[0] - 1), _p(meta), _p(idx),
-                              int(idx.shape[0]), _p(out))
-    return out
 
 
 def build_grids(meshes, n: int, margin: float):

@@ -243,21 +243,6 @@ void oracle_build_grid(const double *verts, int32_t n_verts, const int32_t *tris
     }
 }
 
-/* Build only selected nodes (flat indices) of a grid, for sampled comparisons. */
-void oracle_grid_nodes(const double *verts, const int32_t *tris, const int32_t *comp_offsets,
-                       int32_t n_comp, const double *meta, const int64_t *node_idx,
-                       int64_t n_nodes, double *out) {
-    const int64_t n = (int64_t)meta[4];
-#pragma omp parallel for schedule(dynamic, 8)
-    for (int64_t s = 0; s < n_nodes; ++s) {
-        int64_t idx = node_idx[s];
-        int64_t i = idx % n, j = (idx / n) % n, k = idx / (n * n);
-        double x[3] = {meta[0] + (double)i * meta[3], meta[1] + (double)j * meta[3],
-                       meta[2] + (double)k * meta[3]};
-        out[s] = oracle_mesh_sdf(verts, tris, comp_offsets, n_comp, x);
-    }
-}
-
 /* ------------------------------------------------------- forward kinematics */
 
 /* 4x4 row-major helpers */

@@ -38,6 +38,7 @@ SDF_OPT_TILE_BATCH = 4
 SDF_OPT_TIME_KERNELS = 6
 SDF_OPT_STATS = 7
 SDF_OPT_BLOCK_WARPS = 8
+SDF_OPT_WAIT_POLLS = 9
 SDF_KERNEL_PREP = 0
 SDF_KERNEL_CHECK = 1
 
@@ -133,6 +134,8 @@ def _load():
         "sdf_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, i64, P, P, P, ctypes.POINTER(ctypes.c_double)]),
         "sdf_server_stats": (ctypes.c_int, [P, P, i32, i32]),
         "sdf_ctx_reserve": (ctypes.c_int, [P, i64, i64, i64, i32]),
+        "sdf_debug_fail_alloc": (ctypes.c_int, [i64]),
+        "sdf_debug_alloc_live": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -154,7 +157,8 @@ EXPORTED = ("sdf_ctx_create", "sdf_ctx_destroy", "sdf_ctx_set_stream", "sdf_last
             "sdf_server_poll", "sdf_server_stats", "sdf_measure_gather", "sdf_surrogate_create",
             "sdf_surrogate_destroy", "sdf_surrogate_params", "sdf_surrogate_sample", "sdf_surrogate_grad",
             "sdf_surrogate_train", "sdf_surrogate_eval", "sdf_surrogate_error", "check_trajectory_surrogate",
-            "sdf_server_set_surrogate", "check_trajectory_robot_sdf")
+            "sdf_server_set_surrogate", "check_trajectory_robot_sdf", "sdf_debug_fail_alloc",
+            "sdf_debug_alloc_live")
 
 
 def _ptr(x) -> int:
@@ -308,8 +312,7 @@ def sdf_grids_upload(ctx: Context, values, metas) -> Grids:
         arr[i].h = float(h)
         arr[i].n = int(n)
         arr[i].center[:] = [float(x) for x in c]
-        # round the radius up so the FP32 sphere holds every vertex
-        arr[i].radius = float(np.nextafter(np.float32(r), np.float32(np.inf)))
+        arr[i].radius = float(r)   # the library rounds it up by one ulp
         arr[i].margin = float(mg)
     h = ctypes.c_void_p()
     ctx._check(lib.sdf_grids_upload(ctx.handle, _ptr(vals), ctypes.addressof(arr), len(metas),
@@ -438,6 +441,20 @@ def check_trajectory_noalloc(robot: Robot, stream, q_dev, W: int, points_dev, N:
     return int(lib.check_trajectory_noalloc(robot.handle, _stream_handle(stream), _ptr(q_dev), int(W),
                                             _ptr(points_dev), int(N), _ptr(dist_dev), _ptr(argmin_link_dev),
                                             _ptr(argmin_point_dev), _ptr(status_dev)))
+
+
+def sdf_debug_fail_alloc(k: int) -> None:
+    """Make the k-th library allocation from now fail as out of memory (0 disarms)."""
+    rc = int(lib.sdf_debug_fail_alloc(int(k)))
+    if rc != SDF_OK:
+        raise SdfError(rc, "sdf_debug_fail_alloc")
+
+
+def sdf_debug_alloc_live():
+    """(live allocations, their bytes, remaining fail countdown) of the library."""
+    out = np.zeros(3, np.int64)
+    lib.sdf_debug_alloc_live(_ptr(out[0:1]), _ptr(out[1:2]), _ptr(out[2:3]))
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 class Server:

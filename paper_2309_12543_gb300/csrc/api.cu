@@ -65,11 +65,11 @@ int grow(sdf_ctx* ctx, T** buf, size_t* cap, size_t need, bool fill_ff) {
     if (need <= *cap) return SDF_OK;
     drop_host_graphs(ctx);
     size_t n = std::max(need, *cap * 2);
-    if (*buf) cudaFree(*buf);
+    if (*buf) sdf::dfree(*buf);
     *buf = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMalloc((void**)buf, n * sizeof(T));
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(scratch)");
+    cudaError_t e = sdf::dmalloc(buf, n * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device allocation (scratch)");
     e = cudaMemsetAsync(*buf, fill_ff ? 0xff : 0, n * sizeof(T), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync(scratch)");
     *cap = n;
@@ -97,12 +97,12 @@ int sdf_ctx_create(sdf_ctx** out, int device, void* cuda_stream) {
     ctx->num_sms = prop.multiProcessorCount;
     ctx->stream = (cudaStream_t)cuda_stream;
     DeviceGuard g(device);
-    if (cudaMalloc((void**)&ctx->status, sizeof(int)) != cudaSuccess ||
+    if (sdf::dmalloc(&ctx->status, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess ||
-        cudaHostAlloc((void**)&ctx->h_status, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->d_seq, sizeof(unsigned)) != cudaSuccess ||
+        sdf::hmalloc(&ctx->h_status, sizeof(int)) != cudaSuccess ||
+        sdf::dmalloc(&ctx->d_seq, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(ctx->d_seq, 0, sizeof(unsigned)) != cudaSuccess ||
-        cudaHostAlloc((void**)&ctx->h_done, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess ||
+        sdf::hmalloc(&ctx->h_done, sizeof(unsigned)) != cudaSuccess ||
         cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
         cudaEventCreate(&ctx->ev2) != cudaSuccess) {
         sdf_ctx_destroy(ctx);
@@ -122,30 +122,30 @@ void sdf_ctx_destroy(sdf_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     drop_host_graphs(ctx);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
-    cudaFree(ctx->sorted);
-    cudaFree(ctx->tiles);
-    cudaFree(ctx->supers);
-    cudaFree(ctx->n_valid);
-    cudaFree(ctx->d_stats);
-    cudaFree(ctx->status);
-    if (ctx->h_status) cudaFreeHost(ctx->h_status);
-    cudaFree(ctx->d_seq);
-    if (ctx->h_done) cudaFreeHost(ctx->h_done);
-    cudaFree(ctx->st_q);
-    cudaFree(ctx->st_pts);
-    cudaFree(ctx->st_dist);
-    cudaFree(ctx->st_link);
-    cudaFree(ctx->st_point);
-    cudaFree(ctx->rs_sdf);
-    cudaFree(ctx->rs_bits);
-    cudaFree(ctx->rs_list);
-    cudaFree(ctx->rs_poses);
-    cudaFree(ctx->sur_poses);
-    cudaFree(ctx->sur_keys);
-    cudaFree(ctx->sur_mask);
-    cudaFree(ctx->sur_xq);
-    cudaFree(ctx->sur_tag);
-    cudaFree(ctx->sur_count);
+    sdf::dfree(ctx->sorted);
+    sdf::dfree(ctx->tiles);
+    sdf::dfree(ctx->supers);
+    sdf::dfree(ctx->n_valid);
+    sdf::dfree(ctx->d_stats);
+    sdf::dfree(ctx->status);
+    if (ctx->h_status) sdf::hfree(ctx->h_status);
+    sdf::dfree(ctx->d_seq);
+    if (ctx->h_done) sdf::hfree(ctx->h_done);
+    sdf::dfree(ctx->st_q);
+    sdf::dfree(ctx->st_pts);
+    sdf::dfree(ctx->st_dist);
+    sdf::dfree(ctx->st_link);
+    sdf::dfree(ctx->st_point);
+    sdf::dfree(ctx->rs_sdf);
+    sdf::dfree(ctx->rs_bits);
+    sdf::dfree(ctx->rs_list);
+    sdf::dfree(ctx->rs_poses);
+    sdf::dfree(ctx->sur_poses);
+    sdf::dfree(ctx->sur_keys);
+    sdf::dfree(ctx->sur_mask);
+    sdf::dfree(ctx->sur_xq);
+    sdf::dfree(ctx->sur_tag);
+    sdf::dfree(ctx->sur_count);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);
@@ -187,10 +187,14 @@ int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t v) {
             if (v != 0 && v != 8 && v != 16) return fail(ctx, SDF_ERR_INVALID_ARG, "block warps must be 0, 8 or 16");
             ctx->block_warps = (int)v;
             return SDF_OK;
+        case SDF_OPT_WAIT_POLLS:
+            if (v < 0 || v > (int64_t)UINT32_MAX) return fail(ctx, SDF_ERR_INVALID_ARG, "wait polls must be 0..2^32-1");
+            ctx->wait_polls = (unsigned)v;
+            return SDF_OK;
         case SDF_OPT_STATS:
             if (v && !ctx->d_stats) {
                 DeviceGuard g(ctx->device);
-                cudaError_t e = cudaMalloc((void**)&ctx->d_stats, sdf::kStatCount * sizeof(unsigned long long));
+                cudaError_t e = sdf::dmalloc(&ctx->d_stats, sdf::kStatCount * sizeof(unsigned long long));
                 if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, sdf::kStatCount * sizeof(unsigned long long));
                 if (e == cudaSuccess) e = cudaMemset(ctx->d_stats + 17, 0xff, sizeof(unsigned long long));
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "statistics buffer");
@@ -211,6 +215,7 @@ int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* v) {
         case SDF_OPT_TIME_KERNELS: *v = ctx->time_kernels; return SDF_OK;
         case SDF_OPT_STATS: *v = ctx->stats; return SDF_OK;
         case SDF_OPT_BLOCK_WARPS: *v = ctx->block_warps; return SDF_OK;
+        case SDF_OPT_WAIT_POLLS: *v = (int64_t)ctx->wait_polls; return SDF_OK;
         default: return SDF_ERR_INVALID_ARG;
     }
 }
@@ -325,10 +330,10 @@ int sdf_build_grids(sdf_ctx* ctx, const sdf_mesh* links, int32_t n_links, int32_
     G->device = ctx->device;
     G->n_links = n_links;
     G->n = n;
-    cudaError_t e = cudaMalloc((void**)&G->values, per * n_links * sizeof(float));
+    cudaError_t e = sdf::dmalloc(&G->values, per * n_links * sizeof(float));
     if (e != cudaSuccess) {
         delete G;
-        return cuda_fail(ctx, e, "cudaMalloc(grids)");
+        return cuda_fail(ctx, e, "device allocation (grids)");
     }
     float* d_tris = nullptr;
     int* d_off = nullptr;
@@ -377,8 +382,8 @@ int sdf_build_grids(sdf_ctx* ctx, const sdf_mesh* links, int32_t n_links, int32_
             off[0] = 0;
             off[1] = m.n_tris;
         }
-        e = cudaMalloc((void**)&d_tris, tri9.size() * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc((void**)&d_off, off.size() * sizeof(int));
+        e = sdf::dmalloc(&d_tris, tri9.size() * sizeof(float));
+        if (e == cudaSuccess) e = sdf::dmalloc(&d_off, off.size() * sizeof(int));
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d_tris, tri9.data(), tri9.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess)
@@ -388,8 +393,8 @@ int sdf_build_grids(sdf_ctx* ctx, const sdf_mesh* links, int32_t n_links, int32_
                                        md.origin[2], md.h, n, G->values + per * l, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) rc = cuda_fail(ctx, e, "grid build");
-        cudaFree(d_tris);
-        cudaFree(d_off);
+        sdf::dfree(d_tris);
+        sdf::dfree(d_off);
         d_tris = nullptr;
         d_off = nullptr;
     }
@@ -421,9 +426,13 @@ int sdf_grids_upload(sdf_ctx* ctx, const float* host_values, const sdf_grid_meta
     G->device = ctx->device;
     G->n_links = n_links;
     G->n = n;
-    for (int l = 0; l < n_links; ++l) G->meta[l] = meta[l];
+    for (int l = 0; l < n_links; ++l) {
+        G->meta[l] = meta[l];
+        // one ulp up: a nearest-FP32 radius may lie just below the exact bound
+        G->meta[l].radius = nextafterf(meta[l].radius, INFINITY);
+    }
     const size_t bytes = (size_t)n * n * n * n_links * sizeof(float);
-    cudaError_t e = cudaMalloc((void**)&G->values, bytes);
+    cudaError_t e = sdf::dmalloc(&G->values, bytes);
     if (e == cudaSuccess) e = cudaMemcpyAsync(G->values, host_values, bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
@@ -457,7 +466,7 @@ int sdf_grids_info(const sdf_grids* G, int32_t* n_links, int32_t* resolution) {
 void sdf_grids_destroy(sdf_grids* G) {
     if (!G) return;
     DeviceGuard g(G->device);
-    cudaFree(G->values);
+    sdf::dfree(G->values);
     delete G;
 }
 
@@ -630,7 +639,7 @@ int sdf_robot_create(sdf_ctx* ctx, const sdf_dh* dh, int32_t dof, const float* b
     }
     T.values = grids->values;
     DeviceGuard g(ctx->device);
-    cudaError_t e = cudaMalloc((void**)&R->d_table, sizeof(sdf::LinkTable));
+    cudaError_t e = sdf::dmalloc(&R->d_table, sizeof(sdf::LinkTable));
     if (e == cudaSuccess) e = cudaMemcpy(R->d_table, &T, sizeof(sdf::LinkTable), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         sdf_robot_destroy(R);
@@ -644,7 +653,7 @@ void sdf_robot_destroy(sdf_robot* R) {
     if (!R) return;
     if (R->d_table) {
         DeviceGuard g(R->device);
-        cudaFree(R->d_table);
+        sdf::dfree(R->d_table);
     }
     delete R;
 }
@@ -715,6 +724,7 @@ int sort_cloud(sdf_ctx* ctx, const float* points_dev, int N, BatchParams* p) {
     p->supers = ctx->supers;
     p->n_valid = ctx->n_valid;
     p->status = ctx->status;
+    p->wait_polls = ctx->wait_polls;
     p->stats = nullptr;
     const cudaError_t e = launch_prep(*p, ctx->stream);
     return e == cudaSuccess ? SDF_OK : cuda_fail(ctx, e, "cloud sort");
@@ -863,6 +873,7 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     p->supers = ctx->supers;
     p->n_valid = ctx->n_valid;
     p->status = ctx->status;
+    p->wait_polls = ctx->wait_polls;
     p->stats = ctx->stats ? ctx->d_stats : nullptr;
     cudaError_t e = cudaSuccess;
     if (ctx->time_kernels) e = cudaEventRecord(ctx->ev0, ctx->stream);
@@ -977,16 +988,16 @@ int check_trajectory_host(sdf_ctx* ctx, const sdf_robot* R, const float* q_host,
     if (rc == SDF_OK) rc = grow(ctx, &ctx->st_pts, &ctx->st_pts_cap, np, false);
     if (rc == SDF_OK && (size_t)W > ctx->st_out_cap) {
         drop_host_graphs(ctx);
-        cudaFree(ctx->st_dist);
-        cudaFree(ctx->st_link);
-        cudaFree(ctx->st_point);
+        sdf::dfree(ctx->st_dist);
+        sdf::dfree(ctx->st_link);
+        sdf::dfree(ctx->st_point);
         ctx->st_dist = nullptr;
         ctx->st_link = ctx->st_point = nullptr;
         ctx->st_out_cap = 0;
         const size_t cap = std::max((size_t)W, (size_t)1024);
-        if (cudaMalloc((void**)&ctx->st_dist, cap * sizeof(float)) != cudaSuccess ||
-            cudaMalloc((void**)&ctx->st_link, cap * sizeof(int32_t)) != cudaSuccess ||
-            cudaMalloc((void**)&ctx->st_point, cap * sizeof(int32_t)) != cudaSuccess)
+        if (sdf::dmalloc(&ctx->st_dist, cap * sizeof(float)) != cudaSuccess ||
+            sdf::dmalloc(&ctx->st_link, cap * sizeof(int32_t)) != cudaSuccess ||
+            sdf::dmalloc(&ctx->st_point, cap * sizeof(int32_t)) != cudaSuccess)
             rc = fail(ctx, SDF_ERR_OOM, "staging allocation");
         else
             ctx->st_out_cap = cap;

@@ -517,11 +517,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after kMaxWaitPolls polls (each poll may itself block
-// for a short, hardware-defined time) instead of spinning forever.
-constexpr int kMaxWaitPolls = 1 << 22;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-    for (int i = 0; i < kMaxWaitPolls; ++i)
+// Bounded wait: gives up after `limit` polls (each poll may itself block for a
+// short, hardware-defined time) instead of spinning forever.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit) {
+    for (unsigned i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -699,10 +698,11 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     // waypoint j of this block: b + j * n_blk (interleaved: a block's waypoints come
     // from distant parts of the trajectory, which evens out the blocks' work), else b * tw + j
     const int b_loc = (int)blockIdx.x - I.block_base;
-    const int n_blk = (I.W + I.tw - 1) / I.tw;
-    const int w0 = I.interleave ? b_loc : b_loc * I.tw;
+    const int n_blk = (int)(((long long)I.W + I.tw - 1) / I.tw);   // no int overflow for W near 2^31
+    const int w0 = I.interleave ? b_loc : b_loc * I.tw;             // < W
     const int w_step = I.interleave ? n_blk : 1;
-    const int nw = I.interleave ? min(I.tw, (I.W - b_loc + n_blk - 1) / n_blk) : min(I.tw, I.W - w0);
+    const int nw = I.interleave ? (int)min((long long)I.tw, ((long long)I.W - b_loc + n_blk - 1) / n_blk)
+                                : min(I.tw, I.W - w0);
     const int n_pair = nw * L;
     if (I.mask) {   // a masked re-check: blocks without a selected waypoint leave at once
         const bool any = tid < nw && I.mask[w0 + tid * w_step] != 0;
@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     // overlaps the prefetch
     if (P.warm_l2 && I.warm && warp == NW - 1 && lane == 0) {
         const unsigned long long chunks = I.warm_bytes >> 4;   // whole 16-byte units
-        const unsigned long long nb = (unsigned long long)((I.W + I.tw - 1) / I.tw);
+        const unsigned long long nb = (unsigned long long)n_blk;
         const unsigned long long per = (chunks + nb - 1) / nb;
         unsigned long long c = (unsigned long long)((int)blockIdx.x - I.block_base) * per;
         const unsigned long long end = min(c + per, chunks);
@@ -789,14 +789,17 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     }
     __syncthreads();
     if (staged) {
-        const bool ok = mbar_wait_bounded(&s_mbar, 0);
+        const bool ok = mbar_wait_bounded(&s_mbar, 0, P.wait_polls);
         if (!__syncthreads_and(ok)) {
-            // the copy did not complete in time: report it and leave; one more
-            // bounded wait first so no transfer into this block is left in flight
+            // the copy did not complete in time: report it and leave.  A drain wait of
+            // the default length first, so that the copy has landed before the block's
+            // shared memory is released; should that wait give up too, the status
+            // already says that every output of this launch is invalid.
             if (tid == 0) {
                 atomicOr(P.status, kStatusTimeout);
-                mbar_wait_bounded(&s_mbar, 0);
+                mbar_wait_bounded(&s_mbar, 0, kDefaultWaitPolls);
             }
+            __syncthreads();
             return;
         }
     }

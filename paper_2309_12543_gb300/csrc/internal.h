@@ -84,6 +84,7 @@ struct BatchParams {
     float4* supers;           // sphere of each 32-tile super-tile
     int* n_valid;             // finite points per cloud
     int* status;              // device status bits
+    unsigned wait_polls;      // polls of the sphere-staging wait before it gives up
     unsigned long long* stats;  // kStatCount counters, or null (statistics off)
     CloudDesc cloud[kMaxBatch];
     InstDesc inst[kMaxBatch];
@@ -91,8 +92,25 @@ struct BatchParams {
 
 enum StatusBits : int { kStatusNonFinite = 1, kStatusTimeout = 2 };
 
+// Default poll limit of the bounded device waits (SDF_OPT_WAIT_POLLS); every wait
+// that gave up is followed by a drain wait of this many polls, so that no copy or
+// MMA issued by a block is still in flight when it releases its memory.
+constexpr unsigned kDefaultWaitPolls = 1u << 22;
+
 // Statistics counters (SDF_OPT_STATS); indices match SDF_STAT_* in sdfcheck.h.
 constexpr int kStatCount = 32;
+
+// Allocations (alloc.cu): every device and page-locked host allocation of the
+// library goes through these, so that a test can make one fail on the host
+// (sdf_debug_fail_alloc) and count what is live (sdf_debug_alloc_live).
+cudaError_t dmalloc_raw(void** p, size_t bytes);
+cudaError_t hmalloc_raw(void** p, size_t bytes);   // page-locked, cudaHostAllocDefault
+template <typename T>
+inline cudaError_t dmalloc(T** p, size_t bytes) { return dmalloc_raw(reinterpret_cast<void**>(p), bytes); }
+template <typename T>
+inline cudaError_t hmalloc(T** p, size_t bytes) { return hmalloc_raw(reinterpret_cast<void**>(p), bytes); }
+void dfree(void* p);   // null is a no-op
+void hfree(void* p);
 
 // Launchers (check.cu / grid_build.cu).  Each returns the launch's cudaError_t.
 cudaError_t configure_kernels();           // once per device, that device current
@@ -161,6 +179,7 @@ struct sdf_ctx {
     int tile_batch = 0;                    // list entries per warp step (0: tuned or 4)
     int reuse_sort = 0;                    // internal: the next check reuses the scratch's sorted cloud
     int block_warps = 0;                   // warps per check block (0: tuned or 16)
+    unsigned wait_polls = sdf::kDefaultWaitPolls;  // polls of a bounded device wait (SDF_OPT_WAIT_POLLS)
     struct Shape { int tw, tb, nw; };
     std::map<uint64_t, Shape> tuned;       // launch shape key -> (waypoints per block, tile batch, warps)
     // scratch owned by the context (grown on demand, or up front by sdf_ctx_reserve)

@@ -101,7 +101,7 @@ extern "C" int sdf_measure_gather(sdf_ctx* ctx, const sdf_grids* grids, double* 
     const uint32_t n_gather = (uint32_t)std::min<size_t>(total, 0xffffffffu);
     float* sink = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaMalloc(&sink, sizeof(float));
+    cudaError_t e = sdf::dmalloc(&sink, sizeof(float));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     double best_g = 0.0, best_c = 0.0;
@@ -132,7 +132,7 @@ extern "C" int sdf_measure_gather(sdf_ctx* ctx, const sdf_grids* grids, double* 
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaFree(sink);
+    sdf::dfree(sink);
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return set_err(ctx, SDF_ERR_CUDA, std::string("sdf_measure_gather: ") + cudaGetErrorString(e));
     if (gathers_per_s) *gathers_per_s = best_g;

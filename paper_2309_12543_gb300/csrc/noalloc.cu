@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "internal.h"
@@ -35,8 +36,8 @@ static_assert(SDF_NOALLOC_MAX_POINTS == kNoAllocMaxPoints, "header limit");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 struct PerDevice {
-    std::once_flag once;
-    cudaError_t err = cudaSuccess;
+    std::mutex mu;
+    std::atomic<bool> ready{false};  // set-up done on this device
     unsigned char* base = nullptr;   // device address of g_noalloc_scratch on this device
     int num_sms = 0;
 };
@@ -44,13 +45,27 @@ constexpr int kMaxDevices = 64;
 PerDevice g_per_device[kMaxDevices];
 
 // Once per device, with that device current: look up the array's device address
-// and set the check kernel's shared-memory limit (neither allocates).
-void setup_device(PerDevice* pd) {
-    pd->err = cudaGetSymbolAddress((void**)&pd->base, g_noalloc_scratch);
-    if (pd->err == cudaSuccess) pd->err = sdf::configure_kernels();
-    int dev = 0;
-    if (pd->err == cudaSuccess) pd->err = cudaGetDevice(&dev);
-    if (pd->err == cudaSuccess) pd->err = cudaDeviceGetAttribute(&pd->num_sms, cudaDevAttrMultiProcessorCount, dev);
+// and set the check kernel's shared-memory limit (neither allocates).  A set-up
+// that failed (for instance inside a stream capture) is not remembered: the next
+// call tries again.
+cudaError_t setup_device(PerDevice* pd) {
+    if (pd->ready.load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(pd->mu);
+    if (pd->ready.load(std::memory_order_relaxed)) return cudaSuccess;
+    unsigned char* base = nullptr;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetSymbolAddress((void**)&base, g_noalloc_scratch);
+    if (e == cudaSuccess) e = sdf::configure_kernels();
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // do not leave the failure for the caller's next CUDA call
+        return e;
+    }
+    pd->base = base;
+    pd->num_sms = sms;
+    pd->ready.store(true, std::memory_order_release);
+    return cudaSuccess;
 }
 
 // The launch parameters are large (one kernel-parameter table); keep one per
@@ -63,6 +78,8 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
                                         const float* points_dev, int32_t N, float* dist_dev,
                                         int32_t* argmin_link_dev, int32_t* argmin_point_dev,
                                         int32_t* status_dev) {
+    // W is an int32, so the block count ceil(W / tw) fits an int; it is still
+    // computed in 64 bits below so that no W can wrap it
     if (!R || W < 0 || N < 0 || N > kNoAllocMaxPoints) return SDF_ERR_INVALID_ARG;
     if (W == 0) return SDF_OK;
     if (!dist_dev || !argmin_link_dev || !argmin_point_dev || (R->dof > 0 && !q_dev) || (N > 0 && !points_dev))
@@ -74,8 +91,7 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
     if (cudaGetDevice(&prev) != cudaSuccess) return SDF_ERR_CUDA;
     if (prev != R->device && cudaSetDevice(R->device) != cudaSuccess) return SDF_ERR_CUDA;
     PerDevice* pd = &g_per_device[R->device];
-    std::call_once(pd->once, setup_device, pd);
-    int rc = pd->err == cudaSuccess ? SDF_OK : SDF_ERR_CUDA;
+    int rc = setup_device(pd) == cudaSuccess ? SDF_OK : SDF_ERR_CUDA;
 
     if (rc == SDF_OK) {
         const cudaStream_t stream = (cudaStream_t)cuda_stream;
@@ -107,9 +123,10 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         I.warm = R->table.values;
         I.warm_bytes = (unsigned long long)I.L * R->table.n * R->table.n * R->table.n * sizeof(float);
         const int n_tiles = (N + 31) / 32;
+        const long long n_blocks = ((long long)W + I.tw - 1) / I.tw;   // <= W < 2^31
         p.n_inst = 1;
         p.n_cloud = 1;
-        p.n_blocks = (W + I.tw - 1) / I.tw;
+        p.n_blocks = (int)n_blocks;
         I.interleave = sdf::interleave_waypoints(p.n_blocks, I.tw, 16, pd->num_sms);
         p.stride = 3;
         p.cull = 1;
@@ -122,6 +139,7 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         p.supers = reinterpret_cast<float4*>(base + kSupersOff);
         p.n_valid = reinterpret_cast<int*>(base + kValidOff);
         p.status = status;
+        p.wait_polls = sdf::kDefaultWaitPolls;
         p.stats = nullptr;
         if (e == cudaSuccess) e = sdf::launch_batch(p, sdf::kDefaultTileBatch, stream, nullptr);
         if (e != cudaSuccess) rc = SDF_ERR_CUDA;

@@ -178,10 +178,10 @@ template <typename T>
 cudaError_t grow_buf(cudaStream_t st, T** buf, size_t* cap, size_t need) {
     if (need <= *cap) return cudaSuccess;
     cudaStreamSynchronize(st);
-    cudaFree(*buf);
+    sdf::dfree(*buf);
     *buf = nullptr;
     *cap = 0;
-    const cudaError_t e = cudaMalloc((void**)buf, need * sizeof(T));
+    const cudaError_t e = sdf::dmalloc(buf, need * sizeof(T));
     if (e == cudaSuccess) *cap = need;
     return e;
 }

@@ -276,14 +276,14 @@ void free_server(sdf_server* S) {
     for (auto& sp : S->slots) {
         Slot& s = *sp;
         if (s.stream) cudaStreamSynchronize(s.stream);
-        cudaFreeHost(s.h_q);
-        cudaFreeHost(s.h_out);
+        sdf::hfree(s.h_q);
+        sdf::hfree(s.h_out);
         if (s.ctx) sdf_ctx_destroy(s.ctx);
         if (s.stream) cudaStreamDestroy(s.stream);
     }
     for (auto& c : S->clouds) {
-        cudaFree(c.d);
-        cudaFreeHost(c.h);
+        sdf::dfree(c.d);
+        sdf::hfree(c.h);
         if (c.ready) cudaEventDestroy(c.ready);
     }
     if (S->upload) cudaStreamDestroy(S->upload);
@@ -319,8 +319,8 @@ int sdf_server_create(const sdf_server_config* cfg, sdf_server** out) {
     S->clouds.resize(kClouds);
     for (auto& cb : S->clouds) {
         if (rc != SDF_OK) break;
-        if (cudaMalloc((void**)&cb.d, np * 3 * sizeof(float)) != cudaSuccess ||
-            cudaMallocHost((void**)&cb.h, np * 3 * sizeof(float)) != cudaSuccess ||
+        if (sdf::dmalloc(&cb.d, np * 3 * sizeof(float)) != cudaSuccess ||
+            sdf::hmalloc(&cb.h, np * 3 * sizeof(float)) != cudaSuccess ||
             cudaEventCreateWithFlags(&cb.ready, cudaEventDisableTiming) != cudaSuccess)
             rc = SDF_ERR_OOM;
     }
@@ -335,8 +335,8 @@ int sdf_server_create(const sdf_server_config* cfg, sdf_server** out) {
         rc = sdf_ctx_reserve(s.ctx, c.max_points, c.max_waypoints, (int64_t)c.max_waypoints * (c.max_dof + 1),
                              c.max_batch);
         if (rc != SDF_OK) break;
-        if (cudaMallocHost((void**)&s.h_q, qn * sizeof(float)) != cudaSuccess ||
-            cudaMallocHost((void**)&s.h_out, 3 * (size_t)c.max_waypoints * sizeof(float)) != cudaSuccess)
+        if (sdf::hmalloc(&s.h_q, qn * sizeof(float)) != cudaSuccess ||
+            sdf::hmalloc(&s.h_out, 3 * (size_t)c.max_waypoints * sizeof(float)) != cudaSuccess)
             rc = SDF_ERR_OOM;
     }
     if (rc != SDF_OK) {

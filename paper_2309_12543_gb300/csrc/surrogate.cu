@@ -51,7 +51,7 @@ static_assert(kOB4 + 1 == kPar, "parameter layout");
 constexpr int kTileBytes = kH * kH * 2;        // one 128 x 128 bf16 operand tile
 constexpr int kAuxCols = 16;                    // [x0 x1 x2 1 g 0 ...] per sample
 constexpr int kAuxBytes = kH * kAuxCols * 2;
-constexpr uint32_t kWaitPolls = 1u << 22;
+constexpr uint32_t kWaitPolls = 1u << 22;   // drain wait after a timeout (MMAs in flight end)
 
 // training kernel shared memory (dynamic part)
 constexpr int kSW2 = 0, kSW3 = kTileBytes, kSH1 = 2 * kTileBytes, kSH2 = 3 * kTileBytes, kSDZ = 4 * kTileBytes,
@@ -97,9 +97,10 @@ __device__ __forceinline__ void sync_for_mma() {
     tc::fence_after_sync();
 }
 
-// Wait for the MMA batch just committed; the block agrees on the outcome.
-__device__ __forceinline__ bool wait_mma(uint64_t* mbar, uint32_t& phase) {
-    const bool ok = tc::mbar_wait(mbar, phase, kWaitPolls);
+// Wait for the MMA batch just committed, at most `limit` polls (SDF_OPT_WAIT_POLLS);
+// the block agrees on the outcome.
+__device__ __forceinline__ bool wait_mma(uint64_t* mbar, uint32_t& phase, uint32_t limit) {
+    const bool ok = tc::mbar_wait(mbar, phase, limit);
     phase ^= 1u;
     tc::fence_after_sync();
     return __syncthreads_and(ok) != 0;
@@ -198,6 +199,7 @@ struct TrainArgs {
     float* grad_out;          // gradient mode: [kPar] in the public layout (no update)
     float* loss_out;          // [L]: sum over the steps of the batch loss
     int* status;
+    uint32_t wait_polls;      // polls of an MMA completion wait before it gives up
 };
 
 __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant__ TrainArgs A) {
@@ -258,14 +260,14 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
             mma_k128(tm + kTZ2, KMAJ(aH1), KMAJ(aW2), kN128KK);
             tc::mma_commit(&mbar);
         }
-        if (!(ok = wait_mma(&mbar, phase))) break;
+        if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
         hidden_epilogue(lane_addr + kTZ2, b2, sH2, t);
         sync_for_mma();
         if (t == 0) {
             mma_k128(tm + kTZ3, KMAJ(aH2), KMAJ(aW3), kN128KK);
             tc::mma_commit(&mbar);
         }
-        if (!(ok = wait_mma(&mbar, phase))) break;
+        if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
         // output layer and the loss gradient g = sign(f - y) / 128
         float f = small[384 + 4 * kH];
         for (int c0 = 0; c0 < kH; c0 += 32) {
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
             mma_k128(tm + kTS4, MNMAJ(aH3), AUXMN(aAux), kN16MM);    // dw4 (column 4)
             tc::mma_commit(&mbar);
         }
-        if (!(ok = wait_mma(&mbar, phase))) break;
+        if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
         // dz2 = dH2 s'(z2)
         for (int c0 = 0; c0 < kH; c0 += 32) {
             float dh[32], zz[32];
@@ -349,7 +351,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
             mma_k128(tm + kTS2, MNMAJ(aDZ), AUXMN(aAux), kN16MM);    // db2 (column 3)
             tc::mma_commit(&mbar);
         }
-        if (!(ok = wait_mma(&mbar, phase))) break;
+        if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
         // dz1 = dH1 s'(z1), z1 recomputed
         for (int c0 = 0; c0 < kH; c0 += 32) {
             float dh[32];
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
             mma_k128(tm + kTS1, MNMAJ(aDZ), AUXMN(aAux), kN16MM);    // [dW1 db1] (columns 0..3)
             tc::mma_commit(&mbar);
         }
-        if (!(ok = wait_mma(&mbar, phase))) break;
+        if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
         const float batch_loss = (red[0][0] + red[0][1] + red[0][2] + red[0][3]) * (1.f / 128.f);
         const float db4 = red[1][0] + red[1][1] + red[1][2] + red[1][3];
         loss_sum += batch_loss;
@@ -503,6 +505,7 @@ struct EvalArgs {
     unsigned long long* keys;          // check mode: per-waypoint packed keys
     float scale[kMaxLinks];            // half-span a of each link's box
     int* status;
+    uint32_t wait_polls;               // polls of an MMA completion wait before it gives up
 };
 
 constexpr int kEvalThreads = 512;   // 16 warps: 4 column groups x the 4 lane quarters
@@ -603,7 +606,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) mlp_eval_kernel(const __grid_
             mma_k128(tm + 0, KMAJ(aH1), KMAJ(aW2), kN128KK);
             tc::mma_commit(&mbar);
         }
-        if (!(ok = wait_mma(&mbar, phase))) break;
+        if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
         {
             float v[32];
             tc::tmem_ld32(lane_addr + c0, v);
@@ -623,7 +626,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) mlp_eval_kernel(const __grid_
             mma_k128(tm + 128, KMAJ(aH2), KMAJ(aW3), kN128KK);
             tc::mma_commit(&mbar);
         }
-        if (!(ok = wait_mma(&mbar, phase))) break;
+        if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
         {
             float v[32];
             tc::tmem_ld32(lane_addr + 128 + c0, v);
@@ -1127,11 +1130,11 @@ int sdf_surrogate_create(sdf_ctx* ctx, const sdf_grids* grids, const float* para
     S->L = grids->n_links;
     S->grids = grids;
     const size_t bytes = sizeof(float) * (size_t)kPar * S->L;
-    cudaError_t e = cudaMalloc(&S->master, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&S->adam_m, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&S->adam_v, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&S->step, sizeof(int) * S->L);
-    if (e == cudaSuccess) e = cudaMalloc(&S->loss, sizeof(float) * S->L);
+    cudaError_t e = sdf::dmalloc(&S->master, bytes);
+    if (e == cudaSuccess) e = sdf::dmalloc(&S->adam_m, bytes);
+    if (e == cudaSuccess) e = sdf::dmalloc(&S->adam_v, bytes);
+    if (e == cudaSuccess) e = sdf::dmalloc(&S->step, sizeof(int) * S->L);
+    if (e == cudaSuccess) e = sdf::dmalloc(&S->loss, sizeof(float) * S->L);
     std::vector<float> dev((size_t)kPar * S->L);
     for (int l = 0; l < S->L; ++l) to_device_layout(params_host + (size_t)l * kPar, dev.data() + (size_t)l * kPar);
     if (e == cudaSuccess) e = cudaMemcpy(S->master, dev.data(), bytes, cudaMemcpyHostToDevice);
@@ -1156,11 +1159,11 @@ int sdf_surrogate_create(sdf_ctx* ctx, const sdf_grids* grids, const float* para
 void sdf_surrogate_destroy(sdf_surrogate* S) {
     if (!S) return;
     Dev guard(S->device);
-    cudaFree(S->master);
-    cudaFree(S->adam_m);
-    cudaFree(S->adam_v);
-    cudaFree(S->step);
-    cudaFree(S->loss);
+    sdf::dfree(S->master);
+    sdf::dfree(S->adam_m);
+    sdf::dfree(S->adam_v);
+    sdf::dfree(S->step);
+    sdf::dfree(S->loss);
     delete S;
 }
 
@@ -1201,16 +1204,16 @@ int sdf_surrogate_sample(sdf_ctx* ctx, const sdf_grids* G, int32_t link, int64_t
     const int nb = (chunk + 1023) / 1024;
     int* counts = nullptr;
     long long* found = nullptr;   // [0] found, [1] found before this chunk
-    e = cudaMalloc(&counts, sizeof(int) * nb);
-    if (e == cudaSuccess) e = cudaMalloc(&found, 2 * sizeof(long long));
+    e = sdf::dmalloc(&counts, sizeof(int) * nb);
+    if (e == cudaSuccess) e = sdf::dmalloc(&found, 2 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(found, 0, 2 * sizeof(long long), st);
     long long have = 0;
     long long start = 0;
     const long long max_candidates = 1ll << 32;   // the counter is 32 bits wide
     while (e == cudaSuccess && have < A.n_near) {
         if (start >= max_candidates) {
-            cudaFree(counts);
-            cudaFree(found);
+            sdf::dfree(counts);
+            sdf::dfree(found);
             return sfail(ctx, SDF_ERR_INVALID_ARG, "sdf_surrogate_sample: too few candidates within the band");
         }
         A.start = start;
@@ -1227,8 +1230,8 @@ int sdf_surrogate_sample(sdf_ctx* ctx, const sdf_grids* G, int32_t link, int64_t
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         start += chunk;
     }
-    cudaFree(counts);
-    cudaFree(found);
+    sdf::dfree(counts);
+    sdf::dfree(found);
     if (e != cudaSuccess) return scuda(ctx, e, "sdf_surrogate_sample");
     return SDF_OK;
 }
@@ -1255,6 +1258,7 @@ int launch_train(sdf_ctx* ctx, sdf_surrogate* S, int link0, int links, const flo
     A.grad_out = grad_out;
     A.loss_out = loss_out;
     A.status = ctx->status;
+    A.wait_polls = ctx->wait_polls;
     sdf::mlp_train_kernel<<<links, 128, sdf::kTrainSmem, ctx->stream>>>(A);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SDF_OK : scuda(ctx, e, "mlp_train_kernel");
@@ -1302,6 +1306,7 @@ int sdf_surrogate_eval(sdf_ctx* ctx, const sdf_surrogate* S, int32_t link, const
     A.link0 = link;
     A.f_out = f_dev;
     A.status = ctx->status;
+    A.wait_polls = ctx->wait_polls;
     const int tiles = (n + 127) / 128;
     const int grid = std::min(tiles, ctx->num_sms);
     sdf::mlp_eval_kernel<<<grid, sdf::kEvalThreads, sdf::kEvalSmem, ctx->stream>>>(A);
@@ -1332,16 +1337,16 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
     if ((size_t)W > ctx->sur_w_cap || (size_t)L > ctx->sur_links) {
         const size_t cap = std::max<size_t>((size_t)W, 2 * ctx->sur_w_cap);
         cudaStreamSynchronize(st);
-        cudaFree(ctx->sur_poses);
-        cudaFree(ctx->sur_keys);
-        cudaFree(ctx->sur_mask);
+        sdf::dfree(ctx->sur_poses);
+        sdf::dfree(ctx->sur_keys);
+        sdf::dfree(ctx->sur_mask);
         ctx->sur_poses = nullptr;
         ctx->sur_keys = nullptr;
         ctx->sur_mask = nullptr;
         ctx->sur_w_cap = 0;
-        e = cudaMalloc(&ctx->sur_poses, sizeof(float) * 16 * SDF_MAX_LINKS * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&ctx->sur_keys, sizeof(unsigned long long) * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&ctx->sur_mask, cap);
+        e = sdf::dmalloc(&ctx->sur_poses, sizeof(float) * 16 * SDF_MAX_LINKS * cap);
+        if (e == cudaSuccess) e = sdf::dmalloc(&ctx->sur_keys, sizeof(unsigned long long) * cap);
+        if (e == cudaSuccess) e = sdf::dmalloc(&ctx->sur_mask, cap);
         if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate: workspace");
         ctx->sur_w_cap = cap;
     }
@@ -1350,15 +1355,15 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
     if (want > ctx->sur_cap || (size_t)L > ctx->sur_links) {
         const size_t cap = std::max(want, ctx->sur_cap);
         cudaStreamSynchronize(st);
-        cudaFree(ctx->sur_xq);
-        cudaFree(ctx->sur_tag);
+        sdf::dfree(ctx->sur_xq);
+        sdf::dfree(ctx->sur_tag);
         ctx->sur_xq = nullptr;
         ctx->sur_tag = nullptr;
         ctx->sur_cap = 0;
         ctx->sur_links = 0;
-        if (!ctx->sur_count) e = cudaMalloc(&ctx->sur_count, sizeof(int) * SDF_MAX_LINKS);
-        if (e == cudaSuccess) e = cudaMalloc(&ctx->sur_xq, sizeof(float4) * L * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&ctx->sur_tag, sizeof(uint2) * L * cap);
+        if (!ctx->sur_count) e = sdf::dmalloc(&ctx->sur_count, sizeof(int) * SDF_MAX_LINKS);
+        if (e == cudaSuccess) e = sdf::dmalloc(&ctx->sur_xq, sizeof(float4) * L * cap);
+        if (e == cudaSuccess) e = sdf::dmalloc(&ctx->sur_tag, sizeof(uint2) * L * cap);
         if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate: query buffers");
         ctx->sur_cap = cap;
         ctx->sur_links = (size_t)L;
@@ -1411,6 +1416,7 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
     E.keys = ctx->sur_keys;
     for (int l = 0; l < L; ++l) E.scale[l] = S->box_a[l];
     E.status = ctx->status;
+    E.wait_polls = ctx->wait_polls;
     const unsigned pair_blocks = (unsigned)(((size_t)W * L * 32 + 255) / 256);
     const int eval_grid = ctx->num_sms;
     if (rc == SDF_OK && e == cudaSuccess) {
@@ -1474,11 +1480,11 @@ int sdf_surrogate_error(sdf_ctx* ctx, const sdf_surrogate* S, int32_t link, int6
     float *x = nullptr, *y = nullptr, *f = nullptr;
     unsigned* mx = nullptr;
     double* sum = nullptr;
-    cudaError_t e = cudaMalloc(&x, sizeof(float) * 3 * n);
-    if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(float) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&f, sizeof(float) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&mx, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&sum, sizeof(double));
+    cudaError_t e = sdf::dmalloc(&x, sizeof(float) * 3 * n);
+    if (e == cudaSuccess) e = sdf::dmalloc(&y, sizeof(float) * n);
+    if (e == cudaSuccess) e = sdf::dmalloc(&f, sizeof(float) * n);
+    if (e == cudaSuccess) e = sdf::dmalloc(&mx, sizeof(unsigned));
+    if (e == cudaSuccess) e = sdf::dmalloc(&sum, sizeof(double));
     int rc = e == cudaSuccess ? SDF_OK : scuda(ctx, e, "sdf_surrogate_error");
     if (rc == SDF_OK) rc = sdf_surrogate_sample(ctx, S->grids, link, n, near_per_10, band, seed, x, y, nullptr);
     if (rc == SDF_OK) rc = sdf_surrogate_eval(ctx, S, link, x, (int32_t)n, f);
@@ -1496,11 +1502,11 @@ int sdf_surrogate_error(sdf_ctx* ctx, const sdf_surrogate* S, int32_t link, int6
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) rc = scuda(ctx, e, "sdf_surrogate_error");
     }
-    cudaFree(x);
-    cudaFree(y);
-    cudaFree(f);
-    cudaFree(mx);
-    cudaFree(sum);
+    sdf::dfree(x);
+    sdf::dfree(y);
+    sdf::dfree(f);
+    sdf::dfree(mx);
+    sdf::dfree(sum);
     if (rc == SDF_OK) {
         float m;
         std::memcpy(&m, &hm, sizeof(float));

@@ -46,3 +46,17 @@ def test_binding_constants_match_header():
     for name, val in re.findall(r"#define (SDF_\w+) \(?(-?\d+)\)?", text):
         if hasattr(sdf._native, name):
             assert getattr(sdf._native, name) == int(val), name
+
+
+def test_fault_injection_counter_on_the_host(libpath):
+    """The allocation-failure countdown is host state: armed, read back and
+    disarmed without a GPU; a negative countdown is rejected."""
+    import paper_2309_12543_gb300 as sdf
+    count, nbytes, countdown = sdf.sdf_debug_alloc_live()
+    assert count >= 0 and nbytes >= 0 and countdown == 0
+    sdf.sdf_debug_fail_alloc(5)
+    assert sdf.sdf_debug_alloc_live()[2] == 5
+    sdf.sdf_debug_fail_alloc(0)
+    assert sdf.sdf_debug_alloc_live()[2] == 0
+    with pytest.raises(sdf.SdfError):
+        sdf.sdf_debug_fail_alloc(-1)
