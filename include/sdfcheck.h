@@ -123,6 +123,18 @@ const char* sdf_last_error(const sdf_ctx* ctx);
                                      drains its own copies or MMAs with a wait of the default
                                      length, then leaves.  Small values exist for tests of the
                                      timeout path. */
+#define SDF_OPT_TEX3D 10          /* 1: grid lookups by the texture unit's trilinear filter
+                                     (Sec. III-A's grid-sample interpolation in hardware)
+                                     instead of the FP32 software interpolation; 0 (default).
+                                     The filter keeps each axis weight with 8 fractional bits,
+                                     so a value may differ from the FP32 interpolation by up
+                                     to about 3 h / 256 (h the grid spacing): at h = 5 mm it
+                                     does not meet a 1e-5 m tolerance, hence off by default.
+                                     The culls stay exact for the filtered values (each link's
+                                     bounding volume grows by sqrt(3) h / 256).  The first
+                                     check of a grids object with the option on makes its
+                                     texture copy (n^3 FP32 per link; allocates and
+                                     synchronises); sdf_grids_destroy frees it. */
 int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t value);
 int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* value);
 

@@ -61,6 +61,20 @@ cudaError_t hmalloc_raw(void** p, size_t bytes) {
     return track(cudaHostAlloc(p, bytes, cudaHostAllocDefault), *p, bytes);
 }
 
+cudaError_t amalloc3d(cudaArray_t* a, int n) {
+    *a = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    const cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
+    return track(cudaMalloc3DArray(a, &fd, make_cudaExtent((size_t)n, (size_t)n, (size_t)n)), (void*)*a,
+                 (size_t)n * n * n * sizeof(float));
+}
+
+void afree(cudaArray_t a) {
+    if (!a) return;
+    untrack((void*)a);
+    cudaFreeArray(a);
+}
+
 void dfree(void* p) {
     if (!p) return;
     untrack(p);

@@ -191,6 +191,7 @@ int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t v) {
             if (v < 0 || v > (int64_t)UINT32_MAX) return fail(ctx, SDF_ERR_INVALID_ARG, "wait polls must be 0..2^32-1");
             ctx->wait_polls = (unsigned)v;
             return SDF_OK;
+        case SDF_OPT_TEX3D: ctx->tex3d = v ? 1 : 0; return SDF_OK;
         case SDF_OPT_STATS:
             if (v && !ctx->d_stats) {
                 DeviceGuard g(ctx->device);
@@ -216,6 +217,7 @@ int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* v) {
         case SDF_OPT_STATS: *v = ctx->stats; return SDF_OK;
         case SDF_OPT_BLOCK_WARPS: *v = ctx->block_warps; return SDF_OK;
         case SDF_OPT_WAIT_POLLS: *v = (int64_t)ctx->wait_polls; return SDF_OK;
+        case SDF_OPT_TEX3D: *v = ctx->tex3d; return SDF_OK;
         default: return SDF_ERR_INVALID_ARG;
     }
 }
@@ -466,6 +468,11 @@ int sdf_grids_info(const sdf_grids* G, int32_t* n_links, int32_t* resolution) {
 void sdf_grids_destroy(sdf_grids* G) {
     if (!G) return;
     DeviceGuard g(G->device);
+    for (int l = 0; l < SDF_MAX_LINKS; ++l) {
+        if (G->tex[l]) cudaDestroyTextureObject(G->tex[l]);
+        sdf::afree(G->tex_arr[l]);
+    }
+    sdf::dfree(G->d_tex);
     sdf::dfree(G->values);
     delete G;
 }
@@ -565,6 +572,51 @@ void link_capsule(const float* v, int n, const sdf_grid_meta& m, float4* ca, flo
     const float rf = std::nextafter((float)r, INFINITY);
     *ca = make_float4((float)A[0], (float)A[1], (float)A[2], rf);
     *cb = make_float4((float)B[0], (float)B[1], (float)B[2], 0.f);
+}
+
+// The hardware-filtered copy of the grids (SDF_OPT_TEX3D): per link a 3-D array of
+// the FP32 values and a texture object with linear filtering, clamped addressing
+// and unnormalised coordinates (texel (i,j,k) is sampled at (i,j,k) + 1/2).  Made
+// once per grids object; allocates and synchronises.
+int grid_textures(sdf_ctx* ctx, sdf_grids* G) {
+    if (G->d_tex) return SDF_OK;
+    const int n = G->n;
+    const size_t n3 = (size_t)n * n * n;
+    unsigned long long h[SDF_MAX_LINKS] = {0};
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < G->n_links && e == cudaSuccess; ++l) {
+        if (!G->tex_arr[l]) e = sdf::amalloc3d(&G->tex_arr[l], n);
+        if (e != cudaSuccess) break;
+        cudaMemcpy3DParms cp = {};
+        cp.srcPtr = make_cudaPitchedPtr(G->values + l * n3, (size_t)n * sizeof(float), (size_t)n, (size_t)n);
+        cp.dstArray = G->tex_arr[l];
+        cp.extent = make_cudaExtent((size_t)n, (size_t)n, (size_t)n);
+        cp.kind = cudaMemcpyDeviceToDevice;
+        e = cudaMemcpy3DAsync(&cp, ctx->stream);
+        if (e != cudaSuccess) break;
+        if (!G->tex[l]) {
+            cudaResourceDesc rd = {};
+            rd.resType = cudaResourceTypeArray;
+            rd.res.array.array = G->tex_arr[l];
+            cudaTextureDesc td = {};
+            td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+            td.filterMode = cudaFilterModeLinear;
+            td.readMode = cudaReadModeElementType;
+            td.normalizedCoords = 0;
+            e = cudaCreateTextureObject(&G->tex[l], &rd, &td, nullptr);
+        }
+        h[l] = (unsigned long long)G->tex[l];
+    }
+    unsigned long long* d = nullptr;
+    if (e == cudaSuccess) e = sdf::dmalloc(&d, sizeof h);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h, sizeof h, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        sdf::dfree(d);   // the arrays and objects stay with G (freed by sdf_grids_destroy)
+        return cuda_fail(ctx, e, "texture copy of the grids");
+    }
+    G->d_tex = d;
+    return SDF_OK;
 }
 
 int grid_capsules(sdf_ctx* ctx, sdf_grids* G) {
@@ -795,6 +847,14 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
         const int rc = validate_request(ctx, reqs[i], i);
         if (rc != SDF_OK) return rc;
     }
+    if (ctx->tex3d) {   // the texture copy of every robot's grids (made once; may synchronise)
+        DeviceGuard g(ctx->device);
+        for (int i = 0; i < n; ++i)
+            if (reqs[i].W > 0) {
+                const int rc = grid_textures(ctx, const_cast<sdf_grids*>(reqs[i].robot->grids));
+                if (rc != SDF_OK) return rc;
+            }
+    }
     sdf::BatchParams* p = new (std::nothrow) sdf::BatchParams();
     if (!p) return fail(ctx, SDF_ERR_OOM, "host allocation");
     const uint64_t key = shape_key(reqs, n);
@@ -839,9 +899,11 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
         I.dof = r.robot->dof;
         I.cloud = c;
         I.mask = r.mask_dev;
-        I.warm = r.robot->table.values;
+        I.tex = ctx->tex3d ? r.robot->grids->d_tex : nullptr;
+        // the linear grids are prefetched into L2 only when the lookups read them
+        I.warm = ctx->tex3d ? nullptr : r.robot->table.values;
         I.warm_bytes = (unsigned long long)I.L * r.robot->table.n * r.robot->table.n * r.robot->table.n * sizeof(float);
-        for (int j = 0; j < k - 1; ++j)
+        for (int j = 0; j < k - 1 && I.warm; ++j)
             if (p->inst[j].warm == I.warm) I.warm = nullptr;   // warmed by an earlier trajectory
         launch_shape(ctx, key, I.L, nw, &I.tw, &tile_batch);
         I.block_base = (int)blocks;

@@ -547,6 +547,7 @@ struct BlockState {
     const uchar2* pair_wl;     // per pair: (waypoint of the block, link), no division in the hot loops
     const float4* grid_o;      // per link (shared memory)
     const float* grid_h;
+    const unsigned long long* tex;  // per link texture objects (shared memory), or null
     unsigned* best;            // per waypoint of the block
     unsigned long long* key;
     int cull;
@@ -589,7 +590,8 @@ __device__ __forceinline__ void evaluate(const BlockState& B, int pos, int pair)
     const float lx = fmaf(r0.x, p.x, fmaf(r0.y, p.y, fmaf(r0.z, p.z, r0.w)));
     const float ly = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
     const float lz = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
-    const float g = grid_lookup(B.values + (size_t)(l * B.n3), B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz);
+    const float g = B.tex ? tex_lookup(B.tex[l], B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz)
+                          : grid_lookup(B.values + (size_t)(l * B.n3), B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz);
     const unsigned long long key = pack_key(g, __float_as_int(p.w), l);
     const unsigned ob = (unsigned)(key >> 32);
     if (ob <= B.best[wl]) {
@@ -668,6 +670,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     __shared__ uchar2 s_pair_wl[NW];
     __shared__ float4 s_grid_o[kMaxLinks];
     __shared__ float s_grid_h[kMaxLinks];
+    __shared__ unsigned long long s_tex[kMaxLinks];
     __shared__ unsigned s_best[NW];
     __shared__ unsigned long long s_key[NW];
     __shared__ unsigned s_list[kBlockList];
@@ -715,6 +718,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     if (tid < L) {
         s_grid_o[tid] = T.grid_o[tid];
         s_grid_h[tid] = T.grid_h[tid];
+        if (I.tex) s_tex[tid] = I.tex[tid];
     }
     if (tid < n_pair) s_pair_wl[tid] = make_uchar2((unsigned char)(tid / L), (unsigned char)(tid % L));
     if (tid == 0) {
@@ -753,7 +757,8 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
             }
             const float dx = Bw[0] - A[0], dy = Bw[1] - A[1], dz = Bw[2] - A[2];
             const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            dst[4] = make_float4(A[0], A[1], A[2], a.w);
+            // under the texture lookup the capsule grows by the filter's point shift
+            dst[4] = make_float4(A[0], A[1], A[2], I.tex ? a.w + tex_cull_pad(T.grid_h[lane]) : a.w);
             dst[5] = make_float4(dx, dy, dz, dd > 0.f ? 1.f / dd : 0.f);
         }
     }
@@ -820,6 +825,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     B.pose = s_pose;
     B.grid_o = s_grid_o;
     B.grid_h = s_grid_h;
+    B.tex = I.tex ? s_tex : nullptr;
     B.best = s_best;
     B.key = s_key;
     B.cull = P.cull;

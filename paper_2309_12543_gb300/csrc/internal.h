@@ -61,6 +61,8 @@ struct InstDesc {
     int tw;                   // waypoints per check block (tw * L <= kCheckWarps)
     int block_base;           // first check block of this trajectory
     const uint8_t* mask;      // optional: only waypoints with a non-zero byte are checked
+    const unsigned long long* tex;  // SDF_OPT_TEX3D: the robot's per-link texture objects
+                                    // (device), null for the FP32 software lookup
     const float* warm;        // the robot's grids, for the first trajectory of each robot
                               // in the launch (null otherwise): its blocks prefetch them
                               // into L2 while the sort runs
@@ -111,6 +113,8 @@ template <typename T>
 inline cudaError_t hmalloc(T** p, size_t bytes) { return hmalloc_raw(reinterpret_cast<void**>(p), bytes); }
 void dfree(void* p);   // null is a no-op
 void hfree(void* p);
+cudaError_t amalloc3d(cudaArray_t* a, int n);   // n^3 FP32 texels (one channel)
+void afree(cudaArray_t a);
 
 // Launchers (check.cu / grid_build.cu).  Each returns the launch's cudaError_t.
 cudaError_t configure_kernels();           // once per device, that device current
@@ -153,6 +157,12 @@ struct sdf_grids {
     sdf_grid_meta meta[SDF_MAX_LINKS];
     bool capsules = false;    // cap_a / cap_b computed (on first use)
     float4 cap_a[SDF_MAX_LINKS], cap_b[SDF_MAX_LINKS];
+    // hardware-filtered copy (SDF_OPT_TEX3D), made by the first check that asks for it:
+    // one 3-D array and linear-filtering texture object per link, the objects' handles
+    // in device memory for the kernels
+    cudaArray_t tex_arr[SDF_MAX_LINKS] = {};
+    cudaTextureObject_t tex[SDF_MAX_LINKS] = {};
+    unsigned long long* d_tex = nullptr;
 };
 
 struct sdf_robot {
@@ -179,6 +189,7 @@ struct sdf_ctx {
     int tile_batch = 0;                    // list entries per warp step (0: tuned or 4)
     int reuse_sort = 0;                    // internal: the next check reuses the scratch's sorted cloud
     int block_warps = 0;                   // warps per check block (0: tuned or 16)
+    int tex3d = 0;                         // lookups by the texture unit's trilinear filter
     unsigned wait_polls = sdf::kDefaultWaitPolls;  // polls of a bounded device wait (SDF_OPT_WAIT_POLLS)
     struct Shape { int tw, tb, nw; };
     std::map<uint64_t, Shape> tuned;       // launch shape key -> (waypoints per block, tile batch, warps)

@@ -134,7 +134,9 @@ extern "C" int sdf_measure_gather(sdf_ctx* ctx, const sdf_grids* grids, double* 
     if (e1) cudaEventDestroy(e1);
     sdf::dfree(sink);
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
-    if (e != cudaSuccess) return set_err(ctx, SDF_ERR_CUDA, std::string("sdf_measure_gather: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess)
+        return set_err(ctx, e == cudaErrorMemoryAllocation ? SDF_ERR_OOM : SDF_ERR_CUDA,
+                       std::string("sdf_measure_gather: ") + cudaGetErrorString(e));
     if (gathers_per_s) *gathers_per_s = best_g;
     if (cells_per_s) *cells_per_s = best_c;
     return SDF_OK;

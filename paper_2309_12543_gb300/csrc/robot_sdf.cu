@@ -245,6 +245,7 @@ extern "C" int check_trajectory_robot_sdf(sdf_ctx* ctx, const sdf_robot* R, cons
         e = cudaGetLastError();
     }
     if (e != cudaSuccess)
-        return rfail(ctx, SDF_ERR_CUDA, std::string("check_trajectory_robot_sdf: ") + cudaGetErrorString(e));
+        return rfail(ctx, e == cudaErrorMemoryAllocation ? SDF_ERR_OOM : SDF_ERR_CUDA,
+                     std::string("check_trajectory_robot_sdf: ") + cudaGetErrorString(e));
     return SDF_OK;
 }

@@ -1056,7 +1056,8 @@ int sfail(sdf_ctx* ctx, int code, const std::string& msg) {
     return code;
 }
 int scuda(sdf_ctx* ctx, cudaError_t e, const char* what) {
-    return sfail(ctx, SDF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return sfail(ctx, e == cudaErrorMemoryAllocation ? SDF_ERR_OOM : SDF_ERR_CUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
 }
 
 struct Dev {
