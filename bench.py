@@ -31,14 +31,34 @@ sys.path.insert(0, ROOT)
 
 METRIC = "µs per 500-waypoint×20k-point check (p50/p99); SDF queries/s vs gather roofline"
 UNIT = "µs per check"
-# one cull test per (waypoint, link, point) pair: 3 sub, 1 mul, 2 fma, 1 compare
-CULL_OPS_PER_PAIR = 7
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of one check_kernel launch on the 500 x 20k workload,
-# from ncu (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
-# launch), taken on a launch with per-kernel events like the ones kernel_us times;
-# the check kernel's ncu summary under profiles/ gives the capture and its command.
-CHECK_KERNEL_DRAM_BYTES = 8_632_832
+# L1/tex data path of one SM: 128 bytes per clock (four 32-byte sectors)
+L1_BYTES_PER_CLK = 128
+# Bytes the check kernel moves through L1/tex for each unit of work it does (the
+# work counted by the SDF_OPT_STATS pass, so that nothing is credited for pairs the
+# culls skip):
+#   point test       16 B  one sorted point (float4) of a surviving (pair, tile) entry
+#   tile/super test  16 B  one sphere (float4) from shared memory
+#   lookup          144 B  the point again (16 B) + the 8 corner values of one grid
+#                          cell, which lie in 4 distinct 32-byte sectors (x pairs share
+#                          a sector; the y and z neighbours are 384 B and 36 KB away)
+BYTES_PER_POINT_TEST = 16
+BYTES_PER_SPHERE_TEST = 16
+BYTES_PER_LOOKUP = 16 + 4 * 32
+# FP32 operations per unit of work (capsule distance test: 3 sub, 3 fma dot, 1 mul,
+# 2 clamp, 3 fma, 3 fma, 1 compare; lookup: 9 fma transform, 3 fma + 6 clamp index,
+# 3 sub + 3 fma + sqrt out-of-box, 7 lerps x 2, key packing)
+OPS_PER_CAPSULE_TEST = 16
+OPS_PER_LOOKUP = 40
+# From the committed ncu capture of check_kernel on this workload (one launch timed
+# apart, caches flushed first); the check kernel's ncu summary under profiles/ gives
+# the capture and its command.  None once the kernel has changed since.
+CHECK_KERNEL_NCU = {
+    "dram_bytes": 8_632_832,                  # dram__bytes_read.sum + dram__bytes_write.sum
+    "l1tex_throughput_pct": 44.50,            # l1tex__throughput.avg.pct_of_peak_sustained_active
+    "lts_sector_hit_rate_pct": 64.94,         # lts__t_sector_hit_rate.pct
+    "duration_us": 32.19,                     # gpu__time_duration.sum
+}
 
 
 def parse():
@@ -58,6 +78,7 @@ def parse():
     ap.add_argument("--rates", default="", help="serve: extra arrival rates (per cycle) to sweep, grid form")
     ap.add_argument("--order", default="voxel", choices=["voxel", "random"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="paper: skip the 64-request batched measurement")
     ap.add_argument("--e2e-steps", type=int, default=100)
     return ap.parse_args()
 
@@ -194,6 +215,50 @@ def time_oracle(scene, vals, metas, budget_s=15.0, max_reps=5):
     return us, len(times), cores, sample
 
 
+def time_oracle_one_thread(scene, vals, metas, budget_s=8.0):
+    """The oracle check on one host thread, on a slice of waypoints scaled to the
+    full check (median of up to 3 runs)."""
+    import oracle
+    W = scene.q.shape[0]
+    oracle.set_threads(1)
+    try:
+        k = max(1, min(W, 4))
+        t = time.perf_counter()
+        oracle.check(scene.dh, scene.base, vals, metas, scene.q[:k], scene.points)
+        probe = time.perf_counter() - t
+        wsel = int(min(W, max(1, k * budget_s / 3.0 / max(probe, 1e-9))))
+        times = []
+        for _ in range(3):
+            t = time.perf_counter()
+            oracle.check(scene.dh, scene.base, vals, metas, scene.q[:wsel], scene.points)
+            times.append((time.perf_counter() - t) * W / wsel)
+    finally:
+        oracle.set_threads(cpu_cores())
+    return statistics.median(times) * 1e6, f"{wsel} of {W} waypoints, 1 thread, median of 3, scaled to the full check"
+
+
+def tiny_oracle_baseline():
+    """The small scene (6-DoF, 32^3 grids, 50 waypoints x 1,000 points): the oracle on
+    all cores and on one thread, median of 5 full checks each."""
+    import oracle
+    import scenegen
+    sc = scenegen.make_scene("tiny")
+    vals, metas = oracle_grids(sc)
+    out = {}
+    for name, threads in (("all_cores", cpu_cores()), ("one_thread", 1)):
+        oracle.set_threads(threads)
+        times = []
+        for _ in range(5):
+            t = time.perf_counter()
+            oracle.check(sc.dh, sc.base, vals, metas, sc.q, sc.points)
+            times.append(time.perf_counter() - t)
+        out[name] = statistics.median(times) * 1e6
+    oracle.set_threads(cpu_cores())
+    return {"value": out["all_cores"], "one_thread": out["one_thread"], "unit": UNIT, "cores": cpu_cores(),
+            "sample": "tiny: 6-DoF, 7 links x 512-triangle capsules, 32^3 grids, W=50, N=1000; full check, "
+                      "median of 5"}
+
+
 # --------------------------------------------------------------- reference
 
 def run_reference(args):
@@ -308,6 +373,24 @@ def run_ours(args):
     if rc != 0:
         raise RuntimeError(f"timed checks failed: {ctx.last_error()}")
 
+    # the hardware trilinear option (SDF_OPT_TEX3D): the same timed steps with the
+    # texture unit's filter doing the lookups (off by default: it misses 1e-5 m)
+    ctx.set_option(sdf.SDF_OPT_TEX3D, 1)
+    step()
+    torch.cuda.synchronize(dev)
+    tex_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        tex_ev[i][0].record(stream)
+        step()
+        tex_ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.set_option(sdf.SDF_OPT_TEX3D, 0)
+    tex_us = [a.elapsed_time(b) * 1e3 for a, b in tex_ev]
+    if ctx.synchronize() != 0:
+        raise RuntimeError(f"tex3d checks failed: {ctx.last_error()}")
+
     # per-kernel device times for the roofline: the same steps with the library's
     # events around each kernel (the kernels then run back to back, not overlapped)
     ctx.set_option(sdf.SDF_OPT_TIME_KERNELS, 1)
@@ -378,9 +461,19 @@ def run_ours(args):
     kern_us = statistics.mean(kernel_ms) * 1e3
     pairs = W * L * N
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    max_mhz = clk.get("sm_max_mhz") or 2070.0
-    peak_ops = sms * FP32_LANES_PER_SM * max_mhz * 1e6         # FP32 lane-ops/s
-    achieved_ops = pairs * CULL_OPS_PER_PAIR / (kern_us * 1e-6)
+    clock_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0     # median SM clock under load
+    lookups = st["seed_lookups"] + st["lookups"]
+    sphere_tests = st["super_tests"] + st["tile_tests"]
+    l1_bytes = (st["point_tests"] * BYTES_PER_POINT_TEST + sphere_tests * BYTES_PER_SPHERE_TEST
+                + lookups * BYTES_PER_LOOKUP)
+    l1_peak = sms * L1_BYTES_PER_CLK * clock_mhz * 1e6                   # B/s
+    l1_achieved = l1_bytes / (kern_us * 1e-6)
+    alu_ops = (st["point_tests"] + sphere_tests) * OPS_PER_CAPSULE_TEST + lookups * OPS_PER_LOOKUP
+    alu_peak = sms * FP32_LANES_PER_SM * clock_mhz * 1e6
+    alu_achieved = alu_ops / (kern_us * 1e-6)
+    dense_lookups_ps = pairs / (dense_us * 1e-6)
+    ncu = dict(CHECK_KERNEL_NCU) if scene.name == "paper" else None
+    hbm_bytes = int(N * 12 + W * scene.dof * 4 + W * 12 + N * 16)   # cloud in, q, outputs, sorted cloud
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
@@ -389,27 +482,51 @@ def run_ours(args):
         "p50_us": percentile([s * 1e3 for s in step_ms], 50),
         "p99_us": percentile([s * 1e3 for s in step_ms], 99),
         "queries_per_s": pairs / (value * 1e-6),
+        "queries": "(waypoint, link, point) distance queries answered per second of step time; the culls "
+                   "answer all but the looked-up ones without a gather",
         "grid_build_s": grid_build_s,
         "gpu_launches": 2 * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved_ops / peak_ops,
-                     "traffic": CHECK_KERNEL_DRAM_BYTES if scene.name == "paper" else None,
+        "roofline": {"bound": "l1tex", "achieved": l1_achieved / 1e9, "peak": l1_peak / 1e9, "unit": "GB/s",
+                     "frac": l1_achieved / l1_peak,
+                     "traffic": ncu["dram_bytes"] if ncu else None,
                      "kernel": "check_kernel", "kernel_us": kern_us,
                      "prep_kernel_us": statistics.mean(prep_ms) * 1e3,
-                     "algorithmic": f"{CULL_OPS_PER_PAIR} FP32 ops x {pairs} (waypoint, link, point) pairs",
-                     "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz"},
-        "gather": {"lookups_per_check": st["seed_lookups"] + st["lookups"],
-                   "achieved_lookups_per_s": (st["seed_lookups"] + st["lookups"]) / (kern_us * 1e-6),
+                     "algorithmic_bytes": l1_bytes,
+                     "algorithmic": (f"{st['point_tests']} point tests x {BYTES_PER_POINT_TEST} B + {sphere_tests} "
+                                     f"tile/super-tile sphere tests x {BYTES_PER_SPHERE_TEST} B + {lookups} lookups x "
+                                     f"{BYTES_PER_LOOKUP} B, counted by an untimed statistics pass of the same check "
+                                     f"(only work done; nothing for culled pairs)"),
+                     "peak_source": f"{sms} SMs x {L1_BYTES_PER_CLK} B/clk x {clock_mhz:.0f} MHz (median SM clock "
+                                    f"sampled under load)",
+                     "alu": {"ops": alu_ops, "achieved_tops": alu_achieved / 1e12, "peak_tops": alu_peak / 1e12,
+                             "frac": alu_achieved / alu_peak,
+                             "counted": f"{OPS_PER_CAPSULE_TEST} FP32 ops per capsule test, {OPS_PER_LOOKUP} per lookup"},
+                     "ncu": ncu,
+                     "traffic_note": (f"DRAM bytes of one launch timed apart after an L2 flush, against {hbm_bytes} B "
+                                      "of algorithmic HBM traffic (cloud, q, outputs): the rest is the touched part "
+                                      "of the 24.8 MB of grids, re-read from DRAM because the bench flushes L2 before "
+                                      "every step; in a control loop they stay L2-resident") if ncu else None},
+        "gather": {"lookups_per_check": lookups,
+                   "achieved_lookups_per_s": lookups / (kern_us * 1e-6),
                    "peak_cell_reads_per_s": cells_ps, "peak_gathers_per_s": gathers_ps,
-                   "frac": (st["seed_lookups"] + st["lookups"]) / (kern_us * 1e-6) / cells_ps,
+                   "frac": lookups / (kern_us * 1e-6) / cells_ps,
+                   "theoretical_lookups_per_s": l1_peak / (4 * 32),
+                   "frac_of_theoretical": lookups / (kern_us * 1e-6) / (l1_peak / (4 * 32)),
                    "effective_pairs_per_s": pairs / (kern_us * 1e-6),
-                   "effective_frac": pairs / (kern_us * 1e-6) / cells_ps,
                    "point_tests_per_check": st["point_tests"],
-                   "dense_lookups_per_s": W * L * N / (dense_us * 1e-6),
-                   "dense_frac": W * L * N / (dense_us * 1e-6) / cells_ps,
+                   "sphere_tests_per_check": sphere_tests,
+                   "dense_lookups_per_s": dense_lookups_ps,
+                   "dense_frac": dense_lookups_ps / cells_ps,
+                   "dense_frac_of_theoretical": dense_lookups_ps / (l1_peak / (4 * 32)),
                    "dense_kernel_us": dense_us,
-                   "peak_source": "sdf_measure_gather on the check's grids (random cells, 2-8 blocks/SM, best)",
+                   "peak_source": "sdf_measure_gather on the check's grids (random cells, 2-8 blocks/SM, best); "
+                                  "not a ceiling for sorted points, which the dense pass shows by exceeding it; "
+                                  "theoretical = one 4-sector cell per SM clock slot of the L1 data path",
                    "dense": "culling off: every (waypoint, link, point) pair looked up, check kernel alone"},
+        "tex3d": {"mean_us": statistics.mean(tex_us), "p50_us": percentile(tex_us, 50),
+                  "p99_us": percentile(tex_us, 99),
+                  "note": "SDF_OPT_TEX3D: lookups by the texture unit's trilinear filter (8-bit weights; off by "
+                          "default because it misses the 1e-5 m tolerance); same steps, L2 flushed"},
         "e2e": {"value": statistics.median(e2e), "unit": UNIT, "p99": percentile(e2e, 99),
                 "call": "sdf.HostCheck (prepared host-buffer check)",
                 "oneshot_value": statistics.median(e2e_oneshot), "oneshot_p99": percentile(e2e_oneshot, 99),
@@ -417,10 +534,18 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(dh_.nbytes + lh.nbytes + ph_.nbytes)},
         "clocks": clk,
     }
+    if scene.name == "paper" and not args.no_batched:
+        b = batched_measurement(args, dev, local, steps=max(20, min(args.steps, 200)), warmup=max(args.warmup, 3))
+        b.pop("step_us")
+        b.pop("clocks")
+        out["batched"] = b
     if ws == 1 and not args.no_cpu_baseline:
         vals, metas = oracle_grids(scene)
         us, reps, cores, sample = time_oracle(scene, vals, metas)
-        out["cpu_baseline"] = {"value": us, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        one_us, one_sample = time_oracle_one_thread(scene, vals, metas)
+        out["cpu_baseline"] = {"value": us, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                               "one_thread": {"value": one_us, "unit": UNIT, "cores": 1, "sample": one_sample},
+                               "tiny": tiny_oracle_baseline()}
     print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -431,21 +556,13 @@ def run_ours(args):
 BATCH_METRIC = "µs per batch of 64 uneven trajectory checks (one graph replay)"
 
 
-def run_batched(args):
+def batched_measurement(args, dev, local, steps, warmup, clocks=None):
     """64 independent checks (W ~ U[50,1000], N log-uniform [1k,100k], 6- and 7-DoF
-    arms with 96^3 grids) in one graph-captured launch of the batched engine."""
+    arms with 96^3 grids) in one graph-captured launch of the batched engine, timed
+    per replay with CUDA events, L2 flushed before each.  Returns a dict."""
     import torch
     import paper_2309_12543_gb300 as sdf
     import scenegen
-    from paper_2309_12543_gb300 import build as pkg_build
-
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    pkg_build.build()
     bs = scenegen.make_batched(order=args.order)
     stream = torch.cuda.Stream(dev)
     ctx = sdf.Context(local, stream)
@@ -467,7 +584,7 @@ def run_batched(args):
     sdf.sdf_ctx_reserve(ctx, tot_n, tot_w, tot_pairs, len(reqs))
     tw, tb, tuned_us = sdf.sdf_autotune(ctx, reqs, repeats=5)
     with torch.cuda.stream(stream):
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(max(warmup, 3)):
             sdf.check_batch(ctx, reqs)
     if ctx.synchronize() != 0:
         raise RuntimeError(ctx.last_error())
@@ -478,24 +595,52 @@ def run_batched(args):
     main = torch.cuda.current_stream(dev)
     for _ in range(3):
         graph.replay()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if ws > 1:
-        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize(dev)
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    for i in range(args.steps):
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    for i in range(steps):
         flush.zero_()
         ev[i][0].record(main)
         graph.replay()
         ev[i][1].record(main)
     torch.cuda.synchronize(dev)
-    clk = clocks.stop()
-    step_ms = [x.elapsed_time(y) for x, y in ev]
-    total_ms = max_over_ranks(float(sum(step_ms)))
+    clk = clocks.stop() if clocks else None
+    step_us = [x.elapsed_time(y) * 1e3 for x, y in ev]
     if ctx.synchronize() != 0:
         raise RuntimeError(ctx.last_error())
+    del graph
+    return {"mean_us": statistics.mean(step_us), "p50_us": percentile(step_us, 50), "p99_us": percentile(step_us, 99),
+            "steps": steps, "step_us": step_us, "clocks": clk, "requests": len(reqs),
+            "checks_per_s": len(reqs) / (statistics.mean(step_us) * 1e-6),
+            "waypoints_per_s": tot_w / (statistics.mean(step_us) * 1e-6),
+            "workload": f"batched: {len(reqs)} checks, W in [{min(r[2] for r in reqs)}, {max(r[2] for r in reqs)}] "
+                        f"(total {tot_w}), N in [{min(r[4] for r in reqs)}, {max(r[4] for r in reqs)}] "
+                        f"(total {tot_n}), 6-DoF and 7-DoF arms, 96^3 grids, one CUDA graph replay, "
+                        f"L2 flushed before each",
+            "waypoints": tot_w, "points": tot_n,
+            "autotuned": {"waypoints_per_block": tw, "tile_batch": tb, "median_us_warm": tuned_us}}
+
+
+def run_batched(args):
+    """The 64-request batch of uneven checks as its own bench line."""
+    import torch
+    from paper_2309_12543_gb300 import build as pkg_build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg_build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    m = batched_measurement(args, dev, local, args.steps, args.warmup, clocks=ClockSampler(local))
+    total_ms = max_over_ranks(float(sum(m["step_us"])) / 1e3)
+    if ws > 1:
+        torch.distributed.barrier()
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -505,16 +650,12 @@ def run_batched(args):
         "metric": BATCH_METRIC, "value": value, "unit": "µs per batch", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batched: {len(reqs)} checks, W in [{min(r[2] for r in reqs)}, "
-                               f"{max(r[2] for r in reqs)}] (total {tot_w}), N in [{min(r[4] for r in reqs)}, "
-                               f"{max(r[4] for r in reqs)}] (total {tot_n}), 6-DoF and 7-DoF arms, "
-                               f"96^3 grids, one CUDA graph", "requests": len(reqs),
-                   "waypoints": tot_w, "points": tot_n, "autotuned": {"waypoints_per_block": tw, "tile_batch": tb,
-                                                                      "median_us_warm": tuned_us},
+        "config": {"workload": m["workload"], "requests": m["requests"], "waypoints": m["waypoints"],
+                   "points": m["points"], "autotuned": m["autotuned"],
                    "l2": "flushed before every timed step (256 MiB write)"},
-        "p50_us": percentile([x * 1e3 for x in step_ms], 50), "p99_us": percentile([x * 1e3 for x in step_ms], 99),
-        "checks_per_s": len(reqs) / (value * 1e-6), "waypoints_per_s": tot_w / (value * 1e-6),
-        "gpu_launches": 2 * args.steps, "clocks": clk,
+        "p50_us": m["p50_us"], "p99_us": m["p99_us"],
+        "checks_per_s": m["requests"] / (value * 1e-6), "waypoints_per_s": m["waypoints"] / (value * 1e-6),
+        "gpu_launches": 2 * args.steps, "clocks": m["clocks"],
     }
     print(json.dumps(out), flush=True)
     if ws > 1:

@@ -134,7 +134,9 @@ const char* sdf_last_error(const sdf_ctx* ctx);
                                      bounding volume grows by sqrt(3) h / 256).  The first
                                      check of a grids object with the option on makes its
                                      texture copy (n^3 FP32 per link; allocates and
-                                     synchronises); sdf_grids_destroy frees it. */
+                                     synchronises); sdf_grids_destroy frees it.  The texture
+                                     form is its own kernel and always takes 4 list entries
+                                     per warp step (SDF_OPT_TILE_BATCH does not apply). */
 int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t value);
 int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* value);
 

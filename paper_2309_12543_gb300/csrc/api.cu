@@ -930,6 +930,7 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     p->skip_prep = ctx->reuse_sort;
     p->warm_l2 = !ctx->reuse_sort && !ctx->time_kernels;   // the launches that overlap check and sort
     p->warps = nw;
+    p->tex = ctx->tex3d;
     p->sorted = ctx->sorted;
     p->tiles = ctx->tiles;
     p->supers = ctx->supers;

@@ -547,7 +547,7 @@ struct BlockState {
     const uchar2* pair_wl;     // per pair: (waypoint of the block, link), no division in the hot loops
     const float4* grid_o;      // per link (shared memory)
     const float* grid_h;
-    const unsigned long long* tex;  // per link texture objects (shared memory), or null
+    const unsigned long long* tex;  // per link texture objects (shared memory; texture form only)
     unsigned* best;            // per waypoint of the block
     unsigned long long* key;
     int cull;
@@ -581,7 +581,10 @@ __device__ __forceinline__ bool capsule_reaches(float4 c, float4 A, float4 D, fl
 }
 
 // Interpolated distance of sorted point `pos` for block pair `pair`, folded into
-// the waypoint's best value and key when it can still be the minimum.
+// the waypoint's best value and key when it can still be the minimum.  TEX: the
+// texture unit's filter does the interpolation (a separate kernel instantiation, so
+// that the default kernel holds no texture instruction).
+template <bool TEX>
 __device__ __forceinline__ void evaluate(const BlockState& B, int pos, int pair) {
     const float4 p = __ldg(&B.sorted[pos]);
     const float4 r0 = B.pose[pair][0], r1 = B.pose[pair][1], r2 = B.pose[pair][2];
@@ -590,8 +593,11 @@ __device__ __forceinline__ void evaluate(const BlockState& B, int pos, int pair)
     const float lx = fmaf(r0.x, p.x, fmaf(r0.y, p.y, fmaf(r0.z, p.z, r0.w)));
     const float ly = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
     const float lz = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
-    const float g = B.tex ? tex_lookup(B.tex[l], B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz)
-                          : grid_lookup(B.values + (size_t)(l * B.n3), B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz);
+    float g;
+    if constexpr (TEX)
+        g = tex_lookup(B.tex[l], B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz);
+    else
+        g = grid_lookup(B.values + (size_t)(l * B.n3), B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz);
     const unsigned long long key = pack_key(g, __float_as_int(p.w), l);
     const unsigned ob = (unsigned)(key >> 32);
     if (ob <= B.best[wl]) {
@@ -606,6 +612,7 @@ struct WarpQueue {
     int n;
 };
 
+template <bool TEX>
 __device__ __forceinline__ void queue_push(const BlockState& B, WarpQueue& Q, bool surv, int pos, int pair,
                                            int lane) {
     const unsigned m = __ballot_sync(kFull, surv);
@@ -618,22 +625,23 @@ __device__ __forceinline__ void queue_push(const BlockState& B, WarpQueue& Q, bo
         const uint2 e = Q.q[Q.n - 32 + lane];
         __syncwarp();
         Q.n -= 32;
-        evaluate(B, (int)e.x, (int)e.y);
+        evaluate<TEX>(B, (int)e.x, (int)e.y);
     }
 }
 
+template <bool TEX>
 __device__ __forceinline__ void queue_flush(const BlockState& B, WarpQueue& Q, int lane) {
     __syncwarp();
     if (lane < Q.n) {
         const uint2 e = Q.q[lane];
-        evaluate(B, (int)e.x, (int)e.y);
+        evaluate<TEX>(B, (int)e.x, (int)e.y);
     }
     __syncwarp();
     Q.n = 0;
 }
 
 // Point tests of up to TB (pair, tile) entries, the point loads issued together.
-template <int TB>
+template <int TB, bool TEX>
 __device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, const unsigned (&ent)[TB],
                                            int cnt, int lane) {
     float4 pt[TB];
@@ -657,13 +665,14 @@ __device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, co
     for (int k = 0; k < TB; ++k) {
         if (k >= cnt) break;
         if (B.stat) stat_add(B, kWsPointT, (unsigned)__popc(__ballot_sync(kFull, pos[k] < B.n_valid)), lane);
-        queue_push(B, Q, surv[k], pos[k], (int)(ent[k] >> 28), lane);
+        queue_push<TEX>(B, Q, surv[k], pos[k], (int)(ent[k] >> 28), lane);
     }
 }
 
 // TB: list entries a warp takes per step in phase B (their point loads go out together).
 // NW: warps per block (8 or 16); at 64 registers a thread, 32 / NW blocks fit an SM.
-template <int TB, int NW>
+// TEX: lookups by the texture unit's trilinear filter (SDF_OPT_TEX3D).
+template <int TB, int NW, bool TEX>
 __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_constant__ BatchParams P) {
     extern __shared__ float4 s_spheres[];            // tiles [stage_tiles], then super-tiles
     __shared__ float4 s_pose[NW][6];
@@ -718,7 +727,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     if (tid < L) {
         s_grid_o[tid] = T.grid_o[tid];
         s_grid_h[tid] = T.grid_h[tid];
-        if (I.tex) s_tex[tid] = I.tex[tid];
+        if (TEX) s_tex[tid] = I.tex[tid];
     }
     if (tid < n_pair) s_pair_wl[tid] = make_uchar2((unsigned char)(tid / L), (unsigned char)(tid % L));
     if (tid == 0) {
@@ -758,7 +767,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
             const float dx = Bw[0] - A[0], dy = Bw[1] - A[1], dz = Bw[2] - A[2];
             const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             // under the texture lookup the capsule grows by the filter's point shift
-            dst[4] = make_float4(A[0], A[1], A[2], I.tex ? a.w + tex_cull_pad(T.grid_h[lane]) : a.w);
+            dst[4] = make_float4(A[0], A[1], A[2], TEX ? a.w + tex_cull_pad(T.grid_h[lane]) : a.w);
             dst[5] = make_float4(dx, dy, dz, dd > 0.f ? 1.f / dd : 0.f);
         }
     }
@@ -825,7 +834,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     B.pose = s_pose;
     B.grid_o = s_grid_o;
     B.grid_h = s_grid_h;
-    B.tex = I.tex ? s_tex : nullptr;
+    B.tex = s_tex;
     B.best = s_best;
     B.key = s_key;
     B.cull = P.cull;
@@ -858,7 +867,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
                 const int t_seed = warp_argmin(ts, t < n_tiles ? t : 0x7fffffff);
                 const bool ev = t_seed < n_tiles && t_seed * 32 + lane < n_valid;
                 if (stats) stat_add(B, kWsSeed, (unsigned)__popc(__ballot_sync(kFull, ev)), lane);
-                if (ev) evaluate(B, t_seed * 32 + lane, warp);
+                if (ev) evaluate<TEX>(B, t_seed * 32 + lane, warp);
             }
         }
         if (stats) {
@@ -917,14 +926,14 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
                         over_ent[over_n] = ((unsigned)warp << 28) | (unsigned)(sidx * 32 + __ffs(over) - 1);
                         over &= over - 1;
                         if (++over_n == TB) {
-                            test_tiles<TB>(B, Q, over_ent, over_n, lane);
+                            test_tiles<TB, TEX>(B, Q, over_ent, over_n, lane);
                             over_n = 0;
                         }
                     }
                 }
             }
         }
-        if (over_n) test_tiles<TB>(B, Q, over_ent, over_n, lane);
+        if (over_n) test_tiles<TB, TEX>(B, Q, over_ent, over_n, lane);
         if (stats && lane == 0) s_stat_ns[warp][kWnCull] += global_ns() - t_a;
     }
     __syncthreads();
@@ -947,9 +956,9 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
                 cnt = k + 1;
             }
         }
-        test_tiles<TB>(B, Q, ent, cnt, lane);
+        test_tiles<TB, TEX>(B, Q, ent, cnt, lane);
     }
-    queue_flush(B, Q, lane);
+    queue_flush<TEX>(B, Q, lane);
     if (stats && lane == 0) s_stat_ns[warp][kWnPoints] += global_ns() - t_b0;
     __syncthreads();
     if (stats) {
@@ -1036,11 +1045,12 @@ size_t staged_bytes(int stage_tiles) {
 
 cudaError_t configure_kernels() {
     const int smem = (int)staged_bytes(kMaxStagedTiles);
-    const void* fns[6] = {(const void*)check_kernel<2, 16>, (const void*)check_kernel<4, 16>,
-                          (const void*)check_kernel<8, 16>, (const void*)check_kernel<2, 8>,
-                          (const void*)check_kernel<4, 8>,  (const void*)check_kernel<8, 8>};
+    const void* fns[8] = {(const void*)check_kernel<2, 16, false>, (const void*)check_kernel<4, 16, false>,
+                          (const void*)check_kernel<8, 16, false>, (const void*)check_kernel<2, 8, false>,
+                          (const void*)check_kernel<4, 8, false>,  (const void*)check_kernel<8, 8, false>,
+                          (const void*)check_kernel<4, 16, true>,  (const void*)check_kernel<4, 8, true>};
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k)
         e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
@@ -1070,13 +1080,16 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = (ev_mid || p.skip_prep) ? 0 : 1;
+    if (p.tex)   // the texture form: one list batch (4), either block width
+        return nw == 16 ? cudaLaunchKernelEx(&cfg, check_kernel<4, 16, true>, p)
+                        : cudaLaunchKernelEx(&cfg, check_kernel<4, 8, true>, p);
     switch (tile_batch * 100 + nw) {
-        case 216: return cudaLaunchKernelEx(&cfg, check_kernel<2, 16>, p);
-        case 416: return cudaLaunchKernelEx(&cfg, check_kernel<4, 16>, p);
-        case 816: return cudaLaunchKernelEx(&cfg, check_kernel<8, 16>, p);
-        case 208: return cudaLaunchKernelEx(&cfg, check_kernel<2, 8>, p);
-        case 408: return cudaLaunchKernelEx(&cfg, check_kernel<4, 8>, p);
-        case 808: return cudaLaunchKernelEx(&cfg, check_kernel<8, 8>, p);
+        case 216: return cudaLaunchKernelEx(&cfg, check_kernel<2, 16, false>, p);
+        case 416: return cudaLaunchKernelEx(&cfg, check_kernel<4, 16, false>, p);
+        case 816: return cudaLaunchKernelEx(&cfg, check_kernel<8, 16, false>, p);
+        case 208: return cudaLaunchKernelEx(&cfg, check_kernel<2, 8, false>, p);
+        case 408: return cudaLaunchKernelEx(&cfg, check_kernel<4, 8, false>, p);
+        case 808: return cudaLaunchKernelEx(&cfg, check_kernel<8, 8, false>, p);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -79,6 +79,7 @@ struct BatchParams {
     int stage_tiles;          // tile spheres the dynamic shared memory holds (0: no staging)
     int skip_prep;            // the clouds are already sorted in the scratch: launch the check only
     int warps;                // warps per check block: 8 or 16
+    int tex;                  // lookups by the texture unit (every InstDesc::tex is set)
     int warm_l2;              // the check overlaps the sort (programmatic dependent launch):
                               // its blocks prefetch the grids meanwhile (InstDesc::warm)
     float4* sorted;           // finite points, spatially sorted: x, y, z, original index bits

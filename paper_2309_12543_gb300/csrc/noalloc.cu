@@ -135,6 +135,7 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         p.skip_prep = 0;
         p.warm_l2 = 1;
         p.warps = 16;
+        p.tex = 0;
         p.sorted = reinterpret_cast<float4*>(base + kSortedOff);
         p.tiles = reinterpret_cast<float4*>(base + kTilesOff);
         p.supers = reinterpret_cast<float4*>(base + kSupersOff);
