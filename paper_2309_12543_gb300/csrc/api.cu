@@ -143,9 +143,8 @@ void sdf_ctx_destroy(sdf_ctx* ctx) {
     sdf::dfree(ctx->sur_poses);
     sdf::dfree(ctx->sur_keys);
     sdf::dfree(ctx->sur_mask);
-    sdf::dfree(ctx->sur_xq);
-    sdf::dfree(ctx->sur_tag);
     sdf::dfree(ctx->sur_count);
+    sdf::dfree(ctx->sur_wimg);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);

@@ -234,11 +234,9 @@ struct sdf_ctx {
     unsigned long long* sur_keys = nullptr;
     uint8_t* sur_mask = nullptr;
     size_t sur_w_cap = 0;
-    size_t sur_links = 0;
-    float4* sur_xq = nullptr;
-    uint2* sur_tag = nullptr;
-    int* sur_count = nullptr;
-    size_t sur_cap = 0;
+    int* sur_count = nullptr;              // work-item counter of the fused surrogate check
+    uint8_t* sur_wimg = nullptr;           // the networks' weights as the fused check holds them
+    size_t sur_wimg_cap = 0;
     // timing
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
     bool timed_valid = false;

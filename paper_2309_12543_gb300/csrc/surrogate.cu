@@ -58,8 +58,10 @@ constexpr int kSW2 = 0, kSW3 = kTileBytes, kSH1 = 2 * kTileBytes, kSH2 = 3 * kTi
               kSH3 = 5 * kTileBytes, kSAux = 6 * kTileBytes, kSSmall = kSAux + kAuxBytes;
 constexpr int kSmallFloats = 384 + 4 * kH + 4;  // W1, b1, b2, b3, w4, b4 (+pad)
 constexpr int kTrainSmem = kSSmall + kSmallFloats * 4;
-// evaluation kernel shared memory
-constexpr int kEW2 = 0, kEW3 = kTileBytes, kEH1 = 2 * kTileBytes, kEH2 = 3 * kTileBytes, kESmall = 4 * kTileBytes;
+// evaluation kernel shared memory: W2 and W3 of the current link, then one activation
+// tile per warpgroup pipeline (H1 and H2 of its tile in turn), then the small parameters
+constexpr int kEvalPipes = 4;   // warpgroups of an evaluation CTA, each on its own 128-query tile
+constexpr int kEW2 = 0, kEW3 = kTileBytes, kEH = 2 * kTileBytes, kESmall = kEH + kEvalPipes * kTileBytes;
 constexpr int kEvalSmem = kESmall + kSmallFloats * 4;
 
 // tensor-memory columns
@@ -73,6 +75,39 @@ constexpr uint32_t kRowGroup = 2048, kAuxRowGroup = 256;
 // the results are rounded to bfloat16 or compared at ~1e-3 anyway).  For z below
 // about -88 the exponential overflows and the quotient is 0.
 __device__ __forceinline__ float silu_sigma(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+
+// SiLU for the evaluation kernel, where the transcendental (XU) pipe is the busiest:
+// the exponential always runs there (ex2.approx, 2^x), the reciprocal of 1 + e either
+// there too (rcp.approx) or on the FMA pipe (silu_fma).  The FMA-pipe reciprocal
+// starts from the bit pattern 0x7F000000 - bits(x), which negates the binary exponent
+// and approximates the mantissa linearly, so that x y0 lies in [1, 9/8] for x >= 1;
+// three Newton steps y <- y (2 - x y) square the relative error each time
+// (2^-3 -> 2^-6 -> 2^-12 -> 2^-24).  The argument of ex2 is capped at 126 so that
+// 1 + e stays finite and normal.
+constexpr float kLog2e = 1.4426950408889634f;
+__device__ __forceinline__ float ex2_xu(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_xu(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_fma(float x) {   // x in [1, 2^126]
+    float y = __int_as_float(0x7F000000 - __float_as_int(x));
+    y = y * fmaf(-x, y, 2.0f);
+    y = y * fmaf(-x, y, 2.0f);
+    y = y * fmaf(-x, y, 2.0f);
+    return y;
+}
+__device__ __forceinline__ float silu_xu(float z) { return z * rcp_xu(1.0f + ex2_xu(fminf(-z * kLog2e, 126.0f))); }
+__device__ __forceinline__ float silu_fma(float z) { return z * rcp_fma(1.0f + ex2_xu(fminf(-z * kLog2e, 126.0f))); }
+// unit e of a group of 8: one in four takes the XU reciprocal, so that the XU pipe
+// (16 ops per clock and SM) and the FMA pipe (128) finish about together
+template <int E>
+__device__ __forceinline__ float silu_mix(float z) { return (E & 3) == 0 ? silu_xu(z) : silu_fma(z); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -493,183 +528,188 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
 
 struct EvalArgs {
     const float* master;               // [L][kPar]
-    const float* x3;                   // plain mode: n x 3 normalised points
-    const float4* xq;                  // check mode: normalised point (xyz), added distance (w, metres)
-    const uint2* tag;                  // check mode: (waypoint, point << 4 | link)
-    const int* seg_count;              // check mode: queries per link segment
-    int seg_cap;                       // check mode: queries per segment slot
+    const float* x3;                   // n x 3 normalised points
     int L;
-    int n;                             // plain mode: queries of link `link0`
+    int n;                             // queries of link `link0`
     int link0;
-    float* f_out;                      // plain mode: f(x) (normalised)
-    unsigned long long* keys;          // check mode: per-waypoint packed keys
-    float scale[kMaxLinks];            // half-span a of each link's box
+    float* f_out;                      // f(x) (normalised)
     int* status;
     uint32_t wait_polls;               // polls of an MMA completion wait before it gives up
 };
 
-constexpr int kEvalThreads = 512;   // 16 warps: 4 column groups x the 4 lane quarters
+constexpr int kEvalThreads = 128 * kEvalPipes;
 
-// One 128-query tile at a time: warp w serves tensor-memory lanes 32 (w % 4) .. +31
-// (queries) and hidden units 32 (w / 4) .. +31 of every layer; the output layer's
-// four partial sums meet in shared memory.
-__global__ void __launch_bounds__(kEvalThreads, 1) mlp_eval_kernel(const __grid_constant__ EvalArgs A) {
-    extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ uint64_t mbar;
-    __shared__ uint32_t tmem_slot;
-    __shared__ float partial[4][kH];
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int row = ((warp & 3) << 5) | lane;
-    const int cg = warp >> 2;
-    const int c0 = cg * 32;
-    uint8_t* sW2 = sm + kEW2;
-    uint8_t* sW3 = sm + kEW3;
-    uint8_t* sH1 = sm + kEH1;
-    uint8_t* sH2 = sm + kEH2;
-    float* small = reinterpret_cast<float*>(sm + kESmall);
+// Named barrier of one warpgroup (ids 1..4; id 0 is __syncthreads).
+__device__ __forceinline__ void pipe_sync(int pipe) {
+    asm volatile("bar.sync %0, 128;" ::"r"(pipe + 1) : "memory");
+}
+// Warpgroup-wide AND of a flag.
+__device__ __forceinline__ bool pipe_all(int pipe, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(pipe + 1)
+        : "memory");
+    return r != 0;
+}
+// Shared-memory writes of the warpgroup become visible to the tensor core, and its
+// tensor-memory reads are ordered before the next MMA.
+__device__ __forceinline__ void pipe_sync_for_mma(int pipe) {
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    pipe_sync(pipe);
+    tc::fence_after_sync();
+}
+
+// One hidden layer's epilogue on this thread's tensor-memory lane: s(D + b) of the
+// 128 units into row r of the activation tile H (bf16).
+__device__ __forceinline__ void pipe_hidden(uint32_t taddr, const float* b, uint8_t* H, int r) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(taddr + c0, v);
+#pragma unroll
+        for (int k = 0; k < 32; k += 8) {
+            float h[8];
+            h[0] = silu_mix<0>(v[k + 0] + b[c0 + k + 0]);
+            h[1] = silu_mix<1>(v[k + 1] + b[c0 + k + 1]);
+            h[2] = silu_mix<2>(v[k + 2] + b[c0 + k + 2]);
+            h[3] = silu_mix<3>(v[k + 3] + b[c0 + k + 3]);
+            h[4] = silu_mix<4>(v[k + 4] + b[c0 + k + 4]);
+            h[5] = silu_mix<5>(v[k + 5] + b[c0 + k + 5]);
+            h[6] = silu_mix<6>(v[k + 6] + b[c0 + k + 6]);
+            h[7] = silu_mix<7>(v[k + 7] + b[c0 + k + 7]);
+            store_bf16x8(H, r, c0 + k, kH, h);
+        }
+    }
+}
+
+// The network at one query per thread of a warpgroup (thread r = query row r =
+// tensor-memory lane r): layer 1 and the epilogues on the FP32 cores, the two
+// 128 x 128 layers as tcgen05 MMAs into this pipeline's 128 tensor-memory columns
+// (Z2, then Z3 in the same columns).  H holds H1, then H2 (each MMA has finished
+// reading its operand before the next write).  Returns false if an MMA wait gave up
+// (the pipeline agrees on it); f is valid otherwise.
+__device__ __forceinline__ bool pipe_network(int pipe, int r, const float* small, uint8_t* H, uint32_t aH,
+                                             uint32_t aW2, uint32_t aW3, uint32_t d_tmem, uint32_t taddr,
+                                             uint64_t* mbar, uint32_t& phase, uint32_t limit, float4 x, float& f) {
     const float* W1 = small;
     const float* b1 = small + 384;
     const float* b2 = small + 384 + kH;
     const float* b3 = small + 384 + 2 * kH;
     const float* w4 = small + 384 + 3 * kH;
-
-    // this CTA's range of 128-query tiles over the link segments
-    const bool check_mode = A.keys != nullptr;
-    int counts[kMaxLinks];
-    int total = 0;
-    for (int l = 0; l < kMaxLinks; ++l) {
-        counts[l] = 0;
-        if (l < A.L) counts[l] = check_mode ? min(A.seg_count[l], A.seg_cap) : (l == A.link0 ? A.n : 0);
-        total += (counts[l] + 127) / 128;
+    constexpr uint32_t kN128KK = tc::idesc_bf16(128, 128, 0, 0);
+#pragma unroll 1
+    for (int j0 = 0; j0 < kH; j0 += 8) {
+        float h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int j = j0 + e;
+            const float z = fmaf(W1[3 * j], x.x, fmaf(W1[3 * j + 1], x.y, fmaf(W1[3 * j + 2], x.z, b1[j])));
+            h[e] = (e & 3) == 0 ? silu_xu(z) : silu_fma(z);
+        }
+        store_bf16x8(H, r, j0, kH, h);
     }
+    pipe_sync_for_mma(pipe);
+    if (r == 0) {
+        mma_k128(d_tmem, KMAJ(aH), KMAJ(aW2), kN128KK);
+        tc::mma_commit(mbar);
+    }
+    bool ok = tc::mbar_wait(mbar, phase, limit);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!pipe_all(pipe, ok)) return false;
+    pipe_hidden(taddr, b2, H, r);
+    pipe_sync_for_mma(pipe);
+    if (r == 0) {
+        mma_k128(d_tmem, KMAJ(aH), KMAJ(aW3), kN128KK);
+        tc::mma_commit(mbar);
+    }
+    ok = tc::mbar_wait(mbar, phase, limit);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!pipe_all(pipe, ok)) return false;
+    float acc = small[384 + 4 * kH];
+#pragma unroll 1
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(taddr + c0, v);
+#pragma unroll
+        for (int k = 0; k < 32; k += 8) {
+            acc = fmaf(w4[c0 + k + 0], silu_mix<0>(v[k + 0] + b3[c0 + k + 0]), acc);
+            acc = fmaf(w4[c0 + k + 1], silu_mix<1>(v[k + 1] + b3[c0 + k + 1]), acc);
+            acc = fmaf(w4[c0 + k + 2], silu_mix<2>(v[k + 2] + b3[c0 + k + 2]), acc);
+            acc = fmaf(w4[c0 + k + 3], silu_mix<3>(v[k + 3] + b3[c0 + k + 3]), acc);
+            acc = fmaf(w4[c0 + k + 4], silu_mix<4>(v[k + 4] + b3[c0 + k + 4]), acc);
+            acc = fmaf(w4[c0 + k + 5], silu_mix<5>(v[k + 5] + b3[c0 + k + 5]), acc);
+            acc = fmaf(w4[c0 + k + 6], silu_mix<6>(v[k + 6] + b3[c0 + k + 6]), acc);
+            acc = fmaf(w4[c0 + k + 7], silu_mix<7>(v[k + 7] + b3[c0 + k + 7]), acc);
+        }
+    }
+    f = acc;
+    // the tensor-memory reads above come before the next tile's first MMA
+    tc::fence_before_sync();
+    return true;
+}
+
+// f(x) of one link at n points: four warpgroup pipelines per CTA, each evaluating its
+// own 128-query tiles, so that one pipeline's MMA and waits overlap the others' FP32
+// epilogues; the pipelines share the link's W2/W3 in shared memory.
+__global__ void __launch_bounds__(kEvalThreads, 1) mlp_eval_kernel(const __grid_constant__ EvalArgs A) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t mbar[kEvalPipes];
+    __shared__ uint32_t tmem_slot;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int pipe = warp >> 2, r = t & 127;
+    uint8_t* sW2 = sm + kEW2;
+    uint8_t* sW3 = sm + kEW3;
+    uint8_t* sH = sm + kEH + pipe * kTileBytes;
+    float* small = reinterpret_cast<float*>(sm + kESmall);
+
+    // this CTA's range of 128-query tiles
+    const int total = (A.n + 127) / 128;
     const int first = (int)((long long)total * blockIdx.x / gridDim.x);
     const int last = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
     if (first >= last) return;
 
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, 256);
-    if (t == 0) tc::mbar_init(&mbar, 1);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (t < kEvalPipes) tc::mbar_init(&mbar[t], 1);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tm = tmem_slot;
-    const uint32_t lane_addr = tm + ((uint32_t)((warp & 3) * 32) << 16);
-    const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH1 = tc::smem_u32(sH1), aH2 = tc::smem_u32(sH2);
-    constexpr uint32_t kN128KK = tc::idesc_bf16(128, 128, 0, 0);
+    const uint32_t d_tmem = tm + (uint32_t)(128 * pipe);
+    const uint32_t taddr = d_tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH = tc::smem_u32(sH);
     uint32_t phase = 0;
     bool ok = true;
-    int loaded = -1;
-    int l = 0, tile_in_l = 0;
-    {
-        int acc = 0;
-        for (l = 0; l < A.L; ++l) {
-            const int nt = (counts[l] + 127) / 128;
-            if (first < acc + nt) break;
-            acc += nt;
-        }
-        tile_in_l = first - acc;
-    }
-    for (int tile = first; tile < last && ok; ++tile) {
-        while (tile_in_l * 128 >= counts[l]) {   // next non-empty segment
-            ++l;
-            tile_in_l = 0;
-        }
-        if (l != loaded) {
-            __syncthreads();
-            load_weights(A.master + (size_t)l * kPar, sW2, sW3, small, t, kEvalThreads);
-            loaded = l;
-            __syncthreads();
-        }
-        const int k = tile_in_l * 128 + row;
-        const bool valid = k < counts[l];
-        const size_t qi = check_mode ? (size_t)l * A.seg_cap + k : (size_t)k;
-        float4 xq = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (valid) {
-            if (check_mode)
-                xq = A.xq[qi];
-            else
-                xq = make_float4(A.x3[3 * qi], A.x3[3 * qi + 1], A.x3[3 * qi + 2], 0.f);
-        }
-        // layer 1: this thread's 32 hidden units of its query
-#pragma unroll
-        for (int j0 = 0; j0 < 32; j0 += 8) {
-            float h[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int j = c0 + j0 + e;
-                const float z = fmaf(W1[3 * j], xq.x, fmaf(W1[3 * j + 1], xq.y, fmaf(W1[3 * j + 2], xq.z, b1[j])));
-                h[e] = z * silu_sigma(z);
-            }
-            store_bf16x8(sH1, row, c0 + j0, kH, h);
-        }
-        sync_for_mma();
-        if (t == 0) {
-            mma_k128(tm + 0, KMAJ(aH1), KMAJ(aW2), kN128KK);
-            tc::mma_commit(&mbar);
-        }
-        if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
-        {
-            float v[32];
-            tc::tmem_ld32(lane_addr + c0, v);
-#pragma unroll
-            for (int j0 = 0; j0 < 32; j0 += 8) {
-                float h[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const float z = v[j0 + e] + b2[c0 + j0 + e];
-                    h[e] = z * silu_sigma(z);
-                }
-                store_bf16x8(sH2, row, c0 + j0, kH, h);
-            }
-        }
-        sync_for_mma();
-        if (t == 0) {
-            mma_k128(tm + 128, KMAJ(aH2), KMAJ(aW3), kN128KK);
-            tc::mma_commit(&mbar);
-        }
-        if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
-        {
-            float v[32];
-            tc::tmem_ld32(lane_addr + 128 + c0, v);
-            float f = 0.f;
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                const float z = v[e] + b3[c0 + e];
-                f = fmaf(w4[c0 + e], z * silu_sigma(z), f);
-            }
-            partial[cg][row] = f;
-        }
-        __syncthreads();
-        if (cg == 0) {   // warps 0..3: one query per lane
-            const float f = small[384 + 4 * kH] + ((partial[0][row] + partial[1][row]) +
-                                                   (partial[2][row] + partial[3][row]));
-            if (check_mode) {
-                // lanes of the same waypoint agree on their smallest key first, and one
-                // of them does the atomic
-                const uint2 tg = valid ? A.tag[qi] : make_uint2(0xffffffffu, 0xffffffffu);
-                const float d = fmaf(A.scale[l], f, xq.w);
-                const bool use = valid && !isnan(d);
-                const unsigned hi = use ? ordered_bits(d) : 0xffffffffu;
-                const unsigned peers = __match_any_sync(0xffffffffu, use ? tg.x : 0xffffffffu);
-                const unsigned hmin = __reduce_min_sync(peers, hi);
-                const unsigned lmin = __reduce_min_sync(peers, hi == hmin ? tg.y : 0xffffffffu);
-                if (use && lane == __ffs(peers) - 1)
-                    atomicMin(&A.keys[tg.x], ((unsigned long long)hmin << 32) | lmin);
-            } else if (valid) {
-                A.f_out[k] = f;
-            }
-        }
-        ++tile_in_l;
-        tc::fence_before_sync();
-        __syncthreads();   // H1/H2, the partial sums and tensor memory are rewritten by the next tile
-        tc::fence_after_sync();
+    load_weights(A.master + (size_t)A.link0 * kPar, sW2, sW3, small, t, kEvalThreads);
+    tc::fence_smem_to_async();   // the weights are MMA operands
+    __syncthreads();
+    for (int tl = first + pipe; tl < last; tl += kEvalPipes) {
+        const int k = tl * 128 + r;
+        const bool valid = k < A.n;
+        const float4 xq = valid ? make_float4(A.x3[3 * (size_t)k], A.x3[3 * (size_t)k + 1], A.x3[3 * (size_t)k + 2], 0.f)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        float f = 0.f;
+        ok = pipe_network(pipe, r, small, sH, aH, aW2, aW3, d_tmem, taddr, &mbar[pipe], phase, A.wait_polls, xq, f);
+        if (!ok) break;
+        if (valid) A.f_out[k] = f;
     }
     if (!ok) {
-        if (t == 0) atomicOr(A.status, kStatusTimeout);
-        tc::mbar_wait(&mbar, phase ^ 1u, kWaitPolls);
+        // a wait gave up: report it, then let the MMA still in flight end before the
+        // tensor memory is released
+        if (r == 0) atomicOr(A.status, kStatusTimeout);
+        tc::mbar_wait(&mbar[pipe], phase ^ 1u, kWaitPolls);
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_free(tm, 256);
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_free(tm, 512);
 }
 
 // ------------------------------------------------------------------ sampler
@@ -846,48 +886,80 @@ __global__ void error_reduce_kernel(const float* f, const float* y, int n, float
 
 // ------------------------------------------------------------------ surrogate check
 
-struct SurCheckArgs {
+// The weights of each link as the evaluation kernels hold them in shared memory: W2
+// and W3 as bf16 core-matrix tiles, then the small parameters in FP32.  Made once per
+// check, so that a CTA switching links copies 69 KB with 16-byte loads instead of
+// converting the FP32 master weights again.
+constexpr int kImgBytes = 2 * kTileBytes + kSmallFloats * 4;
+static_assert(kImgBytes % 16 == 0, "16-byte copies");
+
+
+__global__ void __launch_bounds__(512) weight_image_kernel(const float* __restrict__ master, uint8_t* image) {
+    uint8_t* img = image + (size_t)blockIdx.x * kImgBytes;
+    load_weights(master + (size_t)blockIdx.x * kPar, img, img + kTileBytes,
+                 reinterpret_cast<float*>(img + 2 * kTileBytes), threadIdx.x, blockDim.x);
+}
+
+// Copy one link's image to shared memory (all threads of the CTA).
+__device__ __forceinline__ void load_image(const uint8_t* __restrict__ img, uint8_t* sm_w, int t, int nthreads) {
+    const uint4* src = reinterpret_cast<const uint4*>(img);
+    uint4* dst = reinterpret_cast<uint4*>(sm_w);
+    constexpr int kVec = kImgBytes / 16;
+    for (int i = t; i < kVec; i += nthreads) dst[i] = __ldg(src + i);
+}
+
+// The check with the network in place of the grid lookup, in one persistent kernel.
+// Work items, taken in order from a counter: first a seed item per (link, group of
+// kSurGroup waypoints), then a cull item per (link, group), link-major, so that a CTA
+// reloads its weights only when the link changes and the cull items find every
+// link's seed minimum already published.
+//   seed: one warp per waypoint picks the tile nearest to the link's bounding capsule
+//     (nearest super-tile first) and its 32 points become queries;
+//   cull: with the waypoint's minimum so far (over all links) plus the surrogate's
+//     error bound as the threshold, one warp per waypoint culls super-tiles and tiles
+//     against the capsule into a (waypoint, tile) list in shared memory; then every
+//     warp takes list entries, tests the tile's points against the capsule and
+//     appends the survivors to a query ring in shared memory.
+// Whenever the ring holds 3 tiles of 128 queries (or the list is done) the four
+// warpgroup pipelines evaluate its whole tiles on the tensor cores, fold each value into the
+// waypoint's packed key (ordered distance, point, link) and tighten the thresholds.
+// A waypoint whose list overflowed is marked for the grid re-check, which decides it
+// exactly.
+constexpr int kSurGroup = 16;      // waypoints per work item: one warp each in the culls
+constexpr int kSurTake = 2;        // list entries a warp takes per step of the production
+constexpr int kSurFill = 3 * 128;  // the production stops once the ring holds this many queries
+constexpr int kSurRing = kSurFill + 16 * 32 * kSurTake;   // + what 16 warps may add past it
+constexpr int kSurList = 384;      // (waypoint, tile) entries of one cull item
+// shared memory of the fused kernel: the link's image (W2, W3, small parameters), the
+// pipelines' activation tiles, the query ring (points, tags) and the entry list
+constexpr int kSurImg = 0;
+constexpr int kSurH = kImgBytes;
+constexpr int kSurQ = kSurH + kEvalPipes * kTileBytes;
+constexpr int kSurTag = kSurQ + kSurRing * 16;
+constexpr int kSurLst = kSurTag + kSurRing * 4;
+constexpr int kSurSmem = kSurLst + kSurList * 4;
+static_assert(kSurSmem + 2048 <= 232448, "dynamic + static shared memory of the fused check within 227 KB");
+constexpr uint32_t kNoTag = 0xffffffffu;
+
+struct SurFusedArgs {
     const float* poses;               // [W][L][16]: link-from-world 3x4, sphere centre (world), radius
-    int W, L;
+    int W, L, group, n_groups;        // waypoints per work item (<= kSurGroup), ceil(W / group)
     const float4* sorted;             // the sorted cloud (x, y, z, original index bits)
     const float4* tiles;              // sphere per 32 sorted points
     const float4* supers;             // sphere per 32 tiles
     const int* n_valid;
-    float lo[kMaxLinks][3], hi[kMaxLinks][3], m[kMaxLinks][3], inv_a[kMaxLinks];
+    float lo[kMaxLinks][3], hi[kMaxLinks][3], m[kMaxLinks][3], inv_a[kMaxLinks], scale[kMaxLinks];
     float4 cap_a[kMaxLinks], cap_b[kMaxLinks];   // bounding capsules (link frame), radius in cap_a.w
-    float4* xq;                       // queries per link segment
-    uint2* tag;
-    int* seg_count;
-    int seg_cap;
-    const unsigned long long* keys;   // cull: the seeded per-waypoint minimum
-    float slack;                      // cull: error bound of the surrogate + rounding slack
+    const uint8_t* image;             // [L][kImgBytes] weights as held in shared memory
+    int seed_group;                   // waypoints per seed item (16: four full tiles)
+    unsigned long long* keys;         // [W] packed keys, ~0 = none (set before the launch)
+    uint8_t* recheck;                 // [W] 1 where a list overflowed (zeroed before the launch)
+    int* work;                        // item counter (zeroed before the launch)
+    float slack;                      // error bound of the surrogate + rounding slack
+    int* status;
+    uint32_t wait_polls;
+    unsigned long long* stats;        // statistics counters or null
 };
-
-// Warp-cooperative: lanes with `take` append the query of sorted point p for pair
-// (w, l) to link l's segment.
-__device__ __forceinline__ void emit_query(const SurCheckArgs& A, int w, int l, const float4* M, float4 p,
-                                           bool take, int lane) {
-    const unsigned b = __ballot_sync(0xffffffffu, take);
-    if (!b) return;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(&A.seg_count[l], __popc(b));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (!take) return;
-    const int slot = base + __popc(b & ((1u << lane) - 1u));
-    if (slot >= A.seg_cap) return;   // overflow: the finish kernel sends every waypoint to the grid
-    const float lx = fmaf(M[0].x, p.x, fmaf(M[0].y, p.y, fmaf(M[0].z, p.z, M[0].w)));
-    const float ly = fmaf(M[1].x, p.x, fmaf(M[1].y, p.y, fmaf(M[1].z, p.z, M[1].w)));
-    const float lz = fmaf(M[2].x, p.x, fmaf(M[2].y, p.y, fmaf(M[2].z, p.z, M[2].w)));
-    const float cx = fminf(fmaxf(lx, A.lo[l][0]), A.hi[l][0]);
-    const float cy = fminf(fmaxf(ly, A.lo[l][1]), A.hi[l][1]);
-    const float cz = fminf(fmaxf(lz, A.lo[l][2]), A.hi[l][2]);
-    const float ex = lx - cx, ey = ly - cy, ez = lz - cz;
-    const float extra = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-    const float ia = A.inv_a[l];
-    const size_t q = (size_t)l * A.seg_cap + slot;
-    A.xq[q] = make_float4((cx - A.m[l][0]) * ia, (cy - A.m[l][1]) * ia, (cz - A.m[l][2]) * ia, extra);
-    A.tag[q] = make_uint2((unsigned)w, ((unsigned)__float_as_int(p.w) << 4) | (unsigned)l);
-}
 
 // Distance from sphere s (centre, radius) to the segment A + t D (D.w = 1/|D|^2),
 // minus the sphere's radius.
@@ -898,107 +970,327 @@ __device__ __forceinline__ float capsule_gap(float4 s, float4 A, float4 D) {
     return sqrtf(fmaf(qx, qx, fmaf(qy, qy, qz * qz))) - s.w;
 }
 
-// One warp per (waypoint, link) pair.  Seed mode: the 32 points of the tile nearest
-// to the link's sphere (nearest super-tile first).  Cull mode: every point whose
-// sphere bound ||p - c|| - R does not exceed the seeded minimum + slack.
-template <bool kSeed>
-__global__ void __launch_bounds__(256) sur_pairs_kernel(const __grid_constant__ SurCheckArgs A) {
-    const int lane = threadIdx.x & 31;
-    const int pair = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (pair >= A.W * A.L) return;
-    const int w = pair / A.L, l = pair % A.L;
-    const float4* P = reinterpret_cast<const float4*>(A.poses + (size_t)pair * 16);
-    const float4 M[3] = {P[0], P[1], P[2]};
-    // the link's bounding capsule in the world frame: x = R a + t with R the
-    // transpose of the link-from-world rotation and t = -R w (w its last column)
-    float4 cA, cD;
-    {
-        const float4 a = A.cap_a[l], b = A.cap_b[l];
-        const float ax = a.x - M[0].w, ay = a.y - M[1].w, az = a.z - M[2].w;
-        const float bx = b.x - M[0].w, by = b.y - M[1].w, bz = b.z - M[2].w;
-        const float Ax = fmaf(M[0].x, ax, fmaf(M[1].x, ay, M[2].x * az));
-        const float Ay = fmaf(M[0].y, ax, fmaf(M[1].y, ay, M[2].y * az));
-        const float Az = fmaf(M[0].z, ax, fmaf(M[1].z, ay, M[2].z * az));
-        const float Bx = fmaf(M[0].x, bx, fmaf(M[1].x, by, M[2].x * bz));
-        const float By = fmaf(M[0].y, bx, fmaf(M[1].y, by, M[2].y * bz));
-        const float Bz = fmaf(M[0].z, bx, fmaf(M[1].z, by, M[2].z * bz));
-        const float dx = Bx - Ax, dy = By - Ay, dz = Bz - Az;
-        const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        cA = make_float4(Ax, Ay, Az, a.w);
-        cD = make_float4(dx, dy, dz, dd > 0.f ? 1.f / dd : 0.f);
-    }
-    const int nv = *A.n_valid;
-    const int n_tiles = (nv + 31) >> 5, n_sup = (n_tiles + 31) >> 5;
-    if (nv == 0) return;
-    if (kSeed) {
-        float best = INFINITY;
-        int bi = 0x7fffffff;
-        for (int s = lane; s < n_sup; s += 32) {
-            const float g = capsule_gap(A.supers[s], cA, cD);
-            if (g < best) { best = g; bi = s; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        const int t = bi * 32 + lane;
-        float tb = INFINITY;
-        int ti = 0x7fffffff;
-        if (t < n_tiles) { tb = capsule_gap(A.tiles[t], cA, cD); ti = t; }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, tb, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, ti, o);
-            if (ob < tb || (ob == tb && oi < ti)) { tb = ob; ti = oi; }
-        }
-        const int k = ti * 32 + lane;
-        const bool take = k < nv;
-        emit_query(A, w, l, M, take ? A.sorted[k] : make_float4(0.f, 0.f, 0.f, 0.f), take, lane);
-        return;
-    }
-    const unsigned long long key = A.keys[w];
-    const float T = key == ~0ull ? INFINITY : from_ordered((unsigned)(key >> 32));
-    const float thr = T + A.slack + cA.w;        // keep s when dist(c_s, segment) - r_s <= thr
-    for (int s0 = 0; s0 < n_sup; s0 += 32) {
-        const int s = s0 + lane;
-        unsigned bs = __ballot_sync(0xffffffffu, s < n_sup && capsule_gap(A.supers[s], cA, cD) <= thr);
-        while (bs) {
-            const int sv = s0 + __ffs(bs) - 1;
-            bs &= bs - 1;
-            const int t = sv * 32 + lane;
-            unsigned bt = __ballot_sync(0xffffffffu,
-                                        t < n_tiles && capsule_gap(A.tiles[t], cA, cD) <= thr);
-            while (bt) {
-                const int tv = sv * 32 + __ffs(bt) - 1;
-                bt &= bt - 1;
-                const int k = tv * 32 + lane;
-                const float4 p = k < nv ? A.sorted[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const bool take = k < nv && capsule_gap(make_float4(p.x, p.y, p.z, 0.f), cA, cD) <= thr;
-                emit_query(A, w, l, M, p, take, lane);
-            }
-        }
-    }
+// The network's input for sorted point p of waypoint slot j: the link-frame point
+// clamped to the grid box and normalised to it (xyz), and the distance to the box
+// added outside it (w).
+__device__ __forceinline__ float4 make_query(const SurFusedArgs& A, int l, const float4* M, float4 p) {
+    const float lx = fmaf(M[0].x, p.x, fmaf(M[0].y, p.y, fmaf(M[0].z, p.z, M[0].w)));
+    const float ly = fmaf(M[1].x, p.x, fmaf(M[1].y, p.y, fmaf(M[1].z, p.z, M[1].w)));
+    const float lz = fmaf(M[2].x, p.x, fmaf(M[2].y, p.y, fmaf(M[2].z, p.z, M[2].w)));
+    const float cx = fminf(fmaxf(lx, A.lo[l][0]), A.hi[l][0]);
+    const float cy = fminf(fmaxf(ly, A.lo[l][1]), A.hi[l][1]);
+    const float cz = fminf(fmaxf(lz, A.lo[l][2]), A.hi[l][2]);
+    const float ex = lx - cx, ey = ly - cy, ez = lz - cz;
+    const float ia = A.inv_a[l];
+    return make_float4((cx - A.m[l][0]) * ia, (cy - A.m[l][1]) * ia, (cz - A.m[l][2]) * ia,
+                       sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez))));
 }
 
-// Statistics: queries in the segments (capped at the segment size) added to *out.
-__global__ void count_queries_kernel(const int* seg_count, int L, int cap, unsigned long long* out) {
-    unsigned long long n = 0;
-    for (int l = 0; l < L; ++l) n += (unsigned long long)min(seg_count[l], cap);
-    *out += n;
+__global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid_constant__ SurFusedArgs A) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t mbar[kEvalPipes];
+    __shared__ uint32_t tmem_slot;
+    __shared__ float4 s_M[kSurGroup][3];           // link-from-world rows of each waypoint's link pose
+    __shared__ float4 s_cA[kSurGroup], s_cD[kSurGroup];   // world capsule: start (+radius), axis (+1/len^2)
+    __shared__ unsigned long long s_key[kSurGroup];
+    __shared__ float s_thr[kSurGroup];
+    __shared__ int s_item, s_qn, s_ln, s_lnext, s_fail;
+    __shared__ unsigned s_over;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int pipe = warp >> 2, r = t & 127;
+    uint8_t* sW2 = sm + kSurImg;
+    uint8_t* sW3 = sm + kSurImg + kTileBytes;
+    float* small = reinterpret_cast<float*>(sm + kSurImg + 2 * kTileBytes);
+    uint8_t* sH = sm + kSurH + pipe * kTileBytes;
+    float4* s_q = reinterpret_cast<float4*>(sm + kSurQ);
+    uint32_t* s_tag = reinterpret_cast<uint32_t*>(sm + kSurTag);
+    uint32_t* s_list = reinterpret_cast<uint32_t*>(sm + kSurLst);
+
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (t < kEvalPipes) tc::mbar_init(&mbar[t], 1);
+    if (t == 0) s_fail = 0;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = tmem_slot;
+    const uint32_t d_tmem = tm + (uint32_t)(128 * pipe);
+    const uint32_t taddr = d_tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH = tc::smem_u32(sH);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int nv = *A.n_valid;
+    const int n_tiles = (nv + 31) >> 5, n_sup = (n_tiles + 31) >> 5;
+    const int n_seed_groups = (A.W + A.seed_group - 1) / A.seed_group;
+    const int n_seed_items = A.L * n_seed_groups;
+    const int n_items = n_seed_items + A.L * A.n_groups;
+    unsigned long long n_seed_q = 0, n_cull_q = 0;
+    int loaded = -1;
+
+    // Evaluate queries [0, nq) of the ring, a tile of 128 per pipeline at a time, and
+    // fold them into s_key (warps of one pipeline combine the lanes of a waypoint
+    // first).  Link l's weights are loaded.
+    auto evaluate_ring = [&](int l, int nq) {
+        const int nt = (nq + 127) >> 7;
+        for (int tl = pipe; tl < nt && ok; tl += kEvalPipes) {
+            const int qi = tl * 128 + r;
+            const uint32_t tag = qi < nq ? s_tag[qi] : kNoTag;
+            const float4 x = tag != kNoTag ? s_q[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float f = 0.f;
+            ok = pipe_network(pipe, r, small, sH, aH, aW2, aW3, d_tmem, taddr, &mbar[pipe], phase, A.wait_polls,
+                              x, f);
+            if (!ok) {
+                if (r == 0) s_fail = 1;
+                break;
+            }
+            const float d = fmaf(A.scale[l], f, x.w);
+            const bool use = tag != kNoTag && !isnan(d);
+            const unsigned j = use ? tag >> 24 : kNoTag;
+            const unsigned hi = use ? ordered_bits(d) : 0xffffffffu;
+            const unsigned lo = use ? (((tag & 0xffffffu) << 4) | (unsigned)l) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, j);
+            const unsigned hmin = __reduce_min_sync(peers, hi);
+            const unsigned lmin = __reduce_min_sync(peers, hi == hmin ? lo : 0xffffffffu);
+            if (use && lane == __ffs(peers) - 1) atomicMin(&s_key[j], ((unsigned long long)hmin << 32) | lmin);
+        }
+    };
+
+    for (;;) {
+        __syncthreads();
+        if (t == 0) s_item = atomicAdd(A.work, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items || s_fail) break;
+        const bool seed = item < n_seed_items;
+        const int rem = seed ? item : item - n_seed_items;
+        const int ng = seed ? n_seed_groups : A.n_groups;
+        const int gsz = seed ? A.seed_group : A.group;
+        const int l = rem / ng, g = rem % ng;
+        const int w0 = g * gsz;
+        const int nw = min(gsz, A.W - w0);
+        if (l != loaded) {
+            load_image(A.image + (size_t)l * kImgBytes, sm + kSurImg, t, kEvalThreads);
+            tc::fence_smem_to_async();   // the weights are MMA operands
+            loaded = l;
+        }
+        // the group's poses and world capsules of link l
+        if (warp < nw) {
+            const float4* P = reinterpret_cast<const float4*>(A.poses + ((size_t)(w0 + warp) * A.L + l) * 16);
+            const float4 M0 = P[0], M1 = P[1], M2 = P[2];
+            if (lane == 0) {
+                s_M[warp][0] = M0;
+                s_M[warp][1] = M1;
+                s_M[warp][2] = M2;
+                const float4 a = A.cap_a[l], b = A.cap_b[l];
+                const float ax = a.x - M0.w, ay = a.y - M1.w, az = a.z - M2.w;
+                const float bx = b.x - M0.w, by = b.y - M1.w, bz = b.z - M2.w;
+                const float Ax = fmaf(M0.x, ax, fmaf(M1.x, ay, M2.x * az));
+                const float Ay = fmaf(M0.y, ax, fmaf(M1.y, ay, M2.y * az));
+                const float Az = fmaf(M0.z, ax, fmaf(M1.z, ay, M2.z * az));
+                const float Bx = fmaf(M0.x, bx, fmaf(M1.x, by, M2.x * bz));
+                const float By = fmaf(M0.y, bx, fmaf(M1.y, by, M2.y * bz));
+                const float Bz = fmaf(M0.z, bx, fmaf(M1.z, by, M2.z * bz));
+                const float dx = Bx - Ax, dy = By - Ay, dz = Bz - Az;
+                const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                s_cA[warp] = make_float4(Ax, Ay, Az, a.w);
+                s_cD[warp] = make_float4(dx, dy, dz, dd > 0.f ? 1.f / dd : 0.f);
+                // cull items start from the minimum over every link published so far
+                s_key[warp] = seed ? ~0ull : A.keys[w0 + warp];
+            }
+        }
+        if (t == 0) {
+            s_qn = 0;
+            s_ln = 0;
+            s_lnext = 0;
+            s_over = 0u;
+        }
+        __syncthreads();
+
+        if (seed) {
+            // the 32 points of the tile nearest to the capsule (nearest super-tile first)
+            uint32_t tag = kNoTag;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (warp < nw && nv > 0) {
+                const float4 cA = s_cA[warp], cD = s_cD[warp];
+                float best = INFINITY;
+                int bi = 0x7fffffff;
+                for (int s = lane; s < n_sup; s += 32) {
+                    const float gp = capsule_gap(__ldg(&A.supers[s]), cA, cD);
+                    if (gp < best) { best = gp; bi = s; }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                }
+                if (bi < n_sup) {
+                    const int tt = bi * 32 + lane;
+                    float tb = INFINITY;
+                    int ti = 0x7fffffff;
+                    if (tt < n_tiles) { tb = capsule_gap(__ldg(&A.tiles[tt]), cA, cD); ti = tt; }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float ob = __shfl_xor_sync(0xffffffffu, tb, o);
+                        const int oi = __shfl_xor_sync(0xffffffffu, ti, o);
+                        if (ob < tb || (ob == tb && oi < ti)) { tb = ob; ti = oi; }
+                    }
+                    const int k = ti * 32 + lane;
+                    if (ti < n_tiles && k < nv) {
+                        const float4 p = __ldg(&A.sorted[k]);
+                        q = make_query(A, l, s_M[warp], p);
+                        tag = ((unsigned)warp << 24) | (unsigned)__float_as_int(p.w);
+                    }
+                }
+            }
+            if (warp < gsz) {
+                s_q[warp * 32 + lane] = q;
+                s_tag[warp * 32 + lane] = tag;
+                if (A.stats) n_seed_q += (unsigned)__popc(__ballot_sync(0xffffffffu, tag != kNoTag));
+            }
+            __syncthreads();
+            evaluate_ring(l, gsz * 32);
+            __syncthreads();
+        } else {
+            if (t < nw) {
+                const unsigned long long k = s_key[t];
+                const float best = k == ~0ull ? INFINITY : from_ordered((unsigned)(k >> 32));
+                s_thr[t] = best + A.slack + s_cA[t].w;
+            }
+            __syncthreads();
+            // list: (waypoint slot, tile) entries whose tile sphere reaches the threshold
+            if (warp < nw) {
+                const float4 cA = s_cA[warp], cD = s_cD[warp];
+                const float thr = s_thr[warp];
+                for (int s0 = 0; s0 < n_sup; s0 += 32) {
+                    const int sidx = s0 + lane;
+                    unsigned bs = __ballot_sync(0xffffffffu,
+                                                sidx < n_sup && capsule_gap(__ldg(&A.supers[sidx]), cA, cD) <= thr);
+                    while (bs) {
+                        const int sv = s0 + __ffs(bs) - 1;
+                        bs &= bs - 1;
+                        const int tt = sv * 32 + lane;
+                        const bool reach = tt < n_tiles && capsule_gap(__ldg(&A.tiles[tt]), cA, cD) <= thr;
+                        const unsigned bt = __ballot_sync(0xffffffffu, reach);
+                        if (!bt) continue;
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&s_ln, __popc(bt));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        const int slot = base + __popc(bt & ((1u << lane) - 1u));
+                        if (reach && slot < kSurList) s_list[slot] = ((unsigned)warp << 24) | (unsigned)tt;
+                        if (base + __popc(bt) > kSurList && lane == 0) atomicOr(&s_over, 1u << warp);
+                    }
+                }
+            }
+            __syncthreads();
+            const int n_list = min(s_ln, kSurList);
+            for (;;) {
+                // produce: kSurTake entries per warp step (their point loads go out
+                // together) until the ring holds kSurFill queries
+                for (;;) {
+                    int e0 = 0x7fffffff;
+                    if (lane == 0 && *reinterpret_cast<volatile int*>(&s_qn) < kSurFill)
+                        e0 = atomicAdd(&s_lnext, kSurTake);
+                    e0 = __shfl_sync(0xffffffffu, e0, 0);
+                    if (e0 >= n_list) break;
+                    float4 p[kSurTake];
+                    int jj[kSurTake];
+#pragma unroll
+                    for (int u = 0; u < kSurTake; ++u) {
+                        const bool ve = e0 + u < n_list;
+                        const uint32_t ent = ve ? s_list[e0 + u] : 0u;
+                        jj[u] = ve ? (int)(ent >> 24) : -1;
+                        const int k = (int)(ent & 0xffffffu) * 32 + lane;
+                        p[u] = (ve && k < nv) ? __ldg(&A.sorted[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (!(ve && k < nv)) jj[u] = -1;
+                    }
+                    bool take[kSurTake];
+                    unsigned b[kSurTake];
+                    int cnt = 0;
+#pragma unroll
+                    for (int u = 0; u < kSurTake; ++u) {
+                        const int j = max(jj[u], 0);
+                        take[u] = jj[u] >= 0 &&
+                                  capsule_gap(make_float4(p[u].x, p[u].y, p[u].z, 0.f), s_cA[j], s_cD[j]) <= s_thr[j];
+                        b[u] = __ballot_sync(0xffffffffu, take[u]);
+                        cnt += __popc(b[u]);
+                    }
+                    if (!cnt) continue;
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&s_qn, cnt);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+                    for (int u = 0; u < kSurTake; ++u) {
+                        if (take[u]) {
+                            const int slot = base + __popc(b[u] & ((1u << lane) - 1u));
+                            s_q[slot] = make_query(A, l, s_M[jj[u]], p[u]);
+                            s_tag[slot] = ((unsigned)jj[u] << 24) | (unsigned)__float_as_int(p[u].w);
+                        }
+                        base += __popc(b[u]);
+                    }
+                }
+                __syncthreads();
+                const int nq = s_qn;
+                const bool done = s_lnext >= n_list;
+                if (nq == 0) break;   // then done as well: production stops only at kSurFill or at the end
+                const int take_q = done ? nq : (nq & ~127);
+                if (A.stats && t == 0) n_cull_q += (unsigned)take_q;
+                evaluate_ring(l, take_q);
+                __syncthreads();
+                // the rest (under one tile) to the front of the ring; thresholds tighten
+                const int left = nq - take_q;
+                float4 mq;
+                uint32_t mt = kNoTag;
+                if (t < left) {
+                    mq = s_q[take_q + t];
+                    mt = s_tag[take_q + t];
+                }
+                if (t < nw) {
+                    const unsigned long long k = s_key[t];
+                    const float best = k == ~0ull ? INFINITY : from_ordered((unsigned)(k >> 32));
+                    s_thr[t] = fminf(s_thr[t], best + A.slack + s_cA[t].w);
+                }
+                __syncthreads();
+                if (t < left) {
+                    s_q[t] = mq;
+                    s_tag[t] = mt;
+                }
+                if (t == 0) s_qn = left;
+                __syncthreads();
+                if (done && left == 0) break;
+            }
+        }
+        // publish the group's minima (and the waypoints whose list overflowed)
+        if (t < nw) {
+            if (s_key[t] != ~0ull) atomicMin(&A.keys[w0 + t], s_key[t]);
+            if (s_over & (1u << t)) A.recheck[w0 + t] = 1;
+        }
+    }
+    if (A.stats) {
+        if (lane == 0) {
+            unsigned long long v = n_seed_q;
+            if (v) atomicAdd(&A.stats[26], v);
+        }
+        if (t == 0 && n_cull_q) atomicAdd(&A.stats[27], n_cull_q);
+    }
+    if (!ok) {
+        // a wait gave up: report it, then let the MMA still in flight end before the
+        // tensor memory is released
+        if (r == 0) atomicOr(A.status, kStatusTimeout);
+        tc::mbar_wait(&mbar[pipe], phase ^ 1u, kWaitPolls);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_free(tm, 512);
 }
 
 // Per waypoint: decode the surrogate minimum, write it as the result, and select the
-// waypoint for the grid re-check when it is below margin + error bound (or when a
-// query segment overflowed, every waypoint).
-__global__ void sur_finish_kernel(const unsigned long long* keys, const int* seg_count, int L, int seg_cap, int W,
-                                  float limit, float* dist, int32_t* arg_link, int32_t* arg_point, float* sur_dist,
-                                  uint8_t* mask) {
+// waypoint for the grid re-check when it is below margin + error bound, or when its
+// list overflowed (recheck already 1).
+__global__ void sur_finish_kernel(const unsigned long long* keys, int W, float limit, float* dist, int32_t* arg_link,
+                                  int32_t* arg_point, float* sur_dist, uint8_t* recheck) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= W) return;
-    bool overflow = false;
-    for (int l = 0; l < L; ++l) overflow |= seg_count[l] > seg_cap;
     const unsigned long long key = keys[w];
     float d;
     if (key == ~0ull) {
@@ -1012,7 +1304,7 @@ __global__ void sur_finish_kernel(const unsigned long long* keys, const int* seg
     }
     dist[w] = d;
     if (sur_dist) sur_dist[w] = d;
-    mask[w] = (overflow || d < limit) ? 1 : 0;
+    recheck[w] = (recheck[w] || d < limit) ? 1 : 0;
 }
 }  // namespace
 
@@ -1022,6 +1314,8 @@ cudaError_t configure_surrogate_kernels() {
     cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mlp_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kEvalSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sur_check_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSurSmem);
     return e;
 }
 
@@ -1334,8 +1628,8 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
     const int L = S->L;
     cudaStream_t st = ctx->stream;
     cudaError_t e = cudaSuccess;
-    // workspace (the context's): poses, keys and mask per waypoint; query segments per link
-    if ((size_t)W > ctx->sur_w_cap || (size_t)L > ctx->sur_links) {
+    // workspace (the context's): poses, keys and re-check mask per waypoint, the item counter
+    if ((size_t)W > ctx->sur_w_cap || !ctx->sur_count) {
         const size_t cap = std::max<size_t>((size_t)W, 2 * ctx->sur_w_cap);
         cudaStreamSynchronize(st);
         sdf::dfree(ctx->sur_poses);
@@ -1348,39 +1642,44 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
         e = sdf::dmalloc(&ctx->sur_poses, sizeof(float) * 16 * SDF_MAX_LINKS * cap);
         if (e == cudaSuccess) e = sdf::dmalloc(&ctx->sur_keys, sizeof(unsigned long long) * cap);
         if (e == cudaSuccess) e = sdf::dmalloc(&ctx->sur_mask, cap);
+        if (e == cudaSuccess && !ctx->sur_count) e = sdf::dmalloc(&ctx->sur_count, sizeof(int) * SDF_MAX_LINKS);
         if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate: workspace");
         ctx->sur_w_cap = cap;
     }
-    const size_t want = std::min<size_t>((size_t)W * (size_t)std::max(N, 1),
-                                         std::max<size_t>((size_t)W * 256, (size_t)1 << 20));
-    if (want > ctx->sur_cap || (size_t)L > ctx->sur_links) {
-        const size_t cap = std::max(want, ctx->sur_cap);
+    if ((size_t)L * sdf::kImgBytes > ctx->sur_wimg_cap) {
         cudaStreamSynchronize(st);
-        sdf::dfree(ctx->sur_xq);
-        sdf::dfree(ctx->sur_tag);
-        ctx->sur_xq = nullptr;
-        ctx->sur_tag = nullptr;
-        ctx->sur_cap = 0;
-        ctx->sur_links = 0;
-        if (!ctx->sur_count) e = sdf::dmalloc(&ctx->sur_count, sizeof(int) * SDF_MAX_LINKS);
-        if (e == cudaSuccess) e = sdf::dmalloc(&ctx->sur_xq, sizeof(float4) * L * cap);
-        if (e == cudaSuccess) e = sdf::dmalloc(&ctx->sur_tag, sizeof(uint2) * L * cap);
-        if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate: query buffers");
-        ctx->sur_cap = cap;
-        ctx->sur_links = (size_t)L;
+        sdf::dfree(ctx->sur_wimg);
+        ctx->sur_wimg = nullptr;
+        ctx->sur_wimg_cap = 0;
+        e = sdf::dmalloc(&ctx->sur_wimg, (size_t)SDF_MAX_LINKS * sdf::kImgBytes);
+        if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate: weight image");
+        ctx->sur_wimg_cap = (size_t)SDF_MAX_LINKS * sdf::kImgBytes;
     }
-    e = cudaMemsetAsync(ctx->sur_keys, 0xff, sizeof(unsigned long long) * W, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_count, 0, sizeof(int) * SDF_MAX_LINKS, st);
+    // the weights in the fused kernel's shared-memory layout, from the current parameters
+    sdf::weight_image_kernel<<<(unsigned)L, 512, 0, st>>>(S->master, ctx->sur_wimg);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_keys, 0xff, sizeof(unsigned long long) * W, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_mask, 0, (size_t)W, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_count, 0, sizeof(int), st);
     if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate");
     sdf::BatchParams* bp = new (std::nothrow) sdf::BatchParams();
     if (!bp) return sfail(ctx, SDF_ERR_OOM, "host allocation");
     int rc = sdf::sort_cloud(ctx, points_dev, N, bp);
-    sdf::SurCheckArgs A{};
+    sdf::SurFusedArgs A{};
     if (rc == SDF_OK) {
         e = sdf::launch_fk(R->table, q_dev, W, ctx->sur_poses, ctx->status, st);
         A.poses = ctx->sur_poses;
         A.W = W;
         A.L = L;
+        // waypoints per work item: the most (16, 8 or 4) that still gives every SM about
+        // three cull items, so that the items even out across the SMs
+        A.group = 4;
+        for (int gsz = sdf::kSurGroup; gsz > 4; gsz /= 2)
+            if ((long long)L * ((W + gsz - 1) / gsz) >= 3LL * ctx->num_sms) {
+                A.group = gsz;
+                break;
+            }
+        A.n_groups = (W + A.group - 1) / A.group;
         A.sorted = bp->sorted;
         A.tiles = bp->tiles;
         A.supers = bp->supers;
@@ -1394,61 +1693,30 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
                 A.m[l][k] = S->box_m[l][k];
             }
             A.inv_a[l] = (float)(1.0 / a);
-        }
-        A.xq = ctx->sur_xq;
-        A.tag = ctx->sur_tag;
-        A.seg_count = ctx->sur_count;
-        A.seg_cap = (int)ctx->sur_cap;
-        A.keys = ctx->sur_keys;
-        A.slack = eps + sdf::kCullSlack;
-        for (int l = 0; l < L; ++l) {
+            A.scale[l] = S->box_a[l];
             A.cap_a[l] = R->table.cap_a[l];
             A.cap_b[l] = R->table.cap_b[l];
         }
+        A.image = ctx->sur_wimg;
+        A.seed_group = sdf::kSurGroup;
+        A.keys = ctx->sur_keys;
+        A.recheck = ctx->sur_mask;
+        A.work = ctx->sur_count;
+        A.slack = eps + sdf::kCullSlack;
+        A.status = ctx->status;
+        A.wait_polls = ctx->wait_polls;
+        A.stats = ctx->stats ? ctx->d_stats : nullptr;
     }
     delete bp;
-    sdf::EvalArgs E{};
-    E.master = S->master;
-    E.xq = ctx->sur_xq;
-    E.tag = ctx->sur_tag;
-    E.seg_count = ctx->sur_count;
-    E.seg_cap = (int)ctx->sur_cap;
-    E.L = L;
-    E.keys = ctx->sur_keys;
-    for (int l = 0; l < L; ++l) E.scale[l] = S->box_a[l];
-    E.status = ctx->status;
-    E.wait_polls = ctx->wait_polls;
-    const unsigned pair_blocks = (unsigned)(((size_t)W * L * 32 + 255) / 256);
-    const int eval_grid = ctx->num_sms;
+    const int items = L * ((W + sdf::kSurGroup - 1) / sdf::kSurGroup) + L * A.n_groups;
     if (rc == SDF_OK && e == cudaSuccess) {
-        sdf::sur_pairs_kernel<true><<<pair_blocks, 256, 0, st>>>(A);
-        e = cudaGetLastError();
-    }
-    if (rc == SDF_OK && e == cudaSuccess) {
-        sdf::mlp_eval_kernel<<<eval_grid, sdf::kEvalThreads, sdf::kEvalSmem, st>>>(E);
-        e = cudaGetLastError();
-    }
-    if (rc == SDF_OK && e == cudaSuccess && ctx->stats && ctx->d_stats) {
-        sdf::count_queries_kernel<<<1, 1, 0, st>>>(ctx->sur_count, L, (int)ctx->sur_cap, ctx->d_stats + 26);
-        e = cudaGetLastError();
-    }
-    if (rc == SDF_OK && e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_count, 0, sizeof(int) * SDF_MAX_LINKS, st);
-    if (rc == SDF_OK && e == cudaSuccess) {
-        sdf::sur_pairs_kernel<false><<<pair_blocks, 256, 0, st>>>(A);
-        e = cudaGetLastError();
-    }
-    if (rc == SDF_OK && e == cudaSuccess) {
-        sdf::mlp_eval_kernel<<<eval_grid, sdf::kEvalThreads, sdf::kEvalSmem, st>>>(E);
-        e = cudaGetLastError();
-    }
-    if (rc == SDF_OK && e == cudaSuccess && ctx->stats && ctx->d_stats) {
-        sdf::count_queries_kernel<<<1, 1, 0, st>>>(ctx->sur_count, L, (int)ctx->sur_cap, ctx->d_stats + 27);
+        sdf::sur_check_kernel<<<(unsigned)std::min(items, ctx->num_sms), sdf::kEvalThreads, sdf::kSurSmem, st>>>(A);
         e = cudaGetLastError();
     }
     if (rc == SDF_OK && e == cudaSuccess) {
         sdf::sur_finish_kernel<<<(unsigned)((W + 255) / 256), 256, 0, st>>>(
-            ctx->sur_keys, ctx->sur_count, L, (int)ctx->sur_cap, W, margin + eps, dist_dev, argmin_link_dev,
-            argmin_point_dev, surrogate_dist_dev, ctx->sur_mask);
+            ctx->sur_keys, W, margin + eps, dist_dev, argmin_link_dev, argmin_point_dev, surrogate_dist_dev,
+            ctx->sur_mask);
         e = cudaGetLastError();
     }
     if (rc == SDF_OK && e == cudaSuccess && rechecked_dev)
