@@ -136,7 +136,9 @@ const char* sdf_last_error(const sdf_ctx* ctx);
                                      texture copy (n^3 FP32 per link; allocates and
                                      synchronises); sdf_grids_destroy frees it.  The texture
                                      form is its own kernel and always takes 4 list entries
-                                     per warp step (SDF_OPT_TILE_BATCH does not apply). */
+                                     per warp step (SDF_OPT_TILE_BATCH does not apply); every
+                                     request of one launch must use the same grids object
+                                     (else SDF_ERR_UNSUPPORTED). */
 int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t value);
 int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* value);
 

@@ -471,7 +471,6 @@ void sdf_grids_destroy(sdf_grids* G) {
         if (G->tex[l]) cudaDestroyTextureObject(G->tex[l]);
         sdf::afree(G->tex_arr[l]);
     }
-    sdf::dfree(G->d_tex);
     sdf::dfree(G->values);
     delete G;
 }
@@ -578,10 +577,9 @@ void link_capsule(const float* v, int n, const sdf_grid_meta& m, float4* ca, flo
 // and unnormalised coordinates (texel (i,j,k) is sampled at (i,j,k) + 1/2).  Made
 // once per grids object; allocates and synchronises.
 int grid_textures(sdf_ctx* ctx, sdf_grids* G) {
-    if (G->d_tex) return SDF_OK;
+    if (G->tex_ready) return SDF_OK;
     const int n = G->n;
     const size_t n3 = (size_t)n * n * n;
-    unsigned long long h[SDF_MAX_LINKS] = {0};
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < G->n_links && e == cudaSuccess; ++l) {
         if (!G->tex_arr[l]) e = sdf::amalloc3d(&G->tex_arr[l], n);
@@ -604,17 +602,11 @@ int grid_textures(sdf_ctx* ctx, sdf_grids* G) {
             td.normalizedCoords = 0;
             e = cudaCreateTextureObject(&G->tex[l], &rd, &td, nullptr);
         }
-        h[l] = (unsigned long long)G->tex[l];
     }
-    unsigned long long* d = nullptr;
-    if (e == cudaSuccess) e = sdf::dmalloc(&d, sizeof h);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h, sizeof h, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) {
-        sdf::dfree(d);   // the arrays and objects stay with G (freed by sdf_grids_destroy)
-        return cuda_fail(ctx, e, "texture copy of the grids");
-    }
-    G->d_tex = d;
+    // on failure the arrays and objects made so far stay with G (sdf_grids_destroy frees them)
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "texture copy of the grids");
+    G->tex_ready = true;
     return SDF_OK;
 }
 
@@ -846,13 +838,19 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
         const int rc = validate_request(ctx, reqs[i], i);
         if (rc != SDF_OK) return rc;
     }
-    if (ctx->tex3d) {   // the texture copy of every robot's grids (made once; may synchronise)
-        DeviceGuard g(ctx->device);
+    const sdf_grids* tex_grids = nullptr;
+    if (ctx->tex3d) {   // the texture copy of the grids (made once; may synchronise)
         for (int i = 0; i < n; ++i)
             if (reqs[i].W > 0) {
-                const int rc = grid_textures(ctx, const_cast<sdf_grids*>(reqs[i].robot->grids));
-                if (rc != SDF_OK) return rc;
+                if (tex_grids && reqs[i].robot->grids != tex_grids)
+                    return fail(ctx, SDF_ERR_UNSUPPORTED, "SDF_OPT_TEX3D: every request of a launch must use one grids object");
+                tex_grids = reqs[i].robot->grids;
             }
+        if (tex_grids) {
+            DeviceGuard g(ctx->device);
+            const int rc = grid_textures(ctx, const_cast<sdf_grids*>(tex_grids));
+            if (rc != SDF_OK) return rc;
+        }
     }
     sdf::BatchParams* p = new (std::nothrow) sdf::BatchParams();
     if (!p) return fail(ctx, SDF_ERR_OOM, "host allocation");
@@ -898,7 +896,6 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
         I.dof = r.robot->dof;
         I.cloud = c;
         I.mask = r.mask_dev;
-        I.tex = ctx->tex3d ? r.robot->grids->d_tex : nullptr;
         // the linear grids are prefetched into L2 only when the lookups read them
         I.warm = ctx->tex3d ? nullptr : r.robot->table.values;
         I.warm_bytes = (unsigned long long)I.L * r.robot->table.n * r.robot->table.n * r.robot->table.n * sizeof(float);
@@ -929,7 +926,9 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     p->skip_prep = ctx->reuse_sort;
     p->warm_l2 = !ctx->reuse_sort && !ctx->time_kernels;   // the launches that overlap check and sort
     p->warps = nw;
-    p->tex = ctx->tex3d;
+    p->tex = tex_grids ? 1 : 0;
+    if (tex_grids)
+        for (int l = 0; l < tex_grids->n_links; ++l) p->tex_h[l] = (unsigned long long)tex_grids->tex[l];
     p->sorted = ctx->sorted;
     p->tiles = ctx->tiles;
     p->supers = ctx->supers;

@@ -547,7 +547,6 @@ struct BlockState {
     const uchar2* pair_wl;     // per pair: (waypoint of the block, link), no division in the hot loops
     const float4* grid_o;      // per link (shared memory)
     const float* grid_h;
-    const unsigned long long* tex;  // per link texture objects (shared memory; texture form only)
     unsigned* best;            // per waypoint of the block
     unsigned long long* key;
     int cull;
@@ -581,10 +580,7 @@ __device__ __forceinline__ bool capsule_reaches(float4 c, float4 A, float4 D, fl
 }
 
 // Interpolated distance of sorted point `pos` for block pair `pair`, folded into
-// the waypoint's best value and key when it can still be the minimum.  TEX: the
-// texture unit's filter does the interpolation (a separate kernel instantiation, so
-// that the default kernel holds no texture instruction).
-template <bool TEX>
+// the waypoint's best value and key when it can still be the minimum.
 __device__ __forceinline__ void evaluate(const BlockState& B, int pos, int pair) {
     const float4 p = __ldg(&B.sorted[pos]);
     const float4 r0 = B.pose[pair][0], r1 = B.pose[pair][1], r2 = B.pose[pair][2];
@@ -593,17 +589,66 @@ __device__ __forceinline__ void evaluate(const BlockState& B, int pos, int pair)
     const float lx = fmaf(r0.x, p.x, fmaf(r0.y, p.y, fmaf(r0.z, p.z, r0.w)));
     const float ly = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
     const float lz = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
-    float g;
-    if constexpr (TEX)
-        g = tex_lookup(B.tex[l], B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz);
-    else
-        g = grid_lookup(B.values + (size_t)(l * B.n3), B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz);
+    const float g = grid_lookup(B.values + (size_t)(l * B.n3), B.n, B.grid_o[l], B.grid_h[l], lx, ly, lz);
     const unsigned long long key = pack_key(g, __float_as_int(p.w), l);
     const unsigned ob = (unsigned)(key >> 32);
     if (ob <= B.best[wl]) {
         atomicMin(&B.best[wl], ob);
         atomicMin(&B.key[wl], key);
     }
+}
+
+// The same through the texture unit's filter (SDF_OPT_TEX3D), called by the whole warp
+// (lanes with `valid` false take part without a point).  A texture fetch is given a
+// handle that is the same in every lane and comes from the kernel parameters: the
+// warp fetches link by link, the link of the first pending lane each round (a
+// handle that differs between lanes is not used).
+__device__ __forceinline__ void evaluate_tex(const BatchParams& P, const BlockState& B, int pos, int pair,
+                                             bool valid) {
+    const float4 p = valid ? __ldg(&B.sorted[pos]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int pr = valid ? pair : 0;
+    const float4 r0 = B.pose[pr][0], r1 = B.pose[pr][1], r2 = B.pose[pr][2];
+    const uchar2 pw = B.pair_wl[pr];
+    const int wl = pw.x, l = valid ? (int)pw.y : -1;
+    const int ll = valid ? l : 0;
+    const float lx = fmaf(r0.x, p.x, fmaf(r0.y, p.y, fmaf(r0.z, p.z, r0.w)));
+    const float ly = fmaf(r1.x, p.x, fmaf(r1.y, p.y, fmaf(r1.z, p.z, r1.w)));
+    const float lz = fmaf(r2.x, p.x, fmaf(r2.y, p.y, fmaf(r2.z, p.z, r2.w)));
+    TexCoord c = tex_coord(B.n, B.grid_o[ll], B.grid_h[ll], lx, ly, lz);
+    float v = 0.f;
+    unsigned pending = __ballot_sync(kFull, valid);
+    while (pending) {
+        const int k = __shfl_sync(kFull, l, __ffs(pending) - 1);
+        unsigned long long h = 0;
+        switch (k) {
+#define SDF_TEX_CASE(i) case i: h = P.tex_h[i]; break;
+            SDF_TEX_CASE(0) SDF_TEX_CASE(1) SDF_TEX_CASE(2) SDF_TEX_CASE(3) SDF_TEX_CASE(4) SDF_TEX_CASE(5)
+            SDF_TEX_CASE(6) SDF_TEX_CASE(7) SDF_TEX_CASE(8) SDF_TEX_CASE(9) SDF_TEX_CASE(10) SDF_TEX_CASE(11)
+            SDF_TEX_CASE(12) SDF_TEX_CASE(13) SDF_TEX_CASE(14) SDF_TEX_CASE(15)
+#undef SDF_TEX_CASE
+            default: break;
+        }
+        const float t = tex3D<float>((cudaTextureObject_t)h, c.x, c.y, c.z);
+        if (l == k) v = t;
+        pending &= ~__ballot_sync(kFull, l == k);
+    }
+    if (!valid) return;
+    const float g = c.dout + v;
+    const unsigned long long key = pack_key(g, __float_as_int(p.w), l);
+    const unsigned ob = (unsigned)(key >> 32);
+    if (ob <= B.best[wl]) {
+        atomicMin(&B.best[wl], ob);
+        atomicMin(&B.key[wl], key);
+    }
+}
+
+template <bool TEX>
+__device__ __forceinline__ void evaluate_lane(const BatchParams& P, const BlockState& B, int pos, int pair,
+                                              bool valid) {
+    if constexpr (TEX)
+        evaluate_tex(P, B, pos, pair, valid);
+    else if (valid)
+        evaluate(B, pos, pair);
 }
 
 // Per-warp queue of (sorted point, pair) entries; 32 entries are evaluated at once.
@@ -613,7 +658,8 @@ struct WarpQueue {
 };
 
 template <bool TEX>
-__device__ __forceinline__ void queue_push(const BlockState& B, WarpQueue& Q, bool surv, int pos, int pair,
+__device__ __forceinline__ void queue_push(const BatchParams& P, const BlockState& B, WarpQueue& Q, bool surv,
+                                           int pos, int pair,
                                            int lane) {
     const unsigned m = __ballot_sync(kFull, surv);
     if (!m) return;
@@ -625,16 +671,19 @@ __device__ __forceinline__ void queue_push(const BlockState& B, WarpQueue& Q, bo
         const uint2 e = Q.q[Q.n - 32 + lane];
         __syncwarp();
         Q.n -= 32;
-        evaluate<TEX>(B, (int)e.x, (int)e.y);
+        evaluate_lane<TEX>(P, B, (int)e.x, (int)e.y, true);
     }
 }
 
 template <bool TEX>
-__device__ __forceinline__ void queue_flush(const BlockState& B, WarpQueue& Q, int lane) {
+__device__ __forceinline__ void queue_flush(const BatchParams& P, const BlockState& B, WarpQueue& Q, int lane) {
     __syncwarp();
-    if (lane < Q.n) {
+    if constexpr (TEX) {
+        const uint2 e = lane < Q.n ? Q.q[lane] : make_uint2(0u, 0u);
+        evaluate_tex(P, B, (int)e.x, (int)e.y, lane < Q.n);
+    } else if (lane < Q.n) {
         const uint2 e = Q.q[lane];
-        evaluate<TEX>(B, (int)e.x, (int)e.y);
+        evaluate(B, (int)e.x, (int)e.y);
     }
     __syncwarp();
     Q.n = 0;
@@ -642,7 +691,8 @@ __device__ __forceinline__ void queue_flush(const BlockState& B, WarpQueue& Q, i
 
 // Point tests of up to TB (pair, tile) entries, the point loads issued together.
 template <int TB, bool TEX>
-__device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, const unsigned (&ent)[TB],
+__device__ __forceinline__ void test_tiles(const BatchParams& P, const BlockState& B, WarpQueue& Q,
+                                           const unsigned (&ent)[TB],
                                            int cnt, int lane) {
     float4 pt[TB];
     int pos[TB];
@@ -665,7 +715,7 @@ __device__ __forceinline__ void test_tiles(const BlockState& B, WarpQueue& Q, co
     for (int k = 0; k < TB; ++k) {
         if (k >= cnt) break;
         if (B.stat) stat_add(B, kWsPointT, (unsigned)__popc(__ballot_sync(kFull, pos[k] < B.n_valid)), lane);
-        queue_push<TEX>(B, Q, surv[k], pos[k], (int)(ent[k] >> 28), lane);
+        queue_push<TEX>(P, B, Q, surv[k], pos[k], (int)(ent[k] >> 28), lane);
     }
 }
 
@@ -679,7 +729,6 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     __shared__ uchar2 s_pair_wl[NW];
     __shared__ float4 s_grid_o[kMaxLinks];
     __shared__ float s_grid_h[kMaxLinks];
-    __shared__ unsigned long long s_tex[kMaxLinks];
     __shared__ unsigned s_best[NW];
     __shared__ unsigned long long s_key[NW];
     __shared__ unsigned s_list[kBlockList];
@@ -727,7 +776,6 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     if (tid < L) {
         s_grid_o[tid] = T.grid_o[tid];
         s_grid_h[tid] = T.grid_h[tid];
-        if (TEX) s_tex[tid] = I.tex[tid];
     }
     if (tid < n_pair) s_pair_wl[tid] = make_uchar2((unsigned char)(tid / L), (unsigned char)(tid % L));
     if (tid == 0) {
@@ -834,7 +882,6 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     B.pose = s_pose;
     B.grid_o = s_grid_o;
     B.grid_h = s_grid_h;
-    B.tex = s_tex;
     B.best = s_best;
     B.key = s_key;
     B.cull = P.cull;
@@ -867,7 +914,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
                 const int t_seed = warp_argmin(ts, t < n_tiles ? t : 0x7fffffff);
                 const bool ev = t_seed < n_tiles && t_seed * 32 + lane < n_valid;
                 if (stats) stat_add(B, kWsSeed, (unsigned)__popc(__ballot_sync(kFull, ev)), lane);
-                if (ev) evaluate<TEX>(B, t_seed * 32 + lane, warp);
+                evaluate_lane<TEX>(P, B, t_seed * 32 + lane, warp, ev);
             }
         }
         if (stats) {
@@ -926,14 +973,14 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
                         over_ent[over_n] = ((unsigned)warp << 28) | (unsigned)(sidx * 32 + __ffs(over) - 1);
                         over &= over - 1;
                         if (++over_n == TB) {
-                            test_tiles<TB, TEX>(B, Q, over_ent, over_n, lane);
+                            test_tiles<TB, TEX>(P, B, Q, over_ent, over_n, lane);
                             over_n = 0;
                         }
                     }
                 }
             }
         }
-        if (over_n) test_tiles<TB, TEX>(B, Q, over_ent, over_n, lane);
+        if (over_n) test_tiles<TB, TEX>(P, B, Q, over_ent, over_n, lane);
         if (stats && lane == 0) s_stat_ns[warp][kWnCull] += global_ns() - t_a;
     }
     __syncthreads();
@@ -956,9 +1003,9 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
                 cnt = k + 1;
             }
         }
-        test_tiles<TB, TEX>(B, Q, ent, cnt, lane);
+        test_tiles<TB, TEX>(P, B, Q, ent, cnt, lane);
     }
-    queue_flush<TEX>(B, Q, lane);
+    queue_flush<TEX>(P, B, Q, lane);
     if (stats && lane == 0) s_stat_ns[warp][kWnPoints] += global_ns() - t_b0;
     __syncthreads();
     if (stats) {

@@ -61,8 +61,6 @@ struct InstDesc {
     int tw;                   // waypoints per check block (tw * L <= kCheckWarps)
     int block_base;           // first check block of this trajectory
     const uint8_t* mask;      // optional: only waypoints with a non-zero byte are checked
-    const unsigned long long* tex;  // SDF_OPT_TEX3D: the robot's per-link texture objects
-                                    // (device), null for the FP32 software lookup
     const float* warm;        // the robot's grids, for the first trajectory of each robot
                               // in the launch (null otherwise): its blocks prefetch them
                               // into L2 while the sort runs
@@ -79,7 +77,8 @@ struct BatchParams {
     int stage_tiles;          // tile spheres the dynamic shared memory holds (0: no staging)
     int skip_prep;            // the clouds are already sorted in the scratch: launch the check only
     int warps;                // warps per check block: 8 or 16
-    int tex;                  // lookups by the texture unit (every InstDesc::tex is set)
+    int tex;                  // lookups by the texture unit (SDF_OPT_TEX3D)
+    unsigned long long tex_h[kMaxLinks];  // texture objects of the launch's grids, by link
     int warm_l2;              // the check overlaps the sort (programmatic dependent launch):
                               // its blocks prefetch the grids meanwhile (InstDesc::warm)
     float4* sorted;           // finite points, spatially sorted: x, y, z, original index bits
@@ -159,11 +158,10 @@ struct sdf_grids {
     bool capsules = false;    // cap_a / cap_b computed (on first use)
     float4 cap_a[SDF_MAX_LINKS], cap_b[SDF_MAX_LINKS];
     // hardware-filtered copy (SDF_OPT_TEX3D), made by the first check that asks for it:
-    // one 3-D array and linear-filtering texture object per link, the objects' handles
-    // in device memory for the kernels
+    // one 3-D array and linear-filtering texture object per link
     cudaArray_t tex_arr[SDF_MAX_LINKS] = {};
     cudaTextureObject_t tex[SDF_MAX_LINKS] = {};
-    unsigned long long* d_tex = nullptr;
+    bool tex_ready = false;
 };
 
 struct sdf_robot {

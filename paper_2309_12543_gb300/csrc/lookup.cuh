@@ -53,14 +53,18 @@ __device__ __forceinline__ float grid_lookup(const float* __restrict__ G, int n,
     return dout + fmaf(fz, c1 - c0, c0);
 }
 
-// The same lookup through the texture unit (SDF_OPT_TEX3D): the hardware trilinear
+// The texture unit's form of the lookup (SDF_OPT_TEX3D): the hardware trilinear
 // filter of a linear-filtering texture object over the link's grid (unnormalised
 // coordinates, node (i,j,k) at texel centre (i,j,k) + 1/2, clamped addressing).  The
-// out-of-box rule stays in software.  The filter holds each axis's interpolation
-// weight in fixed point with 8 fractional bits, so the result is the exact trilinear
-// value at a point moved by at most h/256 per axis from the query point.
-__device__ __forceinline__ float tex_lookup(unsigned long long tex, int n, float4 o_ih, float h, float px,
-                                           float py, float pz) {
+// out-of-box rule stays in software: tex_coord gives the texel coordinates of the
+// clamped point and the distance to the box; the value is dout + tex3D(x, y, z).
+// The filter holds each axis's interpolation weight in fixed point with 8 fractional
+// bits, so the value is the exact trilinear value at a point moved by at most h/256
+// per axis from the query point.
+struct TexCoord {
+    float x, y, z, dout;
+};
+__device__ __forceinline__ TexCoord tex_coord(int n, float4 o_ih, float h, float px, float py, float pz) {
     const float top = (float)(n - 1);
     const float ux = (px - o_ih.x) * o_ih.w;
     const float uy = (py - o_ih.y) * o_ih.w;
@@ -69,8 +73,12 @@ __device__ __forceinline__ float tex_lookup(unsigned long long tex, int n, float
     const float cy = fminf(fmaxf(uy, 0.f), top);
     const float cz = fminf(fmaxf(uz, 0.f), top);
     const float ex = ux - cx, ey = uy - cy, ez = uz - cz;
-    const float dout = h * sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-    return dout + tex3D<float>((cudaTextureObject_t)tex, cx + 0.5f, cy + 0.5f, cz + 0.5f);
+    TexCoord c;
+    c.x = cx + 0.5f;
+    c.y = cy + 0.5f;
+    c.z = cz + 0.5f;
+    c.dout = h * sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+    return c;
 }
 
 // Extra radius for the bounding-volume culls under the texture lookup: the filtered

@@ -120,7 +120,6 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         I.tw = sdf::kCheckWarps / I.L > 0 ? sdf::kCheckWarps / I.L : 1;
         I.block_base = 0;
         I.mask = nullptr;
-        I.tex = nullptr;
         I.warm = R->table.values;
         I.warm_bytes = (unsigned long long)I.L * R->table.n * R->table.n * R->table.n * sizeof(float);
         const int n_tiles = (N + 31) / 32;
