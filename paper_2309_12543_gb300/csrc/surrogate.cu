@@ -161,6 +161,12 @@ __device__ __forceinline__ void mma_k128(uint32_t d, uint32_t a_addr, uint32_t a
 // Load one link's weights: the W2/W3 blocks (stored [in][out]) into K-major bf16
 // tiles [out][in], the small parameters into FP32.  All `nthreads` threads help;
 // consecutive threads read consecutive output units (coalesced).
+// Small parameters in the evaluation kernels' layout: (W1 row j, b1 j) as one float4
+// per unit, then b2, b3, w4 and b4, so that each is read with 16-byte loads.
+constexpr int kEWB = 0, kEB2 = 4 * kH, kEB3 = 5 * kH, kEW4 = 6 * kH, kEB4 = 7 * kH;
+static_assert(kEB4 + 1 <= kSmallFloats, "evaluation layout of the small parameters");
+
+template <bool kEvalLayout = false>
 __device__ __forceinline__ void load_weights(const float* __restrict__ P, uint8_t* w2, uint8_t* w3, float* small,
                                              int t, int nthreads) {
     constexpr int kChunks = kH * (kH / 8);   // 8-element row chunks per block
@@ -172,6 +178,17 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ P, uint8_
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] = src[(i0 + k) * kH + o];
         store_bf16x8(blk == 0 ? w2 : w3, o, i0, kH, v);
+    }
+    if constexpr (kEvalLayout) {
+        for (int i = t; i < kH; i += nthreads) {
+            reinterpret_cast<float4*>(small + kEWB)[i] =
+                make_float4(P[kOW1 + 3 * i], P[kOW1 + 3 * i + 1], P[kOW1 + 3 * i + 2], P[kOB1 + i]);
+            small[kEB2 + i] = P[kOB2 + i];
+            small[kEB3 + i] = P[kOB3 + i];
+            small[kEW4 + i] = P[kOW4 + i];
+        }
+        if (t == 0) small[kEB4] = P[kOB4];
+        return;
     }
     for (int i = t; i < 384; i += nthreads) small[i] = P[kOW1 + i];
     for (int i = t; i < kH; i += nthreads) {
@@ -566,7 +583,7 @@ __device__ __forceinline__ void pipe_sync_for_mma(int pipe) {
 }
 
 // One hidden layer's epilogue on this thread's tensor-memory lane: s(D + b) of the
-// 128 units into row r of the activation tile H (bf16).
+// 128 units into row r of the activation tile H (bf16).  b is 16-byte aligned.
 __device__ __forceinline__ void pipe_hidden(uint32_t taddr, const float* b, uint8_t* H, int r) {
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 32) {
@@ -574,15 +591,17 @@ __device__ __forceinline__ void pipe_hidden(uint32_t taddr, const float* b, uint
         tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
         for (int k = 0; k < 32; k += 8) {
+            const float4 b0 = *reinterpret_cast<const float4*>(b + c0 + k);
+            const float4 b1 = *reinterpret_cast<const float4*>(b + c0 + k + 4);
             float h[8];
-            h[0] = silu_mix<0>(v[k + 0] + b[c0 + k + 0]);
-            h[1] = silu_mix<1>(v[k + 1] + b[c0 + k + 1]);
-            h[2] = silu_mix<2>(v[k + 2] + b[c0 + k + 2]);
-            h[3] = silu_mix<3>(v[k + 3] + b[c0 + k + 3]);
-            h[4] = silu_mix<4>(v[k + 4] + b[c0 + k + 4]);
-            h[5] = silu_mix<5>(v[k + 5] + b[c0 + k + 5]);
-            h[6] = silu_mix<6>(v[k + 6] + b[c0 + k + 6]);
-            h[7] = silu_mix<7>(v[k + 7] + b[c0 + k + 7]);
+            h[0] = silu_mix<0>(v[k + 0] + b0.x);
+            h[1] = silu_mix<1>(v[k + 1] + b0.y);
+            h[2] = silu_mix<2>(v[k + 2] + b0.z);
+            h[3] = silu_mix<3>(v[k + 3] + b0.w);
+            h[4] = silu_mix<4>(v[k + 4] + b1.x);
+            h[5] = silu_mix<5>(v[k + 5] + b1.y);
+            h[6] = silu_mix<6>(v[k + 6] + b1.z);
+            h[7] = silu_mix<7>(v[k + 7] + b1.w);
             store_bf16x8(H, r, c0 + k, kH, h);
         }
     }
@@ -592,24 +611,23 @@ __device__ __forceinline__ void pipe_hidden(uint32_t taddr, const float* b, uint
 // tensor-memory lane r): layer 1 and the epilogues on the FP32 cores, the two
 // 128 x 128 layers as tcgen05 MMAs into this pipeline's 128 tensor-memory columns
 // (Z2, then Z3 in the same columns).  H holds H1, then H2 (each MMA has finished
-// reading its operand before the next write).  Returns false if an MMA wait gave up
-// (the pipeline agrees on it); f is valid otherwise.
+// reading its operand before the next write).  `small` is in the evaluation layout.
+// Returns false if an MMA wait gave up (the pipeline agrees on it); f is valid
+// otherwise.
 __device__ __forceinline__ bool pipe_network(int pipe, int r, const float* small, uint8_t* H, uint32_t aH,
                                              uint32_t aW2, uint32_t aW3, uint32_t d_tmem, uint32_t taddr,
                                              uint64_t* mbar, uint32_t& phase, uint32_t limit, float4 x, float& f) {
-    const float* W1 = small;
-    const float* b1 = small + 384;
-    const float* b2 = small + 384 + kH;
-    const float* b3 = small + 384 + 2 * kH;
-    const float* w4 = small + 384 + 3 * kH;
+    const float4* wb = reinterpret_cast<const float4*>(small + kEWB);
+    const float* b3 = small + kEB3;
+    const float* w4 = small + kEW4;
     constexpr uint32_t kN128KK = tc::idesc_bf16(128, 128, 0, 0);
 #pragma unroll 1
     for (int j0 = 0; j0 < kH; j0 += 8) {
         float h[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int j = j0 + e;
-            const float z = fmaf(W1[3 * j], x.x, fmaf(W1[3 * j + 1], x.y, fmaf(W1[3 * j + 2], x.z, b1[j])));
+            const float4 w = wb[j0 + e];
+            const float z = fmaf(w.x, x.x, fmaf(w.y, x.y, fmaf(w.z, x.z, w.w)));
             h[e] = (e & 3) == 0 ? silu_xu(z) : silu_fma(z);
         }
         store_bf16x8(H, r, j0, kH, h);
@@ -623,7 +641,7 @@ __device__ __forceinline__ bool pipe_network(int pipe, int r, const float* small
     phase ^= 1u;
     tc::fence_after_sync();
     if (!pipe_all(pipe, ok)) return false;
-    pipe_hidden(taddr, b2, H, r);
+    pipe_hidden(taddr, small + kEB2, H, r);
     pipe_sync_for_mma(pipe);
     if (r == 0) {
         mma_k128(d_tmem, KMAJ(aH), KMAJ(aW3), kN128KK);
@@ -633,21 +651,19 @@ __device__ __forceinline__ bool pipe_network(int pipe, int r, const float* small
     phase ^= 1u;
     tc::fence_after_sync();
     if (!pipe_all(pipe, ok)) return false;
-    float acc = small[384 + 4 * kH];
+    float acc = small[kEB4];
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 32) {
         float v[32];
         tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
-        for (int k = 0; k < 32; k += 8) {
-            acc = fmaf(w4[c0 + k + 0], silu_mix<0>(v[k + 0] + b3[c0 + k + 0]), acc);
-            acc = fmaf(w4[c0 + k + 1], silu_mix<1>(v[k + 1] + b3[c0 + k + 1]), acc);
-            acc = fmaf(w4[c0 + k + 2], silu_mix<2>(v[k + 2] + b3[c0 + k + 2]), acc);
-            acc = fmaf(w4[c0 + k + 3], silu_mix<3>(v[k + 3] + b3[c0 + k + 3]), acc);
-            acc = fmaf(w4[c0 + k + 4], silu_mix<4>(v[k + 4] + b3[c0 + k + 4]), acc);
-            acc = fmaf(w4[c0 + k + 5], silu_mix<5>(v[k + 5] + b3[c0 + k + 5]), acc);
-            acc = fmaf(w4[c0 + k + 6], silu_mix<6>(v[k + 6] + b3[c0 + k + 6]), acc);
-            acc = fmaf(w4[c0 + k + 7], silu_mix<7>(v[k + 7] + b3[c0 + k + 7]), acc);
+        for (int k = 0; k < 32; k += 4) {
+            const float4 b = *reinterpret_cast<const float4*>(b3 + c0 + k);
+            const float4 w = *reinterpret_cast<const float4*>(w4 + c0 + k);
+            acc = fmaf(w.x, silu_mix<0>(v[k + 0] + b.x), acc);
+            acc = fmaf(w.y, silu_mix<1>(v[k + 1] + b.y), acc);
+            acc = fmaf(w.z, silu_mix<2>(v[k + 2] + b.z), acc);
+            acc = fmaf(w.w, silu_mix<3>(v[k + 3] + b.w), acc);
         }
     }
     f = acc;
@@ -687,7 +703,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) mlp_eval_kernel(const __grid_
     const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH = tc::smem_u32(sH);
     uint32_t phase = 0;
     bool ok = true;
-    load_weights(A.master + (size_t)A.link0 * kPar, sW2, sW3, small, t, kEvalThreads);
+    load_weights<true>(A.master + (size_t)A.link0 * kPar, sW2, sW3, small, t, kEvalThreads);
     tc::fence_smem_to_async();   // the weights are MMA operands
     __syncthreads();
     for (int tl = first + pipe; tl < last; tl += kEvalPipes) {
@@ -896,7 +912,7 @@ static_assert(kImgBytes % 16 == 0, "16-byte copies");
 
 __global__ void __launch_bounds__(512) weight_image_kernel(const float* __restrict__ master, uint8_t* image) {
     uint8_t* img = image + (size_t)blockIdx.x * kImgBytes;
-    load_weights(master + (size_t)blockIdx.x * kPar, img, img + kTileBytes,
+    load_weights<true>(master + (size_t)blockIdx.x * kPar, img, img + kTileBytes,
                  reinterpret_cast<float*>(img + 2 * kTileBytes), threadIdx.x, blockDim.x);
 }
 
