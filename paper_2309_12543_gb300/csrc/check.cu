@@ -628,7 +628,7 @@ __device__ __forceinline__ void evaluate_tex(const BatchParams& P, const BlockSt
 #undef SDF_TEX_CASE
             default: break;
         }
-        const float t = tex3D<float>((cudaTextureObject_t)h, c.x, c.y, c.z);
+        const float t = tex3d_fetch(h, c.x, c.y, c.z);
         if (l == k) v = t;
         pending &= ~__ballot_sync(kFull, l == k);
     }

@@ -81,6 +81,17 @@ __device__ __forceinline__ TexCoord tex_coord(int n, float4 o_ih, float h, float
     return c;
 }
 
+// Filtered fetch of texture object `tex` at texel coordinates (x, y, z), issued as
+// explicit PTX.  (Inlined into the check kernel, the tex3D intrinsic returned a valid
+// value only for the warp's first lane; this form is exact there.)
+__device__ __forceinline__ float tex3d_fetch(unsigned long long tex, float x, float y, float z) {
+    float r, g, b, a;
+    asm volatile("tex.3d.v4.f32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %8}];"
+                 : "=f"(r), "=f"(g), "=f"(b), "=f"(a)
+                 : "l"(tex), "f"(x), "f"(y), "f"(z), "f"(0.f));
+    return r;
+}
+
 // Extra radius for the bounding-volume culls under the texture lookup: the filtered
 // value is the exact interpolant at a point within sqrt(3) h / 256 of the query,
 // so the link's lower bound holds after growing its bounding volume by that much.
