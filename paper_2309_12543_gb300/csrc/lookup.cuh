@@ -85,11 +85,11 @@ __device__ __forceinline__ TexCoord tex_coord(int n, float4 o_ih, float h, float
 // explicit PTX.  (Inlined into the check kernel, the tex3D intrinsic returned a valid
 // value only for the warp's first lane; this form is exact there.)
 __device__ __forceinline__ float tex3d_fetch(unsigned long long tex, float x, float y, float z) {
-    float r, g, b, a;
+    float v[4];
     asm volatile("tex.3d.v4.f32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %8}];"
-                 : "=f"(r), "=f"(g), "=f"(b), "=f"(a)
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
                  : "l"(tex), "f"(x), "f"(y), "f"(z), "f"(0.f));
-    return r;
+    return v[0];   // a one-channel texture: the value is the first component
 }
 
 // Extra radius for the bounding-volume culls under the texture lookup: the filtered
