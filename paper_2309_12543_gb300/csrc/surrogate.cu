@@ -972,6 +972,7 @@ struct SurFusedArgs {
     unsigned long long* keys;         // [W] packed keys, ~0 = none (set before the launch)
     uint8_t* recheck;                 // [W] 1 where a list overflowed (zeroed before the launch)
     int* work;                        // [L] items taken per link (zeroed before the launch)
+    int phase;                        // 0: the seed items of every link; 1: the cull items
     float slack;                      // error bound of the surrogate + rounding slack
     int* status;
     uint32_t wait_polls;
@@ -1198,7 +1199,9 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
     } else {
         // ----------------------------------------------------------------- producer
         const int pw = warp & 3, pt = r;
-        const int per_link = A.n_seed_groups + A.n_groups;
+        // one launch takes the seed items, a second one the cull items, so that every
+        // cull finds each link's seed minimum published
+        const int per_link = A.phase == 0 ? A.n_seed_groups : A.n_groups;
         int home = (int)(blockIdx.x % (unsigned)A.L);
         int loaded = -1;
         bool ok = true;
@@ -1214,9 +1217,9 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
             const int item = S.item, l = S.item_link;
             prod_sync();   // S.item is rewritten only after every producer thread has read it
             if (item < 0) break;
-            const bool seed = item < A.n_seed_groups;
+            const bool seed = A.phase == 0;
             const int gsz = seed ? kSurGroup : A.group;
-            const int g = seed ? item : item - A.n_seed_groups;
+            const int g = item;
             const int w0 = g * gsz, nw = min(gsz, A.W - w0);
             if (l != loaded) {
                 // finish the current tile, let the pipelines evaluate every tile, then
@@ -1341,6 +1344,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                     if (e0 >= n_list) break;
                     float4 p[kWsTake];
                     int jj[kWsTake];
+                    unsigned long long kk[kWsTake];
 #pragma unroll
                     for (int u = 0; u < kWsTake; ++u) {
                         const bool ve = e0 + u < n_list;
@@ -1348,12 +1352,16 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                         const int k = (int)(ent & 0xffffffu) * 32 + lane;
                         jj[u] = (ve && k < nv) ? (int)(ent >> 24) : -1;
                         p[u] = jj[u] >= 0 ? __ldg(&A.sorted[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        // the waypoint's minimum as it stands now (the pipelines keep lowering it)
+                        kk[u] = ve ? __ldcg(&A.keys[w0 + (int)(ent >> 24)]) : ~0ull;
                     }
 #pragma unroll
                     for (int u = 0; u < kWsTake; ++u) {
                         const int j = max(jj[u], 0);
+                        const float now = kk[u] == ~0ull ? INFINITY : from_ordered((unsigned)(kk[u] >> 32)) + A.slack + S.cA[j].w;
+                        const float thr = fminf(S.thr[j], now);
                         const bool take = jj[u] >= 0 &&
-                                          capsule_gap(make_float4(p[u].x, p[u].y, p[u].z, 0.f), S.cA[j], S.cD[j]) <= S.thr[j];
+                                          capsule_gap(make_float4(p[u].x, p[u].y, p[u].z, 0.f), S.cA[j], S.cD[j]) <= thr;
                         if (!__any_sync(0xffffffffu, take)) continue;
                         if (A.stats) n_cull += (unsigned)__popc(__ballot_sync(0xffffffffu, take));
                         const float4 q = make_query(A, l, S.M[j], p[u]);
@@ -1805,9 +1813,13 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
         A.stats = ctx->stats ? ctx->d_stats : nullptr;
     }
     delete bp;
-    if (rc == SDF_OK && e == cudaSuccess) {
-        sdf::sur_check_kernel<<<(unsigned)ctx->num_sms, sdf::kEvalThreads, sdf::kSurSmem, st>>>(A);
-        e = cudaGetLastError();
+    for (int ph = 0; ph < 2 && rc == SDF_OK && e == cudaSuccess; ++ph) {   // seeds, then culls
+        A.phase = ph;
+        if (ph == 1) e = cudaMemsetAsync(ctx->sur_count, 0, sizeof(int) * SDF_MAX_LINKS, st);
+        if (e == cudaSuccess) {
+            sdf::sur_check_kernel<<<(unsigned)ctx->num_sms, sdf::kEvalThreads, sdf::kSurSmem, st>>>(A);
+            e = cudaGetLastError();
+        }
     }
     if (rc == SDF_OK && e == cudaSuccess) {
         sdf::sur_finish_kernel<<<(unsigned)((W + 255) / 256), 256, 0, st>>>(
