@@ -1035,28 +1035,51 @@ __device__ __forceinline__ bool wait_at_least(const int* p, int target, WsShared
 // Named barrier of the producer warpgroup (id 5; the pipelines use 1-3).
 __device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 5, 128;" ::: "memory"); }
 
-// Warp-cooperative: the lanes with `take` write their query and tag to the ring.
-// Returns false if a wait for a free slot gave up.
-__device__ __forceinline__ bool ws_emit(WsShared& S, float4* ring_q, uint2* ring_t, bool take, float4 q, uint2 tg,
-                                        int lane) {
-    const unsigned b = __ballot_sync(0xffffffffu, take);
-    if (!b) return true;
+// Warp-cooperative: the queries of K entries (lane i holds entry u's point i: take[u],
+// q[u], tg[u]) go to the ring with one reservation.  Lane 0 waits until the slots of
+// the reserved range are free (their previous tiles evaluated), the lanes write, and
+// lane 0 adds each tile's count to its slot once the writes are done.  Returns false
+// if a wait gave up.
+template <int K>
+__device__ __forceinline__ bool ws_emit(WsShared& S, float4* ring_q, uint2* ring_t, const bool (&take)[K],
+                                        const float4 (&q)[K], const uint2 (&tg)[K], int lane) {
+    unsigned b[K];
+    int cnt = 0;
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        b[u] = __ballot_sync(0xffffffffu, take[u]);
+        cnt += __popc(b[u]);
+    }
+    if (!cnt) return true;
     int base = 0;
-    if (lane == 0) base = atomicAdd(&S.reserved, __popc(b));
-    base = __shfl_sync(0xffffffffu, base, 0);
     bool ok = true;
-    if (take) {
-        const int pos = base + __popc(b & ((1u << lane) - 1u));
-        const int tile = pos >> 7, slot = tile % kWsSlots, gen = tile / kWsSlots;
-        ok = wait_at_least(&S.consumed[slot], gen, S);   // the slot's previous tile is evaluated
-        if (ok) {
-            ring_q[slot * 128 + (pos & 127)] = q;
-            ring_t[slot * 128 + (pos & 127)] = tg;
-            __threadfence_block();
-            atomicAdd(&S.written[slot], 1);
+    if (lane == 0) {
+        base = atomicAdd(&S.reserved, cnt);
+        for (int tile = base >> 7; tile <= (base + cnt - 1) >> 7 && ok; ++tile)
+            ok = wait_at_least(&S.consumed[tile % kWsSlots], tile / kWsSlots, S);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+    int pos = base;
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        if (take[u]) {
+            const int at = pos + __popc(b[u] & ((1u << lane) - 1u));
+            const int slot = (at >> 7) % kWsSlots;
+            ring_q[slot * 128 + (at & 127)] = q[u];
+            ring_t[slot * 128 + (at & 127)] = tg[u];
+        }
+        pos += __popc(b[u]);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence_block();
+        for (int tile = base >> 7; tile <= (base + cnt - 1) >> 7; ++tile) {
+            const int lo = max(base, tile << 7), hi = min(base + cnt, (tile + 1) << 7);
+            atomicAdd(&S.written[tile % kWsSlots], hi - lo);
         }
     }
-    return __all_sync(0xffffffffu, ok);
+    return true;
 }
 
 // Producer warpgroup: the positions from S.reserved to the next multiple of 128 get
@@ -1274,41 +1297,73 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
             }
             prod_sync();
             if (seed) {
-                // per waypoint, the 32 points of the tile nearest to the capsule
-                for (int j = pw; j < nw && ok; j += 4) {
-                    if (nv == 0) break;
-                    const float4 cA = S.cA[j], cD = S.cD[j];
-                    float best = INFINITY;
-                    int bi = 0x7fffffff;
-                    for (int s = lane; s < n_sup; s += 32) {
-                        const float gp = capsule_gap(__ldg(&A.supers[s]), cA, cD);
-                        if (gp < best) { best = gp; bi = s; }
+                // per waypoint, the 32 points of the tile nearest to the capsule; warp pw
+                // serves waypoint slots pw, pw + 4, pw + 8, pw + 12 together (their loads
+                // go out together)
+                constexpr int kSeedPer = kSurGroup / 4;
+                bool live[kSeedPer];
+                float4 cA[kSeedPer], cD[kSeedPer];
+                float best[kSeedPer];
+                int bi[kSeedPer];
+#pragma unroll
+                for (int u = 0; u < kSeedPer; ++u) {
+                    const int j = pw + 4 * u;
+                    live[u] = j < nw && nv > 0;
+                    cA[u] = live[u] ? S.cA[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    cD[u] = live[u] ? S.cD[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    best[u] = INFINITY;
+                    bi[u] = 0x7fffffff;
+                }
+                for (int sidx = lane; sidx < n_sup; sidx += 32) {
+                    const float4 sp = __ldg(&A.supers[sidx]);
+#pragma unroll
+                    for (int u = 0; u < kSeedPer; ++u) {
+                        const float gp = capsule_gap(sp, cA[u], cD[u]);
+                        if (gp < best[u]) { best[u] = gp; bi[u] = sidx; }
                     }
+                }
+                float4 tsph[kSeedPer];
+#pragma unroll
+                for (int u = 0; u < kSeedPer; ++u) {
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
-                        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                        if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                        const float ob = __shfl_xor_sync(0xffffffffu, best[u], o);
+                        const int oi = __shfl_xor_sync(0xffffffffu, bi[u], o);
+                        if (ob < best[u] || (ob == best[u] && oi < bi[u])) { best[u] = ob; bi[u] = oi; }
                     }
-                    if (bi >= n_sup) continue;
-                    const int tt = bi * 32 + lane;
+                    if (bi[u] >= n_sup) live[u] = false;
+                    const int tt = live[u] ? bi[u] * 32 + lane : n_tiles;
+                    tsph[u] = tt < n_tiles ? __ldg(&A.tiles[tt]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    bi[u] = tt;
+                }
+                int ti[kSeedPer];
+#pragma unroll
+                for (int u = 0; u < kSeedPer; ++u) {
                     float tb = INFINITY;
-                    int ti = 0x7fffffff;
-                    if (tt < n_tiles) { tb = capsule_gap(__ldg(&A.tiles[tt]), cA, cD); ti = tt; }
+                    int tix = 0x7fffffff;
+                    if (bi[u] < n_tiles) { tb = capsule_gap(tsph[u], cA[u], cD[u]); tix = bi[u]; }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         const float ob = __shfl_xor_sync(0xffffffffu, tb, o);
-                        const int oi = __shfl_xor_sync(0xffffffffu, ti, o);
-                        if (ob < tb || (ob == tb && oi < ti)) { tb = ob; ti = oi; }
+                        const int oi = __shfl_xor_sync(0xffffffffu, tix, o);
+                        if (ob < tb || (ob == tb && oi < tix)) { tb = ob; tix = oi; }
                     }
-                    const int k = ti * 32 + lane;
-                    const bool take = ti < n_tiles && k < nv;
-                    const float4 p = take ? __ldg(&A.sorted[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float4 q = make_query(A, l, S.M[j], p);
-                    const uint2 tg = make_uint2((unsigned)(w0 + j), ((unsigned)__float_as_int(p.w) << 4) | (unsigned)l);
-                    if (A.stats) n_seed += (unsigned)__popc(__ballot_sync(0xffffffffu, take));
-                    ok = ws_emit(S, ring_q, ring_t, take, q, tg, lane);
+                    ti[u] = tix;
                 }
+                bool take[kSeedPer];
+                float4 q[kSeedPer];
+                uint2 tg[kSeedPer];
+#pragma unroll
+                for (int u = 0; u < kSeedPer; ++u) {
+                    const int j = pw + 4 * u;
+                    const int k = ti[u] * 32 + lane;
+                    take[u] = live[u] && ti[u] < n_tiles && k < nv;
+                    const float4 pnt = take[u] ? __ldg(&A.sorted[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    q[u] = take[u] ? make_query(A, l, S.M[j], pnt) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    tg[u] = make_uint2((unsigned)(w0 + j), ((unsigned)__float_as_int(pnt.w) << 4) | (unsigned)l);
+                    if (A.stats) n_seed += (unsigned)__popc(__ballot_sync(0xffffffffu, take[u]));
+                }
+                ok = ws_emit<kSeedPer>(S, ring_q, ring_t, take, q, tg, lane);
             } else {
                 // list: (waypoint slot, tile) entries whose tile sphere reaches the threshold
                 for (int j = pw; j < nw; j += 4) {
@@ -1355,20 +1410,21 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                         // the waypoint's minimum as it stands now (the pipelines keep lowering it)
                         kk[u] = ve ? __ldcg(&A.keys[w0 + (int)(ent >> 24)]) : ~0ull;
                     }
+                    bool take[kWsTake];
+                    float4 q[kWsTake];
+                    uint2 tg[kWsTake];
 #pragma unroll
                     for (int u = 0; u < kWsTake; ++u) {
                         const int j = max(jj[u], 0);
                         const float now = kk[u] == ~0ull ? INFINITY : from_ordered((unsigned)(kk[u] >> 32)) + A.slack + S.cA[j].w;
                         const float thr = fminf(S.thr[j], now);
-                        const bool take = jj[u] >= 0 &&
-                                          capsule_gap(make_float4(p[u].x, p[u].y, p[u].z, 0.f), S.cA[j], S.cD[j]) <= thr;
-                        if (!__any_sync(0xffffffffu, take)) continue;
-                        if (A.stats) n_cull += (unsigned)__popc(__ballot_sync(0xffffffffu, take));
-                        const float4 q = make_query(A, l, S.M[j], p[u]);
-                        const uint2 tg =
-                            make_uint2((unsigned)(w0 + j), ((unsigned)__float_as_int(p[u].w) << 4) | (unsigned)l);
-                        if (!(ok = ws_emit(S, ring_q, ring_t, take, q, tg, lane))) break;
+                        take[u] = jj[u] >= 0 &&
+                                  capsule_gap(make_float4(p[u].x, p[u].y, p[u].z, 0.f), S.cA[j], S.cD[j]) <= thr;
+                        q[u] = take[u] ? make_query(A, l, S.M[j], p[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        tg[u] = make_uint2((unsigned)(w0 + j), ((unsigned)__float_as_int(p[u].w) << 4) | (unsigned)l);
+                        if (A.stats) n_cull += (unsigned)__popc(__ballot_sync(0xffffffffu, take[u]));
                     }
+                    ok = ws_emit<kWsTake>(S, ring_q, ring_t, take, q, tg, lane);
                 }
             }
             if (!ok) {
