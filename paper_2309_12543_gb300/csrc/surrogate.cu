@@ -925,30 +925,32 @@ __device__ __forceinline__ void load_image(const uint8_t* __restrict__ img, uint
 }
 
 // The check with the network in place of the grid lookup, in one persistent kernel
-// whose warps are specialised: warpgroup 3 produces queries, warpgroups 0-2 are
-// evaluation pipelines that consume them, and a ring of kWsSlots tiles of 128 queries
-// in shared memory sits between them.
-//   producer: takes work items -- first a seed item, then the cull items, of its CTA's
-//     link (a CTA stays on one link while that link has items, so that the weights in
-//     shared memory rarely change; when its link is done it moves to the link with the
-//     most items left).  A seed item of kSurGroup waypoints takes, per waypoint, the 32
-//     points of the tile nearest to the link's bounding capsule (nearest super-tile
-//     first).  A cull item culls super-tiles and tiles against the capsule with the
-//     waypoint's minimum so far over every link (read from global memory) plus the
-//     surrogate's error bound, into a (waypoint, tile) list, then tests the points of
-//     the listed tiles, kWsTake entries per warp step with their loads together.
-//     Surviving points become queries written to the ring: positions are reserved
-//     with one shared counter, a position waits until its slot's previous tile has
-//     been consumed, and each write is counted per slot.
-//   consumers: pipeline p evaluates tiles p, p + 3, ... of the ring as their slots
-//     fill, and folds each value into the waypoint's packed key in global memory.
+// whose warps are specialised: warpgroups 2 and 3 produce queries, warpgroups 0 and 1
+// are evaluation pipelines that consume them, and a ring of kWsSlots tiles of 128
+// queries in shared memory sits between them.  It runs twice per check, first over
+// the seed items of every link, then over the cull items, so that every cull finds
+// each link's seed minimum published.
+//   producer: takes work items of its CTA's link (a CTA stays on one link while that
+//     link has items, so that the weights in shared memory rarely change; when its
+//     link is done it moves to the link with the most items left).  A seed item of
+//     kSurGroup waypoints takes, per waypoint, the 32 points of the tile nearest to the
+//     link's bounding capsule (nearest super-tile first).  A cull item culls
+//     super-tiles and tiles against the capsule with the waypoint's minimum so far over
+//     every link (read from global memory, again at every step) plus the surrogate's
+//     error bound, into a (waypoint, tile) list, then tests the points of the listed
+//     tiles, kWsTake entries per warp step with their loads together.  Surviving points
+//     become queries written to the ring: one reservation per step, a wait until the
+//     slots' previous tiles have been consumed, one count per tile.
+//   consumers: pipeline p evaluates tiles p, p + kWsPipes, ... of the ring as their
+//     slots fill, and folds each value into the waypoint's packed key in global memory.
 // When the producer changes link it pads the current tile, waits until every tile is
 // consumed and copies the new link's weights.  Every wait is bounded.
 constexpr int kSurGroup = 16;      // waypoints per seed item, and the most per cull item
-constexpr int kWsPipes = 3;        // evaluation pipelines (warpgroups 0-2)
-constexpr int kWsSlots = 16;       // ring tiles of 128 queries
+constexpr int kWsPipes = 2;        // evaluation pipelines (warpgroups 0-1)
+constexpr int kProdWarps = 16 - 4 * kWsPipes;   // producer warps (the other warpgroups)
+constexpr int kWsSlots = 24;       // ring tiles of 128 queries
 constexpr int kWsTake = 8;         // list entries a producer warp takes per step
-constexpr int kWsList = 512;       // (waypoint, tile) entries of one cull item
+constexpr int kWsList = 1024;      // (waypoint, tile) entries of one cull item
 constexpr int kWsH = kImgBytes;                                   // activation tiles of the pipelines
 constexpr int kWsQ = kWsH + kWsPipes * kTileBytes;                // ring: queries (float4)
 constexpr int kWsT = kWsQ + kWsSlots * 128 * 16;                  // ring: tags (uint2)
@@ -1032,8 +1034,8 @@ __device__ __forceinline__ bool wait_at_least(const int* p, int target, WsShared
     return false;
 }
 
-// Named barrier of the producer warpgroup (id 5; the pipelines use 1-3).
-__device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 5, 128;" ::: "memory"); }
+// Named barrier of the producer warps (id 5; the pipelines use 1-2).
+__device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 5, %0;" ::"n"(32 * kProdWarps) : "memory"); }
 
 // Warp-cooperative: the queries of K entries (lane i holds entry u's point i: take[u],
 // q[u], tg[u]) go to the ring with one reservation.  Lane 0 waits until the slots of
@@ -1142,7 +1144,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
     uint2* ring_t = reinterpret_cast<uint2*>(sm + kWsT);
     uint32_t* s_list = reinterpret_cast<uint32_t*>(sm + kWsL);
 
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 128 * kWsPipes);
     if (t < kWsPipes) tc::mbar_init(&mbar[t], 1);
     if (t < kWsSlots) {
         S.written[t] = 0;
@@ -1221,7 +1223,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
         if (!ok) tc::mbar_wait(&mbar[pipe], phase ^ 1u, kWaitPolls);   // the MMA in flight ends first
     } else {
         // ----------------------------------------------------------------- producer
-        const int pw = warp & 3, pt = r;
+        const int pw = warp - 4 * kWsPipes, pt = t - 128 * kWsPipes;
         // one launch takes the seed items, a second one the cull items, so that every
         // cull finds each link's seed minimum published
         const int per_link = A.phase == 0 ? A.n_seed_groups : A.n_groups;
@@ -1257,14 +1259,14 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 }
                 prod_sync();
                 if (vload(&S.abort)) break;
-                load_image(A.image + (size_t)l * kImgBytes, sm, pt, 128);
+                load_image(A.image + (size_t)l * kImgBytes, sm, pt, 32 * kProdWarps);
                 tc::fence_smem_to_async();   // the weights are MMA operands
                 __threadfence_block();
                 loaded = l;
                 prod_sync();
             }
             // the group's poses, world capsules and thresholds for link l
-            for (int j = pw; j < nw; j += 4) {
+            for (int j = pw; j < nw; j += kProdWarps) {
                 const float4* P = reinterpret_cast<const float4*>(A.poses + ((size_t)(w0 + j) * A.L + l) * 16);
                 const float4 M0 = P[0], M1 = P[1], M2 = P[2];
                 if (lane == 0) {
@@ -1298,16 +1300,16 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
             prod_sync();
             if (seed) {
                 // per waypoint, the 32 points of the tile nearest to the capsule; warp pw
-                // serves waypoint slots pw, pw + 4, pw + 8, pw + 12 together (their loads
-                // go out together)
-                constexpr int kSeedPer = kSurGroup / 4;
+                // serves waypoint slots pw, pw + kProdWarps, ... together (their loads go
+                // out together)
+                constexpr int kSeedPer = kSurGroup / kProdWarps;
                 bool live[kSeedPer];
                 float4 cA[kSeedPer], cD[kSeedPer];
                 float best[kSeedPer];
                 int bi[kSeedPer];
 #pragma unroll
                 for (int u = 0; u < kSeedPer; ++u) {
-                    const int j = pw + 4 * u;
+                    const int j = pw + kProdWarps * u;
                     live[u] = j < nw && nv > 0;
                     cA[u] = live[u] ? S.cA[j] : make_float4(0.f, 0.f, 0.f, 0.f);
                     cD[u] = live[u] ? S.cD[j] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1355,7 +1357,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 uint2 tg[kSeedPer];
 #pragma unroll
                 for (int u = 0; u < kSeedPer; ++u) {
-                    const int j = pw + 4 * u;
+                    const int j = pw + kProdWarps * u;
                     const int k = ti[u] * 32 + lane;
                     take[u] = live[u] && ti[u] < n_tiles && k < nv;
                     const float4 pnt = take[u] ? __ldg(&A.sorted[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1365,8 +1367,10 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 }
                 ok = ws_emit<kSeedPer>(S, ring_q, ring_t, take, q, tg, lane);
             } else {
-                // list: (waypoint slot, tile) entries whose tile sphere reaches the threshold
-                for (int j = pw; j < nw; j += 4) {
+                // list: (waypoint slot, tile) entries whose tile sphere reaches the threshold;
+                // the tiles of up to four surviving super-tiles are tested per round (their
+                // loads go out together)
+                for (int j = pw; j < nw; j += kProdWarps) {
                     const float4 cA = S.cA[j], cD = S.cD[j];
                     const float thr = S.thr[j];
                     for (int s0 = 0; s0 < n_sup; s0 += 32) {
@@ -1374,18 +1378,29 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                         unsigned bs = __ballot_sync(0xffffffffu,
                                                     sidx < n_sup && capsule_gap(__ldg(&A.supers[sidx]), cA, cD) <= thr);
                         while (bs) {
-                            const int sv = s0 + __ffs(bs) - 1;
-                            bs &= bs - 1;
-                            const int tt = sv * 32 + lane;
-                            const bool reach = tt < n_tiles && capsule_gap(__ldg(&A.tiles[tt]), cA, cD) <= thr;
-                            const unsigned bt = __ballot_sync(0xffffffffu, reach);
-                            if (!bt) continue;
-                            int base = 0;
-                            if (lane == 0) base = atomicAdd(&S.list_n, __popc(bt));
-                            base = __shfl_sync(0xffffffffu, base, 0);
-                            const int slot = base + __popc(bt & ((1u << lane) - 1u));
-                            if (reach && slot < kWsList) s_list[slot] = ((unsigned)j << 24) | (unsigned)tt;
-                            if (base + __popc(bt) > kWsList && lane == 0) atomicOr(&S.over, 1u << j);
+                            int tt[4];
+                            float4 sp[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                tt[u] = n_tiles;
+                                if (bs) {
+                                    tt[u] = (s0 + __ffs(bs) - 1) * 32 + lane;
+                                    bs &= bs - 1;
+                                }
+                                sp[u] = tt[u] < n_tiles ? __ldg(&A.tiles[tt[u]]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const bool reach = tt[u] < n_tiles && capsule_gap(sp[u], cA, cD) <= thr;
+                                const unsigned bt = __ballot_sync(0xffffffffu, reach);
+                                if (!bt) continue;
+                                int base = 0;
+                                if (lane == 0) base = atomicAdd(&S.list_n, __popc(bt));
+                                base = __shfl_sync(0xffffffffu, base, 0);
+                                const int slot = base + __popc(bt & ((1u << lane) - 1u));
+                                if (reach && slot < kWsList) s_list[slot] = ((unsigned)j << 24) | (unsigned)tt[u];
+                                if (base + __popc(bt) > kWsList && lane == 0) atomicOr(&S.over, 1u << j);
+                            }
                         }
                     }
                 }
@@ -1448,7 +1463,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_free(tm, 512);
+    if (warp == 0) tc::tmem_free(tm, 128 * kWsPipes);
 }
 
 // Per waypoint: decode the surrogate minimum, write it as the result, and select the
