@@ -924,46 +924,42 @@ __device__ __forceinline__ void load_image(const uint8_t* __restrict__ img, uint
     for (int i = t; i < kVec; i += nthreads) dst[i] = __ldg(src + i);
 }
 
-// The check with the network in place of the grid lookup, in one persistent kernel
-// whose warps are specialised: warpgroups 2 and 3 produce queries, warpgroups 0 and 1
-// are evaluation pipelines that consume them, and a ring of kWsSlots tiles of 128
-// queries in shared memory sits between them.  It runs twice per check, first over
-// the seed items of every link, then over the cull items, so that every cull finds
-// each link's seed minimum published.
-//   producer: takes work items of its CTA's link (a CTA stays on one link while that
-//     link has items, so that the weights in shared memory rarely change; when its
-//     link is done it moves to the link with the most items left).  A seed item of
-//     kSurGroup waypoints takes, per waypoint, the 32 points of the tile nearest to the
-//     link's bounding capsule (nearest super-tile first).  A cull item culls
-//     super-tiles and tiles against the capsule with the waypoint's minimum so far over
-//     every link (read from global memory, again at every step) plus the surrogate's
-//     error bound, into a (waypoint, tile) list, then tests the points of the listed
-//     tiles, kWsTake entries per warp step with their loads together.  Surviving points
-//     become queries written to the ring: one reservation per step, a wait until the
-//     slots' previous tiles have been consumed, one count per tile.
-//   consumers: pipeline p evaluates tiles p, p + kWsPipes, ... of the ring as their
-//     slots fill, and folds each value into the waypoint's packed key in global memory.
-// When the producer changes link it pads the current tile, waits until every tile is
-// consumed and copies the new link's weights.  Every wait is bounded.
-constexpr int kSurGroup = 16;      // waypoints per seed item, and the most per cull item
-constexpr int kWsPipes = 2;        // evaluation pipelines (warpgroups 0-1)
-constexpr int kProdWarps = 16 - 4 * kWsPipes;   // producer warps (the other warpgroups)
-constexpr int kWsSlots = 24;       // ring tiles of 128 queries
-constexpr int kWsTake = 8;         // list entries a producer warp takes per step
-constexpr int kWsList = 1024;      // (waypoint, tile) entries of one cull item
-constexpr int kWsH = kImgBytes;                                   // activation tiles of the pipelines
-constexpr int kWsQ = kWsH + kWsPipes * kTileBytes;                // ring: queries (float4)
-constexpr int kWsT = kWsQ + kWsSlots * 128 * 16;                  // ring: tags (uint2)
-constexpr int kWsL = kWsT + kWsSlots * 128 * 8;                   // list entries
-constexpr int kSurSmem = kWsL + kWsList * 4;
-static_assert(kSurSmem + 3072 <= 232448, "dynamic + static shared memory of the fused check within 227 KB");
+// The check with the network in place of the grid lookup, in one persistent kernel.
+// Work items, taken in order from a counter: first a seed item per (link, group of
+// kSurGroup waypoints), then a cull item per (link, group), link-major, so that a CTA
+// reloads its weights only when the link changes and the cull items find every
+// link's seed minimum already published.
+//   seed: one warp per waypoint picks the tile nearest to the link's bounding capsule
+//     (nearest super-tile first) and its 32 points become queries;
+//   cull: with the waypoint's minimum so far (over all links) plus the surrogate's
+//     error bound as the threshold, one warp per waypoint culls super-tiles and tiles
+//     against the capsule into a (waypoint, tile) list in shared memory; then every
+//     warp takes list entries, tests the tile's points against the capsule and
+//     appends the survivors to a query ring in shared memory.
+// Whenever the ring holds 3 tiles of 128 queries (or the list is done) the four
+// warpgroup pipelines evaluate its whole tiles on the tensor cores, fold each value into the
+// waypoint's packed key (ordered distance, point, link) and tighten the thresholds.
+// A waypoint whose list overflowed is marked for the grid re-check, which decides it
+// exactly.
+constexpr int kSurGroup = 16;      // waypoints per work item: one warp each in the culls
+constexpr int kSurTake = 2;        // list entries a warp takes per step of the production
+constexpr int kSurFill = 3 * 128;  // the production stops once the ring holds this many queries
+constexpr int kSurRing = kSurFill + 16 * 32 * kSurTake;   // + what 16 warps may add past it
+constexpr int kSurList = 384;      // (waypoint, tile) entries of one cull item
+// shared memory of the fused kernel: the link's image (W2, W3, small parameters), the
+// pipelines' activation tiles, the query ring (points, tags) and the entry list
+constexpr int kSurImg = 0;
+constexpr int kSurH = kImgBytes;
+constexpr int kSurQ = kSurH + kEvalPipes * kTileBytes;
+constexpr int kSurTag = kSurQ + kSurRing * 16;
+constexpr int kSurLst = kSurTag + kSurRing * 4;
+constexpr int kSurSmem = kSurLst + kSurList * 4;
+static_assert(kSurSmem + 2048 <= 232448, "dynamic + static shared memory of the fused check within 227 KB");
 constexpr uint32_t kNoTag = 0xffffffffu;
-constexpr uint32_t kWsPollLimit = 1u << 24;   // polls of a ring wait (with a short sleep each)
 
 struct SurFusedArgs {
     const float* poses;               // [W][L][16]: link-from-world 3x4, sphere centre (world), radius
-    int W, L, group, n_groups;        // waypoints per cull item (<= kSurGroup), ceil(W / group)
-    int n_seed_groups;                // ceil(W / kSurGroup)
+    int W, L, group, n_groups;        // waypoints per work item (<= kSurGroup), ceil(W / group)
     const float4* sorted;             // the sorted cloud (x, y, z, original index bits)
     const float4* tiles;              // sphere per 32 sorted points
     const float4* supers;             // sphere per 32 tiles
@@ -971,10 +967,10 @@ struct SurFusedArgs {
     float lo[kMaxLinks][3], hi[kMaxLinks][3], m[kMaxLinks][3], inv_a[kMaxLinks], scale[kMaxLinks];
     float4 cap_a[kMaxLinks], cap_b[kMaxLinks];   // bounding capsules (link frame), radius in cap_a.w
     const uint8_t* image;             // [L][kImgBytes] weights as held in shared memory
+    int seed_group;                   // waypoints per seed item (16: four full tiles)
     unsigned long long* keys;         // [W] packed keys, ~0 = none (set before the launch)
     uint8_t* recheck;                 // [W] 1 where a list overflowed (zeroed before the launch)
-    int* work;                        // [L] items taken per link (zeroed before the launch)
-    int phase;                        // 0: the seed items of every link; 1: the cull items
+    int* work;                        // item counter (zeroed before the launch)
     float slack;                      // error bound of the surrogate + rounding slack
     int* status;
     uint32_t wait_polls;
@@ -990,9 +986,9 @@ __device__ __forceinline__ float capsule_gap(float4 s, float4 A, float4 D) {
     return sqrtf(fmaf(qx, qx, fmaf(qy, qy, qz * qz))) - s.w;
 }
 
-// The network's input for sorted point p in the frame given by the rows M: the
-// link-frame point clamped to the grid box and normalised to it (xyz), and the
-// distance to the box added outside it (w).
+// The network's input for sorted point p of waypoint slot j: the link-frame point
+// clamped to the grid box and normalised to it (xyz), and the distance to the box
+// added outside it (w).
 __device__ __forceinline__ float4 make_query(const SurFusedArgs& A, int l, const float4* M, float4 p) {
     const float lx = fmaf(M[0].x, p.x, fmaf(M[0].y, p.y, fmaf(M[0].z, p.z, M[0].w)));
     const float ly = fmaf(M[1].x, p.x, fmaf(M[1].y, p.y, fmaf(M[1].z, p.z, M[1].w)));
@@ -1006,464 +1002,302 @@ __device__ __forceinline__ float4 make_query(const SurFusedArgs& A, int l, const
                        sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez))));
 }
 
-// Shared state of the ring and the producer.
-struct WsShared {
-    int written[kWsSlots];            // queries written into each slot, over all its tiles
-    int consumed[kWsSlots];           // tiles of each slot evaluated
-    int tiles_done;                   // tiles evaluated
-    int reserved;                     // ring positions reserved by the producer
-    int final_pos;                    // -1 while producing; then the (tile-aligned) end of the ring
-    int abort;                        // a bounded wait gave up: everyone leaves
-    int item, item_link;              // the producer's current item
-    int list_n, list_next;
-    unsigned over;                    // cull item: waypoint slots whose list overflowed
-    float4 M[kSurGroup][3];           // link-from-world rows of each waypoint's link pose
-    float4 cA[kSurGroup], cD[kSurGroup];   // world capsule: start (+radius), axis (+1/len^2)
-    float thr[kSurGroup];
-};
-
-__device__ __forceinline__ int vload(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
-
-// Bounded spin until *p >= target (or the ring is aborted).  Returns false on give-up.
-__device__ __forceinline__ bool wait_at_least(const int* p, int target, WsShared& S) {
-    for (uint32_t i = 0; i < kWsPollLimit; ++i) {
-        if (vload(p) >= target) return true;
-        if (vload(&S.abort)) return false;
-        __nanosleep(64);
-    }
-    return false;
-}
-
-// Named barrier of the producer warps (id 5; the pipelines use 1-2).
-__device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 5, %0;" ::"n"(32 * kProdWarps) : "memory"); }
-
-// Warp-cooperative: the queries of K entries (lane i holds entry u's point i: take[u],
-// q[u], tg[u]) go to the ring with one reservation.  Lane 0 waits until the slots of
-// the reserved range are free (their previous tiles evaluated), the lanes write, and
-// lane 0 adds each tile's count to its slot once the writes are done.  Returns false
-// if a wait gave up.
-template <int K>
-__device__ __forceinline__ bool ws_emit(WsShared& S, float4* ring_q, uint2* ring_t, const bool (&take)[K],
-                                        const float4 (&q)[K], const uint2 (&tg)[K], int lane) {
-    unsigned b[K];
-    int cnt = 0;
-#pragma unroll
-    for (int u = 0; u < K; ++u) {
-        b[u] = __ballot_sync(0xffffffffu, take[u]);
-        cnt += __popc(b[u]);
-    }
-    if (!cnt) return true;
-    int base = 0;
-    bool ok = true;
-    if (lane == 0) {
-        base = atomicAdd(&S.reserved, cnt);
-        for (int tile = base >> 7; tile <= (base + cnt - 1) >> 7 && ok; ++tile)
-            ok = wait_at_least(&S.consumed[tile % kWsSlots], tile / kWsSlots, S);
-    }
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
-    int pos = base;
-#pragma unroll
-    for (int u = 0; u < K; ++u) {
-        if (take[u]) {
-            const int at = pos + __popc(b[u] & ((1u << lane) - 1u));
-            const int slot = (at >> 7) % kWsSlots;
-            ring_q[slot * 128 + (at & 127)] = q[u];
-            ring_t[slot * 128 + (at & 127)] = tg[u];
-        }
-        pos += __popc(b[u]);
-    }
-    __syncwarp();
-    if (lane == 0) {
-        __threadfence_block();
-        for (int tile = base >> 7; tile <= (base + cnt - 1) >> 7; ++tile) {
-            const int lo = max(base, tile << 7), hi = min(base + cnt, (tile + 1) << 7);
-            atomicAdd(&S.written[tile % kWsSlots], hi - lo);
-        }
-    }
-    return true;
-}
-
-// Producer warpgroup: the positions from S.reserved to the next multiple of 128 get
-// empty queries, so that the current tile completes.  Returns false on give-up.
-__device__ __forceinline__ bool ws_pad(WsShared& S, float4* ring_q, uint2* ring_t, int pt) {
-    prod_sync();
-    const int p0 = vload(&S.reserved);
-    const int p1 = (p0 + 127) & ~127;
-    bool ok = true;
-    if (pt < p1 - p0) {
-        const int pos = p0 + pt;
-        const int tile = pos >> 7, slot = tile % kWsSlots, gen = tile / kWsSlots;
-        ok = wait_at_least(&S.consumed[slot], gen, S);
-        if (ok) {
-            ring_q[slot * 128 + (pos & 127)] = make_float4(0.f, 0.f, 0.f, 0.f);
-            ring_t[slot * 128 + (pos & 127)] = make_uint2(kNoTag, kNoTag);
-            __threadfence_block();
-            atomicAdd(&S.written[slot], 1);
-        }
-    }
-    prod_sync();
-    if (pt == 0) S.reserved = p1;
-    prod_sync();
-    return ok;
-}
-
-// The next item of link `home` (an index within the link: seed groups first, then
-// cull groups), moving to the link with the most items left when `home` has none.
-// Returns -1 when every link is done.
-__device__ __forceinline__ int ws_pick(const SurFusedArgs& A, int& home, int per_link) {
-    for (int round = 0; round <= A.L; ++round) {
-        const int i = atomicAdd(&A.work[home], 1);
-        if (i < per_link) return i;
-        int best = -1, left_best = 0;
-        for (int l = 0; l < A.L; ++l) {
-            const int left = per_link - __ldcg(&A.work[l]);
-            if (left > left_best) {
-                left_best = left;
-                best = l;
-            }
-        }
-        if (best < 0) return -1;
-        home = best;
-    }
-    return -1;
-}
-
 __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid_constant__ SurFusedArgs A) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ uint64_t mbar[kWsPipes];
+    __shared__ uint64_t mbar[kEvalPipes];
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_cmd[kWsPipes];
-    __shared__ WsShared S;
+    __shared__ float4 s_M[kSurGroup][3];           // link-from-world rows of each waypoint's link pose
+    __shared__ float4 s_cA[kSurGroup], s_cD[kSurGroup];   // world capsule: start (+radius), axis (+1/len^2)
+    __shared__ unsigned long long s_key[kSurGroup];
+    __shared__ float s_thr[kSurGroup];
+    __shared__ int s_item, s_qn, s_ln, s_lnext, s_fail;
+    __shared__ unsigned s_over;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int wg = warp >> 2, r = t & 127;
-    uint8_t* sW2 = sm;
-    uint8_t* sW3 = sm + kTileBytes;
-    float* small = reinterpret_cast<float*>(sm + 2 * kTileBytes);
-    float4* ring_q = reinterpret_cast<float4*>(sm + kWsQ);
-    uint2* ring_t = reinterpret_cast<uint2*>(sm + kWsT);
-    uint32_t* s_list = reinterpret_cast<uint32_t*>(sm + kWsL);
+    const int pipe = warp >> 2, r = t & 127;
+    uint8_t* sW2 = sm + kSurImg;
+    uint8_t* sW3 = sm + kSurImg + kTileBytes;
+    float* small = reinterpret_cast<float*>(sm + kSurImg + 2 * kTileBytes);
+    uint8_t* sH = sm + kSurH + pipe * kTileBytes;
+    float4* s_q = reinterpret_cast<float4*>(sm + kSurQ);
+    uint32_t* s_tag = reinterpret_cast<uint32_t*>(sm + kSurTag);
+    uint32_t* s_list = reinterpret_cast<uint32_t*>(sm + kSurLst);
 
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, 128 * kWsPipes);
-    if (t < kWsPipes) tc::mbar_init(&mbar[t], 1);
-    if (t < kWsSlots) {
-        S.written[t] = 0;
-        S.consumed[t] = 0;
-    }
-    if (t == 0) {
-        S.tiles_done = 0;
-        S.reserved = 0;
-        S.final_pos = -1;
-        S.abort = 0;
-    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (t < kEvalPipes) tc::mbar_init(&mbar[t], 1);
+    if (t == 0) s_fail = 0;
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tm = tmem_slot;
+    const uint32_t d_tmem = tm + (uint32_t)(128 * pipe);
+    const uint32_t taddr = d_tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH = tc::smem_u32(sH);
+    uint32_t phase = 0;
+    bool ok = true;
     const int nv = *A.n_valid;
     const int n_tiles = (nv + 31) >> 5, n_sup = (n_tiles + 31) >> 5;
+    const int n_seed_groups = (A.W + A.seed_group - 1) / A.seed_group;
+    const int n_seed_items = A.L * n_seed_groups;
+    const int n_items = n_seed_items + A.L * A.n_groups;
+    unsigned long long n_seed_q = 0, n_cull_q = 0;
+    int loaded = -1;
 
-    if (wg < kWsPipes) {
-        // ---------------------------------------------------------------- consumers
-        const int pipe = wg;
-        uint8_t* sH = sm + kWsH + pipe * kTileBytes;
-        const uint32_t d_tmem = tm + (uint32_t)(128 * pipe);
-        const uint32_t taddr = d_tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH = tc::smem_u32(sH);
-        uint32_t phase = 0;
-        bool ok = true;
-        for (int tile = pipe;; tile += kWsPipes) {
-            const int slot = tile % kWsSlots, gen = tile / kWsSlots;
-            if (r == 0) {
-                int cmd = -1;
-                for (uint32_t i = 0; i < kWsPollLimit; ++i) {
-                    if (vload(&S.written[slot]) >= 128 * (gen + 1)) { cmd = 1; break; }
-                    const int fp = vload(&S.final_pos);
-                    if (fp >= 0 && tile * 128 >= fp) { cmd = 0; break; }
-                    if (vload(&S.abort)) break;
-                    __nanosleep(64);
-                }
-                if (cmd < 0) {
-                    S.abort = 1;
-                    atomicOr(A.status, kStatusTimeout);
-                }
-                s_cmd[pipe] = cmd;
-            }
-            pipe_sync(pipe);
-            if (s_cmd[pipe] <= 0) break;
-            __threadfence_block();
-            const int qi = slot * 128 + r;
-            const uint2 tg = ring_t[qi];
-            const float4 x = ring_q[qi];
+    // Evaluate queries [0, nq) of the ring, a tile of 128 per pipeline at a time, and
+    // fold them into s_key (warps of one pipeline combine the lanes of a waypoint
+    // first).  Link l's weights are loaded.
+    auto evaluate_ring = [&](int l, int nq) {
+        const int nt = (nq + 127) >> 7;
+        for (int tl = pipe; tl < nt && ok; tl += kEvalPipes) {
+            const int qi = tl * 128 + r;
+            const uint32_t tag = qi < nq ? s_tag[qi] : kNoTag;
+            const float4 x = tag != kNoTag ? s_q[qi] : make_float4(0.f, 0.f, 0.f, 0.f);
             float f = 0.f;
-            ok = pipe_network(pipe, r, small, sH, aH, aW2, aW3, d_tmem, taddr, &mbar[pipe], phase, A.wait_polls, x, f);
+            ok = pipe_network(pipe, r, small, sH, aH, aW2, aW3, d_tmem, taddr, &mbar[pipe], phase, A.wait_polls,
+                              x, f);
             if (!ok) {
-                if (r == 0) {
-                    S.abort = 1;
-                    atomicOr(A.status, kStatusTimeout);
-                }
+                if (r == 0) s_fail = 1;
                 break;
             }
-            const bool valid = tg.x != kNoTag;
-            const int l = (int)(tg.y & 15u);
-            const float d = valid ? fmaf(A.scale[l], f, x.w) : 0.f;
-            const bool use = valid && !isnan(d);
+            const float d = fmaf(A.scale[l], f, x.w);
+            const bool use = tag != kNoTag && !isnan(d);
+            const unsigned j = use ? tag >> 24 : kNoTag;
             const unsigned hi = use ? ordered_bits(d) : 0xffffffffu;
-            const unsigned peers = __match_any_sync(0xffffffffu, use ? tg.x : kNoTag);
+            const unsigned lo = use ? (((tag & 0xffffffu) << 4) | (unsigned)l) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, j);
             const unsigned hmin = __reduce_min_sync(peers, hi);
-            const unsigned lmin = __reduce_min_sync(peers, hi == hmin ? tg.y : 0xffffffffu);
-            if (use && lane == __ffs(peers) - 1) atomicMin(&A.keys[tg.x], ((unsigned long long)hmin << 32) | lmin);
-            pipe_sync(pipe);   // every row has read its slot entry
-            if (r == 0) {
-                __threadfence_block();
-                atomicAdd(&S.consumed[slot], 1);
-                atomicAdd(&S.tiles_done, 1);
+            const unsigned lmin = __reduce_min_sync(peers, hi == hmin ? lo : 0xffffffffu);
+            if (use && lane == __ffs(peers) - 1) atomicMin(&s_key[j], ((unsigned long long)hmin << 32) | lmin);
+        }
+    };
+
+    for (;;) {
+        __syncthreads();
+        if (t == 0) s_item = atomicAdd(A.work, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items || s_fail) break;
+        const bool seed = item < n_seed_items;
+        const int rem = seed ? item : item - n_seed_items;
+        const int ng = seed ? n_seed_groups : A.n_groups;
+        const int gsz = seed ? A.seed_group : A.group;
+        const int l = rem / ng, g = rem % ng;
+        const int w0 = g * gsz;
+        const int nw = min(gsz, A.W - w0);
+        if (l != loaded) {
+            load_image(A.image + (size_t)l * kImgBytes, sm + kSurImg, t, kEvalThreads);
+            tc::fence_smem_to_async();   // the weights are MMA operands
+            loaded = l;
+        }
+        // the group's poses and world capsules of link l
+        if (warp < nw) {
+            const float4* P = reinterpret_cast<const float4*>(A.poses + ((size_t)(w0 + warp) * A.L + l) * 16);
+            const float4 M0 = P[0], M1 = P[1], M2 = P[2];
+            if (lane == 0) {
+                s_M[warp][0] = M0;
+                s_M[warp][1] = M1;
+                s_M[warp][2] = M2;
+                const float4 a = A.cap_a[l], b = A.cap_b[l];
+                const float ax = a.x - M0.w, ay = a.y - M1.w, az = a.z - M2.w;
+                const float bx = b.x - M0.w, by = b.y - M1.w, bz = b.z - M2.w;
+                const float Ax = fmaf(M0.x, ax, fmaf(M1.x, ay, M2.x * az));
+                const float Ay = fmaf(M0.y, ax, fmaf(M1.y, ay, M2.y * az));
+                const float Az = fmaf(M0.z, ax, fmaf(M1.z, ay, M2.z * az));
+                const float Bx = fmaf(M0.x, bx, fmaf(M1.x, by, M2.x * bz));
+                const float By = fmaf(M0.y, bx, fmaf(M1.y, by, M2.y * bz));
+                const float Bz = fmaf(M0.z, bx, fmaf(M1.z, by, M2.z * bz));
+                const float dx = Bx - Ax, dy = By - Ay, dz = Bz - Az;
+                const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                s_cA[warp] = make_float4(Ax, Ay, Az, a.w);
+                s_cD[warp] = make_float4(dx, dy, dz, dd > 0.f ? 1.f / dd : 0.f);
+                // cull items start from the minimum over every link published so far
+                s_key[warp] = seed ? ~0ull : A.keys[w0 + warp];
             }
         }
-        if (!ok) tc::mbar_wait(&mbar[pipe], phase ^ 1u, kWaitPolls);   // the MMA in flight ends first
-    } else {
-        // ----------------------------------------------------------------- producer
-        const int pw = warp - 4 * kWsPipes, pt = t - 128 * kWsPipes;
-        // one launch takes the seed items, a second one the cull items, so that every
-        // cull finds each link's seed minimum published
-        const int per_link = A.phase == 0 ? A.n_seed_groups : A.n_groups;
-        int home = (int)(blockIdx.x % (unsigned)A.L);
-        int loaded = -1;
-        bool ok = true;
-        unsigned long long n_seed = 0, n_cull = 0;
-        for (;;) {
-            if (pt == 0) {
-                const int h0 = home;
-                S.item = ws_pick(A, home, per_link);
-                S.item_link = home;
-                (void)h0;
-            }
-            prod_sync();
-            const int item = S.item, l = S.item_link;
-            prod_sync();   // S.item is rewritten only after every producer thread has read it
-            if (item < 0) break;
-            const bool seed = A.phase == 0;
-            const int gsz = seed ? kSurGroup : A.group;
-            const int g = item;
-            const int w0 = g * gsz, nw = min(gsz, A.W - w0);
-            if (l != loaded) {
-                // finish the current tile, let the pipelines evaluate every tile, then
-                // copy link l's weights
-                if (!(ok = ws_pad(S, ring_q, ring_t, pt))) break;
-                if (pt == 0) {
-                    const int want = vload(&S.reserved) >> 7;
-                    if (!wait_at_least(&S.tiles_done, want, S)) {
-                        S.abort = 1;
-                        atomicOr(A.status, kStatusTimeout);
-                    }
+        if (t == 0) {
+            s_qn = 0;
+            s_ln = 0;
+            s_lnext = 0;
+            s_over = 0u;
+        }
+        __syncthreads();
+
+        if (seed) {
+            // the 32 points of the tile nearest to the capsule (nearest super-tile first)
+            uint32_t tag = kNoTag;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (warp < nw && nv > 0) {
+                const float4 cA = s_cA[warp], cD = s_cD[warp];
+                float best = INFINITY;
+                int bi = 0x7fffffff;
+                for (int s = lane; s < n_sup; s += 32) {
+                    const float gp = capsule_gap(__ldg(&A.supers[s]), cA, cD);
+                    if (gp < best) { best = gp; bi = s; }
                 }
-                prod_sync();
-                if (vload(&S.abort)) break;
-                load_image(A.image + (size_t)l * kImgBytes, sm, pt, 32 * kProdWarps);
-                tc::fence_smem_to_async();   // the weights are MMA operands
-                __threadfence_block();
-                loaded = l;
-                prod_sync();
-            }
-            // the group's poses, world capsules and thresholds for link l
-            for (int j = pw; j < nw; j += kProdWarps) {
-                const float4* P = reinterpret_cast<const float4*>(A.poses + ((size_t)(w0 + j) * A.L + l) * 16);
-                const float4 M0 = P[0], M1 = P[1], M2 = P[2];
-                if (lane == 0) {
-                    S.M[j][0] = M0;
-                    S.M[j][1] = M1;
-                    S.M[j][2] = M2;
-                    const float4 a = A.cap_a[l], b = A.cap_b[l];
-                    const float ax = a.x - M0.w, ay = a.y - M1.w, az = a.z - M2.w;
-                    const float bx = b.x - M0.w, by = b.y - M1.w, bz = b.z - M2.w;
-                    const float Ax = fmaf(M0.x, ax, fmaf(M1.x, ay, M2.x * az));
-                    const float Ay = fmaf(M0.y, ax, fmaf(M1.y, ay, M2.y * az));
-                    const float Az = fmaf(M0.z, ax, fmaf(M1.z, ay, M2.z * az));
-                    const float Bx = fmaf(M0.x, bx, fmaf(M1.x, by, M2.x * bz));
-                    const float By = fmaf(M0.y, bx, fmaf(M1.y, by, M2.y * bz));
-                    const float Bz = fmaf(M0.z, bx, fmaf(M1.z, by, M2.z * bz));
-                    const float dx = Bx - Ax, dy = By - Ay, dz = Bz - Az;
-                    const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    S.cA[j] = make_float4(Ax, Ay, Az, a.w);
-                    S.cD[j] = make_float4(dx, dy, dz, dd > 0.f ? 1.f / dd : 0.f);
-                    // the minimum over every link published so far
-                    const unsigned long long k = __ldcg(&A.keys[w0 + j]);
-                    const float best = k == ~0ull ? INFINITY : from_ordered((unsigned)(k >> 32));
-                    S.thr[j] = best + A.slack + a.w;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
                 }
-            }
-            if (pt == 0) {
-                S.list_n = 0;
-                S.list_next = 0;
-                S.over = 0u;
-            }
-            prod_sync();
-            if (seed) {
-                // per waypoint, the 32 points of the tile nearest to the capsule; warp pw
-                // serves waypoint slots pw, pw + kProdWarps, ... together (their loads go
-                // out together)
-                constexpr int kSeedPer = kSurGroup / kProdWarps;
-                bool live[kSeedPer];
-                float4 cA[kSeedPer], cD[kSeedPer];
-                float best[kSeedPer];
-                int bi[kSeedPer];
-#pragma unroll
-                for (int u = 0; u < kSeedPer; ++u) {
-                    const int j = pw + kProdWarps * u;
-                    live[u] = j < nw && nv > 0;
-                    cA[u] = live[u] ? S.cA[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    cD[u] = live[u] ? S.cD[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    best[u] = INFINITY;
-                    bi[u] = 0x7fffffff;
-                }
-                for (int sidx = lane; sidx < n_sup; sidx += 32) {
-                    const float4 sp = __ldg(&A.supers[sidx]);
-#pragma unroll
-                    for (int u = 0; u < kSeedPer; ++u) {
-                        const float gp = capsule_gap(sp, cA[u], cD[u]);
-                        if (gp < best[u]) { best[u] = gp; bi[u] = sidx; }
-                    }
-                }
-                float4 tsph[kSeedPer];
-#pragma unroll
-                for (int u = 0; u < kSeedPer; ++u) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const float ob = __shfl_xor_sync(0xffffffffu, best[u], o);
-                        const int oi = __shfl_xor_sync(0xffffffffu, bi[u], o);
-                        if (ob < best[u] || (ob == best[u] && oi < bi[u])) { best[u] = ob; bi[u] = oi; }
-                    }
-                    if (bi[u] >= n_sup) live[u] = false;
-                    const int tt = live[u] ? bi[u] * 32 + lane : n_tiles;
-                    tsph[u] = tt < n_tiles ? __ldg(&A.tiles[tt]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    bi[u] = tt;
-                }
-                int ti[kSeedPer];
-#pragma unroll
-                for (int u = 0; u < kSeedPer; ++u) {
+                if (bi < n_sup) {
+                    const int tt = bi * 32 + lane;
                     float tb = INFINITY;
-                    int tix = 0x7fffffff;
-                    if (bi[u] < n_tiles) { tb = capsule_gap(tsph[u], cA[u], cD[u]); tix = bi[u]; }
+                    int ti = 0x7fffffff;
+                    if (tt < n_tiles) { tb = capsule_gap(__ldg(&A.tiles[tt]), cA, cD); ti = tt; }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         const float ob = __shfl_xor_sync(0xffffffffu, tb, o);
-                        const int oi = __shfl_xor_sync(0xffffffffu, tix, o);
-                        if (ob < tb || (ob == tb && oi < tix)) { tb = ob; tix = oi; }
+                        const int oi = __shfl_xor_sync(0xffffffffu, ti, o);
+                        if (ob < tb || (ob == tb && oi < ti)) { tb = ob; ti = oi; }
                     }
-                    ti[u] = tix;
-                }
-                bool take[kSeedPer];
-                float4 q[kSeedPer];
-                uint2 tg[kSeedPer];
-#pragma unroll
-                for (int u = 0; u < kSeedPer; ++u) {
-                    const int j = pw + kProdWarps * u;
-                    const int k = ti[u] * 32 + lane;
-                    take[u] = live[u] && ti[u] < n_tiles && k < nv;
-                    const float4 pnt = take[u] ? __ldg(&A.sorted[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    q[u] = take[u] ? make_query(A, l, S.M[j], pnt) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    tg[u] = make_uint2((unsigned)(w0 + j), ((unsigned)__float_as_int(pnt.w) << 4) | (unsigned)l);
-                    if (A.stats) n_seed += (unsigned)__popc(__ballot_sync(0xffffffffu, take[u]));
-                }
-                ok = ws_emit<kSeedPer>(S, ring_q, ring_t, take, q, tg, lane);
-            } else {
-                // list: (waypoint slot, tile) entries whose tile sphere reaches the threshold;
-                // the tiles of up to four surviving super-tiles are tested per round (their
-                // loads go out together)
-                for (int j = pw; j < nw; j += kProdWarps) {
-                    const float4 cA = S.cA[j], cD = S.cD[j];
-                    const float thr = S.thr[j];
-                    for (int s0 = 0; s0 < n_sup; s0 += 32) {
-                        const int sidx = s0 + lane;
-                        unsigned bs = __ballot_sync(0xffffffffu,
-                                                    sidx < n_sup && capsule_gap(__ldg(&A.supers[sidx]), cA, cD) <= thr);
-                        while (bs) {
-                            int tt[4];
-                            float4 sp[4];
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                tt[u] = n_tiles;
-                                if (bs) {
-                                    tt[u] = (s0 + __ffs(bs) - 1) * 32 + lane;
-                                    bs &= bs - 1;
-                                }
-                                sp[u] = tt[u] < n_tiles ? __ldg(&A.tiles[tt[u]]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                            }
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const bool reach = tt[u] < n_tiles && capsule_gap(sp[u], cA, cD) <= thr;
-                                const unsigned bt = __ballot_sync(0xffffffffu, reach);
-                                if (!bt) continue;
-                                int base = 0;
-                                if (lane == 0) base = atomicAdd(&S.list_n, __popc(bt));
-                                base = __shfl_sync(0xffffffffu, base, 0);
-                                const int slot = base + __popc(bt & ((1u << lane) - 1u));
-                                if (reach && slot < kWsList) s_list[slot] = ((unsigned)j << 24) | (unsigned)tt[u];
-                                if (base + __popc(bt) > kWsList && lane == 0) atomicOr(&S.over, 1u << j);
-                            }
-                        }
+                    const int k = ti * 32 + lane;
+                    if (ti < n_tiles && k < nv) {
+                        const float4 p = __ldg(&A.sorted[k]);
+                        q = make_query(A, l, s_M[warp], p);
+                        tag = ((unsigned)warp << 24) | (unsigned)__float_as_int(p.w);
                     }
                 }
-                prod_sync();
-                const int n_list = min(vload(&S.list_n), kWsList);
-                // the listed tiles' points, kWsTake entries per warp step
-                while (ok) {
-                    int e0 = 0;
-                    if (lane == 0) e0 = atomicAdd(&S.list_next, kWsTake);
+            }
+            if (warp < gsz) {
+                s_q[warp * 32 + lane] = q;
+                s_tag[warp * 32 + lane] = tag;
+                if (A.stats) n_seed_q += (unsigned)__popc(__ballot_sync(0xffffffffu, tag != kNoTag));
+            }
+            __syncthreads();
+            evaluate_ring(l, gsz * 32);
+            __syncthreads();
+        } else {
+            if (t < nw) {
+                const unsigned long long k = s_key[t];
+                const float best = k == ~0ull ? INFINITY : from_ordered((unsigned)(k >> 32));
+                s_thr[t] = best + A.slack + s_cA[t].w;
+            }
+            __syncthreads();
+            // list: (waypoint slot, tile) entries whose tile sphere reaches the threshold
+            if (warp < nw) {
+                const float4 cA = s_cA[warp], cD = s_cD[warp];
+                const float thr = s_thr[warp];
+                for (int s0 = 0; s0 < n_sup; s0 += 32) {
+                    const int sidx = s0 + lane;
+                    unsigned bs = __ballot_sync(0xffffffffu,
+                                                sidx < n_sup && capsule_gap(__ldg(&A.supers[sidx]), cA, cD) <= thr);
+                    while (bs) {
+                        const int sv = s0 + __ffs(bs) - 1;
+                        bs &= bs - 1;
+                        const int tt = sv * 32 + lane;
+                        const bool reach = tt < n_tiles && capsule_gap(__ldg(&A.tiles[tt]), cA, cD) <= thr;
+                        const unsigned bt = __ballot_sync(0xffffffffu, reach);
+                        if (!bt) continue;
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&s_ln, __popc(bt));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        const int slot = base + __popc(bt & ((1u << lane) - 1u));
+                        if (reach && slot < kSurList) s_list[slot] = ((unsigned)warp << 24) | (unsigned)tt;
+                        if (base + __popc(bt) > kSurList && lane == 0) atomicOr(&s_over, 1u << warp);
+                    }
+                }
+            }
+            __syncthreads();
+            const int n_list = min(s_ln, kSurList);
+            for (;;) {
+                // produce: kSurTake entries per warp step (their point loads go out
+                // together) until the ring holds kSurFill queries
+                for (;;) {
+                    int e0 = 0x7fffffff;
+                    if (lane == 0 && *reinterpret_cast<volatile int*>(&s_qn) < kSurFill)
+                        e0 = atomicAdd(&s_lnext, kSurTake);
                     e0 = __shfl_sync(0xffffffffu, e0, 0);
                     if (e0 >= n_list) break;
-                    float4 p[kWsTake];
-                    int jj[kWsTake];
-                    unsigned long long kk[kWsTake];
+                    float4 p[kSurTake];
+                    int jj[kSurTake];
 #pragma unroll
-                    for (int u = 0; u < kWsTake; ++u) {
+                    for (int u = 0; u < kSurTake; ++u) {
                         const bool ve = e0 + u < n_list;
                         const uint32_t ent = ve ? s_list[e0 + u] : 0u;
+                        jj[u] = ve ? (int)(ent >> 24) : -1;
                         const int k = (int)(ent & 0xffffffu) * 32 + lane;
-                        jj[u] = (ve && k < nv) ? (int)(ent >> 24) : -1;
-                        p[u] = jj[u] >= 0 ? __ldg(&A.sorted[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        // the waypoint's minimum as it stands now (the pipelines keep lowering it)
-                        kk[u] = ve ? __ldcg(&A.keys[w0 + (int)(ent >> 24)]) : ~0ull;
+                        p[u] = (ve && k < nv) ? __ldg(&A.sorted[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (!(ve && k < nv)) jj[u] = -1;
                     }
-                    bool take[kWsTake];
-                    float4 q[kWsTake];
-                    uint2 tg[kWsTake];
+                    bool take[kSurTake];
+                    unsigned b[kSurTake];
+                    int cnt = 0;
 #pragma unroll
-                    for (int u = 0; u < kWsTake; ++u) {
+                    for (int u = 0; u < kSurTake; ++u) {
                         const int j = max(jj[u], 0);
-                        const float now = kk[u] == ~0ull ? INFINITY : from_ordered((unsigned)(kk[u] >> 32)) + A.slack + S.cA[j].w;
-                        const float thr = fminf(S.thr[j], now);
                         take[u] = jj[u] >= 0 &&
-                                  capsule_gap(make_float4(p[u].x, p[u].y, p[u].z, 0.f), S.cA[j], S.cD[j]) <= thr;
-                        q[u] = take[u] ? make_query(A, l, S.M[j], p[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        tg[u] = make_uint2((unsigned)(w0 + j), ((unsigned)__float_as_int(p[u].w) << 4) | (unsigned)l);
-                        if (A.stats) n_cull += (unsigned)__popc(__ballot_sync(0xffffffffu, take[u]));
+                                  capsule_gap(make_float4(p[u].x, p[u].y, p[u].z, 0.f), s_cA[j], s_cD[j]) <= s_thr[j];
+                        b[u] = __ballot_sync(0xffffffffu, take[u]);
+                        cnt += __popc(b[u]);
                     }
-                    ok = ws_emit<kWsTake>(S, ring_q, ring_t, take, q, tg, lane);
+                    if (!cnt) continue;
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&s_qn, cnt);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+                    for (int u = 0; u < kSurTake; ++u) {
+                        if (take[u]) {
+                            const int slot = base + __popc(b[u] & ((1u << lane) - 1u));
+                            s_q[slot] = make_query(A, l, s_M[jj[u]], p[u]);
+                            s_tag[slot] = ((unsigned)jj[u] << 24) | (unsigned)__float_as_int(p[u].w);
+                        }
+                        base += __popc(b[u]);
+                    }
                 }
+                __syncthreads();
+                const int nq = s_qn;
+                const bool done = s_lnext >= n_list;
+                if (nq == 0) break;   // then done as well: production stops only at kSurFill or at the end
+                const int take_q = done ? nq : (nq & ~127);
+                if (A.stats && t == 0) n_cull_q += (unsigned)take_q;
+                evaluate_ring(l, take_q);
+                __syncthreads();
+                // the rest (under one tile) to the front of the ring; thresholds tighten
+                const int left = nq - take_q;
+                float4 mq;
+                uint32_t mt = kNoTag;
+                if (t < left) {
+                    mq = s_q[take_q + t];
+                    mt = s_tag[take_q + t];
+                }
+                if (t < nw) {
+                    const unsigned long long k = s_key[t];
+                    const float best = k == ~0ull ? INFINITY : from_ordered((unsigned)(k >> 32));
+                    s_thr[t] = fminf(s_thr[t], best + A.slack + s_cA[t].w);
+                }
+                __syncthreads();
+                if (t < left) {
+                    s_q[t] = mq;
+                    s_tag[t] = mt;
+                }
+                if (t == 0) s_qn = left;
+                __syncthreads();
+                if (done && left == 0) break;
             }
-            if (!ok) {
-                S.abort = 1;
-                atomicOr(A.status, kStatusTimeout);
-                break;
-            }
-            prod_sync();
-            // waypoints whose list overflowed are decided by the grid re-check
-            if (!seed && pt < nw && (S.over & (1u << pt))) A.recheck[w0 + pt] = 1;
         }
-        // the last tile completes; then the pipelines may stop at the end of the ring
-        if (ok && !vload(&S.abort)) ok = ws_pad(S, ring_q, ring_t, pt);
-        if (pt == 0) {
-            __threadfence_block();
-            S.final_pos = vload(&S.reserved);
+        // publish the group's minima (and the waypoints whose list overflowed)
+        if (t < nw) {
+            if (s_key[t] != ~0ull) atomicMin(&A.keys[w0 + t], s_key[t]);
+            if (s_over & (1u << t)) A.recheck[w0 + t] = 1;
         }
-        if (A.stats && lane == 0 && n_seed) atomicAdd(&A.stats[26], n_seed);
-        if (A.stats && lane == 0 && n_cull) atomicAdd(&A.stats[27], n_cull);
+    }
+    if (A.stats) {
+        if (lane == 0) {
+            unsigned long long v = n_seed_q;
+            if (v) atomicAdd(&A.stats[26], v);
+        }
+        if (t == 0 && n_cull_q) atomicAdd(&A.stats[27], n_cull_q);
+    }
+    if (!ok) {
+        // a wait gave up: report it, then let the MMA still in flight end before the
+        // tensor memory is released
+        if (r == 0) atomicOr(A.status, kStatusTimeout);
+        tc::mbar_wait(&mbar[pipe], phase ^ 1u, kWaitPolls);
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_free(tm, 128 * kWsPipes);
+    if (warp == 0) tc::tmem_free(tm, 512);
 }
 
 // Per waypoint: decode the surrogate minimum, write it as the result, and select the
@@ -1842,7 +1676,7 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_keys, 0xff, sizeof(unsigned long long) * W, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_mask, 0, (size_t)W, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_count, 0, sizeof(int) * SDF_MAX_LINKS, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_count, 0, sizeof(int), st);
     if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate");
     sdf::BatchParams* bp = new (std::nothrow) sdf::BatchParams();
     if (!bp) return sfail(ctx, SDF_ERR_OOM, "host allocation");
@@ -1853,10 +1687,15 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
         A.poses = ctx->sur_poses;
         A.W = W;
         A.L = L;
-        // waypoints per cull item (seed items take kSurGroup)
-        A.group = 8;
+        // waypoints per work item: the most (16, 8 or 4) that still gives every SM about
+        // three cull items, so that the items even out across the SMs
+        A.group = 4;
+        for (int gsz = sdf::kSurGroup; gsz > 4; gsz /= 2)
+            if ((long long)L * ((W + gsz - 1) / gsz) >= 3LL * ctx->num_sms) {
+                A.group = gsz;
+                break;
+            }
         A.n_groups = (W + A.group - 1) / A.group;
-        A.n_seed_groups = (W + sdf::kSurGroup - 1) / sdf::kSurGroup;
         A.sorted = bp->sorted;
         A.tiles = bp->tiles;
         A.supers = bp->supers;
@@ -1875,6 +1714,7 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
             A.cap_b[l] = R->table.cap_b[l];
         }
         A.image = ctx->sur_wimg;
+        A.seed_group = sdf::kSurGroup;
         A.keys = ctx->sur_keys;
         A.recheck = ctx->sur_mask;
         A.work = ctx->sur_count;
@@ -1884,13 +1724,10 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
         A.stats = ctx->stats ? ctx->d_stats : nullptr;
     }
     delete bp;
-    for (int ph = 0; ph < 2 && rc == SDF_OK && e == cudaSuccess; ++ph) {   // seeds, then culls
-        A.phase = ph;
-        if (ph == 1) e = cudaMemsetAsync(ctx->sur_count, 0, sizeof(int) * SDF_MAX_LINKS, st);
-        if (e == cudaSuccess) {
-            sdf::sur_check_kernel<<<(unsigned)ctx->num_sms, sdf::kEvalThreads, sdf::kSurSmem, st>>>(A);
-            e = cudaGetLastError();
-        }
+    const int items = L * ((W + sdf::kSurGroup - 1) / sdf::kSurGroup) + L * A.n_groups;
+    if (rc == SDF_OK && e == cudaSuccess) {
+        sdf::sur_check_kernel<<<(unsigned)std::min(items, ctx->num_sms), sdf::kEvalThreads, sdf::kSurSmem, st>>>(A);
+        e = cudaGetLastError();
     }
     if (rc == SDF_OK && e == cudaSuccess) {
         sdf::sur_finish_kernel<<<(unsigned)((W + 255) / 256), 256, 0, st>>>(
