@@ -139,6 +139,13 @@ const char* sdf_last_error(const sdf_ctx* ctx);
                                      per warp step (SDF_OPT_TILE_BATCH does not apply); every
                                      request of one launch must use the same grids object
                                      (else SDF_ERR_UNSUPPORTED). */
+#define SDF_OPT_SORT_CTAS 11     /* CTAs of the thread-block cluster that sorts each cloud: 8
+                                     (the portable cluster size), 16 (a non-portable size;
+                                     SDF_ERR_UNSUPPORTED where the device cannot place it), or
+                                     0 (default) = 16 where the device can place it, else 8.
+                                     The sorted order and every result are the same either
+                                     way; a wider cluster gives each CTA fewer points.  Get
+                                     returns the size in use. */
 int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t value);
 int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* value);
 

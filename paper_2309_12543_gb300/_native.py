@@ -40,6 +40,7 @@ SDF_OPT_STATS = 7
 SDF_OPT_BLOCK_WARPS = 8
 SDF_OPT_WAIT_POLLS = 9
 SDF_OPT_TEX3D = 10
+SDF_OPT_SORT_CTAS = 11
 SDF_KERNEL_PREP = 0
 SDF_KERNEL_CHECK = 1
 

@@ -191,6 +191,13 @@ int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t v) {
             ctx->wait_polls = (unsigned)v;
             return SDF_OK;
         case SDF_OPT_TEX3D: ctx->tex3d = v ? 1 : 0; return SDF_OK;
+        case SDF_OPT_SORT_CTAS: {
+            if (v != 0 && v != 8 && v != 16) return fail(ctx, SDF_ERR_INVALID_ARG, "sort CTAs must be 0, 8 or 16");
+            if (v == 16 && sdf::max_sort_ctas(ctx->device) < 16)
+                return fail(ctx, SDF_ERR_UNSUPPORTED, "this device cannot place a 16-CTA cluster for the sort");
+            ctx->sort_ctas = (int)v;
+            return SDF_OK;
+        }
         case SDF_OPT_STATS:
             if (v && !ctx->d_stats) {
                 DeviceGuard g(ctx->device);
@@ -217,6 +224,14 @@ int sdf_ctx_get_option(const sdf_ctx* ctx, int32_t key, int64_t* v) {
         case SDF_OPT_BLOCK_WARPS: *v = ctx->block_warps; return SDF_OK;
         case SDF_OPT_WAIT_POLLS: *v = (int64_t)ctx->wait_polls; return SDF_OK;
         case SDF_OPT_TEX3D: *v = ctx->tex3d; return SDF_OK;
+        case SDF_OPT_SORT_CTAS: {
+            if (ctx->sort_ctas) {
+                *v = ctx->sort_ctas;
+                return SDF_OK;
+            }
+            *v = sdf::max_sort_ctas(ctx->device);
+            return SDF_OK;
+        }
         default: return SDF_ERR_INVALID_ARG;
     }
 }
@@ -768,6 +783,7 @@ int sort_cloud(sdf_ctx* ctx, const float* points_dev, int N, BatchParams* p) {
     p->n_valid = ctx->n_valid;
     p->status = ctx->status;
     p->wait_polls = ctx->wait_polls;
+    p->sort_ctas = ctx->sort_ctas;
     p->stats = nullptr;
     const cudaError_t e = launch_prep(*p, ctx->stream);
     return e == cudaSuccess ? SDF_OK : cuda_fail(ctx, e, "cloud sort");
@@ -935,6 +951,7 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     p->n_valid = ctx->n_valid;
     p->status = ctx->status;
     p->wait_polls = ctx->wait_polls;
+    p->sort_ctas = ctx->sort_ctas;
     p->stats = ctx->stats ? ctx->d_stats : nullptr;
     cudaError_t e = cudaSuccess;
     if (ctx->time_kernels) e = cudaEventRecord(ctx->ev0, ctx->stream);

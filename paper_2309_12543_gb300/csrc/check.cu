@@ -1,7 +1,8 @@
 // Runtime distance check for sm_103a, for one trajectory or a batch of them.
 // Two kernels per launch:
 //
-// prep_kernel -- one thread-block cluster (8 CTAs x 1024 threads) per cloud sorts
+// prep_kernel -- one thread-block cluster (16 CTAs x 1024 threads where the device
+//   allows that non-portable size, else 8) per cloud sorts
 //   its obstacle points in space: bounding box (shared through distributed shared
 //   memory), 16^3-cell Morton key, a counting sort whose partial histograms are
 //   merged slice by slice through distributed shared memory, each CTA scattering
@@ -36,6 +37,7 @@
 // The culls are exact: a skipped pair's interpolated distance exceeds a value
 // already found by more than the FP32 rounding of the bound, so culled and
 // unculled runs give bit-identical results.
+#include <atomic>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -55,7 +57,7 @@ constexpr unsigned kOrderedInf = 0xff800000u;   // ordered_bits(+inf): "no value
 constexpr int kCellsPerAxis = 16;
 constexpr int kCells = kCellsPerAxis * kCellsPerAxis * kCellsPerAxis;   // Morton cells of the cloud sort
 constexpr int kPrepThreads = 1024;
-constexpr int kPrepCtas = 8;                        // one portable-size cluster
+constexpr int kPrepCtas = 8;                        // the portable cluster size (16 where allowed)
 constexpr int kPrepChunk = 4;                       // points a thread loads before using them
 
 // Affine 3x4 composition C = X * Y (row-major, implicit last row 0 0 0 1).
@@ -187,16 +189,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// One cluster of kPrepCtas CTAs per cloud sorts it by 16^3-cell Morton key, a
+// One cluster of CT CTAs (8, or 16 where the device allows that non-portable size) per
+// cloud sorts it by 16^3-cell Morton key, a
 // counting sort without remote atomics: each CTA histograms its share of the points
-// in its own shared memory; every CTA then reads the eight partial histograms
+// in its own shared memory; every CTA then reads the CT partial histograms
 // through distributed shared memory, which gives each cell's start and this CTA's
 // first slot in it; each CTA scatters its own points with local atomics.
-__global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads, 1)
-    prep_kernel(const __grid_constant__ BatchParams P) {
+template <int CT>
+__global__ void __launch_bounds__(kPrepThreads, 1) prep_kernel(const __grid_constant__ BatchParams P) {
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned rank = cluster.block_rank();
-    const int cidx = blockIdx.x / kPrepCtas;
+    const int cidx = blockIdx.x / CT;
     const CloudDesc& C = P.cloud[cidx];
     // the check grid may start now: its set-up reads nothing this kernel writes
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -207,12 +210,12 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     __shared__ float s_gbox[6];
     __shared__ unsigned s_warp_total[32];
     __shared__ unsigned s_cloud_total, s_slice_off;
-    __shared__ __align__(16) unsigned s_slice_cnt[kPrepCtas];   // this CTA's points in each slice
-    __shared__ unsigned s_cnt[kPrepCtas][kCells / kPrepCtas];   // the slice's counts, by rank
+    __shared__ __align__(16) unsigned s_slice_cnt[CT];   // this CTA's points in each slice
+    __shared__ unsigned s_cnt[CT][kCells / CT];   // the slice's counts, by rank
     __shared__ float4 s_tile[4][32];                             // tile spheres of four super-tiles
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gtid = (int)rank * kPrepThreads + tid;
-    constexpr int kStride = kPrepCtas * kPrepThreads;
+    constexpr int kStride = CT * kPrepThreads;
     const float kInf = __int_as_float(0x7f800000);
     const int N = C.N;
     const float* pts = C.points;
@@ -262,7 +265,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
 #pragma unroll
         for (int a = 0; a < 6; ++a) s_box6[warp][a] = e6[a];
     for (int b = tid; b < kCells; b += kPrepThreads) bins[b] = 0u;
-    if (tid < kPrepCtas) s_slice_cnt[tid] = 0u;
+    if (tid < CT) s_slice_cnt[tid] = 0u;
     if (__syncthreads_or(bad) && tid == 0) atomicOr(P.status, kStatusNonFinite);
     if (warp == 0) {
 #pragma unroll
@@ -272,11 +275,11 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         }
     }
     cluster.sync();
-    // lane r < kPrepCtas of warp 0 reads rank r's box; the cluster's box goes to all
+    // lane r < CT of warp 0 reads rank r's box; the cluster's box goes to all
     // threads through this CTA's shared memory
     if (warp == 0) {
         float g[6] = {kInf, kInf, kInf, kInf, kInf, kInf};   // minima and negated maxima
-        if (lane < kPrepCtas) {
+        if (lane < CT) {
             const float4* b = reinterpret_cast<const float4*>(cluster.map_shared_rank(s_box, lane));
             const float4 b0 = b[0], b1 = b[1];
             g[0] = b0.x; g[1] = b0.y; g[2] = b0.z; g[3] = -b0.w; g[4] = -b1.x; g[5] = -b1.y;
@@ -322,7 +325,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
         for (int i0 = gtid; i0 < N; i0 += kStride * kPrepChunk) count_chunk(i0, true);
     }
     // this CTA's count in each slice of kSlice cells: warp w sums cells 128 w .. 128 w + 127
-    constexpr int kSlice = kCells / kPrepCtas;
+    constexpr int kSlice = kCells / CT;
     static_assert(kCells == 4 * kPrepThreads && kSlice % 128 == 0, "four cells a thread, whole warps a slice");
     __syncthreads();
     {
@@ -340,19 +343,22 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     //    of the slice (the histogram becomes its cursors).  The cells of slice r are
     //    read and written by CTA r alone, so no barrier separates the reads from the
     //    writes.  Thread t serves cell t mod kSlice and ranks 4 (t / kSlice) + 0..3.
-    static_assert(2 * kSlice == kPrepThreads && kPrepCtas == 8, "two threads per slice cell");
-    const int cl = tid & (kSlice - 1), half = tid / kSlice;
+    static_assert(kSlice * (CT / 4) == kPrepThreads, "CT / 4 threads per slice cell, four ranks each");
+    const int cl = tid & (kSlice - 1), half = tid / kSlice;   // half: the thread's group of four ranks
     const int cell = (int)rank * kSlice + cl;
     if (warp == 1) {
         unsigned below = 0, total = 0;
-        if (lane < kPrepCtas) {
+        if (lane < CT) {
             const uint4* c = reinterpret_cast<const uint4*>(cluster.map_shared_rank(s_slice_cnt, lane));
-            const uint4 c0 = c[0], c1 = c[1];
-            const unsigned v[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
-            for (int j = 0; j < kPrepCtas; ++j) {
-                total += v[j];
-                below += j < (int)rank ? v[j] : 0u;
+            for (int q = 0; q < CT / 4; ++q) {
+                const uint4 cq = c[q];
+                const unsigned v[4] = {cq.x, cq.y, cq.z, cq.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    total += v[e];
+                    below += 4 * q + e < (int)rank ? v[e] : 0u;
+                }
             }
         }
         below = __reduce_add_sync(kFull, below);
@@ -367,7 +373,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     __syncthreads();
     unsigned total_c = 0;
 #pragma unroll
-    for (int r = 0; r < kPrepCtas; ++r) total_c += s_cnt[r][cl];
+    for (int r = 0; r < CT; ++r) total_c += s_cnt[r][cl];
     unsigned incl = total_c;   // inclusive scan over the slice's cells (threads 0 .. kSlice-1)
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -391,8 +397,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     {
         const unsigned start = s_slice_off + s_warp_total[warp % (kSlice / 32)] + incl - total_c;
         unsigned pre = 0;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) pre += half ? s_cnt[r][cl] : 0u;
+        for (int r = 0; r < 4 * half; ++r) pre += s_cnt[r][cl];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int r = 4 * half + k;
@@ -427,7 +432,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     cluster.sync();   // orders every CTA's scatter before the reads below (cluster scope)
     mark(23);
 
-    // 5. tile and super-tile spheres.  CTA r builds super-tiles r, r + kPrepCtas, ...,
+    // 5. tile and super-tile spheres.  CTA r builds super-tiles r, r + CT, ...,
     //    kRounds of them at a time: warp w loads tile 32 s + w of each (all loads in
     //    flight before the first use) and computes its sphere (centre of the tile's
     //    box, radius to its farthest point); warp k then forms super-tile k of the
@@ -439,18 +444,18 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
     float4* supers = P.supers + C.super_base;
     static_assert(kPrepThreads / 32 == 32, "one warp per tile of a super-tile");
     constexpr int kRounds = 4;
-    for (int s0 = (int)rank; s0 < n_super; s0 += kRounds * kPrepCtas) {
+    for (int s0 = (int)rank; s0 < n_super; s0 += kRounds * CT) {
         float4 p[kRounds];
         bool v[kRounds];
 #pragma unroll
         for (int k = 0; k < kRounds; ++k) {
-            const int t = (s0 + k * kPrepCtas) * 32 + warp;
+            const int t = (s0 + k * CT) * 32 + warp;
             v[k] = t * 32 + lane < n_valid;
             p[k] = v[k] ? __ldcg(&sorted[t * 32 + lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int k = 0; k < kRounds; ++k) {
-            const int t = (s0 + k * kPrepCtas) * 32 + warp;
+            const int t = (s0 + k * CT) * 32 + warp;
             if (t < n_tiles) {   // uniform across the warp
                 const float mn[3] = {warp_min(v[k] ? p[k].x : kInf), warp_min(v[k] ? p[k].y : kInf),
                                      warp_min(v[k] ? p[k].z : kInf)};
@@ -469,7 +474,7 @@ __global__ void __cluster_dims__(kPrepCtas, 1, 1) __launch_bounds__(kPrepThreads
             }
         }
         __syncthreads();
-        const int s = s0 + warp * kPrepCtas;
+        const int s = s0 + warp * CT;
         if (warp < kRounds && s < n_super) {
             const bool vt = s * 32 + lane < n_tiles;
             const float4 c = vt ? s_tile[warp][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1090,7 +1095,67 @@ size_t staged_bytes(int stage_tiles) {
     return stage_tiles > 0 ? (size_t)(stage_tiles + stage_tiles / 32 + 1) * sizeof(float4) : 0;
 }
 
+namespace {
+// Whether each device can run the sort as one 16-CTA cluster (a non-portable cluster
+// size) instead of 8 CTAs: decided once per device by configure_kernels.
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_prep_ctas[kMaxDevices] = {};
+}  // namespace
+
+int max_sort_ctas(int device) {
+    return device >= 0 && device < kMaxDevices && g_prep_ctas[device].load(std::memory_order_relaxed) == 16 ? 16 : kPrepCtas;
+}
+
+namespace {
+
+template <int CT>
+cudaError_t launch_prep_ct(const BatchParams& p, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(CT * p.n_cloud));
+    cfg.blockDim = dim3(kPrepThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CT;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, prep_kernel<CT>, p);
+}
+
+cudaError_t launch_prep_kernel(const BatchParams& p, cudaStream_t s) {
+    int dev = 0;
+    if (!p.sort_ctas && cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    const int ctas = p.sort_ctas ? p.sort_ctas : max_sort_ctas(dev);
+    return ctas == 16 ? launch_prep_ct<16>(p, s) : launch_prep_ct<kPrepCtas>(p, s);
+}
+
+}  // namespace
+
 cudaError_t configure_kernels() {
+    {   // a 16-CTA cluster for the sort, where the device can place one
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        int ctas = kPrepCtas;
+        if (cudaFuncSetAttribute(prep_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(16);
+            cfg.blockDim = dim3(kPrepThreads);
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 16;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, prep_kernel<16>, &cfg) == cudaSuccess && clusters > 0) ctas = 16;
+        }
+        cudaGetLastError();   // a refused attribute or query is not an error here
+        if (dev >= 0 && dev < kMaxDevices) g_prep_ctas[dev].store(ctas, std::memory_order_relaxed);
+    }
     const int smem = (int)staged_bytes(kMaxStagedTiles);
     const void* fns[8] = {(const void*)check_kernel<2, 16, false>, (const void*)check_kernel<4, 16, false>,
                           (const void*)check_kernel<8, 16, false>, (const void*)check_kernel<2, 8, false>,
@@ -1106,8 +1171,7 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
     if (p.n_inst <= 0 || p.n_blocks <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     if (!p.skip_prep) {
-        prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, 0, s>>>(p);
-        e = cudaGetLastError();
+        e = launch_prep_kernel(p, s);
         if (e != cudaSuccess) return e;
     }
     if (ev_mid) {   // a timing event between the kernels; the check then starts after the sort ends
@@ -1143,8 +1207,7 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
 
 cudaError_t launch_prep(const BatchParams& p, cudaStream_t s) {
     if (p.n_cloud <= 0) return cudaSuccess;
-    prep_kernel<<<kPrepCtas * p.n_cloud, kPrepThreads, 0, s>>>(p);
-    return cudaGetLastError();
+    return launch_prep_kernel(p, s);
 }
 
 cudaError_t launch_finish(int* status, int* h_status, unsigned* d_seq, unsigned* h_done, cudaStream_t s) {

@@ -87,6 +87,7 @@ struct BatchParams {
     int* n_valid;             // finite points per cloud
     int* status;              // device status bits
     unsigned wait_polls;      // polls of the sphere-staging wait before it gives up
+    int sort_ctas;            // CTAs of the sort's cluster: 8, 16 (allowed by the device), 0 = widest
     unsigned long long* stats;  // kStatCount counters, or null (statistics off)
     CloudDesc cloud[kMaxBatch];
     InstDesc inst[kMaxBatch];
@@ -118,6 +119,9 @@ void afree(cudaArray_t a);
 
 // Launchers (check.cu / grid_build.cu).  Each returns the launch's cudaError_t.
 cudaError_t configure_kernels();           // once per device, that device current
+// The widest cluster the sort runs as on a device (16 where the device can place that
+// non-portable size, else 8); known after configure_kernels ran for that device.
+int max_sort_ctas(int device);
 // One thread: moves the device status word to page-locked host memory (and clears
 // it), then publishes ++(*d_seq) in *h_done behind a system-scope fence.
 cudaError_t launch_finish(int* status, int* h_status, unsigned* d_seq, unsigned* h_done, cudaStream_t s);
@@ -189,6 +193,7 @@ struct sdf_ctx {
     int reuse_sort = 0;                    // internal: the next check reuses the scratch's sorted cloud
     int block_warps = 0;                   // warps per check block (0: tuned or 16)
     int tex3d = 0;                         // lookups by the texture unit's trilinear filter
+    int sort_ctas = 0;                     // CTAs of the sort's cluster (SDF_OPT_SORT_CTAS)
     unsigned wait_polls = sdf::kDefaultWaitPolls;  // polls of a bounded device wait (SDF_OPT_WAIT_POLLS)
     struct Shape { int tw, tb, nw; };
     std::map<uint64_t, Shape> tuned;       // launch shape key -> (waypoints per block, tile batch, warps)

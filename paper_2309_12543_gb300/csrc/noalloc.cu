@@ -141,6 +141,7 @@ extern "C" int check_trajectory_noalloc(const sdf_robot* R, void* cuda_stream, c
         p.n_valid = reinterpret_cast<int*>(base + kValidOff);
         p.status = status;
         p.wait_polls = sdf::kDefaultWaitPolls;
+        p.sort_ctas = 0;
         p.stats = nullptr;
         if (e == cudaSuccess) e = sdf::launch_batch(p, sdf::kDefaultTileBatch, stream, nullptr);
         if (e != cudaSuccess) rc = SDF_ERR_CUDA;
