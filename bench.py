@@ -914,6 +914,7 @@ def run_surrogate(args):
         "network_queries": {"seed": st["sur_seed_queries"], "after_cull": st["sur_queries"],
                             "flops_per_query": MLP_FLOPS_PER_QUERY,
                             "tflops_over_the_check": queries * MLP_FLOPS_PER_QUERY / (percentile(sur_us, 50) * 1e-6) / 1e12},
+        "fused_kernel_phases_us": sur_phases(st, torch.cuda.get_device_properties(dev).multi_processor_count),
         "rechecked_waypoints": int(r.sum()), "fallback_exact": exact, "max_diff_where_surrogate_decided_m": within,
         "eps_m": eps, "errors": errs, "equal_memory_grid_32": coarse_err,
         "memory_bytes_per_link": {"surrogate_fp32_params": sdf.SDF_MLP_PARAMS * 4,
@@ -922,6 +923,18 @@ def run_surrogate(args):
         "clocks": clk,
     }
     print(json.dumps(res), flush=True)
+
+
+def sur_phases(st, n_ctas):
+    """Per-CTA means (and the longest CTA) of the fused surrogate kernel's phases, from
+    one statistics pass: production (weight copies, seed picks, culls, point tests; the
+    cull lists a part of it), network evaluation rounds, and the rest (work fetches)."""
+    n = max(1, int(n_ctas))
+    cta = st["sur_ns_cta"] / n / 1e3
+    prod, ev = st["sur_ns_produce"] / n / 1e3, st["sur_ns_eval"] / n / 1e3
+    return {"cta_mean": cta, "cta_max": st["sur_ns_cta_max"] / 1e3, "produce": prod,
+            "cull_lists": st["sur_ns_list"] / n / 1e3, "evaluate": ev, "other": cta - prod - ev,
+            "ctas": n}
 
 
 # ------------------------------------------------------------------- robot SDF

@@ -182,6 +182,7 @@ int sdf_ctx_last_kernel_ms(sdf_ctx* ctx, int32_t kernel, float* ms);
 #define SDF_STAT_NS_BLOCK 14      /* sum over blocks: whole block                   */
 #define SDF_STAT_NS_BLOCK_MAX 15  /* longest block                                  */
 #define SDF_STAT_NS_SPAN 16       /* first block start to last block end, over the calls */
+#define SDF_STAT_SUR_NS_CTA 19    /* surrogate check, sum over CTAs: whole CTA       */
 #define SDF_STAT_NS_SORT_BOX 20   /* sort phases, first cluster only: bounding box    */
 #define SDF_STAT_NS_SORT_HIST 21  /* histogram                                      */
 #define SDF_STAT_NS_SORT_SCAN 22  /* scan                                           */
@@ -190,6 +191,11 @@ int sdf_ctx_last_kernel_ms(sdf_ctx* ctx, int32_t kernel, float* ms);
 #define SDF_STAT_NS_SORT_SUPERS 25 /* 0: counted with the tile spheres             */
 #define SDF_STAT_SUR_SEED_QUERIES 26 /* surrogate check: seed queries evaluated      */
 #define SDF_STAT_SUR_QUERIES 27   /* surrogate check: queries after the cull        */
+#define SDF_STAT_SUR_NS_PRODUCE 28 /* surrogate check, sum over CTAs: weight copies, seed picks,
+                                      culls and point tests (query production)   */
+#define SDF_STAT_SUR_NS_EVAL 29   /* surrogate check, sum over CTAs: network evaluation rounds */
+#define SDF_STAT_SUR_NS_LIST 30   /* surrogate check, sum over CTAs: the cull lists (part of 28) */
+#define SDF_STAT_SUR_NS_CTA_MAX 31 /* surrogate check: longest CTA                    */
 #define SDF_STAT_COUNT 32
 int sdf_ctx_stats(sdf_ctx* ctx, int64_t* out, int32_t n, int32_t reset);
 

@@ -219,9 +219,10 @@ class Context:
 
     STAT_NAMES = ("pairs", "seed_lookups", "super_tests", "super_pass", "tile_tests", "tile_pass",
                   "point_tests", "lookups", "list_overflow", "blocks", "ns_fk", "ns_seed", "ns_cull",
-                  "ns_points", "ns_block", "ns_block_max", "ns_span", "_17", "_18", "_19", "ns_sort_box",
+                  "ns_points", "ns_block", "ns_block_max", "ns_span", "_17", "_18", "sur_ns_cta", "ns_sort_box",
                   "ns_sort_hist", "ns_sort_scan", "ns_sort_scatter", "ns_sort_tiles", "ns_sort_supers",
-                  "sur_seed_queries", "sur_queries")
+                  "sur_seed_queries", "sur_queries", "sur_ns_produce", "sur_ns_eval", "sur_ns_list",
+                  "sur_ns_cta_max")
 
     def stats(self, reset: bool = False) -> dict:
         """Counters accumulated while SDF_OPT_STATS is on (see sdfcheck.h)."""

@@ -76,38 +76,22 @@ constexpr uint32_t kRowGroup = 2048, kAuxRowGroup = 256;
 // about -88 the exponential overflows and the quotient is 0.
 __device__ __forceinline__ float silu_sigma(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 
-// SiLU for the evaluation kernel, where the transcendental (XU) pipe is the busiest:
-// the exponential always runs there (ex2.approx, 2^x), the reciprocal of 1 + e either
-// there too (rcp.approx) or on the FMA pipe (silu_fma).  The FMA-pipe reciprocal
-// starts from the bit pattern 0x7F000000 - bits(x), which negates the binary exponent
-// and approximates the mantissa linearly, so that x y0 lies in [1, 9/8] for x >= 1;
-// three Newton steps y <- y (2 - x y) square the relative error each time
-// (2^-3 -> 2^-6 -> 2^-12 -> 2^-24).  The argument of ex2 is capped at 126 so that
-// 1 + e stays finite and normal.
-constexpr float kLog2e = 1.4426950408889634f;
-__device__ __forceinline__ float ex2_xu(float x) {
+// SiLU for the evaluation kernels, from sigma(z) = (1 + tanh(z / 2)) / 2:
+//   SiLU(z) = z sigma(z) = u (1 + tanh u) = u + u tanh u,   u = z / 2,
+// one tanh.approx on the transcendental (XU) pipe and one FMA, where the exponential
+// and reciprocal form takes about eleven issue slots.  The evaluation layout of the
+// small parameters holds W1, b1, b2 and b3 halved (exact: a power of two), so that u
+// comes out of the same FMAs that formed z.  tanh.approx.f32 is documented with a
+// maximum relative error near 2^-11, so |error| <= |u| 2^-11 = |z| 2^-12: below half
+// a bfloat16 unit of the result for z > 0, and at most 2.5e-4 |z| in absolute terms
+// for z < 0, where the result tends to 0.  (Large negative u gives tanh = -1 and a
+// result of exactly 0.)
+__device__ __forceinline__ float tanh_xu(float x) {
     float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float rcp_xu(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rcp_fma(float x) {   // x in [1, 2^126]
-    float y = __int_as_float(0x7F000000 - __float_as_int(x));
-    y = y * fmaf(-x, y, 2.0f);
-    y = y * fmaf(-x, y, 2.0f);
-    y = y * fmaf(-x, y, 2.0f);
-    return y;
-}
-__device__ __forceinline__ float silu_xu(float z) { return z * rcp_xu(1.0f + ex2_xu(fminf(-z * kLog2e, 126.0f))); }
-__device__ __forceinline__ float silu_fma(float z) { return z * rcp_fma(1.0f + ex2_xu(fminf(-z * kLog2e, 126.0f))); }
-// unit e of a group of 8: one in four takes the XU reciprocal, so that the XU pipe
-// (16 ops per clock and SM) and the FMA pipe (128) finish about together
-template <int E>
-__device__ __forceinline__ float silu_mix(float z) { return (E & 3) == 0 ? silu_xu(z) : silu_fma(z); }
+__device__ __forceinline__ float silu_half(float u) { return fmaf(u, tanh_xu(u), u); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -162,7 +146,8 @@ __device__ __forceinline__ void mma_k128(uint32_t d, uint32_t a_addr, uint32_t a
 // tiles [out][in], the small parameters into FP32.  All `nthreads` threads help;
 // consecutive threads read consecutive output units (coalesced).
 // Small parameters in the evaluation kernels' layout: (W1 row j, b1 j) as one float4
-// per unit, then b2, b3, w4 and b4, so that each is read with 16-byte loads.
+// per unit, then b2, b3, w4 and b4, so that each is read with 16-byte loads.  W1, b1,
+// b2 and b3 are halved (the evaluation forms z / 2; see silu_half).
 constexpr int kEWB = 0, kEB2 = 4 * kH, kEB3 = 5 * kH, kEW4 = 6 * kH, kEB4 = 7 * kH;
 static_assert(kEB4 + 1 <= kSmallFloats, "evaluation layout of the small parameters");
 
@@ -181,10 +166,10 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ P, uint8_
     }
     if constexpr (kEvalLayout) {
         for (int i = t; i < kH; i += nthreads) {
-            reinterpret_cast<float4*>(small + kEWB)[i] =
-                make_float4(P[kOW1 + 3 * i], P[kOW1 + 3 * i + 1], P[kOW1 + 3 * i + 2], P[kOB1 + i]);
-            small[kEB2 + i] = P[kOB2 + i];
-            small[kEB3 + i] = P[kOB3 + i];
+            reinterpret_cast<float4*>(small + kEWB)[i] = make_float4(0.5f * P[kOW1 + 3 * i], 0.5f * P[kOW1 + 3 * i + 1],
+                                                                     0.5f * P[kOW1 + 3 * i + 2], 0.5f * P[kOB1 + i]);
+            small[kEB2 + i] = 0.5f * P[kOB2 + i];
+            small[kEB3 + i] = 0.5f * P[kOB3 + i];
             small[kEW4 + i] = P[kOW4 + i];
         }
         if (t == 0) small[kEB4] = P[kOB4];
@@ -583,25 +568,25 @@ __device__ __forceinline__ void pipe_sync_for_mma(int pipe) {
 }
 
 // One hidden layer's epilogue on this thread's tensor-memory lane: s(D + b) of the
-// 128 units into row r of the activation tile H (bf16).  b is 16-byte aligned.
-__device__ __forceinline__ void pipe_hidden(uint32_t taddr, const float* b, uint8_t* H, int r) {
+// 128 units into row r of the activation tile H (bf16).  bh = b / 2, 16-byte aligned.
+__device__ __forceinline__ void pipe_hidden(uint32_t taddr, const float* bh, uint8_t* H, int r) {
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 32) {
         float v[32];
         tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
         for (int k = 0; k < 32; k += 8) {
-            const float4 b0 = *reinterpret_cast<const float4*>(b + c0 + k);
-            const float4 b1 = *reinterpret_cast<const float4*>(b + c0 + k + 4);
+            const float4 b0 = *reinterpret_cast<const float4*>(bh + c0 + k);
+            const float4 b1 = *reinterpret_cast<const float4*>(bh + c0 + k + 4);
             float h[8];
-            h[0] = silu_mix<0>(v[k + 0] + b0.x);
-            h[1] = silu_mix<1>(v[k + 1] + b0.y);
-            h[2] = silu_mix<2>(v[k + 2] + b0.z);
-            h[3] = silu_mix<3>(v[k + 3] + b0.w);
-            h[4] = silu_mix<4>(v[k + 4] + b1.x);
-            h[5] = silu_mix<5>(v[k + 5] + b1.y);
-            h[6] = silu_mix<6>(v[k + 6] + b1.z);
-            h[7] = silu_mix<7>(v[k + 7] + b1.w);
+            h[0] = silu_half(fmaf(0.5f, v[k + 0], b0.x));
+            h[1] = silu_half(fmaf(0.5f, v[k + 1], b0.y));
+            h[2] = silu_half(fmaf(0.5f, v[k + 2], b0.z));
+            h[3] = silu_half(fmaf(0.5f, v[k + 3], b0.w));
+            h[4] = silu_half(fmaf(0.5f, v[k + 4], b1.x));
+            h[5] = silu_half(fmaf(0.5f, v[k + 5], b1.y));
+            h[6] = silu_half(fmaf(0.5f, v[k + 6], b1.z));
+            h[7] = silu_half(fmaf(0.5f, v[k + 7], b1.w));
             store_bf16x8(H, r, c0 + k, kH, h);
         }
     }
@@ -627,8 +612,8 @@ __device__ __forceinline__ bool pipe_network(int pipe, int r, const float* small
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const float4 w = wb[j0 + e];
-            const float z = fmaf(w.x, x.x, fmaf(w.y, x.y, fmaf(w.z, x.z, w.w)));
-            h[e] = (e & 3) == 0 ? silu_xu(z) : silu_fma(z);
+            const float u = fmaf(w.x, x.x, fmaf(w.y, x.y, fmaf(w.z, x.z, w.w)));   // z / 2
+            h[e] = silu_half(u);
         }
         store_bf16x8(H, r, j0, kH, h);
     }
@@ -660,10 +645,10 @@ __device__ __forceinline__ bool pipe_network(int pipe, int r, const float* small
         for (int k = 0; k < 32; k += 4) {
             const float4 b = *reinterpret_cast<const float4*>(b3 + c0 + k);
             const float4 w = *reinterpret_cast<const float4*>(w4 + c0 + k);
-            acc = fmaf(w.x, silu_mix<0>(v[k + 0] + b.x), acc);
-            acc = fmaf(w.y, silu_mix<1>(v[k + 1] + b.y), acc);
-            acc = fmaf(w.z, silu_mix<2>(v[k + 2] + b.z), acc);
-            acc = fmaf(w.w, silu_mix<3>(v[k + 3] + b.w), acc);
+            acc = fmaf(w.x, silu_half(fmaf(0.5f, v[k + 0], b.x)), acc);
+            acc = fmaf(w.y, silu_half(fmaf(0.5f, v[k + 1], b.y)), acc);
+            acc = fmaf(w.z, silu_half(fmaf(0.5f, v[k + 2], b.z)), acc);
+            acc = fmaf(w.w, silu_half(fmaf(0.5f, v[k + 3], b.w)), acc);
         }
     }
     f = acc;
@@ -1002,6 +987,12 @@ __device__ __forceinline__ float4 make_query(const SurFusedArgs& A, int l, const
                        sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez))));
 }
 
+__device__ __forceinline__ unsigned long long sur_ns() {
+    unsigned long long v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    return v;
+}
+
 __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid_constant__ SurFusedArgs A) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t mbar[kEvalPipes];
@@ -1041,6 +1032,18 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
     const int n_items = n_seed_items + A.L * A.n_groups;
     unsigned long long n_seed_q = 0, n_cull_q = 0;
     int loaded = -1;
+    // phase times (SDF_OPT_STATS): thread 0 stamps the block-wide phase boundaries,
+    // each taken just after the barrier that closes a phase
+    const bool timed = A.stats != nullptr && t == 0;
+    const unsigned long long t_cta0 = timed ? sur_ns() : 0ull;
+    unsigned long long t_mark = t_cta0, ns_prod = 0, ns_eval = 0, ns_list = 0;
+    auto stamp = [&](unsigned long long* acc) {
+        if (timed) {
+            const unsigned long long n = sur_ns();
+            if (acc) *acc += n - t_mark;
+            t_mark = n;
+        }
+    };
 
     // Evaluate queries [0, nq) of the ring, a tile of 128 per pipeline at a time, and
     // fold them into s_key (warps of one pipeline combine the lanes of a waypoint
@@ -1076,6 +1079,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
         __syncthreads();
         const int item = s_item;
         if (item >= n_items || s_fail) break;
+        stamp(nullptr);
         const bool seed = item < n_seed_items;
         const int rem = seed ? item : item - n_seed_items;
         const int ng = seed ? n_seed_groups : A.n_groups;
@@ -1120,6 +1124,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
             s_over = 0u;
         }
         __syncthreads();
+        stamp(&ns_prod);
 
         if (seed) {
             // the 32 points of the tile nearest to the capsule (nearest super-tile first)
@@ -1164,8 +1169,10 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 if (A.stats) n_seed_q += (unsigned)__popc(__ballot_sync(0xffffffffu, tag != kNoTag));
             }
             __syncthreads();
+            stamp(&ns_prod);
             evaluate_ring(l, gsz * 32);
             __syncthreads();
+            stamp(&ns_eval);
         } else {
             if (t < nw) {
                 const unsigned long long k = s_key[t];
@@ -1198,6 +1205,11 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 }
             }
             __syncthreads();
+            if (timed) {
+                const unsigned long long m = t_mark;
+                stamp(&ns_prod);
+                ns_list += t_mark - m;
+            }
             const int n_list = min(s_ln, kSurList);
             for (;;) {
                 // produce: kSurTake entries per warp step (their point loads go out
@@ -1245,6 +1257,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                     }
                 }
                 __syncthreads();
+                stamp(&ns_prod);
                 const int nq = s_qn;
                 const bool done = s_lnext >= n_list;
                 if (nq == 0) break;   // then done as well: production stops only at kSurFill or at the end
@@ -1252,6 +1265,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 if (A.stats && t == 0) n_cull_q += (unsigned)take_q;
                 evaluate_ring(l, take_q);
                 __syncthreads();
+                stamp(&ns_eval);
                 // the rest (under one tile) to the front of the ring; thresholds tighten
                 const int left = nq - take_q;
                 float4 mq;
@@ -1272,6 +1286,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 }
                 if (t == 0) s_qn = left;
                 __syncthreads();
+                stamp(&ns_prod);
                 if (done && left == 0) break;
             }
         }
@@ -1287,6 +1302,14 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
             if (v) atomicAdd(&A.stats[26], v);
         }
         if (t == 0 && n_cull_q) atomicAdd(&A.stats[27], n_cull_q);
+        if (timed) {
+            const unsigned long long cta = sur_ns() - t_cta0;
+            atomicAdd(&A.stats[19], cta);
+            atomicAdd(&A.stats[28], ns_prod);
+            atomicAdd(&A.stats[29], ns_eval);
+            atomicAdd(&A.stats[30], ns_list);
+            atomicMax(&A.stats[31], cta);
+        }
     }
     if (!ok) {
         // a wait gave up: report it, then let the MMA still in flight end before the
