@@ -47,6 +47,9 @@ constexpr int kPar = SDF_MLP_PARAMS;
 constexpr int kOW1 = 0, kOB1 = 384, kOW2 = 512, kOB2 = kOW2 + kH * kH, kOW3 = kOB2 + kH, kOB3 = kOW3 + kH * kH,
               kOW4 = kOB3 + kH, kOB4 = kOW4 + kH;
 static_assert(kOB4 + 1 == kPar, "parameter layout");
+// Floats between consecutive links' parameters (and Adam moments) in device memory:
+// kPar rounded up to 16, so that every link's block starts 64-byte aligned.
+constexpr int kParStride = (kPar + 15) & ~15;
 
 constexpr int kTileBytes = kH * kH * 2;        // one 128 x 128 bf16 operand tile
 constexpr int kAuxCols = 16;                    // [x0 x1 x2 1 g 0 ...] per sample
@@ -185,11 +188,25 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ P, uint8_
     }
 }
 
-// Layer 1 of one sample into row `row` of the H1 tile (bf16).
-__device__ __forceinline__ void layer1(const float* small, float x0, float x1, float x2, uint8_t* h1, int row) {
+// The training kernel's CTA: four warpgroups over one 128-sample batch.  Thread
+// (g, r) = (t / 128, t % 128) holds sample r (tensor-memory lane r) in the forward and
+// backward passes and output unit r in the update, and takes the 32 columns
+// [32 g, 32 g + 32) of every 128-column product: its layer-1 units, its share of
+// each epilogue, and the inputs of unit r whose W2/W3 weights it updates.  Four warps
+// per SM sub-partition instead of one hide the latency of each other's dependent
+// instructions; the batch and the order of the step are those of one 128-thread CTA.
+constexpr int kTrainGroups = 4;
+constexpr int kTrainThreads = 128 * kTrainGroups;
+constexpr int kTrainCols = kH / kTrainGroups;   // 32
+static_assert(kTrainCols == 32, "one 32-column tensor-memory load per epilogue share");
+
+// Layer 1 of sample `row`, units [c0, c0 + 32), into the H1 tile (bf16).
+__device__ __forceinline__ void layer1(const float* small, float x0, float x1, float x2, uint8_t* h1, int row,
+                                       int c0) {
     const float* W1 = small;
     const float* b1 = small + 384;
-    for (int j0 = 0; j0 < kH; j0 += 8) {
+#pragma unroll 1
+    for (int j0 = c0; j0 < c0 + kTrainCols; j0 += 8) {
         float h[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -201,28 +218,27 @@ __device__ __forceinline__ void layer1(const float* small, float x0, float x1, f
     }
 }
 
-// Hidden layer epilogue: s(D + b) of this thread's lane into row `row` of tile out.
-__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* b, uint8_t* out, int row) {
-    for (int c0 = 0; c0 < kH; c0 += 32) {
-        float v[32];
-        tc::tmem_ld32(taddr + c0, v);
+// Hidden layer epilogue: s(D + b) of columns [c0, c0 + 32) of this thread's lane into
+// row `row` of tile out.
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* b, uint8_t* out, int row, int c0) {
+    float v[32];
+    tc::tmem_ld32(taddr + c0, v);
 #pragma unroll
-        for (int k = 0; k < 32; k += 8) {
-            float h[8];
+    for (int k = 0; k < 32; k += 8) {
+        float h[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const float z = v[k + e] + b[c0 + k + e];
-                h[e] = z * silu_sigma(z);
-            }
-            store_bf16x8(out, row, c0 + k, kH, h);
+        for (int e = 0; e < 8; ++e) {
+            const float z = v[k + e] + b[c0 + k + e];
+            h[e] = z * silu_sigma(z);
         }
+        store_bf16x8(out, row, c0 + k, kH, h);
     }
 }
 
 // ------------------------------------------------------------------ training
 
 struct TrainArgs {
-    float* master;            // [L][kPar], W2/W3 blocks [in][out]
+    float* master;            // [L][kParStride], W2/W3 blocks [in][out]
     float* adam_m;
     float* adam_v;
     int* step;                // [L] Adam steps taken
@@ -239,14 +255,16 @@ struct TrainArgs {
     uint32_t wait_polls;      // polls of an MMA completion wait before it gives up
 };
 
-__global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant__ TrainArgs A) {
+__global__ void __launch_bounds__(kTrainThreads, 1) mlp_train_kernel(const __grid_constant__ TrainArgs A) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     __shared__ float red[2][4];
+    __shared__ float red_f[kTrainGroups][kH];   // each warpgroup's share of the output sums
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int grp = t >> 7, r = t & 127, c0 = grp * kTrainCols;
     const int link = A.link0 + blockIdx.x;
-    float* P = A.master + (size_t)link * kPar;
+    float* P = A.master + (size_t)link * kParStride;
     uint8_t* sW2 = sm + kSW2;
     uint8_t* sW3 = sm + kSW3;
     uint8_t* sH1 = sm + kSH1;
@@ -261,12 +279,12 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
     const float* b3 = small + 384 + 2 * kH;
     const float* w4 = small + 384 + 3 * kH;
 
-    load_weights(P, sW2, sW3, small, t, 128);
+    load_weights(P, sW2, sW3, small, t, kTrainThreads);
     if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
     if (t == 0) tc::mbar_init(&mbar, 1);
     sync_for_mma();
     const uint32_t tm = tmem_slot;
-    const uint32_t lane_addr = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_addr = tm + ((uint32_t)((warp & 3) * 32) << 16);
     const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH1 = tc::smem_u32(sH1),
                    aH2 = tc::smem_u32(sH2), aDZ = tc::smem_u32(sDZ), aH3 = tc::smem_u32(sH3),
                    aAux = tc::smem_u32(sAux);
@@ -277,38 +295,89 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
     uint32_t phase = 0;
     bool ok = true;
     float loss_sum = 0.f;
+    // sample r of step s, loaded one step ahead
+    auto load_sample = [&](int step, float& a0, float& a1, float& a2, float& ay) {
+        const long long idx = ((A.batch0 + step) * 128 + r) % A.n;
+        const float* xs = A.x + ((size_t)link * A.n + idx) * 3;
+        a0 = xs[0];
+        a1 = xs[1];
+        a2 = xs[2];
+        ay = A.y[(size_t)link * A.n + idx];
+    };
+    float nx0 = 0.f, nx1 = 0.f, nx2 = 0.f, ny = 0.f;
+    if (A.steps > 0) load_sample(0, nx0, nx1, nx2, ny);
+    // Adam (Kingma & Ba, Algorithm 1) on the FP32 master weights
+    const float b1c = A.beta1, b2c = A.beta2, lr = A.lr, eps = A.eps;
+    float* M = A.adam_m + (size_t)link * kParStride;
+    float* V = A.adam_v + (size_t)link * kParStride;
+    // one 128 x 128 block (gradient in tensor-memory columns `col`, lane = output unit
+    // o = r): this thread's inputs [c0, c0 + 32), 16 at a time with their loads issued
+    // together (consecutive threads, consecutive outputs: coalesced in the [in][out]
+    // master layout); the new weights go to the bf16 operand tile
+    auto adam_block = [&](uint32_t col, int base, uint8_t* tile, int step) {
+        const int o = r;
+        const int ts = A.step[link] + step + 1;
+        const float c1 = 1.f - powf(b1c, (float)ts), c2 = 1.f - powf(b2c, (float)ts);
+        float* __restrict__ Pr = P;
+        float* __restrict__ Mr = M;
+        float* __restrict__ Vr = V;
+#pragma unroll 1
+        for (int cc = c0; cc < c0 + kTrainCols; cc += 16) {
+            float gr[16], pm[16], pv[16], pp[16];
+            tc::tmem_ld16(lane_addr + col + cc, gr);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int i = base + (cc + e) * kH + o;
+                pm[e] = Mr[i];
+                pv[e] = Vr[i];
+                pp[e] = Pr[i];
+            }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int i = base + (cc + e) * kH + o;
+                const float m = fmaf(b1c, pm[e], (1.f - b1c) * gr[e]);
+                const float v = fmaf(b2c, pv[e], (1.f - b2c) * gr[e] * gr[e]);
+                const float p = pp[e] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+                Mr[i] = m;
+                Vr[i] = v;
+                Pr[i] = p;
+                pp[e] = p;
+            }
+            store_bf16x8(tile, o, cc, kH, pp);
+            store_bf16x8(tile, o, cc + 8, kH, pp + 8);
+        }
+    };
 
     for (int s = 0; s < A.steps && ok; ++s) {
-        // ---- the batch: sample t of this step
-        const long long idx = ((A.batch0 + s) * 128 + t) % A.n;
-        const float* xs = A.x + ((size_t)link * A.n + idx) * 3;
-        const float x0 = xs[0], x1 = xs[1], x2 = xs[2];
-        const float yv = A.y[(size_t)link * A.n + idx];
-        {
+        // ---- the batch: sample r of this step
+        const float x0 = nx0, x1 = nx1, x2 = nx2, yv = ny;
+        if (s + 1 < A.steps) load_sample(s + 1, nx0, nx1, nx2, ny);
+        if (grp == 0) {
             const float aux[8] = {x0, x1, x2, 1.f, 0.f, 0.f, 0.f, 0.f};
             const float zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            store_bf16x8(sAux, t, 0, kAuxCols, aux);
-            store_bf16x8(sAux, t, 8, kAuxCols, zero);
+            store_bf16x8(sAux, r, 0, kAuxCols, aux);
+            store_bf16x8(sAux, r, 8, kAuxCols, zero);
         }
         // ---- forward
-        layer1(small, x0, x1, x2, sH1, t);
+        layer1(small, x0, x1, x2, sH1, r, c0);
         sync_for_mma();
         if (t == 0) {
             mma_k128(tm + kTZ2, KMAJ(aH1), KMAJ(aW2), kN128KK);
             tc::mma_commit(&mbar);
         }
         if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
-        hidden_epilogue(lane_addr + kTZ2, b2, sH2, t);
+        hidden_epilogue(lane_addr + kTZ2, b2, sH2, r, c0);
         sync_for_mma();
         if (t == 0) {
             mma_k128(tm + kTZ3, KMAJ(aH2), KMAJ(aW3), kN128KK);
             tc::mma_commit(&mbar);
         }
         if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
-        // output layer and the loss gradient g = sign(f - y) / 128
-        float f = small[384 + 4 * kH];
-        for (int c0 = 0; c0 < kH; c0 += 32) {
+        // output layer: this warpgroup's share of f, then f and the loss gradient
+        // g = sign(f - y) / 128
+        {
             float v[32];
+            float fp = 0.f;
             tc::tmem_ld32(lane_addr + kTZ3 + c0, v);
 #pragma unroll
             for (int k = 0; k < 32; k += 8) {
@@ -317,19 +386,24 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
                 for (int e = 0; e < 8; ++e) {
                     const float z = v[k + e] + b3[c0 + k + e];
                     h[e] = z * silu_sigma(z);
-                    f = fmaf(w4[c0 + k + e], h[e], f);
+                    fp = fmaf(w4[c0 + k + e], h[e], fp);
                 }
-                store_bf16x8(sH3, t, c0 + k, kH, h);
+                store_bf16x8(sH3, r, c0 + k, kH, h);
             }
+            red_f[grp][r] = fp;
         }
-        const float r = f - yv;
-        const float g = r > 0.f ? (1.f / 128.f) : (r < 0.f ? -(1.f / 128.f) : 0.f);
-        {
+        __syncthreads();
+        float f = small[384 + 4 * kH];
+#pragma unroll
+        for (int q = 0; q < kTrainGroups; ++q) f += red_f[q][r];
+        const float res = f - yv;
+        const float g = res > 0.f ? (1.f / 128.f) : (res < 0.f ? -(1.f / 128.f) : 0.f);
+        if (grp == 0) {
             const float aux[8] = {x0, x1, x2, 1.f, g, 0.f, 0.f, 0.f};
-            store_bf16x8(sAux, t, 0, kAuxCols, aux);
+            store_bf16x8(sAux, r, 0, kAuxCols, aux);
         }
         // dz3 = g w4 s'(z3)
-        for (int c0 = 0; c0 < kH; c0 += 32) {
+        {
             float v[32];
             tc::tmem_ld32(lane_addr + kTZ3 + c0, v);
 #pragma unroll
@@ -341,19 +415,21 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
                     const float sg = silu_sigma(z);
                     d[e] = g * w4[c0 + k + e] * (sg * fmaf(z, 1.f - sg, 1.f));
                 }
-                store_bf16x8(sDZ, t, c0 + k, kH, d);
+                store_bf16x8(sDZ, r, c0 + k, kH, d);
             }
         }
-        // batch loss and db4 = sum g
-        float la = fabsf(r), lg = g;
+        // batch loss and db4 = sum g (warpgroup 0 holds one copy of each sample)
+        if (grp == 0) {
+            float la = fabsf(res), lg = g;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            la += __shfl_xor_sync(0xffffffffu, la, o);
-            lg += __shfl_xor_sync(0xffffffffu, lg, o);
-        }
-        if (lane == 0) {
-            red[0][warp] = la;
-            red[1][warp] = lg;
+            for (int o = 16; o > 0; o >>= 1) {
+                la += __shfl_xor_sync(0xffffffffu, la, o);
+                lg += __shfl_xor_sync(0xffffffffu, lg, o);
+            }
+            if (lane == 0) {
+                red[0][warp] = la;
+                red[1][warp] = lg;
+            }
         }
         sync_for_mma();
         if (t == 0) {
@@ -365,7 +441,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
         }
         if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
         // dz2 = dH2 s'(z2)
-        for (int c0 = 0; c0 < kH; c0 += 32) {
+        {
             float dh[32], zz[32];
             tc::tmem_ld32(lane_addr + kTZ3 + c0, dh);
             tc::tmem_ld32(lane_addr + kTZ2 + c0, zz);
@@ -378,7 +454,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
                     const float sg = silu_sigma(z);
                     d[e] = dh[k + e] * (sg * fmaf(z, 1.f - sg, 1.f));
                 }
-                store_bf16x8(sDZ, t, c0 + k, kH, d);
+                store_bf16x8(sDZ, r, c0 + k, kH, d);
             }
         }
         sync_for_mma();
@@ -388,9 +464,11 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
             mma_k128(tm + kTS2, MNMAJ(aDZ), AUXMN(aAux), kN16MM);    // db2 (column 3)
             tc::mma_commit(&mbar);
         }
+        // W3's update while these products run (they read neither W3 nor dW3)
+        if (!A.grad_out) adam_block(kTDW3, kOW3, sW3, s);
         if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
         // dz1 = dH1 s'(z1), z1 recomputed
-        for (int c0 = 0; c0 < kH; c0 += 32) {
+        {
             float dh[32];
             tc::tmem_ld32(lane_addr + kTZ2 + c0, dh);
 #pragma unroll
@@ -403,7 +481,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
                     const float sg = silu_sigma(z);
                     d[e] = dh[k + e] * (sg * fmaf(z, 1.f - sg, 1.f));
                 }
-                store_bf16x8(sDZ, t, c0 + k, kH, d);
+                store_bf16x8(sDZ, r, c0 + k, kH, d);
             }
         }
         sync_for_mma();
@@ -411,43 +489,46 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
             mma_k128(tm + kTS1, MNMAJ(aDZ), AUXMN(aAux), kN16MM);    // [dW1 db1] (columns 0..3)
             tc::mma_commit(&mbar);
         }
+        // W2's update while this product runs (it reads neither W2 nor dW2)
+        if (!A.grad_out) adam_block(kTZ3, kOW2, sW2, s);
         if (!(ok = wait_mma(&mbar, phase, A.wait_polls))) break;
         const float batch_loss = (red[0][0] + red[0][1] + red[0][2] + red[0][3]) * (1.f / 128.f);
         const float db4 = red[1][0] + red[1][1] + red[1][2] + red[1][3];
         loss_sum += batch_loss;
 
-        // ---- gradients of output unit o = t, then the update
-        const int o = t;
-        float s1[16], s2[16], s3[16], s4[16];
-        tc::tmem_ld16(lane_addr + kTS1, s1);
-        tc::tmem_ld16(lane_addr + kTS2, s2);
-        tc::tmem_ld16(lane_addr + kTS3, s3);
-        tc::tmem_ld16(lane_addr + kTS4, s4);
+        // ---- gradients of output unit o = r (W2/W3 inputs [c0, c0 + 32) here; the
+        // small parameters by warpgroup 0), then the update
+        const int o = r;
+        float s1[16], s2[16], s3[16], s4[16];   // the small parameters' gradient columns
+        auto load_small_grads = [&]() {
+            tc::tmem_ld16(lane_addr + kTS1, s1);
+            tc::tmem_ld16(lane_addr + kTS2, s2);
+            tc::tmem_ld16(lane_addr + kTS3, s3);
+            tc::tmem_ld16(lane_addr + kTS4, s4);
+        };
         if (A.grad_out) {
             float* G = A.grad_out;
-            for (int c0 = 0; c0 < kH; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(lane_addr + kTZ3 + c0, v);
-                for (int k = 0; k < 32; ++k) G[kOW2 + o * kH + c0 + k] = v[k];
-                tc::tmem_ld32(lane_addr + kTDW3 + c0, v);
-                for (int k = 0; k < 32; ++k) G[kOW3 + o * kH + c0 + k] = v[k];
+            float v[32];
+            tc::tmem_ld32(lane_addr + kTZ3 + c0, v);
+            for (int k = 0; k < 32; ++k) G[kOW2 + o * kH + c0 + k] = v[k];
+            tc::tmem_ld32(lane_addr + kTDW3 + c0, v);
+            for (int k = 0; k < 32; ++k) G[kOW3 + o * kH + c0 + k] = v[k];
+            if (grp == 0) {
+                load_small_grads();
+                G[kOW1 + 3 * o] = s1[0];
+                G[kOW1 + 3 * o + 1] = s1[1];
+                G[kOW1 + 3 * o + 2] = s1[2];
+                G[kOB1 + o] = s1[3];
+                G[kOB2 + o] = s2[3];
+                G[kOB3 + o] = s3[3];
+                G[kOW4 + o] = s4[4];
+                if (o == 0) G[kOB4] = db4;
             }
-            G[kOW1 + 3 * o] = s1[0];
-            G[kOW1 + 3 * o + 1] = s1[1];
-            G[kOW1 + 3 * o + 2] = s1[2];
-            G[kOB1 + o] = s1[3];
-            G[kOB2 + o] = s2[3];
-            G[kOB3 + o] = s3[3];
-            G[kOW4 + o] = s4[4];
-            if (o == 0) G[kOB4] = db4;
             break;   // gradient mode: one batch, no update
         }
-        // Adam (Kingma & Ba, Algorithm 1) on the master weights
+        // Adam on the small parameters
         const int tstep = A.step[link] + s + 1;
         const float bc1 = 1.f - powf(A.beta1, (float)tstep), bc2 = 1.f - powf(A.beta2, (float)tstep);
-        const float b1c = A.beta1, b2c = A.beta2, lr = A.lr, eps = A.eps;
-        float* M = A.adam_m + (size_t)link * kPar;
-        float* V = A.adam_v + (size_t)link * kPar;
         auto adam = [&](int i, float gr) -> float {
             const float m = fmaf(b1c, M[i], (1.f - b1c) * gr);
             const float v = fmaf(b2c, V[i], (1.f - b2c) * gr * gr);
@@ -457,58 +538,30 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
             P[i] = p;
             return p;
         };
-        // the 128 x 128 blocks: 32 columns at a time, their loads issued together
-        float* __restrict__ Pr = P;
-        float* __restrict__ Mr = M;
-        float* __restrict__ Vr = V;
-        for (int blk = 0; blk < 2; ++blk) {
-            const uint32_t col = blk == 0 ? kTZ3 : kTDW3;
-            const int base = blk == 0 ? kOW2 : kOW3;
-            uint8_t* tile = blk == 0 ? sW2 : sW3;
-            for (int c0 = 0; c0 < kH; c0 += 32) {
-                float gr[32], pm[32], pv[32], pp[32];
-                tc::tmem_ld32(lane_addr + col + c0, gr);
-#pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const int i = base + (c0 + e) * kH + o;
-                    pm[e] = Mr[i];
-                    pv[e] = Vr[i];
-                    pp[e] = Pr[i];
-                }
-#pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const int i = base + (c0 + e) * kH + o;
-                    const float m = fmaf(b1c, pm[e], (1.f - b1c) * gr[e]);
-                    const float v = fmaf(b2c, pv[e], (1.f - b2c) * gr[e] * gr[e]);
-                    const float p = pp[e] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
-                    Mr[i] = m;
-                    Vr[i] = v;
-                    Pr[i] = p;
-                    pp[e] = p;
-                }
-#pragma unroll
-                for (int k = 0; k < 32; k += 8) store_bf16x8(tile, o, c0 + k, kH, pp + k);
-            }
-        }
         float nw[7];
-        nw[0] = adam(kOW1 + 3 * o, s1[0]);
-        nw[1] = adam(kOW1 + 3 * o + 1, s1[1]);
-        nw[2] = adam(kOW1 + 3 * o + 2, s1[2]);
-        nw[3] = adam(kOB1 + o, s1[3]);
-        nw[4] = adam(kOB2 + o, s2[3]);
-        nw[5] = adam(kOB3 + o, s3[3]);
-        nw[6] = adam(kOW4 + o, s4[4]);
         float nb4 = 0.f;
-        if (o == 0) nb4 = adam(kOB4, db4);
+        if (grp == 0) {
+            load_small_grads();
+            nw[0] = adam(kOW1 + 3 * o, s1[0]);
+            nw[1] = adam(kOW1 + 3 * o + 1, s1[1]);
+            nw[2] = adam(kOW1 + 3 * o + 2, s1[2]);
+            nw[3] = adam(kOB1 + o, s1[3]);
+            nw[4] = adam(kOB2 + o, s2[3]);
+            nw[5] = adam(kOB3 + o, s3[3]);
+            nw[6] = adam(kOW4 + o, s4[4]);
+            if (o == 0) nb4 = adam(kOB4, db4);
+        }
         __syncthreads();   // every thread is done reading the small parameters of this step
-        small[3 * o] = nw[0];
-        small[3 * o + 1] = nw[1];
-        small[3 * o + 2] = nw[2];
-        small[384 + o] = nw[3];
-        small[384 + kH + o] = nw[4];
-        small[384 + 2 * kH + o] = nw[5];
-        small[384 + 3 * kH + o] = nw[6];
-        if (o == 0) small[384 + 4 * kH] = nb4;
+        if (grp == 0) {
+            small[3 * o] = nw[0];
+            small[3 * o + 1] = nw[1];
+            small[3 * o + 2] = nw[2];
+            small[384 + o] = nw[3];
+            small[384 + kH + o] = nw[4];
+            small[384 + 2 * kH + o] = nw[5];
+            small[384 + 3 * kH + o] = nw[6];
+            if (o == 0) small[384 + 4 * kH] = nb4;
+        }
         // the next step reads the new small parameters; its first MMA is preceded by
         // sync_for_mma, which publishes the rewritten weight tiles to the tensor core
         __syncthreads();
@@ -529,7 +582,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __grid_constant
 // ------------------------------------------------------------------ evaluation
 
 struct EvalArgs {
-    const float* master;               // [L][kPar]
+    const float* master;               // [L][kParStride]
     const float* x3;                   // n x 3 normalised points
     int L;
     int n;                             // queries of link `link0`
@@ -688,7 +741,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) mlp_eval_kernel(const __grid_
     const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH = tc::smem_u32(sH);
     uint32_t phase = 0;
     bool ok = true;
-    load_weights<true>(A.master + (size_t)A.link0 * kPar, sW2, sW3, small, t, kEvalThreads);
+    load_weights<true>(A.master + (size_t)A.link0 * kParStride, sW2, sW3, small, t, kEvalThreads);
     tc::fence_smem_to_async();   // the weights are MMA operands
     __syncthreads();
     for (int tl = first + pipe; tl < last; tl += kEvalPipes) {
@@ -897,7 +950,7 @@ static_assert(kImgBytes % 16 == 0, "16-byte copies");
 
 __global__ void __launch_bounds__(512) weight_image_kernel(const float* __restrict__ master, uint8_t* image) {
     uint8_t* img = image + (size_t)blockIdx.x * kImgBytes;
-    load_weights<true>(master + (size_t)blockIdx.x * kPar, img, img + kTileBytes,
+    load_weights<true>(master + (size_t)blockIdx.x * kParStride, img, img + kTileBytes,
                  reinterpret_cast<float*>(img + 2 * kTileBytes), threadIdx.x, blockDim.x);
 }
 
@@ -1383,6 +1436,7 @@ namespace {
 
 using sdf::kH;
 using sdf::kPar;
+using sdf::kParStride;
 
 int sfail(sdf_ctx* ctx, int code, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -1463,14 +1517,14 @@ int sdf_surrogate_create(sdf_ctx* ctx, const sdf_grids* grids, const float* para
     S->device = ctx->device;
     S->L = grids->n_links;
     S->grids = grids;
-    const size_t bytes = sizeof(float) * (size_t)kPar * S->L;
+    const size_t bytes = sizeof(float) * (size_t)kParStride * S->L;
     cudaError_t e = sdf::dmalloc(&S->master, bytes);
     if (e == cudaSuccess) e = sdf::dmalloc(&S->adam_m, bytes);
     if (e == cudaSuccess) e = sdf::dmalloc(&S->adam_v, bytes);
     if (e == cudaSuccess) e = sdf::dmalloc(&S->step, sizeof(int) * S->L);
     if (e == cudaSuccess) e = sdf::dmalloc(&S->loss, sizeof(float) * S->L);
-    std::vector<float> dev((size_t)kPar * S->L);
-    for (int l = 0; l < S->L; ++l) to_device_layout(params_host + (size_t)l * kPar, dev.data() + (size_t)l * kPar);
+    std::vector<float> dev((size_t)kParStride * S->L, 0.f);
+    for (int l = 0; l < S->L; ++l) to_device_layout(params_host + (size_t)l * kPar, dev.data() + (size_t)l * kParStride);
     if (e == cudaSuccess) e = cudaMemcpy(S->master, dev.data(), bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(S->adam_m, 0, bytes);
     if (e == cudaSuccess) e = cudaMemset(S->adam_v, 0, bytes);
@@ -1504,11 +1558,11 @@ void sdf_surrogate_destroy(sdf_surrogate* S) {
 int sdf_surrogate_params(sdf_ctx* ctx, const sdf_surrogate* S, float* params_host) {
     if (!ctx || !S || !params_host) return sfail(ctx, SDF_ERR_INVALID_ARG, "sdf_surrogate_params: null");
     Dev guard(S->device);
-    std::vector<float> dev((size_t)kPar * S->L);
+    std::vector<float> dev((size_t)kParStride * S->L);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpy(dev.data(), S->master, dev.size() * sizeof(float), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return scuda(ctx, e, "sdf_surrogate_params");
-    for (int l = 0; l < S->L; ++l) to_public_layout(dev.data() + (size_t)l * kPar, params_host + (size_t)l * kPar);
+    for (int l = 0; l < S->L; ++l) to_public_layout(dev.data() + (size_t)l * kParStride, params_host + (size_t)l * kPar);
     return SDF_OK;
 }
 
@@ -1593,7 +1647,7 @@ int launch_train(sdf_ctx* ctx, sdf_surrogate* S, int link0, int links, const flo
     A.loss_out = loss_out;
     A.status = ctx->status;
     A.wait_polls = ctx->wait_polls;
-    sdf::mlp_train_kernel<<<links, 128, sdf::kTrainSmem, ctx->stream>>>(A);
+    sdf::mlp_train_kernel<<<links, sdf::kTrainThreads, sdf::kTrainSmem, ctx->stream>>>(A);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SDF_OK : scuda(ctx, e, "mlp_train_kernel");
 }
