@@ -1138,8 +1138,12 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
         const int ng = seed ? n_seed_groups : A.n_groups;
         const int gsz = seed ? A.seed_group : A.group;
         const int l = rem / ng, g = rem % ng;
-        const int w0 = g * gsz;
-        const int nw = min(gsz, A.W - w0);
+        // a seed item takes gsz consecutive waypoints; a cull item takes waypoints g,
+        // g + ng, g + 2 ng, ...: heavy waypoints come in runs along a trajectory, and
+        // spreading each run over many items evens out the items' work
+        const int w0 = seed ? g * gsz : g;
+        const int w_step = seed ? 1 : ng;
+        const int nw = seed ? min(gsz, A.W - w0) : (A.W - g + ng - 1) / ng;
         if (l != loaded) {
             load_image(A.image + (size_t)l * kImgBytes, sm + kSurImg, t, kEvalThreads);
             tc::fence_smem_to_async();   // the weights are MMA operands
@@ -1147,7 +1151,8 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
         }
         // the group's poses and world capsules of link l
         if (warp < nw) {
-            const float4* P = reinterpret_cast<const float4*>(A.poses + ((size_t)(w0 + warp) * A.L + l) * 16);
+            const float4* P =
+                reinterpret_cast<const float4*>(A.poses + ((size_t)(w0 + warp * w_step) * A.L + l) * 16);
             const float4 M0 = P[0], M1 = P[1], M2 = P[2];
             if (lane == 0) {
                 s_M[warp][0] = M0;
@@ -1167,7 +1172,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 s_cA[warp] = make_float4(Ax, Ay, Az, a.w);
                 s_cD[warp] = make_float4(dx, dy, dz, dd > 0.f ? 1.f / dd : 0.f);
                 // cull items start from the minimum over every link published so far
-                s_key[warp] = seed ? ~0ull : A.keys[w0 + warp];
+                s_key[warp] = seed ? ~0ull : A.keys[w0 + warp * w_step];
             }
         }
         if (t == 0) {
@@ -1345,8 +1350,8 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
         }
         // publish the group's minima (and the waypoints whose list overflowed)
         if (t < nw) {
-            if (s_key[t] != ~0ull) atomicMin(&A.keys[w0 + t], s_key[t]);
-            if (s_over & (1u << t)) A.recheck[w0 + t] = 1;
+            if (s_key[t] != ~0ull) atomicMin(&A.keys[w0 + t * w_step], s_key[t]);
+            if (s_over & (1u << t)) A.recheck[w0 + t * w_step] = 1;
         }
     }
     if (A.stats) {
