@@ -1010,6 +1010,10 @@ struct SurFusedArgs {
     uint8_t* recheck;                 // [W] 1 where a list overflowed (zeroed before the launch)
     int* work;                        // item counter (zeroed before the launch)
     float slack;                      // error bound of the surrogate + rounding slack
+    float decided_below;              // a waypoint whose minimum so far is below this (margin +
+                                      // error bound) is decided by the grid re-check, whatever
+                                      // its final surrogate minimum: its culls stop (-inf: never,
+                                      // when the caller wants the surrogate minimum itself)
     int* status;
     uint32_t wait_polls;
     unsigned long long* stats;        // statistics counters or null
@@ -1144,6 +1148,15 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
         const int w0 = seed ? g * gsz : g;
         const int w_step = seed ? 1 : ng;
         const int nw = seed ? min(gsz, A.W - w0) : (A.W - g + ng - 1) / ng;
+        if (!seed && A.decided_below > -INFINITY) {
+            // a cull item whose waypoints are all decided by the grid re-check adds nothing
+            bool open = false;
+            if (t < nw) {
+                const unsigned long long k = __ldcg(&A.keys[w0 + t * w_step]);
+                open = !(k != ~0ull && from_ordered((unsigned)(k >> 32)) < A.decided_below);
+            }
+            if (!__syncthreads_or(open)) continue;
+        }
         if (l != loaded) {
             load_image(A.image + (size_t)l * kImgBytes, sm + kSurImg, t, kEvalThreads);
             tc::fence_smem_to_async();   // the weights are MMA operands
@@ -1235,7 +1248,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
             if (t < nw) {
                 const unsigned long long k = s_key[t];
                 const float best = k == ~0ull ? INFINITY : from_ordered((unsigned)(k >> 32));
-                s_thr[t] = best + A.slack + s_cA[t].w;
+                s_thr[t] = best < A.decided_below ? -INFINITY : best + A.slack + s_cA[t].w;
             }
             __syncthreads();
             // list: (waypoint slot, tile) entries whose tile sphere reaches the threshold
@@ -1335,7 +1348,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 if (t < nw) {
                     const unsigned long long k = s_key[t];
                     const float best = k == ~0ull ? INFINITY : from_ordered((unsigned)(k >> 32));
-                    s_thr[t] = fminf(s_thr[t], best + A.slack + s_cA[t].w);
+                    s_thr[t] = best < A.decided_below ? -INFINITY : fminf(s_thr[t], best + A.slack + s_cA[t].w);
                 }
                 __syncthreads();
                 if (t < left) {
@@ -1799,8 +1812,9 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
         A.seed_group = sdf::kSurGroup;
         A.keys = ctx->sur_keys;
         A.recheck = ctx->sur_mask;
-        A.work = ctx->sur_count;
         A.slack = eps + sdf::kCullSlack;
+        A.decided_below = surrogate_dist_dev ? -INFINITY : margin + eps;
+        A.work = ctx->sur_count;
         A.status = ctx->status;
         A.wait_polls = ctx->wait_polls;
         A.stats = ctx->stats ? ctx->d_stats : nullptr;
