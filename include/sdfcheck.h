@@ -142,7 +142,9 @@ const char* sdf_last_error(const sdf_ctx* ctx);
 #define SDF_OPT_SORT_CTAS 11     /* CTAs of the thread-block cluster that sorts each cloud: 8
                                      (the portable cluster size), 16 (a non-portable size;
                                      SDF_ERR_UNSUPPORTED where the device cannot place it), or
-                                     0 (default) = 16 where the device can place it, else 8.
+                                     0 (default) = the width sdf_autotune picked for the
+                                     launch shape, else 16 where the device can place it,
+                                     else 8.
                                      The sorted order and every result are the same either
                                      way; a wider cluster gives each CTA fewer points.  Get
                                      returns the size in use. */
@@ -318,10 +320,11 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* requests, int32_t n);
 
 /* Autotuner: times every launch shape (waypoints per block 1..16/links x list
  * entries per warp step 2, 4, 8) on these requests, `repeats` runs each (median,
- * caches warm), and remembers the fastest for launches of the same shape -- the
+ * caches warm), then the width of the sort's cluster (8 or 16, where the device
+ * allows 16) at the fastest shape, and remembers the best for launches of the same shape -- the
  * request count, the largest link count and the power-of-two buckets of the total
  * waypoints and points.  Later check_trajectory / check_batch calls of that shape
- * use it unless SDF_OPT_WAYPOINTS_PER_BLOCK / SDF_OPT_TILE_BATCH are set.  Runs the
+ * use it unless SDF_OPT_WAYPOINTS_PER_BLOCK / SDF_OPT_TILE_BATCH / SDF_OPT_SORT_CTAS are set.  Runs the
  * checks (their outputs are overwritten) and synchronises.  Outputs may be NULL. */
 int sdf_autotune(sdf_ctx* ctx, const sdf_check_request* requests, int32_t n, int32_t repeats,
                  int32_t* best_waypoints_per_block, int32_t* best_tile_batch, float* best_us);

@@ -952,6 +952,10 @@ int check_batch(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n) {
     p->status = ctx->status;
     p->wait_polls = ctx->wait_polls;
     p->sort_ctas = ctx->sort_ctas;
+    if (p->sort_ctas == 0) {   // the tuned width for this launch shape, else the widest
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) p->sort_ctas = it->second.sort;
+    }
     p->stats = ctx->stats ? ctx->d_stats : nullptr;
     cudaError_t e = cudaSuccess;
     if (ctx->time_kernels) e = cudaEventRecord(ctx->ev0, ctx->stream);
@@ -978,7 +982,7 @@ int sdf_autotune(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n, int32_t
     DeviceGuard g(ctx->device);
     const uint64_t key = shape_key(reqs, n);
     const int save_tw = ctx->tw, save_tb = ctx->tile_batch, save_time = ctx->time_kernels,
-              save_nw = ctx->block_warps;
+              save_nw = ctx->block_warps, save_sort = ctx->sort_ctas;
     ctx->time_kernels = 0;
     ctx->tuned.erase(key);
     cudaEvent_t a = nullptr, b = nullptr;
@@ -1020,14 +1024,44 @@ int sdf_autotune(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n, int32_t
         }
       }
     }
+    // the sort's cluster width at the best shape: 8, and 16 where the device allows it
+    int bsort = 0;
+    if (rc == SDF_OK && sdf::max_sort_ctas(ctx->device) == 16) {
+        ctx->tw = btw;
+        ctx->tile_batch = btb;
+        ctx->block_warps = bnw;
+        float best_sort = INFINITY;
+        for (int width : {16, 8}) {
+            ctx->sort_ctas = width;
+            rc = check_batch(ctx, reqs, n);
+            std::vector<float> ms;
+            for (int r = 0; r < repeats && rc == SDF_OK; ++r) {
+                cudaEventRecord(a, ctx->stream);
+                rc = check_batch(ctx, reqs, n);
+                cudaEventRecord(b, ctx->stream);
+                float t = 0.f;
+                if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess) rc = SDF_ERR_CUDA;
+                ms.push_back(t);
+            }
+            if (rc != SDF_OK) break;
+            std::nth_element(ms.begin(), ms.begin() + ms.size() / 2, ms.end());
+            const float med = ms[ms.size() / 2];
+            if (med < best_sort) {
+                best_sort = med;
+                bsort = width;
+            }
+        }
+        if (rc == SDF_OK) best = std::min(best, best_sort);
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     ctx->tw = save_tw;
     ctx->tile_batch = save_tb;
     ctx->time_kernels = save_time;
     ctx->block_warps = save_nw;
+    ctx->sort_ctas = save_sort;
     if (rc != SDF_OK) return rc;
-    ctx->tuned[key] = sdf_ctx::Shape{btw, btb, bnw};
+    ctx->tuned[key] = sdf_ctx::Shape{btw, btb, bnw, bsort};
     drop_host_graphs(ctx);
     if (best_tw) *best_tw = btw;
     if (best_tile_batch) *best_tile_batch = btb;

@@ -195,8 +195,9 @@ struct sdf_ctx {
     int tex3d = 0;                         // lookups by the texture unit's trilinear filter
     int sort_ctas = 0;                     // CTAs of the sort's cluster (SDF_OPT_SORT_CTAS)
     unsigned wait_polls = sdf::kDefaultWaitPolls;  // polls of a bounded device wait (SDF_OPT_WAIT_POLLS)
-    struct Shape { int tw, tb, nw; };
-    std::map<uint64_t, Shape> tuned;       // launch shape key -> (waypoints per block, tile batch, warps)
+    struct Shape { int tw, tb, nw, sort; };
+    std::map<uint64_t, Shape> tuned;       // launch shape key -> (waypoints per block, tile batch, warps,
+                                           // CTAs of the sort's cluster)
     // scratch owned by the context (grown on demand, or up front by sdf_ctx_reserve)
     float4* sorted = nullptr;
     size_t sorted_cap = 0;

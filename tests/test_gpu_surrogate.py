@@ -251,6 +251,18 @@ def test_surrogate_check_with_trained_network_and_fallback(sdf, env):
     assert 0 < sel.sum() < len(q)
     assert np.all(np.abs(d[~sel] - g[0][~sel]) <= eps)
     print("eps", eps, "rechecked", int(sel.sum()), "of", len(q))
+    # without the surrogate-minimum output, waypoints already below margin + eps stop
+    # being refined: every output must stay bit-identical
+    W, N = len(q), len(pts)
+    d2 = torch.full((W,), 7.0, dtype=torch.float32, device="cuda")
+    l2 = torch.full((W,), -7, dtype=torch.int32, device="cuda")
+    p2 = torch.full((W,), -7, dtype=torch.int32, device="cuda")
+    r2 = torch.full((W,), 9, dtype=torch.uint8, device="cuda")
+    sdf.check_trajectory_surrogate(ctx, robot, sur, _dev(q), W, _dev(pts), N, margin, eps, d2, l2, p2, r2)
+    assert ctx.synchronize() == 0
+    assert np.array_equal(d2.cpu().numpy().view(np.uint32), d.view(np.uint32))
+    assert np.array_equal(l2.cpu().numpy(), l) and np.array_equal(p2.cpu().numpy(), p)
+    assert np.array_equal(r2.cpu().numpy(), rech)
 
 
 def test_surrogate_check_empty_cloud(sdf, env):
