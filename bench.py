@@ -93,22 +93,32 @@ def scene_for(args):
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) taken while the timed loop runs."""
+    """nvidia-smi samples (every 20 ms), each stamped with the host clock on arrival.
+    mark_start() / mark_end() bracket the timed loop; the summary keeps the samples
+    inside that window (all of them, flagged, if none arrived inside it)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, interval_ms: int = 20):
         self.index = index
+        self.interval_ms = interval_ms
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -117,7 +127,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def stop(self):
         if not self.proc:
@@ -129,7 +139,13 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        in_window = False
+        if self.t0 is not None and self.t1 is not None:
+            inside = [x for x in lines if self.t0 <= x[0] <= self.t1]
+            if inside:
+                lines, in_window = inside, True
+        for _, ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -142,7 +158,9 @@ class ClockSampler:
                 if val.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "samples_in_timed_window": in_window,
+                "interval_ms": self.interval_ms,
+                "window_s": (self.t1 - self.t0) if self.t0 is not None and self.t1 is not None else None}
 
 
 # ----------------------------------------------------------------- helpers
@@ -358,12 +376,14 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    clocks.mark_start()
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
+    clocks.mark_end()
     clk = clocks.stop()
     if ws > 1:
         torch.distributed.barrier()
@@ -600,12 +620,15 @@ def batched_measurement(args, dev, local, steps, warmup, clocks=None):
     if clocks:
         clocks.start()
         time.sleep(0.3)
+        clocks.mark_start()
     for i in range(steps):
         flush.zero_()
         ev[i][0].record(main)
         graph.replay()
         ev[i][1].record(main)
     torch.cuda.synchronize(dev)
+    if clocks:
+        clocks.mark_end()
     clk = clocks.stop() if clocks else None
     step_us = [x.elapsed_time(y) * 1e3 for x, y in ev]
     if ctx.synchronize() != 0:
@@ -721,9 +744,11 @@ def run_serve(args):
     def measure(rate=None):
         run_cycles(50, 0, rate)
         srv.stats(reset=True)
-        clocks = ClockSampler(local)
+        clocks = ClockSampler(local, interval_ms=200)
         clocks.start()
+        clocks.mark_start()
         wall, late = run_cycles(cycles, 50, rate)
+        clocks.mark_end()
         clk = clocks.stop()
         return srv.stats(reset=True), wall, late, clk
 
@@ -893,9 +918,11 @@ def run_surrogate(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    clocks.mark_start()
     sur_us = timed(sur_step, args.steps)
     full_us = timed(sur_step_full, args.steps)
     grid_us = timed(grid_step, args.steps)
+    clocks.mark_end()
     clk = clocks.stop()
     if ctx.synchronize() != 0:
         raise RuntimeError(f"checks failed: {ctx.last_error()}")
@@ -1005,9 +1032,12 @@ def run_robot_sdf(args):
 
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(0.3)
+    clocks.mark_start()
     rs_us = timed(lambda: sdf.check_trajectory_robot_sdf(ctx, robot, lo, voxel, dims, reach, q, W, pts, N, d, v),
                   args.steps)
     pt_us = timed(lambda: sdf.check_trajectory(ctx, robot, q, W, pts, N, *g_out), args.steps)
+    clocks.mark_end()
     clk = clocks.stop()
     if ctx.synchronize() != 0:
         raise RuntimeError(f"checks failed: {ctx.last_error()}")
