@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--order", default="voxel", choices=["voxel", "random"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="paper: skip the 64-request batched measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="paper: skip the brief surrogate and serving measurements in the default line")
+    ap.add_argument("--serve-s", type=float, default=5.0, help="paper: seconds of the brief serving run")
     ap.add_argument("--e2e-steps", type=int, default=100)
     return ap.parse_args()
 
@@ -559,6 +562,32 @@ def run_ours(args):
         b.pop("step_us")
         b.pop("clocks")
         out["batched"] = b
+    if ws == 1 and scene.name == "paper" and not args.no_extras:
+        # configs 4 and 5 in brief, so that the default line carries them: the
+        # surrogate form of this check (training included) and a short serving run
+        sa = argparse.Namespace(**vars(args))
+        sa.steps = max(20, min(args.steps, 200))
+        sa.warmup = max(args.warmup, 3)
+        sr = run_surrogate(sa, emit=False)
+        out["surrogate"] = {
+            "metric": sr["metric"], "p50_us": sr["p50_us"], "p99_us": sr["p99_us"], "unit": sr["unit"],
+            "with_surrogate_minimum": {k: sr["with_surrogate_minimum"][k] for k in ("p50_us", "p99_us",
+                                                                                  "outputs_identical")},
+            "grid_form_p50_us": sr["grid_form"]["p50_us"], "rechecked_waypoints": sr["rechecked_waypoints"],
+            "fallback_exact": sr["fallback_exact"], "eps_m": sr["eps_m"], "train_s": sr["train_s"],
+            "train_steps": sr["config"]["train_steps"], "samples_per_link": sr["config"]["samples_per_link"],
+            "network_queries": sr["network_queries"], "steps": sa.steps, "clocks": sr["clocks"],
+            "workload": sr["config"]["workload"]}
+        va = argparse.Namespace(**vars(args))
+        va.duration = args.serve_s
+        va.forms = "grid"
+        va.rates = ""
+        vr = run_serve(va, emit=False)
+        out["serving"] = {
+            "metric": vr["metric"], "p50_us": vr["p50_us"], "p99_us": vr["p99_us"], "mean_us": vr["mean_us"],
+            "checks_per_s": vr["checks_per_s"], "completed": vr["completed"], "late_cycles": vr["late_cycles"],
+            "cycles": vr["config"]["cycles"], "mean_batch": vr["mean_batch"], "clocks": vr["clocks"],
+            "workload": vr["config"]["workload"]}
     if ws == 1 and not args.no_cpu_baseline:
         vals, metas = oracle_grids(scene)
         us, reps, cores, sample = time_oracle(scene, vals, metas)
@@ -690,17 +719,18 @@ def run_batched(args):
 SERVE_METRIC = "request latency p50/p99 (µs, submit to results in host memory) at 125 Hz; checks/s"
 
 
-def run_serve(args):
+def run_serve(args, emit=True):
     """A 125 Hz control-cycle stream: every cycle publishes a new cloud (5k-80k
     points, drifting human clusters) and submits Poisson(rate) trajectories of
-    100-1000 waypoints; the serving engine batches them as they arrive."""
+    100-1000 waypoints; the serving engine batches them as they arrive.  Prints the
+    JSON line, or (emit=False) returns it."""
     import torch
     import paper_2309_12543_gb300 as sdf
     import scenegen
     from paper_2309_12543_gb300 import build as pkg_build
 
     ws, rank, local = dist_env()
-    if ws > 1:
+    if ws > 1 and not torch.distributed.is_initialized():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -800,6 +830,8 @@ def run_serve(args):
         "form": "grid" if "grid" in forms else "surrogate", "surrogate_form": sur_form, "rate_sweep": sweep,
         "clocks": clk,
     }
+    if not emit:
+        return out
     print(json.dumps(out), flush=True)
 
 
@@ -810,17 +842,18 @@ MLP_FLOPS_PER_QUERY = 2 * (3 * 128 + 2 * 128 * 128 + 128)
 SUR_METRIC = "µs per 500-waypoint×20k-point check, learned surrogate with grid fallback (p50/p99)"
 
 
-def run_surrogate(args):
+def run_surrogate(args, emit=True):
     """Train the per-link surrogates of the paper scene on the GPU, bound their error
     against the grid, and time the surrogate form of the check (with its grid
-    fallback) beside the grid form on the same 500 x 20k workload."""
+    fallback) beside the grid form on the same 500 x 20k workload.  Prints the JSON
+    line, or (emit=False) returns it."""
     import torch
     import paper_2309_12543_gb300 as sdf
     import scenegen
     from paper_2309_12543_gb300 import build as pkg_build
 
     ws, rank, local = dist_env()
-    if ws > 1:
+    if ws > 1 and not torch.distributed.is_initialized():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -958,7 +991,7 @@ def run_surrogate(args):
                     "the grid re-check decides; network_queries and fused_kernel_phases_us are this call's"},
         "network_queries": {"seed": st["sur_seed_queries"], "after_cull": st["sur_queries"],
                             "flops_per_query": MLP_FLOPS_PER_QUERY,
-                            "tflops_over_the_check": queries * MLP_FLOPS_PER_QUERY / (percentile(sur_us, 50) * 1e-6) / 1e12},
+                            "tflops_over_the_check": queries * MLP_FLOPS_PER_QUERY / (percentile(full_us, 50) * 1e-6) / 1e12},
         "fused_kernel_phases_us": sur_phases(st, torch.cuda.get_device_properties(dev).multi_processor_count),
         "rechecked_waypoints": int(r.sum()), "fallback_exact": exact, "max_diff_where_surrogate_decided_m": within,
         "eps_m": eps, "errors": errs, "equal_memory_grid_32": coarse_err,
@@ -967,6 +1000,8 @@ def run_surrogate(args):
         "sample_s": sample_s, "train_s": train_s, "final_loss_per_link": final_loss,
         "clocks": clk,
     }
+    if not emit:
+        return res
     print(json.dumps(res), flush=True)
 
 
