@@ -106,7 +106,7 @@ const char* sdf_last_error(const sdf_ctx* ctx);
 #define SDF_OPT_CULL 1            /* 1 (default): bounding-sphere culling; 0: evaluate every pair */
 #define SDF_OPT_POINT_STRIDE 2    /* floats per point: 3 (default, x y z) or 4 (x y z pad)       */
 #define SDF_OPT_WAYPOINTS_PER_BLOCK 3 /* waypoints per check block, 1..16; 0 (default) = tuned or 16 / links */
-#define SDF_OPT_TILE_BATCH 4      /* list entries per warp step: 2, 4 or 8; 0 (default) = tuned or 4  */
+#define SDF_OPT_TILE_BATCH 4      /* list entries per warp step: 1, 2 or 4; 0 (default) = tuned or 1  */
 #define SDF_OPT_TIME_KERNELS 6    /* 1: record CUDA events around the two kernels of a check      */
 #define SDF_OPT_STATS 7           /* 1: count culls/lookups and time kernel phases (adds atomics)  */
 #define SDF_OPT_BLOCK_WARPS 8     /* warps per check block, 8 or 16 (0 = tuned, else 8 when the
@@ -135,7 +135,7 @@ const char* sdf_last_error(const sdf_ctx* ctx);
                                      check of a grids object with the option on makes its
                                      texture copy (n^3 FP32 per link; allocates and
                                      synchronises); sdf_grids_destroy frees it.  The texture
-                                     form is its own kernel and always takes 4 list entries
+                                     form is its own kernel and always takes 2 list entries
                                      per warp step (SDF_OPT_TILE_BATCH does not apply); every
                                      request of one launch must use the same grids object
                                      (else SDF_ERR_UNSUPPORTED). */
@@ -319,7 +319,7 @@ typedef struct {
 int check_batch(sdf_ctx* ctx, const sdf_check_request* requests, int32_t n);
 
 /* Autotuner: times every launch shape (waypoints per block 1..16/links x list
- * entries per warp step 2, 4, 8) on these requests, `repeats` runs each (median,
+ * entries per warp step 1, 2, 4) on these requests, `repeats` runs each (median,
  * caches warm), then the width of the sort's cluster (8 or 16, where the device
  * allows 16) at the fastest shape, and remembers the best for launches of the same shape -- the
  * request count, the largest link count and the power-of-two buckets of the total

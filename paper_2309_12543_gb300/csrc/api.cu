@@ -177,8 +177,8 @@ int sdf_ctx_set_option(sdf_ctx* ctx, int32_t key, int64_t v) {
             ctx->tw = (int)v;
             return SDF_OK;
         case SDF_OPT_TILE_BATCH:
-            if (v != 0 && v != 2 && v != 4 && v != 8)
-                return fail(ctx, SDF_ERR_INVALID_ARG, "tile batch must be 0, 2, 4 or 8");
+            if (v != 0 && v != 1 && v != 2 && v != 4)
+                return fail(ctx, SDF_ERR_INVALID_ARG, "tile batch must be 0, 1, 2 or 4");
             ctx->tile_batch = (int)v;
             return SDF_OK;
         case SDF_OPT_TIME_KERNELS: ctx->time_kernels = v ? 1 : 0; return SDF_OK;
@@ -990,7 +990,7 @@ int sdf_autotune(sdf_ctx* ctx, const sdf_check_request* reqs, int32_t n, int32_t
     SDF_CUDA(ctx, cudaEventCreate(&b));
     float best = INFINITY;
     int btw = 0, btb = 0, bnw = 16, rc = SDF_OK;
-    const int tbs[3] = {2, 4, 8};
+    const int tbs[3] = {1, 2, 4};
     int Lmax = 1;
     for (int i = 0; i < n; ++i)
         if (reqs[i].W > 0) Lmax = std::max(Lmax, reqs[i].robot->table.L);

@@ -724,12 +724,44 @@ __device__ __forceinline__ void test_tiles(const BatchParams& P, const BlockStat
     }
 }
 
+// Point tests of up to TB listed tiles against every pair whose capsule reached them
+// (mask[t]: one bit per pair of the block), each tile's points loaded once and the
+// TB loads issued together.  The masks are read by every lane alike, so the loop
+// over a tile's pairs is uniform across the warp.
+template <int TB, bool TEX>
+__device__ __forceinline__ void test_tile_groups(const BatchParams& P, const BlockState& B, WarpQueue& Q,
+                                                 const unsigned (&ent)[TB], int cnt, const unsigned* mask,
+                                                 int lane) {
+    float4 pt[TB];
+    int pos[TB];
+    unsigned mk[TB];
+#pragma unroll
+    for (int k = 0; k < TB; ++k) {
+        pos[k] = (int)ent[k] * 32 + lane;
+        pt[k] = (k < cnt && pos[k] < B.n_valid) ? __ldg(&B.sorted[pos[k]]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        mk[k] = k < cnt ? mask[ent[k]] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < TB; ++k) {
+        unsigned m = mk[k];
+        while (m) {
+            const int pair = __ffs(m) - 1;
+            m &= m - 1;
+            const float thr = pair_threshold(B, pair);
+            const bool surv = pos[k] < B.n_valid && thr >= 0.f &&
+                              seg_dist2(pt[k].x, pt[k].y, pt[k].z, B.pose[pair][4], B.pose[pair][5]) <= thr * thr;
+            if (B.stat) stat_add(B, kWsPointT, (unsigned)__popc(__ballot_sync(kFull, pos[k] < B.n_valid)), lane);
+            queue_push<TEX>(P, B, Q, surv, pos[k], pair, lane);
+        }
+    }
+}
+
 // TB: list entries a warp takes per step in phase B (their point loads go out together).
 // NW: warps per block (8 or 16); at 64 registers a thread, 32 / NW blocks fit an SM.
 // TEX: lookups by the texture unit's trilinear filter (SDF_OPT_TEX3D).
 template <int TB, int NW, bool TEX>
 __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_constant__ BatchParams P) {
-    extern __shared__ float4 s_spheres[];            // tiles [stage_tiles], then super-tiles
+    extern __shared__ float4 s_spheres[];            // tiles [stage_tiles], then super-tiles, then pair masks
     __shared__ float4 s_pose[NW][6];
     __shared__ uchar2 s_pair_wl[NW];
     __shared__ float4 s_grid_o[kMaxLinks];
@@ -787,6 +819,9 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
         s_list_n = 0u;
         s_list_next = 0u;
     }
+    // staged launches: per tile, the bits of the pairs whose capsule reaches it
+    unsigned* s_mask = reinterpret_cast<unsigned*>(s_spheres + P.stage_tiles + P.stage_tiles / 32 + 1);
+    for (int i = tid; i < P.stage_tiles; i += NW * 32) s_mask[i] = 0u;
 
     // phase A.1: forward kinematics, one warp per waypoint (before the sort is
     // waited for); lane j writes link j's pose
@@ -961,6 +996,11 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
                 }
                 const unsigned na = (unsigned)__popc(mta);
                 if (!(mta | mtb)) continue;
+                if (staged) {   // the pair's bit in each reached tile's mask (no list, no overflow)
+                    if (ra) atomicOr(&s_mask[ta], 1u << warp);
+                    if (rb) atomicOr(&s_mask[tb], 1u << warp);
+                    continue;
+                }
                 unsigned base = 0;
                 if (lane == 0) base = atomicAdd(&s_list_n, na + (unsigned)__popc(mtb));
                 base = __shfl_sync(kFull, base, 0);
@@ -992,23 +1032,56 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     const unsigned long long t_b0 = stats ? global_ns() : 0ull;
 
     // phase B: every warp takes list entries a few at a time
-    const unsigned n_list = min(s_list_n, (unsigned)kBlockList);
-    for (;;) {
-        unsigned k0 = 0;
-        if (lane == 0) k0 = atomicAdd(&s_list_next, (unsigned)TB);
-        k0 = __shfl_sync(kFull, k0, 0);
-        if (k0 >= n_list) break;
-        unsigned ent[TB];
-        int cnt = 0;
+    auto take = [&](unsigned n_list, auto&& test) {
+        for (;;) {
+            unsigned k0 = 0;
+            if (lane == 0) k0 = atomicAdd(&s_list_next, (unsigned)TB);
+            k0 = __shfl_sync(kFull, k0, 0);
+            if (k0 >= n_list) break;
+            unsigned ent[TB];
+            int cnt = 0;
 #pragma unroll
-        for (int k = 0; k < TB; ++k) {
-            ent[k] = 0u;
-            if (k0 + k < n_list) {
-                ent[k] = s_list[k0 + k];
-                cnt = k + 1;
+            for (int k = 0; k < TB; ++k) {
+                ent[k] = 0u;
+                if (k0 + k < n_list) {
+                    ent[k] = s_list[k0 + k];
+                    cnt = k + 1;
+                }
             }
+            test(ent, cnt);
         }
-        test_tiles<TB, TEX>(P, B, Q, ent, cnt, lane);
+    };
+    if (staged) {
+        // the reached tiles, grouped: each tile's points are loaded once for every pair
+        // that reached it (in the paper scene about four pairs a tile).  The tiles with
+        // a mask are compacted into the block list kBlockList at a time.
+        for (int base = 0; base < n_tiles; base += kBlockList) {
+            if (base > 0) __syncthreads();   // the previous round's tiles are taken
+            if (tid == 0) {
+                s_list_n = 0u;
+                s_list_next = 0u;
+            }
+            __syncthreads();
+            const int end = min(n_tiles, base + kBlockList);
+            for (int t0 = base + warp * 32; t0 < end; t0 += NW * 32) {
+                const int t = t0 + lane;
+                const unsigned m = t < end ? s_mask[t] : 0u;
+                const unsigned b = __ballot_sync(kFull, m != 0u);
+                if (b) {
+                    unsigned off = 0;
+                    if (lane == 0) off = atomicAdd(&s_list_n, (unsigned)__popc(b));
+                    off = __shfl_sync(kFull, off, 0);
+                    if (m) s_list[off + __popc(b & ((1u << lane) - 1u))] = (unsigned)t;
+                }
+            }
+            __syncthreads();
+            take(s_list_n, [&](const unsigned (&ent)[TB], int cnt) {
+                test_tile_groups<TB, TEX>(P, B, Q, ent, cnt, s_mask, lane);
+            });
+        }
+    } else {
+        take(min(s_list_n, (unsigned)kBlockList),
+             [&](const unsigned (&ent)[TB], int cnt) { test_tiles<TB, TEX>(P, B, Q, ent, cnt, lane); });
     }
     queue_flush<TEX>(P, B, Q, lane);
     if (stats && lane == 0) s_stat_ns[warp][kWnPoints] += global_ns() - t_b0;
@@ -1091,8 +1164,12 @@ __global__ void __launch_bounds__(128) fk_kernel(const __grid_constant__ LinkTab
 
 }  // namespace
 
+// Dynamic shared memory of a check block: the staged tile spheres [stage_tiles], the
+// super-tile spheres [stage_tiles / 32 + 1], then one pair mask per staged tile.
 size_t staged_bytes(int stage_tiles) {
-    return stage_tiles > 0 ? (size_t)(stage_tiles + stage_tiles / 32 + 1) * sizeof(float4) : 0;
+    return stage_tiles > 0 ? (size_t)(stage_tiles + stage_tiles / 32 + 1) * sizeof(float4) +
+                                 (size_t)stage_tiles * sizeof(unsigned)
+                           : 0;
 }
 
 namespace {
@@ -1157,10 +1234,10 @@ cudaError_t configure_kernels() {
         if (dev >= 0 && dev < kMaxDevices) g_prep_ctas[dev].store(ctas, std::memory_order_relaxed);
     }
     const int smem = (int)staged_bytes(kMaxStagedTiles);
-    const void* fns[8] = {(const void*)check_kernel<2, 16, false>, (const void*)check_kernel<4, 16, false>,
-                          (const void*)check_kernel<8, 16, false>, (const void*)check_kernel<2, 8, false>,
-                          (const void*)check_kernel<4, 8, false>,  (const void*)check_kernel<8, 8, false>,
-                          (const void*)check_kernel<4, 16, true>,  (const void*)check_kernel<4, 8, true>};
+    const void* fns[8] = {(const void*)check_kernel<1, 16, false>, (const void*)check_kernel<2, 16, false>,
+                          (const void*)check_kernel<4, 16, false>, (const void*)check_kernel<1, 8, false>,
+                          (const void*)check_kernel<2, 8, false>,  (const void*)check_kernel<4, 8, false>,
+                          (const void*)check_kernel<2, 16, true>,  (const void*)check_kernel<2, 8, true>};
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 8 && e == cudaSuccess; ++k)
         e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1191,16 +1268,16 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = (ev_mid || p.skip_prep) ? 0 : 1;
-    if (p.tex)   // the texture form: one list batch (4), either block width
-        return nw == 16 ? cudaLaunchKernelEx(&cfg, check_kernel<4, 16, true>, p)
-                        : cudaLaunchKernelEx(&cfg, check_kernel<4, 8, true>, p);
+    if (p.tex)   // the texture form: one list batch (2), either block width
+        return nw == 16 ? cudaLaunchKernelEx(&cfg, check_kernel<2, 16, true>, p)
+                        : cudaLaunchKernelEx(&cfg, check_kernel<2, 8, true>, p);
     switch (tile_batch * 100 + nw) {
+        case 116: return cudaLaunchKernelEx(&cfg, check_kernel<1, 16, false>, p);
         case 216: return cudaLaunchKernelEx(&cfg, check_kernel<2, 16, false>, p);
         case 416: return cudaLaunchKernelEx(&cfg, check_kernel<4, 16, false>, p);
-        case 816: return cudaLaunchKernelEx(&cfg, check_kernel<8, 16, false>, p);
+        case 108: return cudaLaunchKernelEx(&cfg, check_kernel<1, 8, false>, p);
         case 208: return cudaLaunchKernelEx(&cfg, check_kernel<2, 8, false>, p);
         case 408: return cudaLaunchKernelEx(&cfg, check_kernel<4, 8, false>, p);
-        case 808: return cudaLaunchKernelEx(&cfg, check_kernel<8, 8, false>, p);
         default: return cudaErrorInvalidValue;
     }
 }

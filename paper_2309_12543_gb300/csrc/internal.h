@@ -20,7 +20,7 @@ constexpr int kMaxLinks = SDF_MAX_LINKS;
 constexpr float kCullSlack = 1e-4f;
 constexpr int kMaxBatch = 128;            // trajectories per launch (kernel-parameter table)
 constexpr int kCheckWarps = 16;           // warps per check block (the larger of the two shapes)
-constexpr int kDefaultTileBatch = 4;      // (pair, tile) entries per warp step (2, 4 or 8)
+constexpr int kDefaultTileBatch = 1;      // list entries (tiles) per warp step (1, 2 or 4)
 constexpr int kBlockList = 2048;          // (pair, tile) entries a block can queue in shared memory
 constexpr int kMaxStagedTiles = 4096;     // tile spheres a block can stage in shared memory
 
