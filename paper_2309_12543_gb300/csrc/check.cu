@@ -932,6 +932,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
     if (pair_warp) {
         unsigned long long t_a = stats ? global_ns() : 0ull;
         // phase A.2: seed -- nearest super-tile, nearest tile in it, all its points
+        int seed_tile = -1;   // every point of it evaluated for this pair
         if (P.cull && n_tiles > 0) {
             float bs = kInf;
             int bi = 0x7fffffff;
@@ -952,6 +953,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
                     ts = sqrtf(seg_dist2(c.x, c.y, c.z, capA, capD)) + c.w;
                 }
                 const int t_seed = warp_argmin(ts, t < n_tiles ? t : 0x7fffffff);
+                if (t_seed < n_tiles) seed_tile = t_seed;
                 const bool ev = t_seed < n_tiles && t_seed * 32 + lane < n_valid;
                 if (stats) stat_add(B, kWsSeed, (unsigned)__popc(__ballot_sync(kFull, ev)), lane);
                 evaluate_lane<TEX>(P, B, t_seed * 32 + lane, warp, ev);
@@ -996,9 +998,10 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) check_kernel(const __grid_co
                 }
                 const unsigned na = (unsigned)__popc(mta);
                 if (!(mta | mtb)) continue;
-                if (staged) {   // the pair's bit in each reached tile's mask (no list, no overflow)
-                    if (ra) atomicOr(&s_mask[ta], 1u << warp);
-                    if (rb) atomicOr(&s_mask[tb], 1u << warp);
+                if (staged) {   // the pair's bit in each reached tile's mask (no list, no overflow),
+                                // except its seed tile, whose points it has evaluated already
+                    if (ra && ta != seed_tile) atomicOr(&s_mask[ta], 1u << warp);
+                    if (rb && tb != seed_tile) atomicOr(&s_mask[tb], 1u << warp);
                     continue;
                 }
                 unsigned base = 0;
