@@ -135,7 +135,7 @@ const char* sdf_last_error(const sdf_ctx* ctx);
                                      check of a grids object with the option on makes its
                                      texture copy (n^3 FP32 per link; allocates and
                                      synchronises); sdf_grids_destroy frees it.  The texture
-                                     form is its own kernel and always takes 2 list entries
+                                     form is its own kernel and always takes 1 list entry
                                      per warp step (SDF_OPT_TILE_BATCH does not apply); every
                                      request of one launch must use the same grids object
                                      (else SDF_ERR_UNSUPPORTED). */

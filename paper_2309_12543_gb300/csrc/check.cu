@@ -1240,7 +1240,7 @@ cudaError_t configure_kernels() {
     const void* fns[8] = {(const void*)check_kernel<1, 16, false>, (const void*)check_kernel<2, 16, false>,
                           (const void*)check_kernel<4, 16, false>, (const void*)check_kernel<1, 8, false>,
                           (const void*)check_kernel<2, 8, false>,  (const void*)check_kernel<4, 8, false>,
-                          (const void*)check_kernel<2, 16, true>,  (const void*)check_kernel<2, 8, true>};
+                          (const void*)check_kernel<1, 16, true>,  (const void*)check_kernel<1, 8, true>};
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 8 && e == cudaSuccess; ++k)
         e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1271,9 +1271,9 @@ cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, c
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = (ev_mid || p.skip_prep) ? 0 : 1;
-    if (p.tex)   // the texture form: one list batch (2), either block width
-        return nw == 16 ? cudaLaunchKernelEx(&cfg, check_kernel<2, 16, true>, p)
-                        : cudaLaunchKernelEx(&cfg, check_kernel<2, 8, true>, p);
+    if (p.tex)   // the texture form: one list batch (1), either block width
+        return nw == 16 ? cudaLaunchKernelEx(&cfg, check_kernel<1, 16, true>, p)
+                        : cudaLaunchKernelEx(&cfg, check_kernel<1, 8, true>, p);
     switch (tile_batch * 100 + nw) {
         case 116: return cudaLaunchKernelEx(&cfg, check_kernel<1, 16, false>, p);
         case 216: return cudaLaunchKernelEx(&cfg, check_kernel<2, 16, false>, p);
