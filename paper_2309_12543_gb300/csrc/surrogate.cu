@@ -1084,6 +1084,14 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
     bool ok = true;
     const int nv = *A.n_valid;
     const int n_tiles = (nv + 31) >> 5, n_sup = (n_tiles + 31) >> 5;
+    // The pipelines' activation tiles are idle from an item's start to its first
+    // evaluation round, which is after every read of the sphere tables (the seed scan,
+    // the cull lists): each item copies the tables there when they fit, and the
+    // evaluation then overwrites them.
+    float4* s_sph = reinterpret_cast<float4*>(sm + kSurH);
+    const bool staged = n_tiles + n_sup <= kEvalPipes * kTileBytes / 16;
+    const float4* tiles = staged ? s_sph : A.tiles;
+    const float4* supers = staged ? s_sph + n_tiles : A.supers;
     const int n_seed_groups = (A.W + A.seed_group - 1) / A.seed_group;
     const int n_seed_items = A.L * n_seed_groups;
     const int n_items = n_seed_items + A.L * A.n_groups;
@@ -1194,6 +1202,10 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
             s_lnext = 0;
             s_over = 0u;
         }
+        if (staged) {   // the evaluation rounds of the previous item are over (barrier above)
+            for (int i = t; i < n_tiles; i += kEvalThreads) s_sph[i] = __ldg(&A.tiles[i]);
+            for (int i = t; i < n_sup; i += kEvalThreads) s_sph[n_tiles + i] = __ldg(&A.supers[i]);
+        }
         __syncthreads();
         stamp(&ns_prod);
 
@@ -1206,7 +1218,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 float best = INFINITY;
                 int bi = 0x7fffffff;
                 for (int s = lane; s < n_sup; s += 32) {
-                    const float gp = capsule_gap(__ldg(&A.supers[s]), cA, cD);
+                    const float gp = capsule_gap(supers[s], cA, cD);
                     if (gp < best) { best = gp; bi = s; }
                 }
 #pragma unroll
@@ -1219,7 +1231,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                     const int tt = bi * 32 + lane;
                     float tb = INFINITY;
                     int ti = 0x7fffffff;
-                    if (tt < n_tiles) { tb = capsule_gap(__ldg(&A.tiles[tt]), cA, cD); ti = tt; }
+                    if (tt < n_tiles) { tb = capsule_gap(tiles[tt], cA, cD); ti = tt; }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         const float ob = __shfl_xor_sync(0xffffffffu, tb, o);
@@ -1258,12 +1270,12 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 for (int s0 = 0; s0 < n_sup; s0 += 32) {
                     const int sidx = s0 + lane;
                     unsigned bs = __ballot_sync(0xffffffffu,
-                                                sidx < n_sup && capsule_gap(__ldg(&A.supers[sidx]), cA, cD) <= thr);
+                                                sidx < n_sup && capsule_gap(supers[sidx], cA, cD) <= thr);
                     while (bs) {
                         const int sv = s0 + __ffs(bs) - 1;
                         bs &= bs - 1;
                         const int tt = sv * 32 + lane;
-                        const bool reach = tt < n_tiles && capsule_gap(__ldg(&A.tiles[tt]), cA, cD) <= thr;
+                        const bool reach = tt < n_tiles && capsule_gap(tiles[tt], cA, cD) <= thr;
                         const unsigned bt = __ballot_sync(0xffffffffu, reach);
                         if (!bt) continue;
                         int base = 0;
