@@ -498,7 +498,9 @@ int sdf_surrogate_error(sdf_ctx* ctx, const sdf_surrogate* surrogate, int32_t li
  * the surrogate's (exactly what check_trajectory returns for them).  Outputs as
  * check_trajectory; rechecked_dev (optional, W bytes) is 1 where the grid path
  * decided, surrogate_dist_dev (optional, W FP32) the surrogate minimum before the
- * re-check.  Without surrogate_dist_dev, a waypoint whose surrogate minimum so far
+ * re-check (for a waypoint whose work item's (waypoint, tile) list overflowed, an upper
+ * bound of it; such a waypoint is always re-checked).  Without surrogate_dist_dev, a
+ * waypoint whose surrogate minimum so far
  * is already below margin + eps stops being culled and evaluated (the grid path
  * decides it whatever the rest would give), which changes no output; with it, every
  * waypoint's surrogate minimum is completed.  Uses workspace owned by the context (grown on demand, which
