@@ -504,7 +504,10 @@ int sdf_surrogate_error(sdf_ctx* ctx, const sdf_surrogate* surrogate, int32_t li
  * is already below margin + eps stops being culled and evaluated (the grid path
  * decides it whatever the rest would give), which changes no output; with it, every
  * waypoint's surrogate minimum is completed.  Uses workspace owned by the context (grown on demand, which
- * synchronises); contexts on different streams may share one surrogate.
+ * synchronises); contexts on different streams may share one surrogate.  The context keeps
+ * the networks' weights in the check's layout and makes them again after any
+ * sdf_surrogate_train of that surrogate (a check must be ordered after the training it
+ * is to see, as for any use of the parameters).
  * Asynchronous.
  * Errors: INVALID_ARG (robot and surrogate built on different grids, bad sizes),
  * OOM, CUDA. */

@@ -241,6 +241,7 @@ struct sdf_ctx {
     int* sur_count = nullptr;              // work-item counter of the fused surrogate check
     uint8_t* sur_wimg = nullptr;           // the networks' weights as the fused check holds them
     size_t sur_wimg_cap = 0;
+    uint64_t sur_wimg_id = 0, sur_wimg_version = 0;   // the surrogate (id, version) the image holds
     // timing
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
     bool timed_valid = false;

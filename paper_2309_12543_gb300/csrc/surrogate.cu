@@ -23,6 +23,7 @@
 //
 // The training samples come from a counter-based generator (Philox4x32-10,
 // Salmon et al., SC'11) and are labelled by the link's grid.
+#include <atomic>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -1448,6 +1449,8 @@ cudaError_t configure_surrogate_kernels() {
 struct sdf_surrogate {
     int device = 0;
     int L = 0;
+    uint64_t id = 0;                        // unique over the process (never reused)
+    std::atomic<uint64_t> version{0};       // incremented by every training call
     const sdf_grids* grids = nullptr;
     float* master = nullptr;   // [L][PARAMS], W2/W3 blocks [in][out]
     float* adam_m = nullptr;
@@ -1467,6 +1470,8 @@ namespace {
 using sdf::kH;
 using sdf::kPar;
 using sdf::kParStride;
+
+std::atomic<uint64_t> g_surrogate_ids{0};
 
 int sfail(sdf_ctx* ctx, int code, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -1544,6 +1549,7 @@ int sdf_surrogate_create(sdf_ctx* ctx, const sdf_grids* grids, const float* para
     if (!surrogate_configured(ctx->device)) return sfail(ctx, SDF_ERR_CUDA, "surrogate kernels: attributes");
     sdf_surrogate* S = new (std::nothrow) sdf_surrogate();
     if (!S) return sfail(ctx, SDF_ERR_OOM, "sdf_surrogate_create");
+    S->id = ++g_surrogate_ids;
     S->device = ctx->device;
     S->L = grids->n_links;
     S->grids = grids;
@@ -1706,6 +1712,7 @@ int sdf_surrogate_train(sdf_ctx* ctx, sdf_surrogate* S, const float* x_dev, cons
     float* loss = loss_dev ? loss_dev : S->loss;
     cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float) * S->L, ctx->stream);
     if (e != cudaSuccess) return scuda(ctx, e, "sdf_surrogate_train");
+    ++S->version;   // the checks' cached weight images are stale from here on
     return launch_train(ctx, S, 0, S->L, x_dev, y_dev, n, first_batch, steps, lr, nullptr, loss);
 }
 
@@ -1777,10 +1784,20 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
         e = sdf::dmalloc(&ctx->sur_wimg, (size_t)SDF_MAX_LINKS * sdf::kImgBytes);
         if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate: weight image");
         ctx->sur_wimg_cap = (size_t)SDF_MAX_LINKS * sdf::kImgBytes;
+        ctx->sur_wimg_id = 0;
     }
-    // the weights in the fused kernel's shared-memory layout, from the current parameters
-    sdf::weight_image_kernel<<<(unsigned)L, 512, 0, st>>>(S->master, ctx->sur_wimg);
-    e = cudaGetLastError();
+    // the weights in the fused kernel's shared-memory layout, made again only when the
+    // context last made them for another surrogate or before its latest training
+    const uint64_t version = S->version.load();
+    e = cudaSuccess;
+    if (ctx->sur_wimg_id != S->id || ctx->sur_wimg_version != version) {
+        sdf::weight_image_kernel<<<(unsigned)L, 512, 0, st>>>(S->master, ctx->sur_wimg);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            ctx->sur_wimg_id = S->id;
+            ctx->sur_wimg_version = version;
+        }
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_keys, 0xff, sizeof(unsigned long long) * W, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_mask, 0, (size_t)W, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_count, 0, sizeof(int), st);

@@ -224,6 +224,30 @@ def test_surrogate_check_without_culling_is_the_brute_force_minimum(sdf, env):
     assert np.array_equal(l, g[1]) and np.array_equal(p, g[2])
 
 
+def test_surrogate_check_follows_training(sdf, env):
+    """The context keeps the networks' weights in the fused kernel's layout between
+    checks; a training step in between must reach the next check (the surrogate
+    minima match the oracle for the new parameters, not the old ones)."""
+    sc, ctx, grids, vals, metas = env
+    L = len(metas)
+    sur = sdf.Surrogate(ctx, grids, sg.mlp_init(31, L))
+    robot = sdf.Robot(ctx, sc.dh, grids, sc.base)
+    q, pts = sc.q[:12].astype(np.float32), sc.points[:300].astype(np.float32)
+    _, _, _, _, sd0 = _sur_check(sdf, ctx, robot, sur, q, pts, margin=0.0, eps=100.0)
+    ref0 = mlp.check(sc.dh, sc.base, sur.params().astype(np.float64), metas, q, pts, quantize=True)[0]
+    assert np.max(np.abs(sd0 - ref0)) <= 2e-3
+    rng = np.random.default_rng(32)
+    n = 256
+    X = torch.tensor(rng.uniform(-1, 1, (L, n, 3)).astype(np.float32), device="cuda")
+    Y = torch.tensor(rng.uniform(-0.3, 0.3, (L, n)).astype(np.float32), device="cuda")
+    sur.train(X, Y, n, 0, 20, 1e-2)
+    assert ctx.synchronize() == 0
+    _, _, _, _, sd1 = _sur_check(sdf, ctx, robot, sur, q, pts, margin=0.0, eps=100.0)
+    ref1 = mlp.check(sc.dh, sc.base, sur.params().astype(np.float64), metas, q, pts, quantize=True)[0]
+    assert np.max(np.abs(ref1 - ref0)) > 1e-2          # the training moved the minima
+    assert np.max(np.abs(sd1 - ref1)) <= 2e-3
+
+
 def test_surrogate_check_with_trained_network_and_fallback(sdf, env):
     sc, ctx, grids, vals, metas = env
     L = len(metas)
