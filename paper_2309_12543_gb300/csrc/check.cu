@@ -1165,6 +1165,42 @@ __global__ void __launch_bounds__(128) fk_kernel(const __grid_constant__ LinkTab
     }
 }
 
+// Kinematics as fk_kernel, plus the resets of a surrogate check's keys (~0), re-check
+// flags (0) and work counter (0), launched right after the sort and overlapping it
+// (programmatic dependent launch: the sort lets its dependents start at once).  Every
+// thread waits for the sort before it exits, so that this kernel completes only after
+// the sort: a kernel behind it in the stream sees both.  It writes nothing the sort
+// reads.
+__global__ void __launch_bounds__(128) fk_reset_kernel(const __grid_constant__ LinkTable T,
+                                                       const float* __restrict__ q, int W,
+                                                       float* __restrict__ out, int* status,
+                                                       unsigned long long* keys, uint8_t* recheck, int* counter) {
+    __shared__ float4 s_xf[4][kMaxLinks][3];
+    __shared__ float4 s_sph[4][kMaxLinks];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = blockIdx.x * 4 + warp;
+    if (w < W) {   // whole warps
+        const float* qw = q + (size_t)w * T.dof;
+        if (lane < T.dof && !isfinite(qw[lane])) atomicOr(status, kStatusNonFinite);
+        fk_links(T, qw, lane, s_xf[warp], s_sph[warp]);
+        __syncwarp();
+        for (int l = lane; l < T.L; l += 32) {
+            float4* o = reinterpret_cast<float4*>(out + ((size_t)w * T.L + l) * 16);
+            o[0] = s_xf[warp][l][0];
+            o[1] = s_xf[warp][l][1];
+            o[2] = s_xf[warp][l][2];
+            o[3] = s_sph[warp][l];
+        }
+    }
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int i = gt; i < W; i += stride) {
+        keys[i] = ~0ull;
+        recheck[i] = 0;
+    }
+    if (gt == 0) *counter = 0;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 }  // namespace
 
 // Dynamic shared memory of a check block: the staged tile spheres [stage_tiles], the
@@ -1298,6 +1334,20 @@ cudaError_t launch_finish(int* status, int* h_status, unsigned* d_seq, unsigned*
 cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status, cudaStream_t s) {
     fk_kernel<<<(unsigned)((W + 3) / 4), 128, 0, s>>>(T, q, W, out, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_fk_reset(const LinkTable& T, const float* q, int W, float* out, int* status,
+                            unsigned long long* keys, uint8_t* recheck, int* counter, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(W > 0 ? (W + 3) / 4 : 1));
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fk_reset_kernel, T, q, W, out, status, keys, recheck, counter);
 }
 
 }  // namespace sdf

@@ -1798,16 +1798,15 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
             ctx->sur_wimg_version = version;
         }
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_keys, 0xff, sizeof(unsigned long long) * W, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_mask, 0, (size_t)W, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sur_count, 0, sizeof(int), st);
     if (e != cudaSuccess) return scuda(ctx, e, "check_trajectory_surrogate");
     sdf::BatchParams* bp = new (std::nothrow) sdf::BatchParams();
     if (!bp) return sfail(ctx, SDF_ERR_OOM, "host allocation");
     int rc = sdf::sort_cloud(ctx, points_dev, N, bp);
     sdf::SurFusedArgs A{};
     if (rc == SDF_OK) {
-        e = sdf::launch_fk(R->table, q_dev, W, ctx->sur_poses, ctx->status, st);
+        // kinematics and the resets of the keys, flags and work counter, overlapping the sort
+        e = sdf::launch_fk_reset(R->table, q_dev, W, ctx->sur_poses, ctx->status, ctx->sur_keys, ctx->sur_mask,
+                                 ctx->sur_count, st);
         A.poses = ctx->sur_poses;
         A.W = W;
         A.L = L;
