@@ -1166,7 +1166,7 @@ __global__ void __launch_bounds__(128) fk_kernel(const __grid_constant__ LinkTab
 }
 
 // Kinematics as fk_kernel, plus the resets of a surrogate check's keys (~0), re-check
-// flags (0) and work counter (0), launched right after the sort and overlapping it
+// flags (0) and two work counters (0), launched right after the sort and overlapping it
 // (programmatic dependent launch: the sort lets its dependents start at once).  Every
 // thread waits for the sort before it exits, so that this kernel completes only after
 // the sort: a kernel behind it in the stream sees both.  It writes nothing the sort
@@ -1197,7 +1197,10 @@ __global__ void __launch_bounds__(128) fk_reset_kernel(const __grid_constant__ L
         keys[i] = ~0ull;
         recheck[i] = 0;
     }
-    if (gt == 0) *counter = 0;
+    if (gt == 0) {
+        counter[0] = 0;
+        counter[1] = 0;
+    }
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 

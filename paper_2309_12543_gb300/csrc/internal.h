@@ -139,7 +139,7 @@ inline int interleave_waypoints(long long n_blocks, int tw, int nw, int num_sms)
 cudaError_t launch_batch(const BatchParams& p, int tile_batch, cudaStream_t s, cudaEvent_t ev_mid);
 cudaError_t launch_fk(const LinkTable& T, const float* q, int W, float* out, int* status, cudaStream_t s);
 // Kinematics and the resets of a surrogate check (keys to ~0, re-check flags and the
-// work counter to 0), overlapping the sort launched just before it on s; completes only
+// two work counters to 0), overlapping the sort launched just before it on s; completes only
 // after that sort.
 cudaError_t launch_fk_reset(const LinkTable& T, const float* q, int W, float* out, int* status,
                             unsigned long long* keys, uint8_t* recheck, int* counter, cudaStream_t s);

@@ -1009,7 +1009,13 @@ struct SurFusedArgs {
     int seed_group;                   // waypoints per seed item (16: four full tiles)
     unsigned long long* keys;         // [W] packed keys, ~0 = none (set before the launch)
     uint8_t* recheck;                 // [W] 1 where a list overflowed (zeroed before the launch)
-    int* work;                        // item counter (zeroed before the launch)
+    int* work;                        // [0] item counter, [1] CTAs done (zeroed before the launch)
+    float limit;                      // margin + error bound: below it the grid re-checks
+    float* dist;                      // [W] results (the grid re-check overwrites its waypoints)
+    int32_t* arg_link;
+    int32_t* arg_point;
+    float* sur_dist;                  // [W] surrogate minima, or null
+    uint8_t* recheck_out;             // [W] re-check flags for the caller, or null
     float slack;                      // error bound of the surrogate + rounding slack
     float decided_below;              // a waypoint whose minimum so far is below this (margin +
                                       // error bound) is decided by the grid re-check, whatever
@@ -1402,33 +1408,38 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
         tc::mbar_wait(&mbar[pipe], phase ^ 1u, kWaitPolls);
     }
     tc::fence_before_sync();
+    __threadfence();   // this CTA's key updates and flags, before it counts itself done
     __syncthreads();
     tc::fence_after_sync();
     if (warp == 0) tc::tmem_free(tm, 512);
+    // the last CTA to finish decodes every waypoint's key into the results and selects
+    // the waypoints for the grid re-check (the other CTAs' updates are visible: each
+    // fenced them before counting itself done)
+    __shared__ int s_last;
+    if (t == 0) s_last = atomicAdd(A.work + 1, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int w = t; w < A.W; w += kEvalThreads) {
+        const unsigned long long key = __ldcg(&A.keys[w]);
+        float d;
+        if (key == ~0ull) {
+            d = INFINITY;
+            A.arg_link[w] = -1;
+            A.arg_point[w] = -1;
+        } else {
+            d = from_ordered((unsigned)(key >> 32));
+            A.arg_link[w] = (int)(key & 15u);
+            A.arg_point[w] = (int)((key & 0xffffffffu) >> 4);
+        }
+        A.dist[w] = d;
+        if (A.sur_dist) A.sur_dist[w] = d;
+        const uint8_t r = (__ldcg(&A.recheck[w]) || d < A.limit) ? 1 : 0;
+        A.recheck[w] = r;
+        if (A.recheck_out) A.recheck_out[w] = r;
+    }
 }
 
-// Per waypoint: decode the surrogate minimum, write it as the result, and select the
-// waypoint for the grid re-check when it is below margin + error bound, or when its
-// list overflowed (recheck already 1).
-__global__ void sur_finish_kernel(const unsigned long long* keys, int W, float limit, float* dist, int32_t* arg_link,
-                                  int32_t* arg_point, float* sur_dist, uint8_t* recheck) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= W) return;
-    const unsigned long long key = keys[w];
-    float d;
-    if (key == ~0ull) {
-        d = INFINITY;
-        arg_link[w] = -1;
-        arg_point[w] = -1;
-    } else {
-        d = from_ordered((unsigned)(key >> 32));
-        arg_link[w] = (int)(key & 15u);
-        arg_point[w] = (int)((key & 0xffffffffu) >> 4);
-    }
-    dist[w] = d;
-    if (sur_dist) sur_dist[w] = d;
-    recheck[w] = (recheck[w] || d < limit) ? 1 : 0;
-}
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -1843,6 +1854,12 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
         A.slack = eps + sdf::kCullSlack;
         A.decided_below = surrogate_dist_dev ? -INFINITY : margin + eps;
         A.work = ctx->sur_count;
+        A.limit = margin + eps;
+        A.dist = dist_dev;
+        A.arg_link = argmin_link_dev;
+        A.arg_point = argmin_point_dev;
+        A.sur_dist = surrogate_dist_dev;
+        A.recheck_out = rechecked_dev;
         A.status = ctx->status;
         A.wait_polls = ctx->wait_polls;
         A.stats = ctx->stats ? ctx->d_stats : nullptr;
@@ -1853,14 +1870,6 @@ int check_trajectory_surrogate(sdf_ctx* ctx, const sdf_robot* R, const sdf_surro
         sdf::sur_check_kernel<<<(unsigned)std::min(items, ctx->num_sms), sdf::kEvalThreads, sdf::kSurSmem, st>>>(A);
         e = cudaGetLastError();
     }
-    if (rc == SDF_OK && e == cudaSuccess) {
-        sdf::sur_finish_kernel<<<(unsigned)((W + 255) / 256), 256, 0, st>>>(
-            ctx->sur_keys, W, margin + eps, dist_dev, argmin_link_dev, argmin_point_dev, surrogate_dist_dev,
-            ctx->sur_mask);
-        e = cudaGetLastError();
-    }
-    if (rc == SDF_OK && e == cudaSuccess && rechecked_dev)
-        e = cudaMemcpyAsync(rechecked_dev, ctx->sur_mask, (size_t)W, cudaMemcpyDeviceToDevice, st);
     if (rc == SDF_OK && e != cudaSuccess) rc = scuda(ctx, e, "check_trajectory_surrogate");
     if (rc == SDF_OK) {
         // the grid path re-checks the selected waypoints on the cloud sorted above
