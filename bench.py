@@ -54,10 +54,10 @@ OPS_PER_LOOKUP = 40
 # apart, caches flushed first); the check kernel's ncu summary under profiles/ gives
 # the capture and its command.  None once the kernel has changed since.
 CHECK_KERNEL_NCU = {
-    "dram_bytes": 8_707_840,                  # dram__bytes_read.sum + dram__bytes_write.sum
-    "l1tex_throughput_pct": 38.52,            # l1tex__throughput.avg.pct_of_peak_sustained_active
-    "lts_sector_hit_rate_pct": 64.53,         # lts__t_sector_hit_rate.pct
-    "duration_us": 31.07,                     # gpu__time_duration.sum
+    "dram_bytes": 8_996_608,                  # dram__bytes_read.sum + dram__bytes_write.sum
+    "l1tex_throughput_pct": 38.04,            # l1tex__throughput.avg.pct_of_peak_sustained_active
+    "lts_sector_hit_rate_pct": 64.02,         # lts__t_sector_hit_rate.pct
+    "duration_us": 32.67,                     # gpu__time_duration.sum
 }
 
 
