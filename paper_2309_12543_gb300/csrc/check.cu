@@ -24,10 +24,14 @@
 //     waypoint's warps) a tight upper bound early;
 //   * culls super-tiles, then tiles, against the capsule with best + slack (the
 //     analogue of the paper's "grids in sphere", Sec. III-B); every surviving
-//     (pair, tile) goes to a block-wide list in shared memory.
-//   Phase B, all warps of the block: entries are taken from the list a few at a time
-//   (loads issued together), the tile's points are tested against the pair's
-//   capsule, survivors are compacted into a per-warp queue and evaluated 32 at a
+//     (pair, tile) sets the pair's bit in the tile's mask in shared memory (when the
+//     tile spheres are staged; otherwise it goes to a block-wide list of (pair, tile)
+//     entries).
+//   Phase B, all warps of the block: the tiles with a mask are compacted into the
+//   block list and taken a few at a time (loads issued together); a tile's points
+//   are loaded once and tested against the capsule of every pair in its mask (or,
+//   with the flat list, against the entry's pair); survivors are compacted into a
+//   per-warp queue and evaluated 32 at a
 //   time: transform into the link frame (the per-point form of Sec. II-B / Fig.
 //   2), trilinear lookup in the FP32 link grid (the grid-sample interpolation of
 //   Sec. III-A), distance to the grid box outside it.  Each value is folded into
