@@ -979,7 +979,10 @@ __device__ __forceinline__ void load_image(const uint8_t* __restrict__ img, uint
 // warpgroup pipelines evaluate its whole tiles on the tensor cores, fold each value into the
 // waypoint's packed key (ordered distance, point, link) and tighten the thresholds.
 // A waypoint whose list overflowed is marked for the grid re-check, which decides it
-// exactly.
+// exactly.  Cull items take interleaved waypoints (g, g + n, ...); a waypoint already
+// below margin + error bound stops being refined when its surrogate minimum is not
+// wanted; each item copies the sphere tables into the idle activation tiles before its
+// seed scan or culls; the last CTA to finish writes the results and re-check flags.
 constexpr int kSurGroup = 16;      // waypoints per work item: one warp each in the culls
 constexpr int kSurTake = 2;        // list entries a warp takes per step of the production
 constexpr int kSurFill = 3 * 128;  // the production stops once the ring holds this many queries
