@@ -235,6 +235,28 @@ def test_gpu_pipeline_end_to_end(sdf, ctx, tiny):
     assert_parity(sc.dh, sc.base, vals, metas, sc.q, sc.points, d, al, ap, ref=ref)
 
 
+def test_sixteen_links(sdf, ctx):
+    """A 15-DoF arm (16 links, the most a robot has): a block then holds one waypoint's
+    16 (waypoint, link) pairs, every bit of the per-tile pair masks is in use, and the
+    8-warp block form is not available.  Parity with the oracle, culled and unculled
+    results bit-identical."""
+    sc = sg.make_scene("tiny", dof=15, n_lon=8, n_lat=4, W=24, N=700)
+    vals, metas = oracle.build_grids(sc.meshes, sc.resolution, sc.margin)
+    ref = oracle.check(sc.dh, sc.base, vals, metas, sc.q, sc.points)
+    robot = _robot(sdf, ctx, sc, vals, metas)
+    rc, d, al, ap = device_check(sdf, torch, ctx, robot, sc.q, sc.points)
+    assert rc == 0
+    assert_parity(sc.dh, sc.base, vals, metas, sc.q, sc.points, d, al, ap, ref=ref)
+    ctx.set_option(sdf.SDF_OPT_CULL, 0)
+    try:
+        rc, d0, al0, ap0 = device_check(sdf, torch, ctx, robot, sc.q, sc.points)
+    finally:
+        ctx.set_option(sdf.SDF_OPT_CULL, 1)
+    assert rc == 0
+    assert np.array_equal(d.view(np.uint32), d0.view(np.uint32))
+    assert np.array_equal(al, al0) and np.array_equal(ap, ap0)
+
+
 def test_maximum_cloud_size(sdf, ctx, tiny):
     """N = SDF_MAX_POINTS (2^24 - 1, the largest index the packed key holds):
     the sort's loop paths and the top of the index range, against the oracle on a
