@@ -257,6 +257,21 @@ def test_sixteen_links(sdf, ctx):
     assert np.array_equal(al, al0) and np.array_equal(ap, ap0)
 
 
+@pytest.mark.parametrize("N", [4096 * 32 - 5, 4096 * 32, 4096 * 32 + 1])
+def test_staged_and_flat_phase_b_boundary(sdf, ctx, tiny, N):
+    """Clouds on either side of 4,096 tiles: at most that many tile spheres are staged
+    in shared memory and phase B is grouped by tile; one more tile and the flat
+    (pair, tile) list is used.  Both against the oracle."""
+    sc, vals, metas, ref = tiny
+    robot = _robot(sdf, ctx, sc, vals, metas)
+    rng = np.random.default_rng(N)
+    pts = rng.uniform(-1.2, 1.2, (N, 3))
+    q = sc.q[:6]
+    rc, d, al, ap = device_check(sdf, torch, ctx, robot, q, pts)
+    assert rc == 0
+    assert_parity(sc.dh, sc.base, vals, metas, q, pts, d, al, ap)
+
+
 def test_maximum_cloud_size(sdf, ctx, tiny):
     """N = SDF_MAX_POINTS (2^24 - 1, the largest index the packed key holds):
     the sort's loop paths and the top of the index range, against the oracle on a
