@@ -88,17 +88,20 @@ def test_fk_matches_oracle(sdf, ctx):
         np.testing.assert_allclose(o[..., 12:15], c, atol=5e-6)
 
 
+@pytest.mark.parametrize("tb", [1, 2, 4])
 @pytest.mark.parametrize("warps", [8, 16])
 @pytest.mark.parametrize("tw", [0, 1, 2, 3])
 @pytest.mark.parametrize("cull", [1, 0])
-def test_check_tiny_all_launch_shapes(sdf, ctx, tiny, tw, cull, warps):
+def test_check_tiny_all_launch_shapes(sdf, ctx, tiny, tw, cull, warps, tb):
     # 16-warp blocks hold two waypoints of the 7-link arm; the 19 blocks of W = 37
-    # are one wave, so they take interleaved waypoints (b and b + 19)
+    # are one wave, so they take interleaved waypoints (b and b + 19); tb tiles a
+    # warp takes per step in phase B
     sc, vals, metas, ref = tiny
     robot = _robot(sdf, ctx, sc, vals, metas)
     ctx.set_option(sdf.SDF_OPT_BLOCK_WARPS, warps)
     ctx.set_option(sdf.SDF_OPT_WAYPOINTS_PER_BLOCK, tw)
     ctx.set_option(sdf.SDF_OPT_CULL, cull)
+    ctx.set_option(sdf.SDF_OPT_TILE_BATCH, tb)
     rc, d, al, ap = device_check(sdf, torch, ctx, robot, sc.q, sc.points)
     assert rc == 0
     assert_parity(sc.dh, sc.base, vals, metas, sc.q, sc.points, d, al, ap, ref=ref)
@@ -257,8 +260,9 @@ def test_sixteen_links(sdf, ctx):
     assert np.array_equal(al, al0) and np.array_equal(ap, ap0)
 
 
-@pytest.mark.parametrize("N", [4096 * 32 - 5, 4096 * 32, 4096 * 32 + 1])
-def test_staged_and_flat_phase_b_boundary(sdf, ctx, tiny, N):
+@pytest.mark.parametrize("N,tb", [(4096 * 32 - 5, 1), (4096 * 32, 1), (4096 * 32, 4), (4096 * 32 + 1, 1),
+                                  (4096 * 32 + 1, 2), (4096 * 32 + 1, 4)])
+def test_staged_and_flat_phase_b_boundary(sdf, ctx, tiny, N, tb):
     """Clouds on either side of 4,096 tiles: at most that many tile spheres are staged
     in shared memory and phase B is grouped by tile; one more tile and the flat
     (pair, tile) list is used.  Both against the oracle."""
@@ -267,6 +271,7 @@ def test_staged_and_flat_phase_b_boundary(sdf, ctx, tiny, N):
     rng = np.random.default_rng(N)
     pts = rng.uniform(-1.2, 1.2, (N, 3))
     q = sc.q[:6]
+    ctx.set_option(sdf.SDF_OPT_TILE_BATCH, tb)
     rc, d, al, ap = device_check(sdf, torch, ctx, robot, q, pts)
     assert rc == 0
     assert_parity(sc.dh, sc.base, vals, metas, q, pts, d, al, ap)
