@@ -576,7 +576,8 @@ def run_ours(args):
             "grid_form_p50_us": sr["grid_form"]["p50_us"], "rechecked_waypoints": sr["rechecked_waypoints"],
             "fallback_exact": sr["fallback_exact"], "eps_m": sr["eps_m"], "train_s": sr["train_s"],
             "train_steps": sr["config"]["train_steps"], "samples_per_link": sr["config"]["samples_per_link"],
-            "network_queries": sr["network_queries"], "steps": sa.steps, "clocks": sr["clocks"],
+            "network_queries": sr["network_queries"], "network_roofline": sr["network_roofline"],
+            "steps": sa.steps, "clocks": sr["clocks"],
             "workload": sr["config"]["workload"]}
         va = argparse.Namespace(**vars(args))
         va.duration = args.serve_s
@@ -839,7 +840,51 @@ def run_serve(args, emit=True):
 
 # one network evaluation: 3x128 + 2 x 128x128 + 128x1 multiply-adds
 MLP_FLOPS_PER_QUERY = 2 * (3 * 128 + 2 * 128 * 128 + 128)
+# of which the two 128 x 128 layers run on the tensor cores
+MLP_TENSOR_FLOPS_PER_QUERY = 2 * (2 * 128 * 128)
+# dense bf16 peak when the measured one is missing (one earlier GB300 measurement)
+BF16_TFLOPS_FALLBACK = 1900.0
 SUR_METRIC = "µs per 500-waypoint×20k-point check, learned surrogate with grid fallback (p50/p99)"
+
+
+def bf16_peak_tflops():
+    """The measured dense bf16 burst peak of this machine's GPUs (cuBLAS GEMM timed alone),
+    from MEASURED_PEAKS.json beside this file, else the fallback; and which it is."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = float(json.load(fh)["bf16_tflops"])
+        if v > 0:
+            return v, "measured (bf16 burst)"
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return BF16_TFLOPS_FALLBACK, "fallback"
+
+
+def network_roofline(sur, dev, stream, n=1 << 21, reps=20):
+    """The network evaluation kernel alone at a steady state: link 0 at n queries
+    uniform in its normalised box (every CTA's four pipelines full), event-timed on the
+    context's stream; tensor-core FLOPs per second against the bf16 peak."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    x = (torch.rand((n, 3), generator=g, device=dev) * 2 - 1).contiguous()
+    f = torch.empty(n, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        sur.eval(0, x, n, f)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        sur.eval(0, x, n, f)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    us = statistics.median(a.elapsed_time(b) * 1e3 for a, b in ev)
+    peak, src = bf16_peak_tflops()
+    achieved = n * MLP_TENSOR_FLOPS_PER_QUERY / (us * 1e-6) / 1e12
+    return {"kernel": "mlp_eval_kernel", "bound": "tensor", "queries": n, "us": us,
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src,
+            "flops_per_query": MLP_TENSOR_FLOPS_PER_QUERY,
+            "note": "tensor-core FLOPs of the two 128x128 layers only; the 384 SiLUs a query run on the FP32 "
+                    "and XU pipes, and the kernel is latency-bound with four warps per SM sub-partition"}
 
 
 def run_surrogate(args, emit=True):
@@ -896,6 +941,7 @@ def run_surrogate(args, emit=True):
         nr = sur.error(l, 1 << 20, 10, 0.10, seed=8000 + l)
         errs.append({"link": l, "max_uniform": u[0], "mean_uniform": u[1], "max_near": nr[0], "mean_near": nr[1]})
     eps = max(max(e["max_uniform"], e["max_near"]) for e in errs)
+    net_roof = network_roofline(sur, dev, stream)
     # the same memory as a grid: 32^3 FP32 values (131 KB) vs 33,665 FP32 parameters
     coarse = sdf.sdf_build_grids(ctx, scene.meshes, 32, scene.margin)
     m = 1 << 20
@@ -992,6 +1038,7 @@ def run_surrogate(args, emit=True):
         "network_queries": {"seed": st["sur_seed_queries"], "after_cull": st["sur_queries"],
                             "flops_per_query": MLP_FLOPS_PER_QUERY,
                             "tflops_over_the_check": queries * MLP_FLOPS_PER_QUERY / (percentile(full_us, 50) * 1e-6) / 1e12},
+        "network_roofline": net_roof,
         "fused_kernel_phases_us": sur_phases(st, torch.cuda.get_device_properties(dev).multi_processor_count),
         "rechecked_waypoints": int(r.sum()), "fallback_exact": exact, "max_diff_where_surrogate_decided_m": within,
         "eps_m": eps, "errors": errs, "equal_memory_grid_32": coarse_err,

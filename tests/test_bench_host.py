@@ -1,7 +1,8 @@
 """Host-side logic of the benchmark, without a GPU: the clock sampler keeps only the
 samples inside the timed window (and says when it had to fall back to all of
 them), reports the throttle reasons it saw, and the fused surrogate kernel's phase
-summary divides the statistics counters per CTA."""
+summary divides the statistics counters per CTA, and the bf16 peak of the network
+roofline comes from the measured-peaks file when there is one."""
 import os
 import sys
 
@@ -72,3 +73,18 @@ def test_surrogate_phase_summary_is_per_cta():
     assert ph["cta_mean"] == 140.0 and ph["cta_max"] == 163.0
     assert ph["produce"] == 60.0 and ph["cull_lists"] == 25.0 and ph["evaluate"] == 70.0
     assert abs(ph["other"] - 10.0) < 1e-9 and ph["ctas"] == 152
+
+
+def test_bf16_peak_comes_from_the_measured_file_else_the_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.bf16_peak_tflops() == (bench.BF16_TFLOPS_FALLBACK, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"bf16_tflops": 1945.3, "hbm_gbs": 6681.5}')
+    assert bench.bf16_peak_tflops() == (1945.3, "measured (bf16 burst)")
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6681.5}')
+    assert bench.bf16_peak_tflops()[1] == "fallback"
+
+
+def test_network_flops_split():
+    # the two 128 x 128 layers are the tensor-core part of one query's FLOPs
+    assert bench.MLP_TENSOR_FLOPS_PER_QUERY == 65536
+    assert bench.MLP_FLOPS_PER_QUERY - bench.MLP_TENSOR_FLOPS_PER_QUERY == 2 * (3 * 128 + 128)
