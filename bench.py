@@ -1030,6 +1030,7 @@ def run_surrogate(args, emit=True):
         "p50_us": percentile(sur_us, 50), "p99_us": percentile(sur_us, 99),
         "grid_form": {"p50_us": percentile(grid_us, 50), "p99_us": percentile(grid_us, 99)},
         "decision_queries": {"seed": st_dec["sur_seed_queries"], "after_cull": st_dec["sur_queries"]},
+        "decision_fused_kernel_phases_us": sur_phases(st_dec, torch.cuda.get_device_properties(dev).multi_processor_count),
         "with_surrogate_minimum": {
             "p50_us": percentile(full_us, 50), "p99_us": percentile(full_us, 99),
             "outputs_identical": same,
