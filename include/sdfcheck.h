@@ -489,9 +489,10 @@ int sdf_surrogate_error(sdf_ctx* ctx, const sdf_surrogate* surrogate, int32_t li
 
 /* The check with the surrogate in place of the grid lookup, and the grid path as
  * fallback.  For each waypoint: forward kinematics, then every (link, point) pair
- * whose sphere bound ||p - c_link|| - R_link is within the surrogate minimum found
- * so far plus `eps` (seeded by the 32 points of the nearest tile per link) is
- * evaluated by the link's network, with the out-of-box rule; the minimum and its
+ * whose capsule bound (the distance from p to the link's bounding capsule) is within
+ * the surrogate minimum found so far plus `eps` (seeded, per link, by the 8 points of
+ * the tile nearest to the capsule that lie nearest to it) is evaluated by the link's
+ * network, with the out-of-box rule; the minimum and its
  * arg-min are the surrogate result.  Waypoints whose surrogate minimum is below
  * margin + eps -- eps being the caller's bound on the surrogate's error, e.g. from
  * sdf_surrogate_error -- are checked again by the grid path, whose result replaces

@@ -969,7 +969,9 @@ __device__ __forceinline__ void load_image(const uint8_t* __restrict__ img, uint
 // reloads its weights only when the link changes and the cull items find every
 // link's seed minimum already published.
 //   seed: one warp per waypoint picks the tile nearest to the link's bounding capsule
-//     (nearest super-tile first) and its 32 points become queries;
+//     (nearest super-tile first), and the kSeedPts of its 32 points nearest to the
+//     capsule become queries (a seed only sets the first threshold, and the 8
+//     nearest points set it about as low as all 32, at a quarter of the queries);
 //   cull: with the waypoint's minimum so far (over all links) plus the surrogate's
 //     error bound as the threshold, one warp per waypoint culls super-tiles and tiles
 //     against the capsule into a (waypoint, tile) list in shared memory; then every
@@ -988,6 +990,7 @@ constexpr int kSurTake = 2;        // list entries a warp takes per step of the 
 constexpr int kSurFill = 3 * 128;  // the production stops once the ring holds this many queries
 constexpr int kSurRing = kSurFill + 16 * 32 * kSurTake;   // + what 16 warps may add past it
 constexpr int kSurList = 384;      // (waypoint, tile) entries of one cull item
+constexpr int kSeedPts = 8;        // seed queries per (waypoint, link): a tile's points nearest the capsule
 // shared memory of the fused kernel: the link's image (W2, W3, small parameters), the
 // pipelines' activation tiles, the query ring (points, tags) and the entry list
 constexpr int kSurImg = 0;
@@ -1009,7 +1012,7 @@ struct SurFusedArgs {
     float lo[kMaxLinks][3], hi[kMaxLinks][3], m[kMaxLinks][3], inv_a[kMaxLinks], scale[kMaxLinks];
     float4 cap_a[kMaxLinks], cap_b[kMaxLinks];   // bounding capsules (link frame), radius in cap_a.w
     const uint8_t* image;             // [L][kImgBytes] weights as held in shared memory
-    int seed_group;                   // waypoints per seed item (16: four full tiles)
+    int seed_group;                   // waypoints per seed item (16: one tile of kSeedPts each)
     unsigned long long* keys;         // [W] packed keys, ~0 = none (set before the launch)
     uint8_t* recheck;                 // [W] 1 where a list overflowed (zeroed before the launch)
     int* work;                        // [0] item counter, [1] CTAs done (zeroed before the launch)
@@ -1223,6 +1226,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
             // the 32 points of the tile nearest to the capsule (nearest super-tile first)
             uint32_t tag = kNoTag;
             float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            float gq = INFINITY;
             if (warp < nw && nv > 0) {
                 const float4 cA = s_cA[warp], cD = s_cD[warp];
                 float best = INFINITY;
@@ -1253,17 +1257,27 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                         const float4 p = __ldg(&A.sorted[k]);
                         q = make_query(A, l, s_M[warp], p);
                         tag = ((unsigned)warp << 24) | (unsigned)__float_as_int(p.w);
+                        gq = capsule_gap(make_float4(p.x, p.y, p.z, 0.f), cA, cD);
                     }
                 }
             }
             if (warp < gsz) {
-                s_q[warp * 32 + lane] = q;
-                s_tag[warp * 32 + lane] = tag;
-                if (A.stats) n_seed_q += (unsigned)__popc(__ballot_sync(0xffffffffu, tag != kNoTag));
+                // the kSeedPts points of the tile nearest to the capsule (ties by lane)
+                int rank = 0;
+#pragma unroll 8
+                for (int j = 0; j < 32; ++j) {
+                    const float gj = __shfl_sync(0xffffffffu, gq, j);
+                    rank += (gj < gq || (gj == gq && j < lane)) ? 1 : 0;
+                }
+                if (rank < kSeedPts) {
+                    s_q[warp * kSeedPts + rank] = q;
+                    s_tag[warp * kSeedPts + rank] = tag;
+                }
+                if (A.stats) n_seed_q += (unsigned)__popc(__ballot_sync(0xffffffffu, tag != kNoTag && rank < kSeedPts));
             }
             __syncthreads();
             stamp(&ns_prod);
-            evaluate_ring(l, gsz * 32);
+            evaluate_ring(l, gsz * kSeedPts);
             __syncthreads();
             stamp(&ns_eval);
         } else {
