@@ -224,6 +224,25 @@ def test_surrogate_check_without_culling_is_the_brute_force_minimum(sdf, env):
     assert np.array_equal(l, g[1]) and np.array_equal(p, g[2])
 
 
+@pytest.mark.parametrize("N", [1, 5, 37])
+def test_surrogate_check_ragged_seed_tiles(sdf, env, N):
+    # seed tiles with fewer valid points than a seed takes (8): the surrogate minimum is
+    # still the brute-force one, and the grid path decides every waypoint exactly
+    sc, ctx, grids, vals, metas = env
+    L = len(metas)
+    params = sg.mlp_init(23, L)
+    sur = sdf.Surrogate(ctx, grids, params)
+    robot = sdf.Robot(ctx, sc.dh, grids, sc.base)
+    q, pts = sc.q[:20].astype(np.float32), sc.points[:N].astype(np.float32)
+    d, l, p, rech, sd = _sur_check(sdf, ctx, robot, sur, q, pts, margin=0.0, eps=100.0)   # eps: no culling
+    ref_d, ref_l, ref_p = mlp.check(sc.dh, sc.base, params.astype(np.float64), metas, q, pts, quantize=True)
+    assert np.max(np.abs(sd - ref_d)) <= 2e-3, np.max(np.abs(sd - ref_d))
+    assert np.all(rech == 1)
+    g = _grid_check(sdf, ctx, robot, q, pts)
+    assert np.array_equal(d.view(np.uint32), g[0].view(np.uint32))
+    assert np.array_equal(l, g[1]) and np.array_equal(p, g[2])
+
+
 def test_surrogate_check_follows_training(sdf, env):
     """The context keeps the networks' weights in the fused kernel's layout between
     checks; a training step in between must reach the next check (the surrogate
