@@ -711,6 +711,87 @@ __device__ __forceinline__ bool pipe_network(int pipe, int r, const float* small
     return true;
 }
 
+// Shared-memory writes of the whole block become visible to the tensor core, and its
+// tensor-memory reads are ordered before the next MMA.
+__device__ __forceinline__ void block_sync_for_mma() {
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+// The network at one 128-query tile with all four pipelines on it: thread (p, r) takes
+// row r (tensor-memory lane r) and the 32 units [32p, 32p + 32) of every layer, so that
+// a lone tile runs on four warps per SM sub-partition instead of one.  The tile's
+// accumulator is pipeline 0's tensor-memory columns (d_tmem0; taddr0 = this warp's lane
+// quarter of them), its activations pipeline 0's tile H0; `part` (4 x 128 floats) holds
+// the per-row partial sums of the output layer.  Thread 0 issues the MMAs and commits to
+// `mbar`, which every thread waits on.  Returns false if an MMA wait gave up (the block
+// agrees on it); f is valid in pipeline 0 otherwise.
+__device__ __forceinline__ bool block_network(int pipe, int r, int t, const float* small, uint8_t* H0, uint32_t aH0,
+                                              uint32_t aW2, uint32_t aW3, uint32_t d_tmem0, uint32_t taddr0,
+                                              uint64_t* mbar, uint32_t& phase, uint32_t limit, float4 x,
+                                              float* part, float& f) {
+    const float4* wb = reinterpret_cast<const float4*>(small + kEWB);
+    const int c0 = 32 * pipe;
+    constexpr uint32_t kN128KK = tc::idesc_bf16(128, 128, 0, 0);
+#pragma unroll 1
+    for (int j0 = c0; j0 < c0 + 32; j0 += 8) {
+        float h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float4 w = wb[j0 + e];
+            h[e] = silu_half(fmaf(w.x, x.x, fmaf(w.y, x.y, fmaf(w.z, x.z, w.w))));   // z / 2
+        }
+        store_bf16x8(H0, r, j0, kH, h);
+    }
+    block_sync_for_mma();
+    if (t == 0) {
+        mma_k128(d_tmem0, KMAJ(aH0), KMAJ(aW2), kN128KK);
+        tc::mma_commit(mbar);
+    }
+    bool ok = tc::mbar_wait(mbar, phase, limit);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!__syncthreads_and(ok)) return false;
+    {
+        const float* bh = small + kEB2;
+        float v[32];
+        tc::tmem_ld32(taddr0 + c0, v);
+#pragma unroll
+        for (int k = 0; k < 32; k += 8) {
+            float h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) h[e] = silu_half(fmaf(0.5f, v[k + e], bh[c0 + k + e]));
+            store_bf16x8(H0, r, c0 + k, kH, h);
+        }
+    }
+    block_sync_for_mma();
+    if (t == 0) {
+        mma_k128(d_tmem0, KMAJ(aH0), KMAJ(aW3), kN128KK);
+        tc::mma_commit(mbar);
+    }
+    ok = tc::mbar_wait(mbar, phase, limit);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!__syncthreads_and(ok)) return false;
+    {
+        const float* b3 = small + kEB3;
+        const float* w4 = small + kEW4;
+        float v[32];
+        tc::tmem_ld32(taddr0 + c0, v);
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc = fmaf(w4[c0 + k], silu_half(fmaf(0.5f, v[k], b3[c0 + k])), acc);
+        part[pipe * 128 + r] = acc;
+    }
+    // the tensor-memory reads above come before the next MMA; the partial sums are in
+    tc::fence_before_sync();
+    __syncthreads();
+    if (pipe == 0) f = small[kEB4] + ((part[r] + part[128 + r]) + (part[256 + r] + part[384 + r]));
+    return true;
+}
+
 // f(x) of one link at n points: four warpgroup pipelines per CTA, each evaluating its
 // own 128-query tiles, so that one pipeline's MMA and waits overlap the others' FP32
 // epilogues; the pipelines share the link's W2/W3 in shared memory.
@@ -972,6 +1053,7 @@ __device__ __forceinline__ void load_image(const uint8_t* __restrict__ img, uint
 //     (nearest super-tile first), and the kSeedPts of its 32 points nearest to the
 //     capsule become queries (a seed only sets the first threshold, and the 8
 //     nearest points set it about as low as all 32, at a quarter of the queries);
+//     the item's one tile is evaluated by all four pipelines together (block_network);
 //   cull: with the waypoint's minimum so far (over all links) plus the surrogate's
 //     error bound as the threshold, one warp per waypoint culls super-tiles and tiles
 //     against the capsule into a (waypoint, tile) list in shared memory; then every
@@ -999,6 +1081,7 @@ constexpr int kSurQ = kSurH + kEvalPipes * kTileBytes;
 constexpr int kSurTag = kSurQ + kSurRing * 16;
 constexpr int kSurLst = kSurTag + kSurRing * 4;
 constexpr int kSurSmem = kSurLst + kSurList * 4;
+static_assert(kSeedPts * kSurGroup <= 128, "a seed item is one tile");
 static_assert(kSurSmem + 2048 <= 232448, "dynamic + static shared memory of the fused check within 227 KB");
 constexpr uint32_t kNoTag = 0xffffffffu;
 
@@ -1065,7 +1148,7 @@ __device__ __forceinline__ unsigned long long sur_ns() {
 
 __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid_constant__ SurFusedArgs A) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ uint64_t mbar[kEvalPipes];
+    __shared__ uint64_t mbar[kEvalPipes + 1];   // one per pipeline, one for the whole block
     __shared__ uint32_t tmem_slot;
     __shared__ float4 s_M[kSurGroup][3];           // link-from-world rows of each waypoint's link pose
     __shared__ float4 s_cA[kSurGroup], s_cD[kSurGroup];   // world capsule: start (+radius), axis (+1/len^2)
@@ -1084,7 +1167,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
     uint32_t* s_list = reinterpret_cast<uint32_t*>(sm + kSurLst);
 
     if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
-    if (t < kEvalPipes) tc::mbar_init(&mbar[t], 1);
+    if (t <= kEvalPipes) tc::mbar_init(&mbar[t], 1);
     if (t == 0) s_fail = 0;
     tc::fence_before_sync();
     __syncthreads();
@@ -1093,7 +1176,13 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
     const uint32_t d_tmem = tm + (uint32_t)(128 * pipe);
     const uint32_t taddr = d_tmem + ((uint32_t)((warp & 3) * 32) << 16);
     const uint32_t aW2 = tc::smem_u32(sW2), aW3 = tc::smem_u32(sW3), aH = tc::smem_u32(sH);
-    uint32_t phase = 0;
+    // the whole block on one tile (seed items): pipeline 0's columns and activation tile,
+    // the partial output sums in pipeline 1's activation tile
+    uint8_t* sH0 = sm + kSurH;
+    const uint32_t aH0 = tc::smem_u32(sH0);
+    const uint32_t taddr0 = tm + ((uint32_t)((warp & 3) * 32) << 16);
+    float* s_part = reinterpret_cast<float*>(sm + kSurH + kTileBytes);
+    uint32_t phase = 0, phase_b = 0;
     bool ok = true;
     const int nv = *A.n_valid;
     const int n_tiles = (nv + 31) >> 5, n_sup = (n_tiles + 31) >> 5;
@@ -1139,6 +1228,31 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 if (r == 0) s_fail = 1;
                 break;
             }
+            const float d = fmaf(A.scale[l], f, x.w);
+            const bool use = tag != kNoTag && !isnan(d);
+            const unsigned j = use ? tag >> 24 : kNoTag;
+            const unsigned hi = use ? ordered_bits(d) : 0xffffffffu;
+            const unsigned lo = use ? (((tag & 0xffffffu) << 4) | (unsigned)l) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, j);
+            const unsigned hmin = __reduce_min_sync(peers, hi);
+            const unsigned lmin = __reduce_min_sync(peers, hi == hmin ? lo : 0xffffffffu);
+            if (use && lane == __ffs(peers) - 1) atomicMin(&s_key[j], ((unsigned long long)hmin << 32) | lmin);
+        }
+    };
+
+    // Evaluate queries [0, nq) of the ring, nq <= 128, as one tile with the whole block,
+    // and fold them into s_key as evaluate_ring does.
+    auto evaluate_block = [&](int l, int nq) {
+        const uint32_t tag = r < nq ? s_tag[r] : kNoTag;
+        const float4 x = tag != kNoTag ? s_q[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float f = 0.f;
+        ok = block_network(pipe, r, t, small, sH0, aH0, aW2, aW3, tm, taddr0, &mbar[kEvalPipes], phase_b,
+                           A.wait_polls, x, s_part, f);
+        if (!ok) {
+            if (t == 0) s_fail = 1;
+            return;
+        }
+        if (pipe == 0) {
             const float d = fmaf(A.scale[l], f, x.w);
             const bool use = tag != kNoTag && !isnan(d);
             const unsigned j = use ? tag >> 24 : kNoTag;
@@ -1277,7 +1391,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
             }
             __syncthreads();
             stamp(&ns_prod);
-            evaluate_ring(l, gsz * kSeedPts);
+            evaluate_block(l, gsz * kSeedPts);
             __syncthreads();
             stamp(&ns_eval);
         } else {
@@ -1423,6 +1537,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
         // tensor memory is released
         if (r == 0) atomicOr(A.status, kStatusTimeout);
         tc::mbar_wait(&mbar[pipe], phase ^ 1u, kWaitPolls);
+        tc::mbar_wait(&mbar[kEvalPipes], phase_b ^ 1u, kWaitPolls);
     }
     tc::fence_before_sync();
     __threadfence();   // this CTA's key updates and flags, before it counts itself done
