@@ -1053,7 +1053,8 @@ __device__ __forceinline__ void load_image(const uint8_t* __restrict__ img, uint
 //     (nearest super-tile first), and the kSeedPts of its 32 points nearest to the
 //     capsule become queries (a seed only sets the first threshold, and the 8
 //     nearest points set it about as low as all 32, at a quarter of the queries);
-//     the item's one tile is evaluated by all four pipelines together (block_network);
+//     the item's one tile is evaluated by all four pipelines together (block_network),
+//     as is every evaluation round of one tile;
 //   cull: with the waypoint's minimum so far (over all links) plus the surrogate's
 //     error bound as the threshold, one warp per waypoint culls super-tiles and tiles
 //     against the capsule into a (waypoint, tile) list in shared memory; then every
@@ -1240,8 +1241,9 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
         }
     };
 
-    // Evaluate queries [0, nq) of the ring, nq <= 128, as one tile with the whole block,
-    // and fold them into s_key as evaluate_ring does.
+    // Evaluate queries [0, nq) of the ring, nq <= 128, as one tile with the whole block
+    // (a seed item's tile, and a cull round of one tile), and fold them into s_key as
+    // evaluate_ring does.
     auto evaluate_block = [&](int l, int nq) {
         const uint32_t tag = r < nq ? s_tag[r] : kNoTag;
         const float4 x = tag != kNoTag ? s_q[r] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1484,7 +1486,10 @@ __global__ void __launch_bounds__(kEvalThreads, 1) sur_check_kernel(const __grid
                 if (nq == 0) break;   // then done as well: production stops only at kSurFill or at the end
                 const int take_q = done ? nq : (nq & ~127);
                 if (A.stats && t == 0) n_cull_q += (unsigned)take_q;
-                evaluate_ring(l, take_q);
+                if (take_q <= 128)
+                    evaluate_block(l, take_q);   // one tile: the whole block on it
+                else
+                    evaluate_ring(l, take_q);
                 __syncthreads();
                 stamp(&ns_eval);
                 // the rest (under one tile) to the front of the ring; thresholds tighten
